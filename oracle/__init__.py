@@ -1,0 +1,189 @@
+"""FP64 CPU oracle for the damped, source-driven 3D acoustic leapfrog step.
+
+THIS PACKAGE IS TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it; the library never does,
+and the two share no code (the only shared module is the seeded input
+generator, which holds none of the method's arithmetic).
+
+The arithmetic lives in ``fd_oracle.c`` (plain C, double precision, OpenMP
+loops), compiled on first use with gcc into ``oracle/_build/``. This module
+only marshals numpy arrays into it. What each function computes, and the paper
+passage it follows (arXiv 1912.00695, Sec. 2.1 Eq. 1, Listing 1, Listing 2),
+is stated in the C source beside the function.
+
+Parity status: every function is pinned by tests/test_oracle_*.py against
+closed forms, invariants, Listing 2 or a dense brute force, except the default
+damping profile, whose formula is a convention the paper does not give
+(parity unpinned as a formula; its invariants are tested).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libfdoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile fd_oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_fd_weights.argtypes = [ctypes.c_int, _dp]
+        lib.oracle_fd_weights.restype = ctypes.c_int
+        lib.oracle_laplacian.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_long,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        lib.oracle_laplacian.restype = ctypes.c_int
+        lib.oracle_step.argtypes = [_dp, _dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_long,
+                                    ctypes.c_long, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int]
+        lib.oracle_step.restype = ctypes.c_int
+        lib.oracle_forward.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_long,
+                                       ctypes.c_long, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip, _ip, _ip,
+                                       _dp, ctypes.c_long, ctypes.c_long, ctypes.c_long]
+        lib.oracle_forward.restype = ctypes.c_int
+        lib.oracle_energy.argtypes = [_dp, _dp, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_long,
+                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        lib.oracle_energy.restype = ctypes.c_double
+        lib.oracle_dt_max.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        lib.oracle_dt_max.restype = ctypes.c_double
+        lib.oracle_default_damping.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_long,
+                                               ctypes.c_long, ctypes.c_int, ctypes.c_double]
+        lib.oracle_default_damping.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle runs on."""
+    return int(_load().oracle_num_threads())
+
+
+def fd_weights(space_order: int) -> np.ndarray:
+    """c_0..c_r of the centred 2nd derivative of accuracy order k (closed form)."""
+    r = space_order // 2
+    c = np.zeros(max(r, 0) + 1, dtype=np.float64)
+    if _load().oracle_fd_weights(int(space_order), _ptr(c)) != 0:
+        raise ValueError(f"space_order must be even in [2, 24], got {space_order}")
+    return c
+
+
+def laplacian(u, space_order: int, h: float, periodic: bool = False) -> np.ndarray:
+    u = _f64(u)
+    out = np.empty_like(u)
+    nx, ny, nz = u.shape
+    rc = _load().oracle_laplacian(_ptr(u), _ptr(out), nx, ny, nz, int(space_order), float(h),
+                                  int(periodic))
+    if rc != 0:
+        raise ValueError("bad arguments to oracle laplacian")
+    return out
+
+
+def step(u, u_prev, m, eta, space_order: int, h: float, dt: float,
+         periodic: bool = False) -> np.ndarray:
+    """u^{n+1} from u^n and u^{n-1} without sources (eta may be None)."""
+    u, u_prev, m = _f64(u), _f64(u_prev), _f64(m)
+    eta_a = None if eta is None else _f64(eta)
+    out = np.empty_like(u)
+    nx, ny, nz = u.shape
+    rc = _load().oracle_step(_ptr(u), _ptr(u_prev), _ptr(out), _ptr(m),
+                             None if eta_a is None else _ptr(eta_a), nx, ny, nz,
+                             int(space_order), float(h), float(dt), int(periodic))
+    if rc != 0:
+        raise ValueError("bad arguments to oracle step")
+    return out
+
+
+def forward(m, eta, space_order: int, h: float, dt: float, nt: int, sources=(), wavelets=None,
+            u0=None, u_prev0=None, step0: int = 0, periodic: bool = False):
+    """Advance nt steps; returns (u^{step0+nt}, u^{step0+nt-1}) as float64 arrays.
+
+    sources: sequence of (x, y, z) domain nodes; wavelets: array (ns, ld) of
+    source samples indexed by global step (zero beyond ld).
+    """
+    m = _f64(m)
+    shape = m.shape
+    u = np.zeros(shape) if u0 is None else _f64(u0).copy()
+    up = np.zeros(shape) if u_prev0 is None else _f64(u_prev0).copy()
+    eta_a = None if eta is None else _f64(eta)
+    ns = len(sources)
+    src = np.asarray(sources, dtype=np.int32).reshape(ns, 3)
+    sx, sy, sz = (np.ascontiguousarray(src[:, i]) for i in range(3))
+    if ns:
+        w = _f64(np.asarray(wavelets).reshape(ns, -1))
+        ld = w.shape[1]
+    else:
+        w = np.zeros((1, 1))
+        ld = 0
+    nx, ny, nz = shape
+    rc = _load().oracle_forward(_ptr(u), _ptr(up), _ptr(m),
+                                None if eta_a is None else _ptr(eta_a), nx, ny, nz,
+                                int(space_order), float(h), float(dt), int(periodic), ns,
+                                sx.ctypes.data_as(_ip), sy.ctypes.data_as(_ip),
+                                sz.ctypes.data_as(_ip), _ptr(w), ld, int(step0), int(nt))
+    if rc != 0:
+        raise ValueError(f"oracle forward failed ({rc})")
+    return u, up
+
+
+def energy(u_new, u_old, m, space_order: int, h: float, dt: float,
+           periodic: bool = False) -> float:
+    """Discrete energy E^{n+1/2} between two consecutive levels."""
+    u_new, u_old, m = _f64(u_new), _f64(u_old), _f64(m)
+    nx, ny, nz = m.shape
+    return float(_load().oracle_energy(_ptr(u_new), _ptr(u_old), _ptr(m), nx, ny, nz,
+                                       int(space_order), float(h), float(dt), int(periodic)))
+
+
+def dt_max(space_order: int, h: float, vmax: float) -> float:
+    v = float(_load().oracle_dt_max(int(space_order), float(h), float(vmax)))
+    if v < 0:
+        raise ValueError("bad arguments to oracle dt_max")
+    return v
+
+
+def default_damping(m, nbl: int, h: float) -> np.ndarray:
+    """The default absorbing-layer eta for model m (convention; see fd_oracle.c)."""
+    m = _f64(m)
+    out = np.empty_like(m)
+    nx, ny, nz = m.shape
+    if _load().oracle_default_damping(_ptr(out), _ptr(m), nx, ny, nz, int(nbl), float(h)) != 0:
+        raise ValueError("bad arguments to oracle default_damping")
+    return out
