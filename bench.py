@@ -1,0 +1,393 @@
+"""Benchmark of the damped acoustic FD time step on GB300 (one JSON line).
+
+Default workload: the paper-shaped sweep, a 256^3 interior + 10-cell absorbing
+layer (276^3 points), 4-layer velocity model, space orders 2/4/8/12/16, each in
+the factored and the expanded stencil form, 500 time steps per shot. One bench
+step = the whole sweep (10 shots: reset, 500 steps each). Metric: Gpts/s
+(computational-domain points updated per second) and the fraction of the
+measured HBM roofline of the step kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload sweep|plain] [--n 256] [--nt 500]
+
+With N > 1 (torchrun) every rank runs its own replica of the workload on its
+own GPU (independent shots, no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ORDERS = (2, 4, 8, 12, 16)
+FORMS = ("factored", "expanded")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("fd_stencil.cuh", "fd_internal.h"):
+        with open(os.path.join(ROOT, "paper_1912_00695_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_hash: str, key: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("kernel_hash") != kernel_hash:
+            return None
+        return rec.get("per_launch_bytes", {}).get(key)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- workload -----------------------------------------------------------------
+
+def build_workload(name: str, n: int, nt: int):
+    from paper_1912_00695_gb300 import inputs
+    if name == "plain":
+        spec = inputs.plain_shot()
+        return [(spec, "factored")], "plain 64^3+10, space order 4, 1.5 km/s, 100 steps"
+    runs = []
+    for k in ORDERS:
+        spec = inputs.sweep_shot(k, n=n, nt=nt)
+        for form in FORMS:
+            runs.append((spec, form))
+    desc = (f"sweep {n}^3+10 (4-layer model 1.5-4.5 km/s), space orders "
+            f"{'/'.join(map(str, ORDERS))} x factored/expanded, {nt} steps, 15 Hz Ricker")
+    return runs, desc
+
+
+def layer_points(spec) -> int:
+    N = spec.shape
+    inner = [max(a - 2 * spec.nbl, 0) for a in N]
+    return int(np.prod(N) - np.prod(inner))
+
+
+def algorithmic_bytes_per_step(spec, storage="f32") -> int:
+    """Read u^n, u^{n-1} and the per-point coefficient, write u^{n+1}; read the
+    damping field only in the layer (it vanishes in the interior)."""
+    e = 4 if storage == "f32" else 2
+    return int(spec.points * (3 * e + 4) + layer_points(spec) * 4)
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    runs, desc = build_workload(args.workload, args.n, args.nt)
+    shots = []
+    for spec, form in runs:
+        dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+        shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, form=form)
+        m = spec.m
+        shot.set_model(m)
+        wav = inputs.ricker(spec.f0, dt, spec.nt)
+        shot.inject(*spec.source, wav)
+        shot.set_stream(stream.cuda_stream)
+        shots.append((spec, form, shot, m, wav))
+
+    def bench_step(record=None):
+        for spec, form, shot, _, _ in shots:
+            shot.reset()
+            shot.forward(spec.nt)
+            if record is not None:
+                record.append(shot.last_forward_ms())
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for spec, form, shot, _, _ in shots:
+            shot.reset()
+            shot.forward(spec.nt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    # per-shot kernel time (events around each graph replay on the launching stream)
+    bench_step(kernel_ms)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    pts_per_step = sum(spec.points * spec.nt for spec, *_ in shots)
+    value = pts_per_step * args.steps * world / (total_ms * 1e-3) / 1e9
+    # roofline of the step kernel: algorithmic bytes / kernel time over all shots
+    alg_bytes = sum(algorithmic_bytes_per_step(spec) * spec.nt for spec, *_ in shots)
+    kern_s = sum(kernel_ms) * 1e-3
+    launches = sum(spec.nt for spec, *_ in shots)
+    achieved = alg_bytes / kern_s / 1e9
+    peak, peak_kind = _peaks()
+    khash = _kernel_hash()
+    traffic = _ncu_traffic(khash, f"{args.workload}_n{args.n}")
+    breakdown = {}
+    for (spec, form, shot, _, _), ms in zip(shots, kernel_ms):
+        key = f"so{spec.space_order}_{form}"
+        gbs = algorithmic_bytes_per_step(spec) * spec.nt / (ms * 1e-3) / 1e9
+        breakdown[key] = {"gpts": round(spec.points * spec.nt / (ms * 1e-3) / 1e9, 2),
+                          "us_per_step": round(ms * 1e3 / spec.nt, 2),
+                          "hbm_frac": round(gbs / peak, 4),
+                          "tile_y_x_block": list(shot.config[:2])}
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, shots, stream, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    line = {
+        "metric": "Gpts/s (computational-domain points updated per second) and fraction of "
+                  "measured HBM roofline, 256^3+10 sweep, space orders 2-16",
+        "value": round(value, 3), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered velocity model, Ricker source)",
+        "config": {"workload": desc, "interior": args.n, "nbl": 10, "space_orders": list(ORDERS),
+                   "forms": list(FORMS), "nt": args.nt, "shots_per_step": len(shots),
+                   "points_per_shot": shots[0][0].points,
+                   "l2": "inputs larger than L2 (4 fields x ~98 MB per shot, 10 shots)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "fd_stream_kernel", "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch_avg": int(alg_bytes / launches)},
+        "breakdown": breakdown,
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "kernel_hash": khash,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for *_, shot, _, _ in shots:
+        shot.close()
+
+
+def run_e2e(args, shots, stream, world):
+    """Same metric through the public C-ABI calls with host buffers: per shot,
+    set the model from host memory, inject the host wavelet, reset, run, and
+    read the final wavefield back to the host. Wall clock, synchronised."""
+    import torch
+
+    e2e_steps = max(1, min(args.steps, 2))
+    out = {spec.shape: np.empty(spec.shape, dtype=np.float32) for spec, *_ in shots}
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for spec, form, shot, m, wav in shots:
+            shot.set_model(m)
+            from paper_1912_00695_gb300 import fd_clear_sources
+            fd_clear_sources(shot.handle)
+            shot.inject(*spec.source, wav)
+            shot.reset()
+            shot.forward(spec.nt)
+            shot.wavefield(0, out[spec.shape])
+            h2d += m.nbytes + wav.nbytes
+            d2h += out[spec.shape].nbytes
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    pts = sum(spec.points * spec.nt for spec, *_ in shots) * e2e_steps * world
+    return {"value": round(pts / dt / 1e9, 3), "unit": "Gpts/s",
+            "h2d_bytes_per_step": int(h2d // e2e_steps), "d2h_bytes_per_step": int(d2h // e2e_steps),
+            "steps": e2e_steps}
+
+
+def cpu_baseline(args, target_s: float = 10.0):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of
+    the workload: the space-order-8 shot of the sweep for a few steps."""
+    import oracle
+    from paper_1912_00695_gb300 import inputs
+    spec = inputs.sweep_shot(8, n=args.n, nt=args.nt)
+    m = spec.m.astype(np.float64)
+    eta = oracle.default_damping(m, spec.nbl, inputs.H)
+    dt = 0.9 * oracle.dt_max(8, inputs.H, spec.vmax)
+    wav = inputs.ricker(spec.f0, dt, spec.nt).astype(np.float64)[None, :]
+    src = [tuple(c + spec.nbl for c in spec.source)]
+    t0 = time.perf_counter()
+    u, up = oracle.forward(m, eta, 8, inputs.H, dt, 1, src, wav)
+    one = time.perf_counter() - t0
+    steps = int(max(1, min(20, target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.forward(m, eta, 8, inputs.H, dt, steps, src, wav, u0=u, u_prev0=up, step0=1)
+    el = time.perf_counter() - t0
+    return {"value": round(spec.points * steps / el / 1e9, 5), "unit": "Gpts/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"space order 8 shot of the sweep ({spec.shape[0]}^3 points), {steps} steps, FP64"}
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle timed as the reference arm: each step is a bounded sample of
+    the sweep workload (the space-order-8 shot, 2 time steps) on host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1912_00695_gb300 import inputs
+    spec = inputs.sweep_shot(8, n=args.n, nt=args.nt)
+    m = spec.m.astype(np.float64)
+    eta = oracle.default_damping(m, spec.nbl, inputs.H)
+    dt = 0.9 * oracle.dt_max(8, inputs.H, spec.vmax)
+    wav = inputs.ricker(spec.f0, dt, spec.nt).astype(np.float64)[None, :]
+    src = [tuple(c + spec.nbl for c in spec.source)]
+    per = 2
+    u = up = None
+    step = 0
+    for _ in range(args.warmup):
+        u, up = oracle.forward(m, eta, 8, inputs.H, dt, per, src, wav, u0=u, u_prev0=up, step0=step)
+        step += per
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, up = oracle.forward(m, eta, 8, inputs.H, dt, per, src, wav, u0=u, u_prev0=up, step0=step)
+        step += per
+    el = time.perf_counter() - t0
+    value = spec.points * per * args.steps / el / 1e9
+    _, desc = build_workload(args.workload, args.n, args.nt)
+    sample = f"space order 8 shot of the sweep ({spec.shape[0]}^3 points), {per} steps per bench step, FP64"
+    line = {"impl": "reference",
+            "metric": "Gpts/s (computational-domain points updated per second) and fraction of "
+                      "measured HBM roofline, 256^3+10 sweep, space orders 2-16",
+            "value": round(value, 5), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded layered velocity model, Ricker source)",
+            "config": {"workload": desc, "interior": args.n, "nbl": 10, "nt": args.nt},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Gpts/s", "kind": "oracle",
+                             "cores": oracle.num_threads(), "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--nt", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * fd_acoustic.h — C-ABI of a GB300 (sm_103a) library for the explicit time step
+ * of the 3D acoustic isotropic wave equation with absorbing-layer damping and
+ * point-source injection (arXiv 1912.00695):
+ *
+ *   m u_tt - Lap u + eta u_t = q,   u(.,0) = 0,  u_t(.,0) = 0          (Sec. 2.1, Eq. 1)
+ *
+ * with m = 1/c^2 the squared slowness, eta >= 0 the damping of the absorbing
+ * layer (the `damp` field of Listing 2) and q the point sources. Time is
+ * discretised by the second-order leapfrog (Listing 1: time_order=2) and the
+ * Laplacian by the central finite-difference stencil of accuracy order k
+ * (Listing 1: space_order = k, stencil radius r = k/2), so one step is
+ *
+ *   u^{n+1} = (dt^2 (L u^n + q^n) + m (2u^n - u^{n-1}) + dt/2 eta u^{n-1}) / (m + dt/2 eta),
+ *
+ * the form Listing 2 prints for k = 2 (there with h = 1 and every term divided
+ * by r0 = dt m + dt^2/2 damp).
+ *
+ * Conventions shared by every call:
+ *  - Grid. nx, ny, nz count the interior; the computational domain adds nbl
+ *    absorbing cells on each side: N_a = n_a + 2 nbl. Host and device arrays
+ *    are dense C-order [x][y][z] over the computational domain (z fastest),
+ *    the order Listing 2 indexes u[t][x][y][z]. Beyond the computational
+ *    domain the field is zero (Dirichlet).
+ *  - Errors. Every call returns FD_OK (0) or a negative FD_E* code; the text
+ *    of the last error of the calling thread is available from
+ *    fd_last_error(). No C++ exception crosses the ABI.
+ *  - Ownership. Host arrays passed in are copied; the caller keeps them. The
+ *    library owns the device buffers of a handle until fd_destroy().
+ *  - Threading and streams. A handle is not thread-safe. Its work is queued
+ *    on one CUDA stream (fd_set_stream; default: the legacy default stream).
+ *    Calls that return data to the host synchronise that stream.
+ */
+#ifndef FD_ACOUSTIC_H
+#define FD_ACOUSTIC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define FD_OK 0
+#define FD_EINVAL (-1)      /* an argument is out of its documented range         */
+#define FD_ERANGE (-2)      /* a source node lies outside the interior            */
+#define FD_EUNSTABLE (-3)   /* dt exceeds the stability limit of the model        */
+#define FD_ENOMEM (-4)      /* a device or host allocation failed                 */
+#define FD_ECUDA (-5)       /* a CUDA runtime call failed                         */
+#define FD_ENONFINITE (-6)  /* the wavefield reached NaN/Inf (or 16-bit overflow) */
+#define FD_ETIMEOUT (-7)    /* a bounded device-side wait ran out                 */
+#define FD_ESTATE (-8)      /* call out of order, e.g. fd_forward before a model  */
+#define FD_ENOTSUP (-9)     /* option combination not supported                   */
+#define FD_EFULL (-10)      /* batch/server: no slot or memory budget left        */
+
+/* ---- options -------------------------------------------------------------- */
+/* Storage precision of the wavefields u^n, u^{n-1} (the Laplacian and the
+ * update are always accumulated in FP32; m and eta stay FP32). */
+#define FD_STORAGE_F32 0
+#define FD_STORAGE_BF16 1   /* bfloat16 with a per-field power-of-two scale */
+#define FD_STORAGE_F16 2    /* float16 with a per-field power-of-two scale  */
+
+/* Symbolic form of the stencil expression (Sec. 4: Devito's "basic" versus
+ * "aggressive" symbolic optimisation). Both compute the same update. */
+#define FD_FORM_FACTORED 0  /* common factors hoisted, equal-distance taps summed first,
+                               dt^2/(m + dt/2 eta) precomputed per point */
+#define FD_FORM_EXPANDED 1  /* every tap multiplied by its own coefficient and divided
+                               by (m + dt/2 eta) per point, as Listing 2 is written */
+
+/* Kernel schedule. */
+#define FD_KERNEL_AUTO 0    /* streaming kernel, tile chosen by the autotuner */
+#define FD_KERNEL_STREAM 1  /* 2.5D streaming kernel (x-march, y-z tile in shared memory) */
+#define FD_KERNEL_NAIVE 2   /* one thread per point, all taps from global memory */
+
+typedef struct fd_options {
+    int storage;       /* FD_STORAGE_*                                             */
+    int form;          /* FD_FORM_*                                                */
+    int kernel;        /* FD_KERNEL_*                                              */
+    int tile_y;        /* streaming tile rows along y (4, 8 or 16); 0 = autotune   */
+    int x_block;       /* planes per CTA along x; 0 = autotune                     */
+    int check_finite;  /* 1 = fold a max|u| reduction into each step so that
+                          fd_read_wavefield/fd_status report FD_ENONFINITE          */
+} fd_options;
+
+typedef struct fd_handle fd_handle;
+
+/* Fill *opt with the defaults: FP32, factored, auto kernel, autotuned tile,
+ * finite check on. */
+void fd_options_default(fd_options *opt);
+
+/* ---- single-shot solver --------------------------------------------------- */
+
+/* Create a solver for an nx*ny*nz interior with an nbl-cell absorbing layer on
+ * every side, space order k (even, 2..16), grid spacing h and time step dt
+ * (both > 0, any consistent units). Allocates the device state (two wavefield
+ * levels, the model fields) and zeroes the wavefields (Eq. 1: u = u_t = 0 at
+ * t = 0). FD_EINVAL when k is odd or outside [2,16], n_a < 1, nbl < 0, a
+ * computational extent N_a exceeds 65535, or h, dt are not positive finite;
+ * FD_ENOMEM when the device buffers do not fit. *out is NULL on failure. */
+int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                       fd_handle **out);
+
+/* As fd_acoustic_create with explicit options (opt == NULL: defaults).
+ * FD_ENOTSUP for an unknown storage/form/kernel value or a tile_y other than
+ * 0, 4, 8, 16. */
+int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                          const fd_options *opt, fd_handle **out);
+
+/* Set the model from HOST arrays over the computational domain
+ * (N_x*N_y*N_z floats, C-order): m = 1/v^2 (> 0, finite) and eta (>= 0,
+ * finite). eta == NULL selects the default absorbing profile
+ *   eta = m * sum_a d_max (l_a / nbl)^2,  d_max = 3 v_max ln(1000) / (2 nbl h),
+ * l_a the depth (in cells) into the layer along axis a, v_max = 1/sqrt(min m)
+ * (a convention: the paper names absorbing boundaries but gives no profile).
+ * Checks stability: FD_EUNSTABLE when dt > fd_dt_max(k, h, v_max).
+ * FD_EINVAL for non-positive or non-finite m, negative or non-finite eta.
+ * Resets nothing: the wavefields keep their state. */
+int fd_set_model(fd_handle *hd, const float *m, const float *eta);
+
+/* As fd_set_model, from DEVICE arrays of the same layout (e.g. a torch
+ * tensor's data_ptr()). The arrays are read back once (validation, stability
+ * check and the derived per-point coefficients run on the host); setting a
+ * model is not on the time-stepping path. */
+int fd_set_model_device(fd_handle *hd, const float *d_m, const float *d_eta);
+
+/* Add a point source at INTERIOR node (ix, iy, iz) (offset by nbl internally)
+ * with nt samples: q^n = wavelet[n] for global steps n < nt, 0 afterwards
+ * (the q_s of Eq. 1, entering the update as dt^2 q / (m + dt/2 eta) at that
+ * node). Several sources add up. The wavelet is copied. FD_ERANGE when the node
+ * is outside the interior; FD_EINVAL when nt < 1 or wavelet is NULL. */
+int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int nt);
+
+/* Remove every source. */
+int fd_clear_sources(fd_handle *hd);
+
+/* Queue nt time steps on the handle's stream (asynchronous; returns before
+ * the GPU finishes). The global step counter persists across calls, so
+ * fd_forward(a) followed by fd_forward(b) equals fd_forward(a + b) bit for
+ * bit. Steps are replayed from a cached CUDA graph. FD_ESTATE without a model;
+ * FD_EINVAL for nt < 0. */
+int fd_forward(fd_handle *hd, int nt);
+
+/* Copy a wavefield level to a HOST array of N_x*N_y*N_z floats (dense C-order;
+ * 16-bit storage is converted and scaled to FP32). level 0 = u^n (the newest),
+ * 1 = u^{n-1}. Synchronises the stream. Returns FD_ENONFINITE when the finite
+ * check saw NaN/Inf (or 16-bit overflow) in any step since the last reset. */
+int fd_read_wavefield(fd_handle *hd, float *out, int level);
+
+/* As fd_read_wavefield into a DEVICE array (N_x*N_y*N_z floats); queued on the
+ * handle's stream, returns without synchronising (status not checked). */
+int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level);
+
+/* Bind the handle to a CUDA stream (a cudaStream_t, e.g. torch's
+ * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
+int fd_set_stream(fd_handle *hd, void *cuda_stream);
+
+/* Wait for the handle's queued work; returns the device status (FD_OK,
+ * FD_ENONFINITE) or FD_ECUDA. */
+int fd_synchronize(fd_handle *hd);
+
+/* Device status without waiting beyond what is queued: same as fd_synchronize. */
+int fd_status(fd_handle *hd);
+
+/* Load the solver state from HOST arrays over the computational domain
+ * (N_x*N_y*N_z floats each, dense C-order): u = u^step (level 0) and
+ * u_prev = u^{step-1} (level 1), and set the global step counter to `step`
+ * (>= 0; it indexes the source wavelets). Together with fd_read_wavefield and
+ * fd_get_step this is checkpoint/resume. 16-bit storage picks each level's
+ * power-of-two scale from its max |u|. Clears the device status.
+ * FD_EINVAL for NULL arrays, non-finite values or step < 0. */
+int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long step);
+
+/* Zero both wavefield levels, the step counter and the device status. Keeps
+ * the model and the sources. */
+int fd_reset(fd_handle *hd);
+
+/* Global step counter n (the wavefield level u^n held as level 0). */
+int fd_get_step(fd_handle *hd, long long *step);
+
+/* Computational-domain extents N_x, N_y, N_z of a handle. */
+int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz);
+
+/* Launch configuration the handle uses for its step kernel (tile_y, x_block,
+ * kernel id): what the autotuner picked or the options forced. */
+int fd_get_config(fd_handle *hd, int *tile_y, int *x_block, int *kernel);
+
+/* Device time of the step kernels queued by the last fd_forward, in ms,
+ * measured by CUDA events on the handle's stream around the graph replay
+ * (synchronises). FD_ESTATE if no fd_forward was timed yet. */
+int fd_last_forward_ms(fd_handle *hd, float *ms);
+
+/* Release every device buffer and the handle. NULL is accepted (no-op). */
+int fd_destroy(fd_handle *hd);
+
+/* ---- host numerics -------------------------------------------------------- */
+
+/* Stability limit dt_max = 2 h / (v_max sqrt(3 sum_{j=-r..r} |c_j|)) of the
+ * 3D leapfrog scheme (von Neumann analysis at the Nyquist mode). */
+int fd_dt_max(int space_order, double h, double vmax, double *out);
+
+/* Centred second-derivative weights c_0..c_r of accuracy order k for unit
+ * spacing (out holds k/2 + 1 doubles), computed by Fornberg's recursion.
+ * Listing 2 shows k = 2: c_0 = -2, c_1 = 1. */
+int fd_fd_weights(int space_order, double *out);
+
+/* The default absorbing-layer damping that fd_set_model uses when eta is NULL,
+ * written into the host array eta (Nx*Ny*Nz floats, C-order) for the host
+ * model m of the same layout; v_max = 1/sqrt(min m). Host-only helper. */
+int fd_default_damping(int Nx, int Ny, int Nz, int nbl, double h, const float *m, float *eta);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *fd_last_error(void);
+
+/* Library version string. */
+const char *fd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FD_ACOUSTIC_H */

@@ -1,0 +1,113 @@
+"""GB300 (sm_103a) library for the explicit time step of the 3D acoustic
+isotropic wave equation with absorbing-layer damping and point-source
+injection (arXiv 1912.00695, Sec. 2.1 Eq. 1 and Listing 2).
+
+The compute path is the C-ABI shared library built from ``csrc/`` (declared in
+include/fd_acoustic.h); this package only marshals arguments into it through
+ctypes (:mod:`._abi`, same names as the C functions) and offers :class:`Shot`,
+a small owner object around one solver handle. PyTorch, where used, provides
+device memory and streams only.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD_EUNSTABLE,  # noqa: F401
+                   FD_ERANGE, FD_ESTATE, FD_ETIMEOUT, FD_FORM_EXPANDED, FD_FORM_FACTORED,
+                   FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_OK, FD_STORAGE_BF16,
+                   FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
+                   fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
+                   fd_forward, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_load_state,
+                   fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
+                   fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
+                   fd_set_model_device, fd_set_stream, fd_status, fd_synchronize, fd_version)
+
+STORAGE = {"f32": FD_STORAGE_F32, "bf16": FD_STORAGE_BF16, "f16": FD_STORAGE_F16}
+FORMS = {"factored": FD_FORM_FACTORED, "expanded": FD_FORM_EXPANDED}
+KERNELS = {"auto": FD_KERNEL_AUTO, "stream": FD_KERNEL_STREAM, "naive": FD_KERNEL_NAIVE}
+
+
+def options(storage="f32", form="factored", kernel="auto", tile_y=0, x_block=0,
+            check_finite=True) -> fd_options:
+    o = fd_options_default()
+    o.storage = STORAGE[storage]
+    o.form = FORMS[form]
+    o.kernel = KERNELS[kernel]
+    o.tile_y = int(tile_y)
+    o.x_block = int(x_block)
+    o.check_finite = int(bool(check_finite))
+    return o
+
+
+class Shot:
+    """One single-shot solver handle (owns its device state until close())."""
+
+    def __init__(self, interior, space_order, h, dt, nbl, **opts):
+        nx, ny, nz = interior
+        self.interior = (int(nx), int(ny), int(nz))
+        self.nbl = int(nbl)
+        self.space_order = int(space_order)
+        self.h = float(h)
+        self.dt = float(dt)
+        self.handle = fd_acoustic_create_ex(nx, ny, nz, space_order, h, dt, nbl, options(**opts))
+        self.shape = fd_get_dims(self.handle)
+
+    def set_model(self, m, eta=None):
+        fd_set_model(self.handle, m, eta)
+
+    def set_model_device(self, d_m, d_eta=None):
+        fd_set_model_device(self.handle, d_m, d_eta)
+
+    def inject(self, ix, iy, iz, wavelet):
+        fd_inject(self.handle, ix, iy, iz, wavelet)
+
+    def forward(self, nt):
+        fd_forward(self.handle, nt)
+
+    def wavefield(self, level=0, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        return fd_read_wavefield(self.handle, out, level)
+
+    def read_device(self, d_out, level=0):
+        fd_read_wavefield_device(self.handle, d_out, level)
+
+    def set_stream(self, stream_ptr):
+        fd_set_stream(self.handle, stream_ptr)
+
+    def synchronize(self):
+        fd_synchronize(self.handle)
+
+    def reset(self):
+        fd_reset(self.handle)
+
+    def load_state(self, u, u_prev, step):
+        fd_load_state(self.handle, u, u_prev, step)
+
+    @property
+    def step(self) -> int:
+        return fd_get_step(self.handle)
+
+    @property
+    def config(self):
+        return fd_get_config(self.handle)
+
+    def last_forward_ms(self) -> float:
+        return fd_last_forward_ms(self.handle)
+
+    def close(self):
+        if self.handle:
+            fd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

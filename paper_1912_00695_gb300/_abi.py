@@ -1,0 +1,269 @@
+"""ctypes binding of the C-ABI in include/fd_acoustic.h (argument marshalling only).
+
+Every function keeps the C name. Arrays are passed as raw pointers: host
+arrays as C-contiguous float32 numpy arrays, device arrays as the integer
+address of a CUDA buffer (for example ``tensor.data_ptr()``). Errors come back
+as FdError carrying the status code and ``fd_last_error()``. Loading fails
+loudly when the compiled library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfdgb.so")
+
+FD_OK = 0
+FD_EINVAL = -1
+FD_ERANGE = -2
+FD_EUNSTABLE = -3
+FD_ENOMEM = -4
+FD_ECUDA = -5
+FD_ENONFINITE = -6
+FD_ETIMEOUT = -7
+FD_ESTATE = -8
+FD_ENOTSUP = -9
+FD_EFULL = -10
+
+FD_STORAGE_F32, FD_STORAGE_BF16, FD_STORAGE_F16 = 0, 1, 2
+FD_FORM_FACTORED, FD_FORM_EXPANDED = 0, 1
+FD_KERNEL_AUTO, FD_KERNEL_STREAM, FD_KERNEL_NAIVE = 0, 1, 2
+
+ERROR_NAMES = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ERANGE", -3: "FD_EUNSTABLE", -4: "FD_ENOMEM",
+               -5: "FD_ECUDA", -6: "FD_ENONFINITE", -7: "FD_ETIMEOUT", -8: "FD_ESTATE",
+               -9: "FD_ENOTSUP", -10: "FD_EFULL"}
+
+
+class FdError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        self.code = code
+        super().__init__(f"{func}: {ERROR_NAMES.get(code, code)}: {msg}")
+
+
+class fd_options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("form", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("tile_y", ctypes.c_int), ("x_block", ctypes.c_int),
+                ("check_finite", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_fp = ctypes.POINTER(ctypes.c_float)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+# name -> (restype, argtypes); int-returning calls are checked
+_SIGNATURES = {
+    "fd_options_default": (None, [ctypes.POINTER(fd_options)]),
+    "fd_acoustic_create": (_i, [_i, _i, _i, _i, _d, _d, _i, ctypes.POINTER(_vp)]),
+    "fd_acoustic_create_ex": (_i, [_i, _i, _i, _i, _d, _d, _i, ctypes.POINTER(fd_options),
+                                   ctypes.POINTER(_vp)]),
+    "fd_set_model": (_i, [_vp, _vp, _vp]),
+    "fd_set_model_device": (_i, [_vp, _vp, _vp]),
+    "fd_inject": (_i, [_vp, _i, _i, _i, _vp, _i]),
+    "fd_clear_sources": (_i, [_vp]),
+    "fd_forward": (_i, [_vp, _i]),
+    "fd_read_wavefield": (_i, [_vp, _vp, _i]),
+    "fd_read_wavefield_device": (_i, [_vp, _vp, _i]),
+    "fd_set_stream": (_i, [_vp, _vp]),
+    "fd_synchronize": (_i, [_vp]),
+    "fd_status": (_i, [_vp]),
+    "fd_reset": (_i, [_vp]),
+    "fd_load_state": (_i, [_vp, _vp, _vp, ctypes.c_longlong]),
+    "fd_get_step": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_get_dims": (_i, [_vp, _ip, _ip, _ip]),
+    "fd_get_config": (_i, [_vp, _ip, _ip, _ip]),
+    "fd_last_forward_ms": (_i, [_vp, _fp]),
+    "fd_destroy": (_i, [_vp]),
+    "fd_dt_max": (_i, [_i, _d, _d, _dp]),
+    "fd_fd_weights": (_i, [_i, _dp]),
+    "fd_default_damping": (_i, [_i, _i, _i, _i, _d, _vp, _vp]),
+    "fd_last_error": (ctypes.c_char_p, []),
+    "fd_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library not built ({LIB_PATH} missing); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            h = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(h, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = h
+        return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(rc: int, func: str):
+    if rc != FD_OK:
+        raise FdError(rc, func, lib().fd_last_error().decode())
+
+
+def _host_f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    """Raw address of a numpy array, an integer address, or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ---- thin wrappers with the C names -------------------------------------------
+
+def fd_options_default() -> fd_options:
+    o = fd_options()
+    lib().fd_options_default(ctypes.byref(o))
+    return o
+
+
+def fd_acoustic_create(nx, ny, nz, space_order, h, dt, nbl) -> int:
+    out = _vp()
+    _check(lib().fd_acoustic_create(nx, ny, nz, space_order, h, dt, nbl, ctypes.byref(out)),
+           "fd_acoustic_create")
+    return out.value
+
+
+def fd_acoustic_create_ex(nx, ny, nz, space_order, h, dt, nbl, opt: fd_options | None) -> int:
+    out = _vp()
+    _check(lib().fd_acoustic_create_ex(nx, ny, nz, space_order, h, dt, nbl,
+                                       ctypes.byref(opt) if opt is not None else None,
+                                       ctypes.byref(out)), "fd_acoustic_create_ex")
+    return out.value
+
+
+def fd_set_model(hd, m, eta=None):
+    m = _host_f32(m)
+    eta = None if eta is None else _host_f32(eta)
+    _check(lib().fd_set_model(hd, _ptr(m), _ptr(eta)), "fd_set_model")
+
+
+def fd_set_model_device(hd, d_m, d_eta=None):
+    _check(lib().fd_set_model_device(hd, _ptr(d_m), _ptr(d_eta)), "fd_set_model_device")
+
+
+def fd_inject(hd, ix, iy, iz, wavelet):
+    w = _host_f32(wavelet)
+    _check(lib().fd_inject(hd, ix, iy, iz, _ptr(w), int(w.size)), "fd_inject")
+
+
+def fd_clear_sources(hd):
+    _check(lib().fd_clear_sources(hd), "fd_clear_sources")
+
+
+def fd_forward(hd, nt):
+    _check(lib().fd_forward(hd, nt), "fd_forward")
+
+
+def fd_read_wavefield(hd, out: np.ndarray, level: int = 0):
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _check(lib().fd_read_wavefield(hd, _ptr(out), level), "fd_read_wavefield")
+    return out
+
+
+def fd_read_wavefield_device(hd, d_out, level: int = 0):
+    _check(lib().fd_read_wavefield_device(hd, _ptr(d_out), level), "fd_read_wavefield_device")
+
+
+def fd_set_stream(hd, stream_ptr: int | None):
+    _check(lib().fd_set_stream(hd, stream_ptr), "fd_set_stream")
+
+
+def fd_synchronize(hd):
+    _check(lib().fd_synchronize(hd), "fd_synchronize")
+
+
+def fd_status(hd) -> int:
+    return lib().fd_status(hd)
+
+
+def fd_reset(hd):
+    _check(lib().fd_reset(hd), "fd_reset")
+
+
+def fd_load_state(hd, u, u_prev, step: int):
+    u = _host_f32(u)
+    u_prev = _host_f32(u_prev)
+    _check(lib().fd_load_state(hd, _ptr(u), _ptr(u_prev), int(step)), "fd_load_state")
+
+
+def fd_get_step(hd) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().fd_get_step(hd, ctypes.byref(v)), "fd_get_step")
+    return v.value
+
+
+def fd_get_dims(hd):
+    a, b, c = _i(), _i(), _i()
+    _check(lib().fd_get_dims(hd, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "fd_get_dims")
+    return a.value, b.value, c.value
+
+
+def fd_get_config(hd):
+    a, b, c = _i(), _i(), _i()
+    _check(lib().fd_get_config(hd, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "fd_get_config")
+    return a.value, b.value, c.value
+
+
+def fd_last_forward_ms(hd) -> float:
+    v = ctypes.c_float()
+    _check(lib().fd_last_forward_ms(hd, ctypes.byref(v)), "fd_last_forward_ms")
+    return v.value
+
+
+def fd_destroy(hd):
+    _check(lib().fd_destroy(hd), "fd_destroy")
+
+
+def fd_dt_max(space_order, h, vmax) -> float:
+    v = _d()
+    _check(lib().fd_dt_max(space_order, h, vmax, ctypes.byref(v)), "fd_dt_max")
+    return v.value
+
+
+def fd_fd_weights(space_order) -> np.ndarray:
+    out = np.zeros(space_order // 2 + 1 if space_order >= 2 else 1, dtype=np.float64)
+    _check(lib().fd_fd_weights(space_order, out.ctypes.data_as(_dp)), "fd_fd_weights")
+    return out
+
+
+def fd_default_damping(m, nbl, h) -> np.ndarray:
+    m = _host_f32(m)
+    eta = np.empty_like(m)
+    nx, ny, nz = m.shape
+    _check(lib().fd_default_damping(nx, ny, nz, nbl, h, _ptr(m), _ptr(eta)), "fd_default_damping")
+    return eta
+
+
+def fd_last_error() -> str:
+    return lib().fd_last_error().decode()
+
+
+def fd_version() -> str:
+    return lib().fd_version().decode()

@@ -1,0 +1,776 @@
+// C-ABI of the single-shot solver (include/fd_acoustic.h): handle lifetime,
+// model upload and validation, sources, graph-replayed time stepping, the
+// launch-shape autotuner and read-back.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fd_acoustic.h"
+#include "fd_internal.h"
+
+using namespace fdgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define FD_CUDA(expr)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(FD_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));         \
+    } while (0)
+
+size_t elem_size(int storage) { return storage == kF32 ? 4 : 2; }
+
+struct Source {
+    int x, y, z;  // computational-domain node
+    std::vector<float> wavelet;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int nt = 0, cur = 0;
+    long long step0 = 0;
+    unsigned long long gen = 0;
+};
+
+// Process-wide launch-shape cache: (Nx, Ny, Nz, radius, storage, form, check) -> (tile_y, x_block)
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+}  // namespace
+
+struct fd_handle {
+    int nx = 0, ny = 0, nz = 0, nbl = 0, k = 0, r = 0;
+    double h = 0, dt = 0;
+    int Nx = 0, Ny = 0, Nz = 0, pz = 0;
+    long long plane = 0;
+    size_t n_pitched = 0;
+    fd_options opt{};
+    int tile_y = 0, x_block = 0, kernel = kStream;
+    void *ubuf[2] = {nullptr, nullptr};
+    float *f1 = nullptr, *f2 = nullptr;
+    float *d_wavelet = nullptr;
+    int *d_src = nullptr;  // 3 * ns ints: x[], y[], z[]
+    int ld = 0;
+    std::vector<Source> sources;
+    unsigned *d_status = nullptr;
+    LevelScales *d_scales = nullptr;
+    float *d_unpack = nullptr;
+    long long step = 0;
+    int cur = 0;  // ubuf[cur] holds u^step
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    bool has_model = false;
+    int box[6] = {0, 0, 0, 0, 0, 0};
+    float src_bound = 0.0f;
+    double coef_c[kMaxRadius + 1] = {};
+    std::vector<GraphEntry> graphs;
+    unsigned long long gen = 1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+};
+
+namespace {
+
+bool check_enabled(const fd_handle *hd) { return hd->opt.check_finite != 0 || hd->opt.storage != kF32; }
+
+StepArgs make_args(const fd_handle *hd, long long step, int cur) {
+    StepArgs a{};
+    a.u = hd->ubuf[cur];
+    a.up = hd->ubuf[cur ^ 1];
+    a.f1 = hd->f1;
+    a.f2 = hd->f2;
+    a.Nx = hd->Nx;
+    a.Ny = hd->Ny;
+    a.Nz = hd->Nz;
+    a.pz = hd->pz;
+    a.plane = hd->plane;
+    a.x_block = hd->x_block > 0 ? hd->x_block : hd->Nx;
+    a.bx0 = hd->box[0];
+    a.bx1 = hd->box[1];
+    a.by0 = hd->box[2];
+    a.by1 = hd->box[3];
+    a.bz0 = hd->box[4];
+    a.bz1 = hd->box[5];
+    const double inv_h2 = 1.0 / (hd->h * hd->h);
+    const double scale = hd->opt.form == kExpanded ? hd->dt * hd->dt * inv_h2 : inv_h2;
+    for (int j = 0; j <= kMaxRadius; ++j) a.coef[j] = 0.0f;
+    a.coef[0] = float(3.0 * hd->coef_c[0] * scale);
+    for (int j = 1; j <= hd->r; ++j) a.coef[j] = float(hd->coef_c[j] * scale);
+    a.half_dt = float(0.5 * hd->dt);
+    a.dt2 = float(hd->dt * hd->dt);
+    const int ns = int(hd->sources.size());
+    a.ns = ns < kFusedSources ? ns : kFusedSources;
+    for (int s = 0; s < a.ns; ++s) {
+        a.sx[s] = hd->sources[s].x;
+        a.sy[s] = hd->sources[s].y;
+        a.sz[s] = hd->sources[s].z;
+    }
+    a.wavelet = hd->d_wavelet;
+    a.ld = hd->ld;
+    a.step = step;
+    a.status = check_enabled(hd) ? hd->d_status : nullptr;
+    a.scales = hd->opt.storage != kF32 ? hd->d_scales : nullptr;
+    a.src_bound = hd->src_bound;
+    return a;
+}
+
+cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, int kernel, int tile_y,
+                         cudaStream_t s) {
+    const bool check = check_enabled(hd);
+    cudaError_t e = kernel == kNaive
+                        ? launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s)
+                        : launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
+    if (e != cudaSuccess) return e;
+    const int ns = int(hd->sources.size());
+    if (ns > kFusedSources)
+        e = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources,
+                                ns - kFusedSources, hd->opt.storage, hd->opt.form == kExpanded, s);
+    return e;
+}
+
+void destroy_graphs(fd_handle *hd) {
+    for (auto &g : hd->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    hd->graphs.clear();
+}
+
+int heuristic_x_block(const fd_handle *hd, int tile_y) {
+    const int tiles = ((hd->Nz + kTileZ - 1) / kTileZ) * ((hd->Ny + tile_y - 1) / tile_y);
+    int chunks = (4 * 152 + tiles - 1) / tiles;
+    const int max_chunks = hd->Nx / 16 > 0 ? hd->Nx / 16 : 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    return (hd->Nx + chunks - 1) / chunks;
+}
+
+// Pick (tile_y, x_block) for the streaming kernel by timing candidate launch
+// shapes. The candidates run on scratch wavefields, scale slots and status word
+// (zeroed, no sources), so the handle's own state is never touched.
+int autotune(fd_handle *hd) {
+    const bool force_tile = hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
+    if (force_tile && force_xb) {
+        hd->tile_y = hd->opt.tile_y;
+        hd->x_block = hd->opt.x_block;
+        return FD_OK;
+    }
+    auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.storage, hd->opt.form,
+                               int(check_enabled(hd)));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (!force_tile && !force_xb && it != g_tune_cache.end()) {
+            hd->tile_y = it->second.first;
+            hd->x_block = it->second.second;
+            return FD_OK;
+        }
+    }
+    const char *env = std::getenv("FDGB_NO_TUNE");
+    std::vector<int> tiles = force_tile ? std::vector<int>{hd->opt.tile_y} : std::vector<int>{4, 8, 16};
+    if (env && env[0] == '1') {
+        hd->tile_y = force_tile ? hd->opt.tile_y : 8;
+        hd->x_block = force_xb ? hd->opt.x_block : heuristic_x_block(hd, hd->tile_y);
+        return FD_OK;
+    }
+    std::vector<int> xbs;
+    if (force_xb) {
+        xbs.push_back(hd->opt.x_block);
+    } else {
+        for (int xb : {16, 32, 64, 128})
+            if (xb < hd->Nx) xbs.push_back(xb);
+        xbs.push_back(hd->Nx);
+    }
+    const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
+    void *s0 = nullptr, *s1 = nullptr, *aux = nullptr;
+    if (cudaMalloc(&s0, ub) != cudaSuccess || cudaMalloc(&s1, ub) != cudaSuccess ||
+        cudaMalloc(&aux, 256) != cudaSuccess) {
+        cudaGetLastError();
+        if (s0) cudaFree(s0);
+        if (s1) cudaFree(s1);
+        // not enough memory for scratch fields: fall back to the heuristic shape
+        hd->tile_y = force_tile ? hd->opt.tile_y : 8;
+        hd->x_block = force_xb ? hd->opt.x_block : heuristic_x_block(hd, hd->tile_y);
+        return FD_OK;
+    }
+    LevelScales *ls = static_cast<LevelScales *>(aux);
+    unsigned *st = reinterpret_cast<unsigned *>(static_cast<char *>(aux) + 128);
+    int rc = FD_OK;
+    float best = 1e30f;
+    int best_t = tiles[0], best_xb = xbs[0];
+    cudaError_t e = cudaMemsetAsync(s0, 0, ub, hd->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s1, 0, ub, hd->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aux, 0, 256, hd->stream);
+    if (e == cudaSuccess) e = launch_init_scales(ls, hd->stream);
+    StepArgs a = make_args(hd, 0, 0);
+    a.u = s0;
+    a.up = s1;
+    a.ns = 0;
+    a.scales = hd->opt.storage != kF32 ? ls : nullptr;
+    a.status = check_enabled(hd) ? st : nullptr;
+    const bool check = check_enabled(hd);
+    for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess; ++ti) {
+        for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess; ++xi) {
+            a.x_block = xbs[xi];
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+                e = launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tiles[ti], a, check, hd->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(hd->ev0, hd->stream);
+            for (int w = 0; w < 4 && e == cudaSuccess; ++w)
+                e = launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tiles[ti], a, check, hd->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, hd->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(hd->ev1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, hd->ev0, hd->ev1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_t = tiles[ti];
+                best_xb = xbs[xi];
+            }
+        }
+    }
+    if (e != cudaSuccess) rc = fail(FD_ECUDA, "autotune launch failed: %s", cudaGetErrorString(e));
+    cudaStreamSynchronize(hd->stream);
+    cudaFree(s0);
+    cudaFree(s1);
+    cudaFree(aux);
+    if (rc != FD_OK) return rc;
+    hd->tile_y = best_t;
+    hd->x_block = best_xb;
+    if (!force_tile && !force_xb) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {best_t, best_xb};
+    }
+    return FD_OK;
+}
+
+int upload_sources(fd_handle *hd) {
+    if (hd->d_wavelet) cudaFree(hd->d_wavelet);
+    if (hd->d_src) cudaFree(hd->d_src);
+    hd->d_wavelet = nullptr;
+    hd->d_src = nullptr;
+    const int ns = int(hd->sources.size());
+    hd->ld = 0;
+    for (auto &s : hd->sources) hd->ld = std::max<int>(hd->ld, int(s.wavelet.size()));
+    if (ns == 0) return FD_OK;
+    std::vector<float> w(size_t(ns) * hd->ld, 0.0f);
+    std::vector<int> xyz(3 * size_t(ns));
+    for (int s = 0; s < ns; ++s) {
+        std::copy(hd->sources[s].wavelet.begin(), hd->sources[s].wavelet.end(),
+                  w.begin() + size_t(s) * hd->ld);
+        xyz[s] = hd->sources[s].x;
+        xyz[ns + s] = hd->sources[s].y;
+        xyz[2 * ns + s] = hd->sources[s].z;
+    }
+    if (cudaMalloc(&hd->d_wavelet, w.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&hd->d_src, xyz.size() * sizeof(int)) != cudaSuccess)
+        return fail(FD_ENOMEM, "cannot allocate source arrays");
+    FD_CUDA(cudaMemcpyAsync(hd->d_wavelet, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            hd->stream));
+    FD_CUDA(cudaMemcpyAsync(hd->d_src, xyz.data(), xyz.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    return FD_OK;
+}
+
+// Bound on |dt^2 q / (m + dt/2 eta)| summed over sources, for 16-bit scale selection.
+int update_src_bound(fd_handle *hd) {
+    double bound = 0.0;
+    if (hd->has_model) {
+        for (auto &s : hd->sources) {
+            const size_t p = size_t(s.x) * hd->plane + size_t(s.y) * hd->pz + s.z;
+            float f1 = 0, f2 = 0;
+            FD_CUDA(cudaMemcpy(&f1, hd->f1 + p, sizeof(float), cudaMemcpyDeviceToHost));
+            FD_CUDA(cudaMemcpy(&f2, hd->f2 + p, sizeof(float), cudaMemcpyDeviceToHost));
+            const double w = hd->opt.form == kExpanded ? hd->dt * hd->dt / (f1 + 0.5 * hd->dt * f2) : f1;
+            double qmax = 0.0;
+            for (float q : s.wavelet) qmax = std::max(qmax, std::fabs(double(q)));
+            bound += std::fabs(w) * qmax;
+        }
+    }
+    hd->src_bound = float(bound);
+    return FD_OK;
+}
+
+int set_model_host(fd_handle *hd, const float *m, const float *eta_in) {
+    const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
+    double mmin = INFINITY;
+    for (size_t i = 0; i < n; ++i) {
+        const float v = m[i];
+        if (!(v > 0.0f) || !std::isfinite(v)) return fail(FD_EINVAL, "m[%zu] = %g is not positive finite", i, v);
+        mmin = std::min(mmin, double(v));
+    }
+    std::vector<float> eta_default;
+    const float *eta = eta_in;
+    const double vmax = 1.0 / std::sqrt(mmin);
+    if (!eta) {
+        eta_default.resize(n);
+        default_damping(m, eta_default.data(), hd->Nx, hd->Ny, hd->Nz, hd->nbl, hd->h, vmax);
+        eta = eta_default.data();
+    } else {
+        for (size_t i = 0; i < n; ++i)
+            if (!(eta[i] >= 0.0f) || !std::isfinite(eta[i]))
+                return fail(FD_EINVAL, "eta[%zu] = %g is not non-negative finite", i, eta[i]);
+    }
+    const double dtm = stability_limit(hd->k, hd->h, vmax);
+    if (hd->dt > dtm)
+        return fail(FD_EUNSTABLE, "dt = %g exceeds the stability limit %g for v_max = %g", hd->dt, dtm, vmax);
+    // box where eta vanishes: the interior, when that holds; else nothing
+    bool interior_zero = true;
+    const int lo = hd->nbl;
+    for (int x = lo; x < hd->Nx - lo && interior_zero; ++x)
+        for (int y = lo; y < hd->Ny - lo && interior_zero; ++y) {
+            const size_t row = (size_t(x) * hd->Ny + y) * hd->Nz;
+            for (int z = lo; z < hd->Nz - lo; ++z)
+                if (eta[row + z] != 0.0f) {
+                    interior_zero = false;
+                    break;
+                }
+        }
+    if (interior_zero) {
+        const int b[6] = {lo, hd->Nx - lo, lo, hd->Ny - lo, lo, hd->Nz - lo};
+        std::memcpy(hd->box, b, sizeof b);
+    } else {
+        std::memset(hd->box, 0, sizeof hd->box);
+    }
+    // derived per-point fields
+    std::vector<float> f1(n), f2(n);
+    const double half_dt = 0.5 * hd->dt, dt2 = hd->dt * hd->dt;
+    for (size_t i = 0; i < n; ++i) {
+        if (hd->opt.form == kExpanded) {
+            f1[i] = m[i];
+            f2[i] = eta[i];
+        } else {
+            const double r0 = double(m[i]) + half_dt * double(eta[i]);
+            f1[i] = float(dt2 / r0);
+            f2[i] = float(half_dt * double(eta[i]) / r0);
+        }
+    }
+    const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
+    const size_t pitch = size_t(hd->pz) * sizeof(float);
+    FD_CUDA(cudaMemcpy2DAsync(hd->f1, pitch, f1.data(), row_bytes, row_bytes, size_t(hd->Nx) * hd->Ny,
+                              cudaMemcpyHostToDevice, hd->stream));
+    FD_CUDA(cudaMemcpy2DAsync(hd->f2, pitch, f2.data(), row_bytes, row_bytes, size_t(hd->Nx) * hd->Ny,
+                              cudaMemcpyHostToDevice, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    hd->has_model = true;
+    hd->gen++;
+    return update_src_bound(hd);
+}
+
+int read_status(fd_handle *hd) {
+    unsigned st = 0;
+    FD_CUDA(cudaMemcpyAsync(&st, hd->d_status, sizeof st, cudaMemcpyDeviceToHost, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    if (st & kStatusNonFinite) return fail(FD_ENONFINITE, "wavefield reached NaN/Inf (or 16-bit overflow)");
+    return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fd_options_default(fd_options *opt) {
+    if (!opt) return;
+    opt->storage = FD_STORAGE_F32;
+    opt->form = FD_FORM_FACTORED;
+    opt->kernel = FD_KERNEL_AUTO;
+    opt->tile_y = 0;
+    opt->x_block = 0;
+    opt->check_finite = 1;
+}
+
+const char *fd_last_error(void) { return g_last_error.c_str(); }
+
+const char *fd_version(void) { return "fdgb 0.1 (sm_103a)"; }
+
+int fd_fd_weights(int space_order, double *out) {
+    if (!out) return fail(FD_EINVAL, "out is NULL");
+    if (!fornberg_second_derivative(space_order, out))
+        return fail(FD_EINVAL, "space_order must be even in [2, %d], got %d", 2 * kMaxRadiusHost, space_order);
+    return FD_OK;
+}
+
+int fd_default_damping(int Nx, int Ny, int Nz, int nbl, double h, const float *m, float *eta) {
+    if (!m || !eta) return fail(FD_EINVAL, "m or eta is NULL");
+    if (Nx < 1 || Ny < 1 || Nz < 1 || nbl < 0 || !(h > 0)) return fail(FD_EINVAL, "bad extents, nbl or h");
+    const size_t n = size_t(Nx) * Ny * Nz;
+    double mmin = INFINITY;
+    for (size_t i = 0; i < n; ++i) {
+        if (!(m[i] > 0.0f) || !std::isfinite(m[i])) return fail(FD_EINVAL, "m[%zu] is not positive finite", i);
+        mmin = std::min(mmin, double(m[i]));
+    }
+    default_damping(m, eta, Nx, Ny, Nz, nbl, h, 1.0 / std::sqrt(mmin));
+    return FD_OK;
+}
+
+int fd_dt_max(int space_order, double h, double vmax, double *out) {
+    if (!out) return fail(FD_EINVAL, "out is NULL");
+    const double v = stability_limit(space_order, h, vmax);
+    if (!(v > 0)) return fail(FD_EINVAL, "bad space_order/h/vmax");
+    *out = v;
+    return FD_OK;
+}
+
+int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                          const fd_options *opt_in, fd_handle **out) {
+    if (!out) return fail(FD_EINVAL, "out is NULL");
+    *out = nullptr;
+    fd_options opt;
+    fd_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (space_order < 2 || space_order > 2 * kMaxRadius || space_order % 2)
+        return fail(FD_EINVAL, "space_order must be even in [2, 16], got %d", space_order);
+    if (nx < 1 || ny < 1 || nz < 1 || nbl < 0)
+        return fail(FD_EINVAL, "interior sizes must be >= 1 and nbl >= 0");
+    if (!(h > 0) || !std::isfinite(h) || !(dt > 0) || !std::isfinite(dt))
+        return fail(FD_EINVAL, "h and dt must be positive and finite");
+    const long long Nx = nx + 2LL * nbl, Ny = ny + 2LL * nbl, Nz = nz + 2LL * nbl;
+    if (Nx > kMaxDim || Ny > kMaxDim || Nz > kMaxDim) return fail(FD_EINVAL, "extent above 65535");
+    if (opt.storage < 0 || opt.storage > 2 || opt.form < 0 || opt.form > 1 || opt.kernel < 0 ||
+        opt.kernel > 2)
+        return fail(FD_ENOTSUP, "unknown storage/form/kernel option");
+    if (opt.tile_y != 0 && opt.tile_y != 4 && opt.tile_y != 8 && opt.tile_y != 16)
+        return fail(FD_ENOTSUP, "tile_y must be 0, 4, 8 or 16");
+    if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
+
+    fd_handle *hd = new fd_handle();
+    hd->nx = nx;
+    hd->ny = ny;
+    hd->nz = nz;
+    hd->nbl = nbl;
+    hd->k = space_order;
+    hd->r = space_order / 2;
+    hd->h = h;
+    hd->dt = dt;
+    hd->Nx = int(Nx);
+    hd->Ny = int(Ny);
+    hd->Nz = int(Nz);
+    hd->opt = opt;
+    hd->kernel = opt.kernel == kNaive ? kNaive : kStream;
+    hd->pz = int((Nz + 63) / 64 * 64);  // 128-byte rows for 16-bit and 256-byte rows for FP32
+    hd->plane = (long long)hd->Ny * hd->pz;
+    hd->n_pitched = size_t(hd->Nx) * size_t(hd->plane);
+    fornberg_second_derivative(space_order, hd->coef_c);
+
+    auto bail = [&](int code, const char *msg) {
+        fd_destroy(hd);
+        return fail(code, "%s", msg);
+    };
+    if (cudaStreamCreate(&hd->own_stream) != cudaSuccess) return bail(FD_ECUDA, "cudaStreamCreate failed");
+    hd->stream = hd->own_stream;
+    if (cudaEventCreate(&hd->ev0) != cudaSuccess || cudaEventCreate(&hd->ev1) != cudaSuccess)
+        return bail(FD_ECUDA, "cudaEventCreate failed");
+    const size_t ub = hd->n_pitched * elem_size(opt.storage), fb = hd->n_pitched * sizeof(float);
+    if (cudaMalloc(&hd->ubuf[0], ub) != cudaSuccess || cudaMalloc(&hd->ubuf[1], ub) != cudaSuccess ||
+        cudaMalloc(&hd->f1, fb) != cudaSuccess || cudaMalloc(&hd->f2, fb) != cudaSuccess ||
+        cudaMalloc(&hd->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&hd->d_scales, sizeof(LevelScales)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FD_ENOMEM, "device allocation failed");
+    }
+    if (cudaMemsetAsync(hd->f1, 0, fb, hd->stream) != cudaSuccess ||
+        cudaMemsetAsync(hd->f2, 0, fb, hd->stream) != cudaSuccess)
+        return bail(FD_ECUDA, "cudaMemset failed");
+    int rc = fd_reset(hd);
+    if (rc != FD_OK) {
+        std::string msg = g_last_error;
+        fd_destroy(hd);
+        return fail(rc, "%s", msg.c_str());
+    }
+    *out = hd;
+    return FD_OK;
+}
+
+int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                       fd_handle **out) {
+    return fd_acoustic_create_ex(nx, ny, nz, space_order, h, dt, nbl, nullptr, out);
+}
+
+int fd_set_model(fd_handle *hd, const float *m, const float *eta) {
+    if (!hd || !m) return fail(FD_EINVAL, "handle or m is NULL");
+    return set_model_host(hd, m, eta);
+}
+
+int fd_set_model_device(fd_handle *hd, const float *d_m, const float *d_eta) {
+    if (!hd || !d_m) return fail(FD_EINVAL, "handle or m is NULL");
+    const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
+    std::vector<float> m(n), eta;
+    FD_CUDA(cudaMemcpyAsync(m.data(), d_m, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
+    if (d_eta) {
+        eta.resize(n);
+        FD_CUDA(cudaMemcpyAsync(eta.data(), d_eta, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
+    }
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    return set_model_host(hd, m.data(), d_eta ? eta.data() : nullptr);
+}
+
+int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (!wavelet || nt < 1) return fail(FD_EINVAL, "wavelet is NULL or nt < 1");
+    if (ix < 0 || ix >= hd->nx || iy < 0 || iy >= hd->ny || iz < 0 || iz >= hd->nz)
+        return fail(FD_ERANGE, "source (%d,%d,%d) outside the %dx%dx%d interior", ix, iy, iz, hd->nx,
+                    hd->ny, hd->nz);
+    for (int i = 0; i < nt; ++i)
+        if (!std::isfinite(wavelet[i])) return fail(FD_EINVAL, "wavelet[%d] is not finite", i);
+    Source s{ix + hd->nbl, iy + hd->nbl, iz + hd->nbl, std::vector<float>(wavelet, wavelet + nt)};
+    hd->sources.push_back(std::move(s));
+    int rc = upload_sources(hd);
+    if (rc != FD_OK) {
+        hd->sources.pop_back();
+        return rc;
+    }
+    hd->gen++;
+    return update_src_bound(hd);
+}
+
+int fd_clear_sources(fd_handle *hd) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    hd->sources.clear();
+    int rc = upload_sources(hd);
+    hd->gen++;
+    hd->src_bound = 0.0f;
+    return rc;
+}
+
+int fd_forward(fd_handle *hd, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
+    if (nt == 0) return FD_OK;
+    if (hd->kernel == kStream && (hd->tile_y == 0 || hd->x_block == 0)) {
+        int rc = autotune(hd);
+        if (rc != FD_OK) return rc;
+        hd->gen++;
+    }
+    GraphEntry *entry = nullptr;
+    for (auto &g : hd->graphs)
+        if (g.nt == nt && g.cur == hd->cur && g.gen == hd->gen) entry = &g;
+    if (!entry || entry->step0 != hd->step) {
+        cudaGraph_t graph = nullptr;
+        FD_CUDA(cudaStreamBeginCapture(hd->stream, cudaStreamCaptureModeThreadLocal));
+        int cur = hd->cur;
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < nt && err == cudaSuccess; ++i) {
+            const StepArgs a = make_args(hd, hd->step + i, cur);
+            err = enqueue_step(hd, a, hd->kernel, hd->tile_y, hd->stream);
+            cur ^= 1;
+        }
+        cudaError_t cap = cudaStreamEndCapture(hd->stream, &graph);
+        if (err != cudaSuccess || cap != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(FD_ECUDA, "graph capture failed: %s",
+                        cudaGetErrorString(err != cudaSuccess ? err : cap));
+        }
+        bool updated = false;
+        if (entry) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(entry->exec, graph, &info) == cudaSuccess) {
+                updated = true;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(entry->exec);
+                entry->exec = nullptr;
+            }
+        }
+        if (!updated) {
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(FD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+            }
+            if (!entry) {
+                if (hd->graphs.size() >= 8) {
+                    cudaGraphExecDestroy(hd->graphs.front().exec);
+                    hd->graphs.erase(hd->graphs.begin());
+                }
+                hd->graphs.push_back(GraphEntry{});
+                entry = &hd->graphs.back();
+            }
+            entry->exec = exec;
+        }
+        cudaGraphDestroy(graph);
+        entry->nt = nt;
+        entry->cur = hd->cur;
+        entry->gen = hd->gen;
+        entry->step0 = hd->step;
+    }
+    FD_CUDA(cudaEventRecord(hd->ev0, hd->stream));
+    FD_CUDA(cudaGraphLaunch(entry->exec, hd->stream));
+    FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
+    hd->timed = true;
+    hd->step += nt;
+    hd->cur ^= (nt & 1);
+    return FD_OK;
+}
+
+int fd_read_wavefield(fd_handle *hd, float *out, int level) {
+    if (!hd || !out) return fail(FD_EINVAL, "handle or out is NULL");
+    if (level != 0 && level != 1) return fail(FD_EINVAL, "level must be 0 or 1");
+    const int buf = level == 0 ? hd->cur : hd->cur ^ 1;
+    const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
+    if (hd->opt.storage == kF32) {
+        FD_CUDA(cudaMemcpy2DAsync(out, row_bytes, hd->ubuf[buf], size_t(hd->pz) * sizeof(float), row_bytes,
+                                  size_t(hd->Nx) * hd->Ny, cudaMemcpyDeviceToHost, hd->stream));
+    } else {
+        const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
+        if (!hd->d_unpack && cudaMalloc(&hd->d_unpack, n * sizeof(float)) != cudaSuccess)
+            return fail(FD_ENOMEM, "cannot allocate the read-back buffer");
+        const long long lvl_step = level == 0 ? hd->step : hd->step - 1;
+        const int slot = int(((lvl_step % 3) + 3) % 3);
+        FD_CUDA(launch_unpack_level(hd->ubuf[buf], hd->d_unpack, hd->Nx, hd->Ny, hd->Nz, hd->pz,
+                                    hd->opt.storage, hd->d_scales, slot, hd->stream));
+        FD_CUDA(cudaMemcpyAsync(out, hd->d_unpack, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
+    }
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    return check_enabled(hd) ? read_status(hd) : FD_OK;
+}
+
+int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level) {
+    if (!hd || !d_out) return fail(FD_EINVAL, "handle or out is NULL");
+    if (level != 0 && level != 1) return fail(FD_EINVAL, "level must be 0 or 1");
+    const int buf = level == 0 ? hd->cur : hd->cur ^ 1;
+    const long long lvl_step = level == 0 ? hd->step : hd->step - 1;
+    const int slot = int(((lvl_step % 3) + 3) % 3);
+    FD_CUDA(launch_unpack_level(hd->ubuf[buf], d_out, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
+                                hd->opt.storage == kF32 ? nullptr : hd->d_scales, slot, hd->stream));
+    return FD_OK;
+}
+
+int fd_set_stream(fd_handle *hd, void *cuda_stream) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    hd->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : hd->own_stream;
+    return FD_OK;
+}
+
+int fd_synchronize(fd_handle *hd) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    return check_enabled(hd) ? read_status(hd) : FD_OK;
+}
+
+int fd_status(fd_handle *hd) { return fd_synchronize(hd); }
+
+int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long step) {
+    if (!hd || !u || !u_prev) return fail(FD_EINVAL, "handle or arrays are NULL");
+    if (step < 0) return fail(FD_EINVAL, "step must be >= 0");
+    const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
+    float amax[2] = {0.0f, 0.0f};
+    const float *lv[2] = {u, u_prev};
+    for (int l = 0; l < 2; ++l)
+        for (size_t i = 0; i < n; ++i) {
+            if (!std::isfinite(lv[l][i])) return fail(FD_EINVAL, "state value %zu of level %d is not finite", i, l);
+            amax[l] = std::max(amax[l], std::fabs(lv[l][i]));
+        }
+    float *tmp = nullptr;
+    if (cudaMalloc(&tmp, n * sizeof(float)) != cudaSuccess) return fail(FD_ENOMEM, "cannot allocate staging buffer");
+    int rc = FD_OK;
+    hd->step = step;
+    hd->cur = 0;
+    for (int l = 0; l < 2 && rc == FD_OK; ++l) {
+        // level 0 -> ubuf[cur], level 1 -> ubuf[cur ^ 1]
+        float scale = 1.0f;
+        if (hd->opt.storage != kF32 && amax[l] > 0.0f) {
+            int e;
+            std::frexp(double(amax[l]) / 4096.0, &e);
+            scale = std::ldexp(1.0f, e);
+        }
+        const long long lvl_step = step - l;
+        const int slot = int(((lvl_step % 3) + 3) % 3);
+        unsigned bits;
+        std::memcpy(&bits, &amax[l], sizeof bits);
+        cudaError_t e = cudaMemcpyAsync(tmp, lv[l], n * sizeof(float), cudaMemcpyHostToDevice, hd->stream);
+        if (e == cudaSuccess)
+            e = launch_pack_level(tmp, hd->ubuf[l], hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
+                                  1.0f / scale, hd->stream);
+        if (e == cudaSuccess) e = launch_set_level_scale(hd->d_scales, slot, scale, bits, hd->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
+        if (e != cudaSuccess) rc = fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
+    }
+    if (rc == FD_OK) {
+        // the accumulator of the level the next step writes starts at zero
+        const int next = int(((step + 1) % 3 + 3) % 3);
+        cudaError_t e = launch_set_level_scale(hd->d_scales, next, 1.0f, 0u, hd->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
+        if (e != cudaSuccess) rc = fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
+int fd_reset(fd_handle *hd) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
+    FD_CUDA(cudaMemsetAsync(hd->ubuf[0], 0, ub, hd->stream));
+    FD_CUDA(cudaMemsetAsync(hd->ubuf[1], 0, ub, hd->stream));
+    FD_CUDA(cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream));
+    FD_CUDA(launch_init_scales(hd->d_scales, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    hd->step = 0;
+    hd->cur = 0;
+    return FD_OK;
+}
+
+int fd_get_step(fd_handle *hd, long long *step) {
+    if (!hd || !step) return fail(FD_EINVAL, "NULL argument");
+    *step = hd->step;
+    return FD_OK;
+}
+
+int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz) {
+    if (!hd || !Nx || !Ny || !Nz) return fail(FD_EINVAL, "NULL argument");
+    *Nx = hd->Nx;
+    *Ny = hd->Ny;
+    *Nz = hd->Nz;
+    return FD_OK;
+}
+
+int fd_get_config(fd_handle *hd, int *tile_y, int *x_block, int *kernel) {
+    if (!hd || !tile_y || !x_block || !kernel) return fail(FD_EINVAL, "NULL argument");
+    *tile_y = hd->tile_y;
+    *x_block = hd->x_block;
+    *kernel = hd->kernel;
+    return FD_OK;
+}
+
+int fd_last_forward_ms(fd_handle *hd, float *ms) {
+    if (!hd || !ms) return fail(FD_EINVAL, "NULL argument");
+    if (!hd->timed) return fail(FD_ESTATE, "no fd_forward timed yet");
+    FD_CUDA(cudaEventSynchronize(hd->ev1));
+    FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
+    return FD_OK;
+}
+
+int fd_destroy(fd_handle *hd) {
+    if (!hd) return FD_OK;
+    if (hd->stream) cudaStreamSynchronize(hd->stream);
+    destroy_graphs(hd);
+    void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->f1, hd->f2, hd->d_wavelet, hd->d_src, hd->d_status,
+                    hd->d_scales, hd->d_unpack};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (hd->ev0) cudaEventDestroy(hd->ev0);
+    if (hd->ev1) cudaEventDestroy(hd->ev1);
+    if (hd->own_stream) cudaStreamDestroy(hd->own_stream);
+    delete hd;
+    return FD_OK;
+}
+
+}  // extern "C"

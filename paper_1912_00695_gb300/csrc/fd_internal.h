@@ -1,0 +1,87 @@
+// Internal declarations shared by the host runtime and the kernel translation
+// units. Not part of the public ABI (include/fd_acoustic.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fdgb {
+
+constexpr int kMaxRadius = 8;       // space order 16
+constexpr int kMaxRadiusHost = 12;  // host weight generator reaches space order 24
+constexpr int kFusedSources = 4;    // sources injected inside the step kernel
+constexpr int kTileZ = 32;          // streaming tile width along z (one warp)
+constexpr int kMaxDim = 65535;  // keeps every launch grid dimension within limits
+
+enum Storage : int { kF32 = 0, kBF16 = 1, kF16 = 2 };
+enum Form : int { kFactored = 0, kExpanded = 1 };
+enum KernelKind : int { kAuto = 0, kStream = 1, kNaive = 2 };
+
+// Device status word bits (written by kernels, read by the host).
+constexpr unsigned kStatusNonFinite = 1u;
+
+// Per-level scale bookkeeping for 16-bit storage: value = stored * scale.
+// Three rotating slots, indexed by global step modulo 3: slot (n % 3) holds the
+// scale of u^n and the max |u^n| accumulated while u^n was written.
+struct LevelScales {
+    float scale[3];
+    unsigned amax_bits[3];  // max |u| as float bits (non-negative floats order as uints)
+};
+
+// Arguments of one time step of one shot. Passed by value (kernel parameter
+// space) for the single-shot kernels and stored in device memory for batches.
+struct StepArgs {
+    const void *u;      // u^n, storage type, pitched [Nx][Ny][pz]
+    void *up;           // u^{n-1} on entry, overwritten by u^{n+1}
+    const float *f1;    // factored: w = dt^2/(m + dt/2 eta); expanded: m
+    const float *f2;    // factored: g = (dt/2 eta)/(m + dt/2 eta); expanded: eta
+    int Nx, Ny, Nz;     // computational domain
+    int pz;             // row pitch in elements (multiple of 32)
+    long long plane;    // elements per x-plane = Ny * pz
+    int x_block;        // planes per CTA (streaming kernel)
+    // box where f2 == 0 (damping absent): [bx0,bx1) x [by0,by1) x [bz0,bz1)
+    int bx0, bx1, by0, by1, bz0, bz1;
+    float coef[kMaxRadius + 1];  // factored: c_j/h^2 (coef[0] = 3 c_0/h^2);
+                                 // expanded: c_j dt^2/h^2 (coef[0] = 3 c_0 dt^2/h^2)
+    float half_dt;               // dt/2 (expanded form)
+    float dt2;                   // dt^2 (expanded form: source weight dt^2 / r0)
+    // fused sources: domain node and wavelet row
+    int ns;
+    int sx[kFusedSources], sy[kFusedSources], sz[kFusedSources];
+    const float *wavelet;  // ns rows of ld samples
+    int ld;
+    long long step;        // global step n (u^n -> u^{n+1})
+    // status / 16-bit scales (may be null for FP32 without finite check)
+    unsigned *status;
+    LevelScales *scales;
+    float src_bound;       // max_s |w_s q_s| bound used by 16-bit scale selection
+};
+
+// Host numerics (fd_numerics.cpp)
+bool fornberg_second_derivative(int space_order, double *c);
+double stability_limit(int space_order, double h, double vmax);
+void default_damping(const float *m, float *eta, int Nx, int Ny, int Nz, int nbl, double h,
+                     double vmax);
+
+// Kernel launchers (fd_kernels_r*.cu). Return cudaSuccess or the launch error.
+cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
+                               bool check, cudaStream_t s);
+cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
+                              cudaStream_t s);
+int stream_grid_x_chunks(int Nx, int x_block);
+
+// Utility kernels (fd_kernels_util.cu)
+cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
+                                int first, int count, int storage, int expanded, cudaStream_t s);
+cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int Nz, int pz,
+                                int storage, const LevelScales *scales, int slot,
+                                cudaStream_t s);
+cudaError_t launch_init_scales(LevelScales *scales, cudaStream_t s);
+cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int Nz, int pz,
+                              int storage, float inv_scale, cudaStream_t s);
+cudaError_t launch_set_level_scale(LevelScales *scales, int slot, float scale, unsigned amax_bits,
+                                   cudaStream_t s);
+
+}  // namespace fdgb

@@ -1,0 +1,191 @@
+// Radius dispatch and the small utility kernels around the step kernels:
+// extra-source injection, 16-bit level unpacking for read-back and scale
+// initialisation.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fd_internal.h"
+
+namespace fdgb {
+
+#define FDGB_DECLARE_RADIUS(R)                                                                   \
+    cudaError_t stream_step_radius_##R(int form, int storage, int tile_y, const StepArgs &a,    \
+                                       bool check, cudaStream_t s);                             \
+    cudaError_t naive_step_radius_##R(int form, int storage, const StepArgs &a, bool check,      \
+                                      cudaStream_t s);
+FDGB_DECLARE_RADIUS(1)
+FDGB_DECLARE_RADIUS(2)
+FDGB_DECLARE_RADIUS(3)
+FDGB_DECLARE_RADIUS(4)
+FDGB_DECLARE_RADIUS(5)
+FDGB_DECLARE_RADIUS(6)
+FDGB_DECLARE_RADIUS(7)
+FDGB_DECLARE_RADIUS(8)
+#undef FDGB_DECLARE_RADIUS
+
+cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
+                               bool check, cudaStream_t s) {
+    switch (radius) {
+        case 1: return stream_step_radius_1(form, storage, tile_y, a, check, s);
+        case 2: return stream_step_radius_2(form, storage, tile_y, a, check, s);
+        case 3: return stream_step_radius_3(form, storage, tile_y, a, check, s);
+        case 4: return stream_step_radius_4(form, storage, tile_y, a, check, s);
+        case 5: return stream_step_radius_5(form, storage, tile_y, a, check, s);
+        case 6: return stream_step_radius_6(form, storage, tile_y, a, check, s);
+        case 7: return stream_step_radius_7(form, storage, tile_y, a, check, s);
+        case 8: return stream_step_radius_8(form, storage, tile_y, a, check, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
+                              cudaStream_t s) {
+    switch (radius) {
+        case 1: return naive_step_radius_1(form, storage, a, check, s);
+        case 2: return naive_step_radius_2(form, storage, a, check, s);
+        case 3: return naive_step_radius_3(form, storage, a, check, s);
+        case 4: return naive_step_radius_4(form, storage, a, check, s);
+        case 5: return naive_step_radius_5(form, storage, a, check, s);
+        case 6: return naive_step_radius_6(form, storage, a, check, s);
+        case 7: return naive_step_radius_7(form, storage, a, check, s);
+        case 8: return naive_step_radius_8(form, storage, a, check, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int stream_grid_x_chunks(int Nx, int x_block) { return (Nx + x_block - 1) / x_block; }
+
+namespace {
+
+__device__ __forceinline__ int slot_of(long long n) { return int(((n % 3) + 3) % 3); }
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+// Sources beyond the ones fused into the step kernel, added after the step in
+// one thread (in order, so duplicates of a node add up deterministically). The
+// step kernel already wrote u^{n+1} with the scale of slot n+1.
+template <typename T>
+__global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *sy, const int *sz,
+                                    int first, int count, int expanded) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (a.step < 0 || a.step >= a.ld) return;
+    T *up = static_cast<T *>(a.up);
+    const float s_out = a.scales ? a.scales->scale[slot_of(a.step + 1)] : 1.0f;
+    for (int i = first; i < first + count; ++i) {
+        const long long p = (long long)sx[i] * a.plane + (long long)sy[i] * a.pz + sz[i];
+        const float q = a.wavelet[(long long)i * a.ld + a.step];
+        const float f1 = a.f1[p], f2 = a.f2[p];
+        const float w = expanded ? a.dt2 * __frcp_rn(fmaf(a.half_dt, f2, f1)) : f1;
+        const float v = to_f<T>(up[p]) * s_out + w * q;
+        up[p] = from_f<T>(v / s_out);
+    }
+}
+
+// Pitched storage-type level -> dense FP32 [Nx][Ny][Nz], times the level scale.
+template <typename T>
+__global__ void unpack_kernel(const T *src, float *dst, int Nx, int Ny, int Nz, int pz,
+                              const LevelScales *scales, int slot) {
+    const float s = scales ? scales->scale[slot] : 1.0f;
+    const long long n = (long long)Nx * Ny * Nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long z = i % Nz;
+        const long long xy = i / Nz;
+        dst[i] = to_f<T>(src[xy * pz + z]) * s;
+    }
+}
+
+// Dense FP32 [Nx][Ny][Nz] -> pitched storage-type level, times 1/scale.
+template <typename T>
+__global__ void pack_kernel(const float *src, T *dst, int Nx, int Ny, int Nz, int pz, float inv_scale) {
+    const long long n = (long long)Nx * Ny * Nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long z = i % Nz;
+        const long long xy = i / Nz;
+        dst[xy * pz + z] = from_f<T>(src[i] * inv_scale);
+    }
+}
+
+__global__ void set_level_scale_kernel(LevelScales *ls, int slot, float scale, unsigned amax_bits) {
+    if (threadIdx.x == 0) {
+        ls->scale[slot] = scale;
+        ls->amax_bits[slot] = amax_bits;
+    }
+}
+
+__global__ void init_scales_kernel(LevelScales *ls) {
+    if (threadIdx.x < 3) {
+        ls->scale[threadIdx.x] = 1.0f;
+        ls->amax_bits[threadIdx.x] = 0u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
+                                int first, int count, int storage, int expanded, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (storage == kF32) inject_extra_kernel<float><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+    else if (storage == kBF16)
+        inject_extra_kernel<__nv_bfloat16><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+    else if (storage == kF16)
+        inject_extra_kernel<__half><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int Nz, int pz,
+                                int storage, const LevelScales *scales, int slot, cudaStream_t s) {
+    const int blocks = 1024, threads = 256;
+    if (storage == kF32)
+        unpack_kernel<float><<<blocks, threads, 0, s>>>(static_cast<const float *>(src), dst, Nx, Ny,
+                                                        Nz, pz, nullptr, slot);
+    else if (storage == kBF16)
+        unpack_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(
+            static_cast<const __nv_bfloat16 *>(src), dst, Nx, Ny, Nz, pz, scales, slot);
+    else if (storage == kF16)
+        unpack_kernel<__half><<<blocks, threads, 0, s>>>(static_cast<const __half *>(src), dst, Nx, Ny,
+                                                         Nz, pz, scales, slot);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int Nz, int pz,
+                              int storage, float inv_scale, cudaStream_t s) {
+    const int blocks = 1024, threads = 256;
+    if (storage == kF32)
+        pack_kernel<float><<<blocks, threads, 0, s>>>(src, static_cast<float *>(dst), Nx, Ny, Nz, pz, inv_scale);
+    else if (storage == kBF16)
+        pack_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(src, static_cast<__nv_bfloat16 *>(dst), Nx, Ny,
+                                                              Nz, pz, inv_scale);
+    else if (storage == kF16)
+        pack_kernel<__half><<<blocks, threads, 0, s>>>(src, static_cast<__half *>(dst), Nx, Ny, Nz, pz,
+                                                       inv_scale);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_level_scale(LevelScales *scales, int slot, float scale, unsigned amax_bits,
+                                   cudaStream_t s) {
+    set_level_scale_kernel<<<1, 32, 0, s>>>(scales, slot, scale, amax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_scales(LevelScales *scales, cudaStream_t s) {
+    init_scales_kernel<<<1, 32, 0, s>>>(scales);
+    return cudaGetLastError();
+}
+
+}  // namespace fdgb

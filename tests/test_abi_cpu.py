@@ -1,0 +1,93 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol
+include/fd_acoustic.h declares, and its host numerics (Fornberg weights,
+stability limit, default damping profile) agree with the independent oracle.
+No GPU compute is called here.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1912_00695_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    from paper_1912_00695_gb300 import build
+    build.build()
+    return _abi.lib()
+
+
+def _declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fd_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    declared = _declared_functions()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(built_lib, name), f"{name} declared but not exported"
+    # and the binding covers every declared entry point
+    assert set(declared) <= set(_abi.exported_symbols())
+
+
+@pytest.mark.parametrize("k", list(range(2, 25, 2)))
+def test_fornberg_weights_match_oracle(built_lib, oracle_mod, k):
+    got = _abi.fd_fd_weights(k)
+    want = oracle_mod.fd_weights(k)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+def test_weights_reject_odd_orders(built_lib):
+    for k in (1, 3, 0, 26):
+        with pytest.raises(_abi.FdError) as e:
+            _abi.fd_fd_weights(k)
+        assert e.value.code == _abi.FD_EINVAL
+
+
+@pytest.mark.parametrize("k", [2, 4, 8, 12, 16])
+def test_dt_max_matches_oracle(built_lib, oracle_mod, k):
+    for h, v in ((10.0, 1500.0), (10.0, 4500.0), (3.0, 2000.0)):
+        assert _abi.fd_dt_max(k, h, v) == pytest.approx(oracle_mod.dt_max(k, h, v), rel=1e-13)
+
+
+def test_dt_max_table_values(built_lib):
+    """0.9 dt_max at h = 10 m: 3.464 ms (k=2), 3.000 ms (k=4), 2.717 ms (k=8) at
+    1.5 km/s; 0.847 ms (k=16) at 4.5 km/s."""
+    assert 0.9 * _abi.fd_dt_max(2, 10.0, 1500.0) == pytest.approx(3.4641e-3, rel=1e-4)
+    assert 0.9 * _abi.fd_dt_max(4, 10.0, 1500.0) == pytest.approx(3.0000e-3, rel=1e-4)
+    assert 0.9 * _abi.fd_dt_max(8, 10.0, 1500.0) == pytest.approx(2.7173e-3, rel=1e-3)
+    assert 0.9 * _abi.fd_dt_max(16, 10.0, 4500.0) == pytest.approx(0.8472e-3, rel=1e-3)
+
+
+def test_default_damping_matches_oracle(built_lib, oracle_mod):
+    rng = np.random.default_rng(1)
+    shape = (17, 19, 23)
+    m = (1.0 / rng.uniform(1500, 4500, shape) ** 2).astype(np.float32)
+    for nbl in (0, 3, 6):
+        got = _abi.fd_default_damping(m, nbl, 10.0)
+        want = oracle_mod.default_damping(m.astype(np.float64), nbl, 10.0)
+        np.testing.assert_allclose(got, want, rtol=2e-7, atol=0)
+
+
+def test_version_and_error_text(built_lib):
+    assert "sm_103a" in _abi.fd_version()
+    with pytest.raises(_abi.FdError):
+        _abi.fd_dt_max(3, 10.0, 1500.0)
+    assert "space_order" in _abi.fd_last_error() or _abi.fd_last_error() != ""
+
+
+def test_options_default(built_lib):
+    o = _abi.fd_options_default()
+    assert (o.storage, o.form, o.kernel, o.tile_y, o.x_block, o.check_finite) == (0, 0, 0, 0, 0, 1)
+    assert ctypes.sizeof(o) == 6 * 4

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-5 over the whole computational domain (the FP32
+target), on the same seeded inputs. Grids span several tiles in every axis with
+ragged tails; every space order 2..16, both stencil forms, both kernels, user
+and default damping, sources near edges and in the layer, more sources than
+the fused limit, chunked forwards, and the full 256^3 + 10 workload in the
+benchmark's launch configuration (from a random full-field state, so that every
+boundary and layer path is exercised in a few steps).
+"""
+import numpy as np
+import pytest
+
+import paper_1912_00695_gb300 as fd
+from paper_1912_00695_gb300 import inputs
+from harness import dt_for, eta_for, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def test_plain_config_parity(oracle_mod):
+    """64^3 + 10, space order 4, 1.5 km/s, 10 Hz Ricker at the centre, 100 steps."""
+    spec = inputs.plain_shot()
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
+    for form in ("factored", "expanded"):
+        for kernel in ("stream", "naive"):
+            got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel=kernel)
+            assert shot.step == spec.nt
+            e0, e1 = rel_l2(got, want), rel_l2(got_prev, want_prev)
+            assert e0 <= TOL and e1 <= TOL, (form, kernel, e0, e1)
+            shot.close()
+
+
+def _ragged_spec(k, seed=0):
+    rng = np.random.default_rng(seed + k)
+    interior = (37, 45, 51)
+    nbl = 6
+    vel = inputs.smooth_random_velocity(interior, nbl, rng, sigma=4.0)
+    return inputs.ShotSpec(interior, nbl, k, vel, (1, 43, 25), 25.0, 60)
+
+
+@pytest.mark.parametrize("form", ["factored", "expanded"])
+@pytest.mark.parametrize("k", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_every_space_order_ragged(oracle_mod, k, form):
+    spec = _ragged_spec(k)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
+    got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel="stream",
+                                  tile_y=8, x_block=16)
+    assert rel_l2(got, want) <= TOL
+    assert rel_l2(got_prev, want_prev) <= TOL
+    shot.close()
+
+
+@pytest.mark.parametrize("k", [2, 8, 16])
+def test_naive_kernel_ragged(oracle_mod, k):
+    spec = _ragged_spec(k, seed=3)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    want, _ = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
+    got, _, shot = run_gpu(spec, spec.nt, dt, None, kernel="naive")
+    assert rel_l2(got, want) <= TOL
+    shot.close()
+
+
+def test_user_damping_everywhere_and_many_sources(oracle_mod):
+    """eta nonzero in the interior (no skipped loads), 6 sources (4 fused + 2
+    injected separately), two at the same node, one in the layer corner."""
+    rng = np.random.default_rng(4)
+    spec = _ragged_spec(8, seed=4)
+    dt = dt_for(spec)
+    eta = (spec.m * rng.uniform(0, 15.0, spec.m.shape)).astype(np.float32)
+    srcs = []
+    for i, node in enumerate([(0, 0, 0), (36, 44, 50), (18, 22, 25), (5, 40, 3), (18, 22, 25),
+                              (30, 1, 49)]):
+        srcs.append((node, inputs.ricker(12.0 + i, dt, 40 + 3 * i, amplitude=1.0 + i)))
+    want, want_prev = run_oracle(oracle_mod, spec, 50, dt, eta, sources=srcs)
+    for form in ("factored", "expanded"):
+        got, got_prev, shot = run_gpu(spec, 50, dt, eta, sources=srcs, form=form, tile_y=4,
+                                      x_block=32)
+        assert rel_l2(got, want) <= TOL, form
+        assert rel_l2(got_prev, want_prev) <= TOL, form
+        shot.close()
+
+
+def test_chunked_forward_is_bitwise_identical():
+    spec = _ragged_spec(6, seed=5)
+    dt = dt_for(spec)
+    a, ap, s1 = run_gpu(spec, 100, dt, chunks=[100], tile_y=8, x_block=16)
+    b, bp, s2 = run_gpu(spec, 100, dt, chunks=[50, 50], tile_y=8, x_block=16)
+    c, cp, s3 = run_gpu(spec, 100, dt, chunks=[1, 33, 7, 59], tile_y=8, x_block=16)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ap, bp)
+    np.testing.assert_array_equal(a, c)
+    for s in (s1, s2, s3):
+        s.close()
+
+
+def test_launch_shape_does_not_change_results():
+    """Per-point arithmetic order is independent of the tile shape and x-block,
+    so every launch shape gives the same bits."""
+    spec = _ragged_spec(8, seed=6)
+    dt = dt_for(spec)
+    ref, _, s0 = run_gpu(spec, 40, dt, tile_y=8, x_block=16)
+    s0.close()
+    for ty, xb in ((4, 7), (16, 49), (8, 3), (4, 100)):
+        got, _, s = run_gpu(spec, 40, dt, tile_y=ty, x_block=xb)
+        np.testing.assert_array_equal(got, ref, err_msg=f"tile_y={ty} x_block={xb}")
+        s.close()
+
+
+def test_load_state_resume_matches_oracle(oracle_mod):
+    """Random full-field state (every point nonzero, layer included), resumed at
+    step 7 so that the wavelet index continues."""
+    rng = np.random.default_rng(7)
+    spec = _ragged_spec(12, seed=7)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    u0 = rng.standard_normal(spec.shape).astype(np.float32)
+    u1 = (u0 + 0.05 * rng.standard_normal(spec.shape)).astype(np.float32)
+    state = (u0, u1, 7)
+    want, want_prev = run_oracle(oracle_mod, spec, 30, dt, eta, state=state)
+    got, got_prev, shot = run_gpu(spec, 30, dt, None, state=state, tile_y=16, x_block=16)
+    assert shot.step == 37
+    assert rel_l2(got, want) <= TOL
+    assert rel_l2(got_prev, want_prev) <= TOL
+    shot.close()
+
+
+@pytest.mark.parametrize("k", [2, 8, 16])
+def test_full_size_sweep_parity(oracle_mod, k):
+    """The benchmark workload (256^3 + 10-cell layer, 4-layer model) with the
+    autotuned launch shape, 6 steps from a smooth random full-field state."""
+    spec = inputs.sweep_shot(k)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    rng = np.random.default_rng(k)
+    u0 = inputs._gaussian_smooth(rng.standard_normal(spec.shape), 3.0).astype(np.float32)
+    u1 = (0.98 * u0).astype(np.float32)
+    state = (u0, u1, 0)
+    want, want_prev = run_oracle(oracle_mod, spec, 6, dt, eta, state=state)
+    got, got_prev, shot = run_gpu(spec, 6, dt, None, state=state)
+    assert rel_l2(got, want) <= TOL
+    assert rel_l2(got_prev, want_prev) <= TOL
+    shot.close()
+
+
+def test_error_codes():
+    spec = inputs.plain_shot()
+    dt = dt_for(spec)
+    with pytest.raises(fd.FdError) as e:
+        fd.Shot((8, 8, 8), 5, 10.0, 1e-3, 2)
+    assert e.value.code == fd.FD_EINVAL
+    shot = fd.Shot(spec.interior, 4, inputs.H, dt, spec.nbl)
+    with pytest.raises(fd.FdError) as e:
+        shot.forward(1)
+    assert e.value.code == fd.FD_ESTATE
+    bad = spec.m.copy()
+    bad[3, 3, 3] = -1.0
+    with pytest.raises(fd.FdError) as e:
+        shot.set_model(bad)
+    assert e.value.code == fd.FD_EINVAL
+    with pytest.raises(fd.FdError) as e:
+        shot.inject(64, 0, 0, np.ones(4, np.float32))
+    assert e.value.code == fd.FD_ERANGE
+    shot.close()
+    fast = fd.Shot(spec.interior, 4, inputs.H, 1.2 * dt / 0.9, spec.nbl)
+    with pytest.raises(fd.FdError) as e:
+        fast.set_model(spec.m)
+    assert e.value.code == fd.FD_EUNSTABLE
+    fast.close()
+
+
+def test_nonfinite_is_reported():
+    spec = _ragged_spec(4, seed=8)
+    dt = dt_for(spec)
+    huge = np.full(10, 3e38, dtype=np.float32)
+    shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl)
+    shot.set_model(spec.m)
+    shot.inject(10, 10, 10, huge)
+    shot.forward(30)
+    with pytest.raises(fd.FdError) as e:
+        shot.wavefield(0)
+    assert e.value.code == fd.FD_ENONFINITE
+    shot.reset()
+    shot.synchronize()  # status cleared by reset
+    shot.close()
