@@ -43,8 +43,8 @@ struct StepArgs {
     int x_block;        // planes per CTA (streaming kernel)
     // box where f2 == 0 (damping absent): [bx0,bx1) x [by0,by1) x [bz0,bz1)
     int bx0, bx1, by0, by1, bz0, bz1;
-    float coef[kMaxRadius + 1];  // factored: c_j/h^2 (coef[0] = 3 c_0/h^2);
-                                 // expanded: c_j dt^2/h^2 (coef[0] = 3 c_0 dt^2/h^2)
+    float coef[kMaxRadius + 1];  // factored: c_j/h^2; expanded: c_j dt^2/h^2 (j >= 1;
+                                 // the centre enters as -u_c in every tap)
     float half_dt;               // dt/2 (expanded form)
     float dt2;                   // dt^2 (expanded form: source weight dt^2 / r0)
     // fused sources: domain node and wavelet row

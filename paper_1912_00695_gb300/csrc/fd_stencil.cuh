@@ -105,9 +105,14 @@ __device__ __forceinline__ float source_value(const StepArgs &a, int s) {
     return (a.step >= 0 && a.step < a.ld) ? __ldg(a.wavelet + (long long)s * a.ld + a.step) : 0.0f;
 }
 
-// The point update shared by both kernels. `lap_raw` is the Laplacian of the
-// raw stored values (unscaled; FACTORED: sum c_j/h^2 taps, EXPANDED: the sum of
-// every tap times its own dt^2 c_j / (h^2 r0)).
+// The point update shared by both kernels. The Laplacian arrives computed from
+// the raw stored values (unscaled) and with the centre folded into every tap:
+// since c_0 = -2 sum_j c_j, sum_j c_j (S_j - 6 u_c) equals 3 c_0 u_c + sum_j c_j
+// S_j (S_j = the six taps at distance j) but is exactly zero for a locally
+// constant field in FP32. A separately rounded centre weight would leave an
+// O(ulp) residual that the time loop accumulates as a drift.
+// FACTORED: sum_j (c_j/h^2) (S_j - 6 u_c); EXPANDED: every tap (u_tap - u_c)
+// times its own per-point coefficient (dt^2 c_j / h^2) / r0.
 template <int FORM>
 struct Update;
 
@@ -122,16 +127,18 @@ template <> struct Update<kFactored> {
     }
 };
 // Expanded: u+ = sum_taps (dt^2 c/h^2 / r0) u_tap + (2m/r0) u + ((dt/2 eta - m)/r0) u-,
-// r0 = m + dt/2 eta, inv = 1/r0; the tap sum arrives already divided by r0.
-// Source weight dt^2 / r0.
+// r0 = m + dt/2 eta; the tap sum arrives already divided by r0 (times 1/r0).
+// The two level coefficients are formed from a = m/r0 by a correctly rounded
+// division, so that in the undamped interior they are exactly 2 and -1: a
+// reciprocal-multiply would bias them by an ulp in the same direction at every
+// step and the bias would accumulate over the time loop. Source weight dt^2/r0.
 template <> struct Update<kExpanded> {
     static __device__ __forceinline__ float apply(float taps, float uc, float um, float m, float e,
                                                   float inv, const StepArgs &a, float &src_w) {
         src_w = a.dt2 * inv;
-        float v = taps;
-        v = fmaf(2.0f * m * inv, uc, v);
-        v = fmaf((a.half_dt * e - m) * inv, um, v);
-        return v;
+        const float am = __fdiv_rn(m, fmaf(a.half_dt, e, m));
+        float v = fmaf(2.0f * am, uc, taps);
+        return fmaf(1.0f - 2.0f * am, um, v);
     }
 };
 
@@ -163,26 +170,27 @@ __global__ void __launch_bounds__(256) fd_naive_kernel(const StepArgs a, int che
         const float f2 = in_box ? 0.0f : __ldg(a.f2 + p);
         float v, src_w;
         if constexpr (FORM == kFactored) {
-            float lap = a.coef[0] * uc;
+            const float six_uc = 6.0f * uc;
+            float lap = 0.0f;
 #pragma unroll
             for (int j = 1; j <= R; ++j) {
                 const float s = (at(x - j, y, z) + at(x + j, y, z)) + (at(x, y - j, z) + at(x, y + j, z)) +
                                 (at(x, y, z - j) + at(x, y, z + j));
-                lap = fmaf(a.coef[j], s, lap);
+                lap = fmaf(a.coef[j], s - six_uc, lap);
             }
             v = Update<kFactored>::apply(lap * sc.s_u, uc * sc.s_u, um, f1, f2, 0.0f, a, src_w);
         } else {
             const float inv = __frcp_rn(fmaf(a.half_dt, f2, f1));
-            float taps = (a.coef[0] * inv) * uc;
+            float taps = 0.0f;
 #pragma unroll
             for (int j = 1; j <= R; ++j) {
                 const float cj = a.coef[j] * inv;
-                taps = fmaf(cj, at(x - j, y, z), taps);
-                taps = fmaf(cj, at(x + j, y, z), taps);
-                taps = fmaf(cj, at(x, y - j, z), taps);
-                taps = fmaf(cj, at(x, y + j, z), taps);
-                taps = fmaf(cj, at(x, y, z - j), taps);
-                taps = fmaf(cj, at(x, y, z + j), taps);
+                taps = fmaf(cj, at(x - j, y, z) - uc, taps);
+                taps = fmaf(cj, at(x + j, y, z) - uc, taps);
+                taps = fmaf(cj, at(x, y - j, z) - uc, taps);
+                taps = fmaf(cj, at(x, y + j, z) - uc, taps);
+                taps = fmaf(cj, at(x, y, z - j) - uc, taps);
+                taps = fmaf(cj, at(x, y, z + j) - uc, taps);
             }
             v = Update<kExpanded>::apply(taps * sc.s_u, uc * sc.s_u, um, f1, f2, inv, a, src_w);
         }
@@ -311,28 +319,29 @@ __global__ void __launch_bounds__(32 * TY) fd_stream_kernel(const StepArgs a, in
             const float uc = q[R];
             float v, src_w;
             if constexpr (FORM == kFactored) {
-                float lap = a.coef[0] * uc;
+                const float six_uc = 6.0f * uc;
+                float lap = 0.0f;
 #pragma unroll
                 for (int j = 1; j <= R; ++j) {
                     const float s = (q[R - j] + q[R + j]) +
                                     (Io<T>::to_f(t[cy - j][cz]) + Io<T>::to_f(t[cy + j][cz])) +
                                     (Io<T>::to_f(t[cy][cz - j]) + Io<T>::to_f(t[cy][cz + j]));
-                    lap = fmaf(a.coef[j], s, lap);
+                    lap = fmaf(a.coef[j], s - six_uc, lap);
                 }
                 v = Update<kFactored>::apply(lap * sc.s_u, uc * sc.s_u, cum * sc.s_up, cf1, cf2, 0.0f,
                                              a, src_w);
             } else {
                 const float inv = __frcp_rn(fmaf(a.half_dt, cf2, cf1));
-                float taps = (a.coef[0] * inv) * uc;
+                float taps = 0.0f;
 #pragma unroll
                 for (int j = 1; j <= R; ++j) {
                     const float cj = a.coef[j] * inv;
-                    taps = fmaf(cj, q[R - j], taps);
-                    taps = fmaf(cj, q[R + j], taps);
-                    taps = fmaf(cj, Io<T>::to_f(t[cy - j][cz]), taps);
-                    taps = fmaf(cj, Io<T>::to_f(t[cy + j][cz]), taps);
-                    taps = fmaf(cj, Io<T>::to_f(t[cy][cz - j]), taps);
-                    taps = fmaf(cj, Io<T>::to_f(t[cy][cz + j]), taps);
+                    taps = fmaf(cj, q[R - j] - uc, taps);
+                    taps = fmaf(cj, q[R + j] - uc, taps);
+                    taps = fmaf(cj, Io<T>::to_f(t[cy - j][cz]) - uc, taps);
+                    taps = fmaf(cj, Io<T>::to_f(t[cy + j][cz]) - uc, taps);
+                    taps = fmaf(cj, Io<T>::to_f(t[cy][cz - j]) - uc, taps);
+                    taps = fmaf(cj, Io<T>::to_f(t[cy][cz + j]) - uc, taps);
                 }
                 v = Update<kExpanded>::apply(taps * sc.s_u, uc * sc.s_u, cum * sc.s_up, cf1, cf2, inv,
                                              a, src_w);

@@ -20,6 +20,11 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
+def report(name, *errs):
+    """Print the measured error (visible with pytest -s) and return it."""
+    print(f"PARITY {name} " + " ".join(f"{e:.3e}" for e in errs))
+
+
 def test_plain_config_parity(oracle_mod):
     """64^3 + 10, space order 4, 1.5 km/s, 10 Hz Ricker at the centre, 100 steps."""
     spec = inputs.plain_shot()
@@ -31,6 +36,7 @@ def test_plain_config_parity(oracle_mod):
             got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel=kernel)
             assert shot.step == spec.nt
             e0, e1 = rel_l2(got, want), rel_l2(got_prev, want_prev)
+            report(f"plain_so4_{form}_{kernel}", e0, e1)
             assert e0 <= TOL and e1 <= TOL, (form, kernel, e0, e1)
             shot.close()
 
@@ -52,6 +58,7 @@ def test_every_space_order_ragged(oracle_mod, k, form):
     want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
     got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel="stream",
                                   tile_y=8, x_block=16)
+    report(f"ragged_so{k}_{form}", rel_l2(got, want), rel_l2(got_prev, want_prev))
     assert rel_l2(got, want) <= TOL
     assert rel_l2(got_prev, want_prev) <= TOL
     shot.close()
@@ -145,6 +152,8 @@ def test_full_size_sweep_parity(oracle_mod, k):
     state = (u0, u1, 0)
     want, want_prev = run_oracle(oracle_mod, spec, 6, dt, eta, state=state)
     got, got_prev, shot = run_gpu(spec, 6, dt, None, state=state)
+    report(f"full276_so{k}_factored_autotuned{shot.config[:2]}", rel_l2(got, want),
+           rel_l2(got_prev, want_prev))
     assert rel_l2(got, want) <= TOL
     assert rel_l2(got_prev, want_prev) <= TOL
     shot.close()
