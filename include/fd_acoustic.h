@@ -190,6 +190,47 @@ int fd_last_forward_ms(fd_handle *hd, float *ms);
 /* Release every device buffer and the handle. NULL is accepted (no-op). */
 int fd_destroy(fd_handle *hd);
 
+/* ---- allocation-free stepping -------------------------------------------- */
+
+/* nt time steps on CALLER-OWNED device buffers, allocating no device memory.
+ * (The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory themselves, such as plug-ins inside a
+ * framework whose caching allocator owns the whole device, where a foreign
+ * cudaMalloc would bypass its accounting or fail once the pool holds the
+ * memory, and latency-bound serving loops, where cudaMalloc/cudaFree would
+ * synchronise the device.)
+ *
+ * Layout: dense C-order [Nx][Ny][Nz] float arrays over the computational
+ * domain (no interior/layer split here). d_u = u^{step0}, d_u_prev =
+ * u^{step0-1}; each step writes the new level over the older one, so after the
+ * call the newest level u^{step0+nt} is in d_u when nt is even and in
+ * d_u_prev when nt is odd (the other buffer holds the level before it).
+ * d_m = 1/v^2 (> 0), d_eta = damping (>= 0) or NULL for none; both are read
+ * as given (no validation, no stability check: the caller owns that). The
+ * stencil is the expanded form of fd_forward (same arithmetic per point).
+ * Sources: ns in [0, 4] point sources at DOMAIN nodes src_xyz (host array,
+ * x0,y0,z0, x1,y1,z1, ...), wavelets in the device array d_wavelet (ns rows
+ * of ld samples; q = 0 beyond ld), step n uses sample n (global step, from
+ * step0). stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * Scratch: per-CTA maxima of |u| and the running maximum sit in one static
+ * device array of 65,792 bytes (16,384 CTA slots + header) that every GPU
+ * loading the library holds until exit. FD_EINVAL when one step would need
+ * more than 16,384 CTAs (Ny*Nz above about 4.2 million points) or for bad
+ * arguments; FD_ERANGE for a source outside the domain. The first call on a
+ * device looks up that device's copy of the array (cudaGetSymbolAddress) once;
+ * make that first call before any stream capture. Every call on a device
+ * shares the same array and clears the running maximum at its start, so calls
+ * that overlap on the GPU (other streams, other threads) race on it.
+ *
+ * amax_out (host, may be NULL): when given, the call synchronises the stream,
+ * stores max |u| over every point written by the call's steps and returns
+ * FD_ENONFINITE if it is NaN/Inf; when NULL the call returns after queueing. */
+int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m, const float *d_eta, int Nx,
+                       int Ny, int Nz, int space_order, double h, double dt, int ns,
+                       const int *src_xyz, const float *d_wavelet, int ld, long long step0, int nt,
+                       void *stream, float *amax_out);
+
 /* ---- host numerics -------------------------------------------------------- */
 
 /* Stability limit dt_max = 2 h / (v_max sqrt(3 sum_{j=-r..r} |c_j|)) of the

@@ -86,6 +86,8 @@ _SIGNATURES = {
     "fd_dt_max": (_i, [_i, _d, _d, _dp]),
     "fd_fd_weights": (_i, [_i, _dp]),
     "fd_default_damping": (_i, [_i, _i, _i, _i, _d, _vp, _vp]),
+    "fd_forward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _i, _vp, _vp, _i,
+                               ctypes.c_longlong, _i, _vp, _fp]),
     "fd_last_error": (ctypes.c_char_p, []),
     "fd_version": (ctypes.c_char_p, []),
 }
@@ -259,6 +261,22 @@ def fd_default_damping(m, nbl, h) -> np.ndarray:
     nx, ny, nz = m.shape
     _check(lib().fd_default_damping(nx, ny, nz, nbl, h, _ptr(m), _ptr(eta)), "fd_default_damping")
     return eta
+
+
+def fd_forward_noalloc(d_u, d_u_prev, d_m, d_eta, dims, space_order, h, dt, sources=(),
+                       d_wavelet=None, ld=0, step0=0, nt=1, stream=None, want_amax=True):
+    """Allocation-free stepping on caller-owned device buffers (see the header).
+    sources: domain nodes (x, y, z), at most 4. Returns max |u| when want_amax."""
+    nx, ny, nz = dims
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+    amax = ctypes.c_float(0.0)
+    rc = lib().fd_forward_noalloc(_ptr(d_u), _ptr(d_u_prev), _ptr(d_m), _ptr(d_eta), nx, ny, nz,
+                                  space_order, h, dt, len(sources),
+                                  src.ctypes.data if len(sources) else None, _ptr(d_wavelet),
+                                  int(ld), int(step0), int(nt), stream,
+                                  ctypes.byref(amax) if want_amax else None)
+    _check(rc, "fd_forward_noalloc")
+    return amax.value if want_amax else None
 
 
 def fd_last_error() -> str:

@@ -57,6 +57,10 @@ std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_t
 
 }  // namespace
 
+namespace fdgb {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace fdgb
+
 struct fd_handle {
     int nx = 0, ny = 0, nz = 0, nbl = 0, k = 0, r = 0;
     double h = 0, dt = 0;
