@@ -124,19 +124,24 @@ class ClockSampler:
 
 # ---- workload -----------------------------------------------------------------
 
-def build_workload(name: str, n: int, nt: int):
+def build_workload(name: str, n: int, nt: int, orders=ORDERS, forms=FORMS):
     from paper_1912_00695_gb300 import inputs
     if name == "plain":
         spec = inputs.plain_shot()
-        return [(spec, "factored")], "plain 64^3+10, space order 4, 1.5 km/s, 100 steps"
+        desc = "plain 64^3+10, space order 4, 1.5 km/s, 10 Hz Ricker at the centre, 100 steps"
+        cfg = {"workload": desc, "interior": 64, "nbl": 10, "space_orders": [4],
+               "forms": ["factored"], "nt": spec.nt}
+        return [(spec, "factored")], desc, cfg
     runs = []
-    for k in ORDERS:
+    for k in orders:
         spec = inputs.sweep_shot(k, n=n, nt=nt)
-        for form in FORMS:
+        for form in forms:
             runs.append((spec, form))
     desc = (f"sweep {n}^3+10 (4-layer model 1.5-4.5 km/s), space orders "
-            f"{'/'.join(map(str, ORDERS))} x factored/expanded, {nt} steps, 15 Hz Ricker")
-    return runs, desc
+            f"{'/'.join(map(str, orders))} x {'/'.join(forms)}, {nt} steps, 15 Hz Ricker")
+    cfg = {"workload": desc, "interior": n, "nbl": 10, "space_orders": list(orders),
+           "forms": list(forms), "nt": nt}
+    return runs, desc, cfg
 
 
 def layer_points(spec) -> int:
@@ -161,7 +166,7 @@ def run_ours(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    runs, desc = build_workload(args.workload, args.n, args.nt)
+    runs, desc, wcfg = build_workload(args.workload, args.n, args.nt, args.orders, args.forms)
     shots = []
     for spec, form in runs:
         dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
@@ -244,11 +249,10 @@ def run_ours(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded layered velocity model, Ricker source)",
-        "config": {"workload": desc, "interior": args.n, "nbl": 10, "space_orders": list(ORDERS),
-                   "forms": list(FORMS), "nt": args.nt, "shots_per_step": len(shots),
-                   "points_per_shot": shots[0][0].points,
-                   "l2": "inputs larger than L2 (4 fields x ~98 MB per shot, 10 shots)",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(wcfg, shots_per_step=len(shots), points_per_shot=shots[0][0].points,
+                       l2=("inputs larger than L2 (4 fields per shot, "
+                           f"{4 * shots[0][0].points * 4 / 1e6:.0f} MB per shot, {len(shots)} shots)"),
+                       parallelism=f"replicas x{world}"),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": "fd_stream_kernel", "peak_source": peak_kind,
@@ -344,7 +348,7 @@ def run_reference(args, rank: int, world: int):
         step += per
     el = time.perf_counter() - t0
     value = spec.points * per * args.steps / el / 1e9
-    _, desc = build_workload(args.workload, args.n, args.nt)
+    _, desc, wcfg = build_workload(args.workload, args.n, args.nt, args.orders, args.forms)
     sample = f"space order 8 shot of the sweep ({spec.shape[0]}^3 points), {per} steps per bench step, FP64"
     line = {"impl": "reference",
             "metric": "Gpts/s (computational-domain points updated per second) and fraction of "
@@ -353,7 +357,7 @@ def run_reference(args, rank: int, world: int):
             "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded layered velocity model, Ricker source)",
-            "config": {"workload": desc, "interior": args.n, "nbl": 10, "nt": args.nt},
+            "config": wcfg,
             "cpu_baseline": {"value": round(value, 5), "unit": "Gpts/s", "kind": "oracle",
                              "cores": oracle.num_threads(), "sample": sample},
             "e2e": {"value": round(value, 5), "unit": "Gpts/s", "h2d_bytes_per_step": 0,
@@ -371,6 +375,10 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orders", type=lambda v: tuple(int(x) for x in v.split(",")), default=ORDERS,
+                    help="comma-separated space orders of the sweep (default 2,4,8,12,16)")
+    ap.add_argument("--forms", type=lambda v: tuple(v.split(",")), default=FORMS,
+                    help="comma-separated stencil forms (default factored,expanded)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

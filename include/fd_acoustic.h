@@ -28,7 +28,8 @@
  *  - Ownership. Host arrays passed in are copied; the caller keeps them. The
  *    library owns the device buffers of a handle until fd_destroy().
  *  - Threading and streams. A handle is not thread-safe. Its work is queued
- *    on one CUDA stream (fd_set_stream; default: the legacy default stream).
+ *    on one CUDA stream (fd_set_stream; default: a blocking stream the handle
+ *    creates, which orders with the legacy default stream).
  *    Calls that return data to the host synchronise that stream.
  */
 #ifndef FD_ACOUSTIC_H
@@ -149,7 +150,9 @@ int fd_read_wavefield(fd_handle *hd, float *out, int level);
 int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level);
 
 /* Bind the handle to a CUDA stream (a cudaStream_t, e.g. torch's
- * torch.cuda.current_stream().cuda_stream); NULL = legacy default stream. */
+ * torch.cuda.current_stream().cuda_stream); NULL = the handle's own stream
+ * (created blocking, so it orders with the legacy default stream). Waits for
+ * the work already queued on the previous stream. */
 int fd_set_stream(fd_handle *hd, void *cuda_stream);
 
 /* Wait for the handle's queued work; returns the device status (FD_OK,
@@ -169,7 +172,7 @@ int fd_status(fd_handle *hd);
 int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long step);
 
 /* Zero both wavefield levels, the step counter and the device status. Keeps
- * the model and the sources. */
+ * the model and the sources. Queued on the handle's stream (asynchronous). */
 int fd_reset(fd_handle *hd);
 
 /* Global step counter n (the wavefield level u^n held as level 0). */

@@ -659,6 +659,8 @@ int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level) {
 
 int fd_set_stream(fd_handle *hd, void *cuda_stream) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    // work already queued on the old stream completes before the new one is used
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
     hd->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : hd->own_stream;
     return FD_OK;
 }
@@ -726,7 +728,6 @@ int fd_reset(fd_handle *hd) {
     FD_CUDA(cudaMemsetAsync(hd->ubuf[1], 0, ub, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream));
     FD_CUDA(launch_init_scales(hd->d_scales, hd->stream));
-    FD_CUDA(cudaStreamSynchronize(hd->stream));
     hd->step = 0;
     hd->cur = 0;
     return FD_OK;
