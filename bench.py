@@ -233,7 +233,7 @@ def run_ours(args, rank: int, world: int):
         breakdown[key] = {"gpts": round(spec.points * spec.nt / (ms * 1e-3) / 1e9, 2),
                           "us_per_step": round(ms * 1e3 / spec.nt, 2),
                           "hbm_frac": round(gbs / peak, 4),
-                          "tile_y_x_block": list(shot.config[:2])}
+                          "kernel_tz_ty_xb": list(shot.config)}
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, shots, stream, world)

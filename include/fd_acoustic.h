@@ -47,7 +47,8 @@ extern "C" {
 #define FD_ENOMEM (-4)      /* a device or host allocation failed                 */
 #define FD_ECUDA (-5)       /* a CUDA runtime call failed                         */
 #define FD_ENONFINITE (-6)  /* the wavefield reached NaN/Inf (or 16-bit overflow) */
-#define FD_ETIMEOUT (-7)    /* a bounded device-side wait ran out                 */
+#define FD_ETIMEOUT (-7)    /* a bounded device-side wait ran out (reported by
+                               fd_synchronize / fd_read_wavefield)                */
 #define FD_ESTATE (-8)      /* call out of order, e.g. fd_forward before a model  */
 #define FD_ENOTSUP (-9)     /* option combination not supported                   */
 #define FD_EFULL (-10)      /* batch/server: no slot or memory budget left        */
@@ -67,15 +68,21 @@ extern "C" {
                                by (m + dt/2 eta) per point, as Listing 2 is written */
 
 /* Kernel schedule. */
-#define FD_KERNEL_AUTO 0    /* streaming kernel, tile chosen by the autotuner */
-#define FD_KERNEL_STREAM 1  /* 2.5D streaming kernel (x-march, y-z tile in shared memory) */
+#define FD_KERNEL_AUTO 0    /* TMA kernel for FP32 storage, streaming kernel for 16-bit,
+                               launch shape chosen by the autotuner */
+#define FD_KERNEL_STREAM 1  /* 2.5D streaming kernel, one point per thread (x-march, y-z tile
+                               staged through registers into shared memory); all storages */
 #define FD_KERNEL_NAIVE 2   /* one thread per point, all taps from global memory */
+#define FD_KERNEL_TMA 3     /* 2.5D streaming kernel, four z points per thread, y-z tile with
+                               halo fetched by tensor-map bulk copies; FP32 storage only */
 
 typedef struct fd_options {
     int storage;       /* FD_STORAGE_*                                             */
     int form;          /* FD_FORM_*                                                */
     int kernel;        /* FD_KERNEL_*                                              */
-    int tile_y;        /* streaming tile rows along y (4, 8 or 16); 0 = autotune   */
+    int tile_z;        /* tile width along z: STREAM 32; TMA 32, 64 or 128; 0 = autotune */
+    int tile_y;        /* tile rows along y: STREAM 4, 8, 16; TMA with tile_z 32: 16 or 32,
+                          64: 8 or 16, 128: 8; 0 = autotune                             */
     int x_block;       /* planes per CTA along x; 0 = autotune                     */
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
                           fd_read_wavefield/fd_status report FD_ENONFINITE          */
@@ -83,8 +90,8 @@ typedef struct fd_options {
 
 typedef struct fd_handle fd_handle;
 
-/* Fill *opt with the defaults: FP32, factored, auto kernel, autotuned tile,
- * finite check on. */
+/* Fill *opt with the defaults: FP32, factored, auto kernel, autotuned tile
+ * and x_block, finite check on. */
 void fd_options_default(fd_options *opt);
 
 /* ---- single-shot solver --------------------------------------------------- */
@@ -100,8 +107,8 @@ int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double
                        fd_handle **out);
 
 /* As fd_acoustic_create with explicit options (opt == NULL: defaults).
- * FD_ENOTSUP for an unknown storage/form/kernel value or a tile_y other than
- * 0, 4, 8, 16. */
+ * FD_ENOTSUP for an unknown storage/form/kernel value, FD_KERNEL_TMA with
+ * 16-bit storage, or a (tile_z, tile_y) pair the chosen kernel does not have. */
 int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                           const fd_options *opt, fd_handle **out);
 
@@ -181,9 +188,10 @@ int fd_get_step(fd_handle *hd, long long *step);
 /* Computational-domain extents N_x, N_y, N_z of a handle. */
 int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz);
 
-/* Launch configuration the handle uses for its step kernel (tile_y, x_block,
- * kernel id): what the autotuner picked or the options forced. */
-int fd_get_config(fd_handle *hd, int *tile_y, int *x_block, int *kernel);
+/* Launch configuration the handle uses for its step kernel (FD_KERNEL_* id,
+ * tile_z, tile_y, x_block): what the autotuner picked or the options forced
+ * (zeros before the first fd_forward when the autotuner still has to run). */
+int fd_get_config(fd_handle *hd, int *kernel, int *tile_z, int *tile_y, int *x_block);
 
 /* Device time of the step kernels queued by the last fd_forward, in ms,
  * measured by CUDA events on the handle's stream around the graph replay

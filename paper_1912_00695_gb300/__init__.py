@@ -14,7 +14,7 @@ import numpy as np
 
 from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD_EUNSTABLE,  # noqa: F401
                    FD_ERANGE, FD_ESTATE, FD_ETIMEOUT, FD_FORM_EXPANDED, FD_FORM_FACTORED,
-                   FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_OK, FD_STORAGE_BF16,
+                   FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
                    fd_forward, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_load_state,
@@ -24,15 +24,17 @@ from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD
 
 STORAGE = {"f32": FD_STORAGE_F32, "bf16": FD_STORAGE_BF16, "f16": FD_STORAGE_F16}
 FORMS = {"factored": FD_FORM_FACTORED, "expanded": FD_FORM_EXPANDED}
-KERNELS = {"auto": FD_KERNEL_AUTO, "stream": FD_KERNEL_STREAM, "naive": FD_KERNEL_NAIVE}
+KERNELS = {"auto": FD_KERNEL_AUTO, "stream": FD_KERNEL_STREAM, "naive": FD_KERNEL_NAIVE,
+           "tma": FD_KERNEL_TMA}
 
 
-def options(storage="f32", form="factored", kernel="auto", tile_y=0, x_block=0,
+def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x_block=0,
             check_finite=True) -> fd_options:
     o = fd_options_default()
     o.storage = STORAGE[storage]
     o.form = FORMS[form]
     o.kernel = KERNELS[kernel]
+    o.tile_z = int(tile_z)
     o.tile_y = int(tile_y)
     o.x_block = int(x_block)
     o.check_finite = int(bool(check_finite))

@@ -31,7 +31,7 @@ FD_EFULL = -10
 
 FD_STORAGE_F32, FD_STORAGE_BF16, FD_STORAGE_F16 = 0, 1, 2
 FD_FORM_FACTORED, FD_FORM_EXPANDED = 0, 1
-FD_KERNEL_AUTO, FD_KERNEL_STREAM, FD_KERNEL_NAIVE = 0, 1, 2
+FD_KERNEL_AUTO, FD_KERNEL_STREAM, FD_KERNEL_NAIVE, FD_KERNEL_TMA = 0, 1, 2, 3
 
 ERROR_NAMES = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ERANGE", -3: "FD_EUNSTABLE", -4: "FD_ENOMEM",
                -5: "FD_ECUDA", -6: "FD_ENONFINITE", -7: "FD_ETIMEOUT", -8: "FD_ESTATE",
@@ -46,7 +46,7 @@ class FdError(RuntimeError):
 
 class fd_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("form", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("tile_y", ctypes.c_int), ("x_block", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("tile_y", ctypes.c_int), ("x_block", ctypes.c_int),
                 ("check_finite", ctypes.c_int)]
 
 
@@ -80,7 +80,7 @@ _SIGNATURES = {
     "fd_load_state": (_i, [_vp, _vp, _vp, ctypes.c_longlong]),
     "fd_get_step": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "fd_get_dims": (_i, [_vp, _ip, _ip, _ip]),
-    "fd_get_config": (_i, [_vp, _ip, _ip, _ip]),
+    "fd_get_config": (_i, [_vp, _ip, _ip, _ip, _ip]),
     "fd_last_forward_ms": (_i, [_vp, _fp]),
     "fd_destroy": (_i, [_vp]),
     "fd_dt_max": (_i, [_i, _d, _d, _dp]),
@@ -227,10 +227,10 @@ def fd_get_dims(hd):
 
 
 def fd_get_config(hd):
-    a, b, c = _i(), _i(), _i()
-    _check(lib().fd_get_config(hd, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
-           "fd_get_config")
-    return a.value, b.value, c.value
+    """(kernel, tile_z, tile_y, x_block) of the handle's step kernel."""
+    v = [_i() for _ in range(4)]
+    _check(lib().fd_get_config(hd, *[ctypes.byref(x) for x in v]), "fd_get_config")
+    return tuple(x.value for x in v)
 
 
 def fd_last_forward_ms(hd) -> float:

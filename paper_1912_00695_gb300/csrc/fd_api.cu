@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -51,9 +53,44 @@ struct GraphEntry {
     unsigned long long gen = 0;
 };
 
-// Process-wide launch-shape cache: (Nx, Ny, Nz, radius, storage, form, check) -> (tile_y, x_block)
+// Process-wide launch-shape cache:
+// (Nx, Ny, Nz, radius, storage, form, check, kernel) -> (tile_z, tile_y, x_block)
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry-point lookup (no
+// link-time dependency on the driver library).
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Valid (tile_z, tile_y) pairs of each kernel.
+bool tile_ok(int kernel, int tz, int ty) {
+    if (kernel == kStream) return (tz == 0 || tz == 32) && (ty == 0 || ty == 4 || ty == 8 || ty == 16);
+    if (kernel == kTma) {
+        if (tz == 0 && ty == 0) return true;
+        const int pairs[5][2] = {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
+        for (auto &p : pairs)
+            if ((tz == 0 || tz == p[0]) && (ty == 0 || ty == p[1])) return true;
+        return false;
+    }
+    return true;
+}
 
 }  // namespace
 
@@ -68,7 +105,8 @@ struct fd_handle {
     long long plane = 0;
     size_t n_pitched = 0;
     fd_options opt{};
-    int tile_y = 0, x_block = 0, kernel = kStream;
+    int tile_z = 0, tile_y = 0, x_block = 0, kernel = kStream;
+    CUtensorMap tmaps[2];  // TMA kernel: u^n read through ubuf[0] / ubuf[1]
     void *ubuf[2] = {nullptr, nullptr};
     float *f1 = nullptr, *f2 = nullptr;
     float *d_wavelet = nullptr;
@@ -136,12 +174,18 @@ StepArgs make_args(const fd_handle *hd, long long step, int cur) {
     return a;
 }
 
-cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, int kernel, int tile_y,
-                         cudaStream_t s) {
+// One step with the given launch shape; `map` is the tensor map of a.u (TMA kernel only).
+cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y,
+                          const CUtensorMap *map, bool check, cudaStream_t s) {
+    if (kernel == kNaive) return launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s);
+    if (kernel == kTma) return launch_tma_step(hd->r, hd->opt.form, tile_z, tile_y, *map, a, check, s);
+    return launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
+}
+
+cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, cudaStream_t s) {
     const bool check = check_enabled(hd);
-    cudaError_t e = kernel == kNaive
-                        ? launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s)
-                        : launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
+    const CUtensorMap *map = a.u == hd->ubuf[0] ? &hd->tmaps[0] : &hd->tmaps[1];
+    cudaError_t e = launch_kernel(hd, a, hd->kernel, hd->tile_z, hd->tile_y, map, check, s);
     if (e != cudaSuccess) return e;
     const int ns = int(hd->sources.size());
     if (ns > kFusedSources)
@@ -156,50 +200,86 @@ void destroy_graphs(fd_handle *hd) {
     hd->graphs.clear();
 }
 
-int heuristic_x_block(const fd_handle *hd, int tile_y) {
-    const int tiles = ((hd->Nz + kTileZ - 1) / kTileZ) * ((hd->Ny + tile_y - 1) / tile_y);
-    int chunks = (4 * 152 + tiles - 1) / tiles;
+int encode_map(const fd_handle *hd, void *base, int tile_z, int tile_y, CUtensorMap *out) {
+    int bw = 0, bh = 0, rz = 0;
+    if (!tma_box(hd->r, tile_z, tile_y, &bw, &bh, &rz)) return fail(FD_ENOTSUP, "no TMA tile %dx%d", tile_z, tile_y);
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(FD_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3] = {cuuint64_t(hd->Nz), cuuint64_t(hd->Ny), cuuint64_t(hd->Nx)};
+    cuuint64_t strides[2] = {cuuint64_t(hd->pz) * 4, cuuint64_t(hd->plane) * 4};
+    cuuint32_t box[3] = {cuuint32_t(bw), cuuint32_t(bh), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    return FD_OK;
+}
+
+int build_maps(fd_handle *hd) {
+    if (hd->kernel != kTma) return FD_OK;
+    for (int b = 0; b < 2; ++b) {
+        int rc = encode_map(hd, hd->ubuf[b], hd->tile_z, hd->tile_y, &hd->tmaps[b]);
+        if (rc != FD_OK) return rc;
+    }
+    return FD_OK;
+}
+
+int heuristic_x_block(const fd_handle *hd, int tile_z, int tile_y) {
+    const int tiles = ((hd->Nz + tile_z - 1) / tile_z) * ((hd->Ny + tile_y - 1) / tile_y);
+    int chunks = (2 * 152 + tiles - 1) / tiles;
     const int max_chunks = hd->Nx / 16 > 0 ? hd->Nx / 16 : 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
+    chunks = std::max(1, std::min(chunks, max_chunks));
     return (hd->Nx + chunks - 1) / chunks;
 }
 
-// Pick (tile_y, x_block) for the streaming kernel by timing candidate launch
-// shapes. The candidates run on scratch wavefields, scale slots and status word
-// (zeroed, no sources), so the handle's own state is never touched.
+// Pick (tile_z, tile_y, x_block) for the handle's kernel by timing candidate
+// launch shapes. The candidates run on scratch wavefields, scale slots and
+// status word (zeroed, no sources), so the handle's own state is never touched.
 int autotune(fd_handle *hd) {
-    const bool force_tile = hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
-    if (force_tile && force_xb) {
-        hd->tile_y = hd->opt.tile_y;
-        hd->x_block = hd->opt.x_block;
-        return FD_OK;
+    const int kernel = hd->kernel;
+    const bool force_tile = hd->opt.tile_z > 0 || hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
+    std::vector<std::pair<int, int>> tiles;
+    if (kernel == kTma) {
+        const int pairs[5][2] = {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
+        for (auto &p : pairs)
+            if ((hd->opt.tile_z == 0 || hd->opt.tile_z == p[0]) && (hd->opt.tile_y == 0 || hd->opt.tile_y == p[1]))
+                tiles.push_back({p[0], p[1]});
+    } else {
+        for (int ty : {4, 8, 16})
+            if (hd->opt.tile_y == 0 || hd->opt.tile_y == ty) tiles.push_back({32, ty});
     }
-    auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.storage, hd->opt.form,
-                               int(check_enabled(hd)));
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (!force_tile && !force_xb && it != g_tune_cache.end()) {
-            hd->tile_y = it->second.first;
-            hd->x_block = it->second.second;
-            return FD_OK;
-        }
-    }
-    const char *env = std::getenv("FDGB_NO_TUNE");
-    std::vector<int> tiles = force_tile ? std::vector<int>{hd->opt.tile_y} : std::vector<int>{4, 8, 16};
-    if (env && env[0] == '1') {
-        hd->tile_y = force_tile ? hd->opt.tile_y : 8;
-        hd->x_block = force_xb ? hd->opt.x_block : heuristic_x_block(hd, hd->tile_y);
-        return FD_OK;
-    }
+    if (tiles.empty()) return fail(FD_ENOTSUP, "no tile shape matches the options");
     std::vector<int> xbs;
     if (force_xb) {
         xbs.push_back(hd->opt.x_block);
     } else {
         for (int xb : {16, 32, 64, 128})
-            if (xb < hd->Nx) xbs.push_back(xb);
+            if (xb < hd->Nx && (kernel != kTma || xb >= 32)) xbs.push_back(xb);
         xbs.push_back(hd->Nx);
+    }
+    if (tiles.size() == 1 && xbs.size() == 1) {
+        hd->tile_z = tiles[0].first;
+        hd->tile_y = tiles[0].second;
+        hd->x_block = xbs[0];
+        return FD_OK;
+    }
+    auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.storage, hd->opt.form,
+                               int(check_enabled(hd)), kernel);
+    if (!force_tile && !force_xb) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            std::tie(hd->tile_z, hd->tile_y, hd->x_block) = it->second;
+            return FD_OK;
+        }
+    }
+    const char *env = std::getenv("FDGB_NO_TUNE");
+    if (env && env[0] == '1') {
+        hd->tile_z = tiles[0].first;
+        hd->tile_y = tiles[0].second;
+        hd->x_block = force_xb ? xbs[0] : heuristic_x_block(hd, hd->tile_z, hd->tile_y);
+        return FD_OK;
     }
     const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
     void *s0 = nullptr, *s1 = nullptr, *aux = nullptr;
@@ -208,16 +288,17 @@ int autotune(fd_handle *hd) {
         cudaGetLastError();
         if (s0) cudaFree(s0);
         if (s1) cudaFree(s1);
-        // not enough memory for scratch fields: fall back to the heuristic shape
-        hd->tile_y = force_tile ? hd->opt.tile_y : 8;
-        hd->x_block = force_xb ? hd->opt.x_block : heuristic_x_block(hd, hd->tile_y);
+        // not enough memory for scratch fields: take the first shape, heuristic x_block
+        hd->tile_z = tiles[0].first;
+        hd->tile_y = tiles[0].second;
+        hd->x_block = force_xb ? xbs[0] : heuristic_x_block(hd, hd->tile_z, hd->tile_y);
         return FD_OK;
     }
     LevelScales *ls = static_cast<LevelScales *>(aux);
     unsigned *st = reinterpret_cast<unsigned *>(static_cast<char *>(aux) + 128);
     int rc = FD_OK;
     float best = 1e30f;
-    int best_t = tiles[0], best_xb = xbs[0];
+    int best_t = 0, best_xb = xbs[0];
     cudaError_t e = cudaMemsetAsync(s0, 0, ub, hd->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s1, 0, ub, hd->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(aux, 0, 256, hd->stream);
@@ -229,36 +310,39 @@ int autotune(fd_handle *hd) {
     a.scales = hd->opt.storage != kF32 ? ls : nullptr;
     a.status = check_enabled(hd) ? st : nullptr;
     const bool check = check_enabled(hd);
-    for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess; ++ti) {
-        for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess; ++xi) {
+    for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess && rc == FD_OK; ++ti) {
+        CUtensorMap map;
+        if (kernel == kTma) rc = encode_map(hd, s0, tiles[ti].first, tiles[ti].second, &map);
+        for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess && rc == FD_OK; ++xi) {
             a.x_block = xbs[xi];
             for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-                e = launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tiles[ti], a, check, hd->stream);
+                e = launch_kernel(hd, a, kernel, tiles[ti].first, tiles[ti].second, &map, check, hd->stream);
             if (e == cudaSuccess) e = cudaEventRecord(hd->ev0, hd->stream);
             for (int w = 0; w < 4 && e == cudaSuccess; ++w)
-                e = launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tiles[ti], a, check, hd->stream);
+                e = launch_kernel(hd, a, kernel, tiles[ti].first, tiles[ti].second, &map, check, hd->stream);
             if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, hd->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(hd->ev1);
             float ms = 0;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, hd->ev0, hd->ev1);
             if (e == cudaSuccess && ms < best) {
                 best = ms;
-                best_t = tiles[ti];
+                best_t = int(ti);
                 best_xb = xbs[xi];
             }
         }
     }
-    if (e != cudaSuccess) rc = fail(FD_ECUDA, "autotune launch failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess && rc == FD_OK) rc = fail(FD_ECUDA, "autotune launch failed: %s", cudaGetErrorString(e));
     cudaStreamSynchronize(hd->stream);
     cudaFree(s0);
     cudaFree(s1);
     cudaFree(aux);
     if (rc != FD_OK) return rc;
-    hd->tile_y = best_t;
+    hd->tile_z = tiles[best_t].first;
+    hd->tile_y = tiles[best_t].second;
     hd->x_block = best_xb;
     if (!force_tile && !force_xb) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {best_t, best_xb};
+        g_tune_cache[key] = std::make_tuple(hd->tile_z, hd->tile_y, hd->x_block);
     }
     return FD_OK;
 }
@@ -381,6 +465,7 @@ int read_status(fd_handle *hd) {
     unsigned st = 0;
     FD_CUDA(cudaMemcpyAsync(&st, hd->d_status, sizeof st, cudaMemcpyDeviceToHost, hd->stream));
     FD_CUDA(cudaStreamSynchronize(hd->stream));
+    if (st & kStatusTimeout) return fail(FD_ETIMEOUT, "a device-side wait timed out (bulk copy never landed)");
     if (st & kStatusNonFinite) return fail(FD_ENONFINITE, "wavefield reached NaN/Inf (or 16-bit overflow)");
     return FD_OK;
 }
@@ -394,6 +479,7 @@ void fd_options_default(fd_options *opt) {
     opt->storage = FD_STORAGE_F32;
     opt->form = FD_FORM_FACTORED;
     opt->kernel = FD_KERNEL_AUTO;
+    opt->tile_z = 0;
     opt->tile_y = 0;
     opt->x_block = 0;
     opt->check_finite = 1;
@@ -447,10 +533,13 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     const long long Nx = nx + 2LL * nbl, Ny = ny + 2LL * nbl, Nz = nz + 2LL * nbl;
     if (Nx > kMaxDim || Ny > kMaxDim || Nz > kMaxDim) return fail(FD_EINVAL, "extent above 65535");
     if (opt.storage < 0 || opt.storage > 2 || opt.form < 0 || opt.form > 1 || opt.kernel < 0 ||
-        opt.kernel > 2)
+        opt.kernel > 3)
         return fail(FD_ENOTSUP, "unknown storage/form/kernel option");
-    if (opt.tile_y != 0 && opt.tile_y != 4 && opt.tile_y != 8 && opt.tile_y != 16)
-        return fail(FD_ENOTSUP, "tile_y must be 0, 4, 8 or 16");
+    int kernel = opt.kernel;
+    if (kernel == kAuto) kernel = opt.storage == kF32 ? kTma : kStream;
+    if (kernel == kTma && opt.storage != kF32) return fail(FD_ENOTSUP, "the TMA kernel stores FP32 only");
+    if (!tile_ok(kernel, opt.tile_z, opt.tile_y))
+        return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
 
     fd_handle *hd = new fd_handle();
@@ -466,7 +555,7 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     hd->Ny = int(Ny);
     hd->Nz = int(Nz);
     hd->opt = opt;
-    hd->kernel = opt.kernel == kNaive ? kNaive : kStream;
+    hd->kernel = kernel;
     hd->pz = int((Nz + 63) / 64 * 64);  // 128-byte rows for 16-bit and 256-byte rows for FP32
     hd->plane = (long long)hd->Ny * hd->pz;
     hd->n_pitched = size_t(hd->Nx) * size_t(hd->plane);
@@ -557,9 +646,13 @@ int fd_forward(fd_handle *hd, int nt) {
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
     if (nt == 0) return FD_OK;
-    if (hd->kernel == kStream && (hd->tile_y == 0 || hd->x_block == 0)) {
+    if (hd->kernel != kNaive && (hd->tile_y == 0 || hd->x_block == 0)) {
         int rc = autotune(hd);
-        if (rc != FD_OK) return rc;
+        if (rc == FD_OK) rc = build_maps(hd);
+        if (rc != FD_OK) {
+            hd->tile_y = hd->x_block = 0;
+            return rc;
+        }
         hd->gen++;
     }
     GraphEntry *entry = nullptr;
@@ -572,7 +665,7 @@ int fd_forward(fd_handle *hd, int nt) {
         cudaError_t err = cudaSuccess;
         for (int i = 0; i < nt && err == cudaSuccess; ++i) {
             const StepArgs a = make_args(hd, hd->step + i, cur);
-            err = enqueue_step(hd, a, hd->kernel, hd->tile_y, hd->stream);
+            err = enqueue_step(hd, a, hd->stream);
             cur ^= 1;
         }
         cudaError_t cap = cudaStreamEndCapture(hd->stream, &graph);
@@ -747,11 +840,12 @@ int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz) {
     return FD_OK;
 }
 
-int fd_get_config(fd_handle *hd, int *tile_y, int *x_block, int *kernel) {
-    if (!hd || !tile_y || !x_block || !kernel) return fail(FD_EINVAL, "NULL argument");
+int fd_get_config(fd_handle *hd, int *kernel, int *tile_z, int *tile_y, int *x_block) {
+    if (!hd || !kernel || !tile_z || !tile_y || !x_block) return fail(FD_EINVAL, "NULL argument");
+    *kernel = hd->kernel;
+    *tile_z = hd->tile_z;
     *tile_y = hd->tile_y;
     *x_block = hd->x_block;
-    *kernel = hd->kernel;
     return FD_OK;
 }
 

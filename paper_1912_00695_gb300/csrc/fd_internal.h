@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fdgb {
@@ -17,10 +18,11 @@ constexpr int kMaxDim = 65535;  // keeps every launch grid dimension within limi
 
 enum Storage : int { kF32 = 0, kBF16 = 1, kF16 = 2 };
 enum Form : int { kFactored = 0, kExpanded = 1 };
-enum KernelKind : int { kAuto = 0, kStream = 1, kNaive = 2 };
+enum KernelKind : int { kAuto = 0, kStream = 1, kNaive = 2, kTma = 3 };
 
 // Device status word bits (written by kernels, read by the host).
 constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;  // a bounded device-side wait gave up
 
 // Per-level scale bookkeeping for 16-bit storage: value = stored * scale.
 // Three rotating slots, indexed by global step modulo 3: slot (n % 3) holds the
@@ -71,6 +73,11 @@ cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, co
 cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
                               cudaStream_t s);
 int stream_grid_x_chunks(int Nx, int x_block);
+// TMA-fed FP32 kernel (fd_tma.cuh): tile (tile_z, tile_y) in {(32,32), (64,16), (128,8),
+// (32,16), (64,8)}; `map` describes the u^n buffer with box (box_w, box_h, 1).
+cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const CUtensorMap &map,
+                            const StepArgs &a, bool check, cudaStream_t s);
+bool tma_box(int radius, int tile_z, int tile_y, int *box_w, int *box_h, int *rz);
 
 // Utility kernels (fd_kernels_util.cu)
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,

@@ -1,3 +1,5 @@
 // Step kernels for stencil radius 2 (space order 4).
 #include "fd_stencil.cuh"
+#include "fd_tma.cuh"
 FDGB_INSTANTIATE_RADIUS(2)
+FDGB_INSTANTIATE_TMA_RADIUS(2)

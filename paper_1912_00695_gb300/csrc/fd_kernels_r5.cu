@@ -1,3 +1,5 @@
 // Step kernels for stencil radius 5 (space order 10).
 #include "fd_stencil.cuh"
+#include "fd_tma.cuh"
 FDGB_INSTANTIATE_RADIUS(5)
+FDGB_INSTANTIATE_TMA_RADIUS(5)

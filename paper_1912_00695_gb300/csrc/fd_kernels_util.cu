@@ -23,6 +23,49 @@ FDGB_DECLARE_RADIUS(7)
 FDGB_DECLARE_RADIUS(8)
 #undef FDGB_DECLARE_RADIUS
 
+#define FDGB_DECLARE_TMA_RADIUS(R)                                                               \
+    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const CUtensorMap &map,    \
+                                    const StepArgs &a, bool check, cudaStream_t s);              \
+    bool tma_box_radius_##R(int tile_z, int tile_y, int *w, int *h, int *rz);
+FDGB_DECLARE_TMA_RADIUS(1)
+FDGB_DECLARE_TMA_RADIUS(2)
+FDGB_DECLARE_TMA_RADIUS(3)
+FDGB_DECLARE_TMA_RADIUS(4)
+FDGB_DECLARE_TMA_RADIUS(5)
+FDGB_DECLARE_TMA_RADIUS(6)
+FDGB_DECLARE_TMA_RADIUS(7)
+FDGB_DECLARE_TMA_RADIUS(8)
+#undef FDGB_DECLARE_TMA_RADIUS
+
+cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const CUtensorMap &map,
+                            const StepArgs &a, bool check, cudaStream_t s) {
+    switch (radius) {
+        case 1: return tma_step_radius_1(form, tile_z, tile_y, map, a, check, s);
+        case 2: return tma_step_radius_2(form, tile_z, tile_y, map, a, check, s);
+        case 3: return tma_step_radius_3(form, tile_z, tile_y, map, a, check, s);
+        case 4: return tma_step_radius_4(form, tile_z, tile_y, map, a, check, s);
+        case 5: return tma_step_radius_5(form, tile_z, tile_y, map, a, check, s);
+        case 6: return tma_step_radius_6(form, tile_z, tile_y, map, a, check, s);
+        case 7: return tma_step_radius_7(form, tile_z, tile_y, map, a, check, s);
+        case 8: return tma_step_radius_8(form, tile_z, tile_y, map, a, check, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool tma_box(int radius, int tile_z, int tile_y, int *w, int *h, int *rz) {
+    switch (radius) {
+        case 1: return tma_box_radius_1(tile_z, tile_y, w, h, rz);
+        case 2: return tma_box_radius_2(tile_z, tile_y, w, h, rz);
+        case 3: return tma_box_radius_3(tile_z, tile_y, w, h, rz);
+        case 4: return tma_box_radius_4(tile_z, tile_y, w, h, rz);
+        case 5: return tma_box_radius_5(tile_z, tile_y, w, h, rz);
+        case 6: return tma_box_radius_6(tile_z, tile_y, w, h, rz);
+        case 7: return tma_box_radius_7(tile_z, tile_y, w, h, rz);
+        case 8: return tma_box_radius_8(tile_z, tile_y, w, h, rz);
+        default: return false;
+    }
+}
+
 cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
                                bool check, cudaStream_t s) {
     switch (radius) {

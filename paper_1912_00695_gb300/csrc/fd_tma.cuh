@@ -1,0 +1,382 @@
+// TMA-fed streaming step kernel (FP32 storage), templated on the stencil
+// radius R, the symbolic form and the tile shape. Included by the per-radius
+// translation units after fd_stencil.cuh.
+//
+// Schedule. A CTA of W warps owns a tile of TZ = 4*LZ points along z by
+// TY = (32/LZ)*W points along y and marches x over [x0, x0 + x_block). Each
+// thread owns 4 consecutive z points (one float4) of one y row:
+//  * x taps: a register queue of 2R+1 float4 (u^n at x-R..x+R of the thread's
+//    points); the x loop is unrolled by 2R+1 so the queue rotates by renaming
+//    instead of moving registers;
+//  * y and z taps: the current x-plane of u^n with an R-cell halo (z halo
+//    rounded up to a multiple of 4 so every TMA box starts 16-byte aligned),
+//    fetched by one tensor-map bulk copy per plane into a 3-stage shared ring
+//    guarded by mbarriers; out-of-domain boxes are zero-filled by the copy
+//    engine, which is exactly the Dirichlet halo;
+//  * the queue front u^n(x+R) and the point data u^{n-1}, w (m), g (eta) come
+//    as float4 loads one plane ahead; the result is one float4 store;
+//  * the arithmetic runs on float2 pairs (FFMA2/FADD2), two points per
+//    instruction.
+// The per-point arithmetic (association order included) does not depend on
+// the tile shape or x_block.
+#pragma once
+
+#include <cuda.h>
+
+#include "fd_stencil.cuh"
+
+namespace fdgb {
+
+constexpr int kTmaStages = 3;
+constexpr long long kMbarWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after kMbarWaitLimit polls (well over a second with the
+// back-off), so that a copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kMbarWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 8) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int R, int LZ, int W>
+struct TmaShape {
+    static constexpr int RZ = (R + 3) / 4 * 4;  // z halo, multiple of 4 (16-byte aligned boxes)
+    static constexpr int LY = 32 / LZ;
+    static constexpr int TZ = 4 * LZ;
+    static constexpr int TY = LY * W;
+    static constexpr int SW = TZ + 2 * RZ;  // box width (floats)
+    static constexpr int SH = TY + 2 * R;   // box height (rows)
+    static constexpr int STAGE = (SW * SH + 31) / 32 * 32;  // floats per stage, 128-byte multiple
+    static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64;
+};
+
+template <int R, int FORM, int LZ, int W>
+__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                        const StepArgs a, int check) {
+    using G = TmaShape<R, LZ, W>;
+    constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
+    constexpr int Q = 2 * R + 1;
+    constexpr int NWIN = 4 + 2 * RZ;  // z window floats
+    constexpr int S = kTmaStages;
+    extern __shared__ __align__(128) float smem[];
+    float *tiles = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * G::STAGE);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int lz = lane % LZ, ly = lane / LZ;
+    const int z0 = blockIdx.x * TZ, y0 = blockIdx.y * TY;
+    const int ty = warp * LY + ly;
+    const int y = y0 + ty;
+    const int z4 = z0 + 4 * lz;
+    const int xb = blockIdx.z * a.x_block;
+    const int xe = min(xb + a.x_block, a.Nx);
+    const bool own = (y < a.Ny) && (z4 < a.Nz);
+    const long long P = a.plane;
+    const long long col = (long long)y * a.pz + z4;
+    const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.u) + col);
+    float4 *up4 = reinterpret_cast<float4 *>(static_cast<float *>(a.up) + col);
+    const float4 *__restrict__ f1 = reinterpret_cast<const float4 *>(a.f1 + col);
+    const float4 *__restrict__ f2p = reinterpret_cast<const float4 *>(a.f2 + col);
+    const long long P4 = P / 4;  // plane stride in float4 (pz and Ny*pz are multiples of 4)
+    // the damping field vanishes inside [bx0,bx1) x [by0,by1) x [bz0,bz1)
+    const bool yz_box = y >= a.by0 && y < a.by1 && z4 >= a.bz0 && z4 + 3 < a.bz1;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    constexpr uint32_t kBoxBytes = uint32_t(SW) * SH * 4;
+    auto issue = [&](int x, int stage) {
+        const uint32_t bar = smem_addr(&bars[stage]);
+        mbar_expect_tx(bar, kBoxBytes);
+        tma_load_3d(smem_addr(tiles + stage * G::STAGE), &tmap, bar, z0 - RZ, y0 - R, x);
+    };
+    if (tid == 0)
+        for (int s = 0; s < S - 1 && xb + s < xe; ++s) issue(xb + s, s);
+
+    // sources among this thread's 4 points: bit s set, sub-index in src_p
+    unsigned src_mask = 0;
+    int src_p[kFusedSources];
+#pragma unroll
+    for (int s = 0; s < kFusedSources; ++s) {
+        src_p[s] = 0;
+        if (own && s < a.ns && a.sy[s] == y && a.sz[s] >= z4 && a.sz[s] < z4 + 4 && a.sx[s] >= xb &&
+            a.sx[s] < xe) {
+            src_mask |= 1u << s;
+            src_p[s] = a.sz[s] - z4;
+        }
+    }
+
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load_u = [&](int x) -> float4 {
+        return (own && x >= 0 && x < a.Nx) ? __ldg(u4 + x * P4) : zero4;
+    };
+    float4 q[Q];
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
+    float4 nxt = load_u(xb + R);
+    float4 pum = zero4, pf1 = zero4, pf2 = zero4;
+    auto load_point = [&](int x) {
+        if (own) {
+            pum = up4[x * P4];
+            pf1 = __ldg(f1 + x * P4);
+            const bool in_box = yz_box && x >= a.bx0 && x < a.bx1;
+            pf2 = in_box ? zero4 : __ldg(f2p + x * P4);
+        }
+    };
+    load_point(xb);
+
+    float2 cz2[R + 1];
+#pragma unroll
+    for (int j = 1; j <= R; ++j) cz2[j] = f2(a.coef[j], a.coef[j]);
+    const int rowc = ty + R;
+    const int colw = 4 * lz;  // first float of the thread's z window in a tile row
+    unsigned amax_bits = 0;
+    bool failed = false;
+    int issued = min(S - 1, xe - xb);
+
+    for (int xo = xb; xo < xe; xo += Q) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int x = xo + i;
+            if (x >= xe) break;
+            const int it = x - xb;
+            const int stage = it % S;
+            const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), uint32_t(it / S) & 1u);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && x + S - 1 < xe) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(x + S - 1, (it + S - 1) % S);
+                ++issued;
+            }
+            q[(i + 2 * R) % Q] = nxt;
+            const float4 cum = pum, cf1 = pf1, cf2 = pf2;
+            if (x + 1 < xe) {
+                nxt = load_u(x + 1 + R);
+                load_point(x + 1);
+            }
+            if (own) {
+                const float *t = tiles + stage * G::STAGE;
+                const float *rowp = t + rowc * SW + colw;
+                float win[NWIN];
+#pragma unroll
+                for (int m = 0; m < NWIN / 4; ++m) {
+                    const float4 v = *reinterpret_cast<const float4 *>(rowp + 4 * m);
+                    win[4 * m] = v.x;
+                    win[4 * m + 1] = v.y;
+                    win[4 * m + 2] = v.z;
+                    win[4 * m + 3] = v.w;
+                }
+                const float4 uc = q[(i + R) % Q];
+                float2 lapA = f2(0.f, 0.f), lapB = f2(0.f, 0.f);
+                float4 out;
+                float sw[4];
+                if constexpr (FORM == kFactored) {
+                    const float2 sixA = mul2(f2(6.f, 6.f), lo2(uc)), sixB = mul2(f2(6.f, 6.f), hi2(uc));
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
+                        const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
+                        const float4 xm = q[(i + R - j) % Q], xp = q[(i + R + j) % Q];
+                        float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
+                                         add2(f2(win[RZ - j], win[RZ + 1 - j]), f2(win[RZ + j], win[RZ + 1 + j])));
+                        float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym), hi2(yp))),
+                                         add2(f2(win[RZ + 2 - j], win[RZ + 3 - j]), f2(win[RZ + 2 + j], win[RZ + 3 + j])));
+                        lapA = fma2(cz2[j], sub2(sA, sixA), lapA);
+                        lapB = fma2(cz2[j], sub2(sB, sixB), lapB);
+                    }
+                    // u+ = w L + 2u - u- - 2 g (u - u-)
+                    const float2 wA = lo2(cf1), wB = hi2(cf1), gA = lo2(cf2), gB = hi2(cf2);
+                    const float2 umA = lo2(cum), umB = hi2(cum);
+                    float2 vA = fma2(wA, lapA, fma2(f2(2.f, 2.f), lo2(uc), f2(-umA.x, -umA.y)));
+                    float2 vB = fma2(wB, lapB, fma2(f2(2.f, 2.f), hi2(uc), f2(-umB.x, -umB.y)));
+                    vA = fma2(mul2(f2(-2.f, -2.f), gA), sub2(lo2(uc), umA), vA);
+                    vB = fma2(mul2(f2(-2.f, -2.f), gB), sub2(hi2(uc), umB), vB);
+                    out = make_float4(vA.x, vA.y, vB.x, vB.y);
+                    sw[0] = cf1.x;
+                    sw[1] = cf1.y;
+                    sw[2] = cf1.z;
+                    sw[3] = cf1.w;
+                } else {
+                    // expanded: every tap (u_tap - u_c) times (c_j dt^2/h^2)/r0
+                    const float r0[4] = {fmaf(a.half_dt, cf2.x, cf1.x), fmaf(a.half_dt, cf2.y, cf1.y),
+                                         fmaf(a.half_dt, cf2.z, cf1.z), fmaf(a.half_dt, cf2.w, cf1.w)};
+                    const float inv[4] = {__frcp_rn(r0[0]), __frcp_rn(r0[1]), __frcp_rn(r0[2]),
+                                          __frcp_rn(r0[3])};
+                    const float2 invA = f2(inv[0], inv[1]), invB = f2(inv[2], inv[3]);
+                    const float2 ucA = lo2(uc), ucB = hi2(uc);
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
+                        const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
+                        const float4 xm = q[(i + R - j) % Q], xp = q[(i + R + j) % Q];
+                        const float2 cA = mul2(cz2[j], invA), cB = mul2(cz2[j], invB);
+                        lapA = fma2(cA, sub2(lo2(xm), ucA), lapA);
+                        lapA = fma2(cA, sub2(lo2(xp), ucA), lapA);
+                        lapA = fma2(cA, sub2(lo2(ym), ucA), lapA);
+                        lapA = fma2(cA, sub2(lo2(yp), ucA), lapA);
+                        lapA = fma2(cA, sub2(f2(win[RZ - j], win[RZ + 1 - j]), ucA), lapA);
+                        lapA = fma2(cA, sub2(f2(win[RZ + j], win[RZ + 1 + j]), ucA), lapA);
+                        lapB = fma2(cB, sub2(hi2(xm), ucB), lapB);
+                        lapB = fma2(cB, sub2(hi2(xp), ucB), lapB);
+                        lapB = fma2(cB, sub2(hi2(ym), ucB), lapB);
+                        lapB = fma2(cB, sub2(hi2(yp), ucB), lapB);
+                        lapB = fma2(cB, sub2(f2(win[RZ + 2 - j], win[RZ + 3 - j]), ucB), lapB);
+                        lapB = fma2(cB, sub2(f2(win[RZ + 2 + j], win[RZ + 3 + j]), ucB), lapB);
+                    }
+                    const float ms[4] = {cf1.x, cf1.y, cf1.z, cf1.w};
+                    const float ums[4] = {cum.x, cum.y, cum.z, cum.w};
+                    const float ucs[4] = {uc.x, uc.y, uc.z, uc.w};
+                    const float taps[4] = {lapA.x, lapA.y, lapB.x, lapB.y};
+                    float v[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float am = __fdiv_rn(ms[p], r0[p]);
+                        v[p] = fmaf(1.0f - 2.0f * am, ums[p], fmaf(2.0f * am, ucs[p], taps[p]));
+                        sw[p] = a.dt2 * inv[p];
+                    }
+                    out = make_float4(v[0], v[1], v[2], v[3]);
+                }
+                if (src_mask) {
+#pragma unroll
+                    for (int s = 0; s < kFusedSources; ++s) {
+                        if (((src_mask >> s) & 1u) && a.sx[s] == x) {
+                            const float qv = source_value(a, s);
+                            const int p = src_p[s];
+                            if (p == 0) out.x = fmaf(sw[0], qv, out.x);
+                            if (p == 1) out.y = fmaf(sw[1], qv, out.y);
+                            if (p == 2) out.z = fmaf(sw[2], qv, out.z);
+                            if (p == 3) out.w = fmaf(sw[3], qv, out.w);
+                        }
+                    }
+                }
+                if (z4 + 3 >= a.Nz) {  // row tail: keep the pitch padding zero
+                    if (z4 + 1 >= a.Nz) out.y = 0.f;
+                    if (z4 + 2 >= a.Nz) out.z = 0.f;
+                    if (z4 + 3 >= a.Nz) out.w = 0.f;
+                }
+                up4[x * P4] = out;
+                amax_bits = max(amax_bits, max(max(__float_as_uint(fabsf(out.x)), __float_as_uint(fabsf(out.y))),
+                                               max(__float_as_uint(fabsf(out.z)), __float_as_uint(fabsf(out.w)))));
+            }
+        }
+        if (failed) break;
+    }
+    if (failed) {
+        // record the timeout, let copies still in flight land, then leave
+        if (tid == 0) {
+            if (a.status) atomicOr(a.status, kStatusTimeout);
+            for (int it = 0; it < issued; ++it) mbar_wait_bounded(smem_addr(&bars[it % S]), uint32_t(it / S) & 1u);
+        }
+        return;
+    }
+    if (check) reduce_amax(a, amax_bits, false);
+}
+
+template <int R, int FORM, int LZ, int W>
+cudaError_t tma_launch(const CUtensorMap &map, const StepArgs &a, bool check, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W>;
+    auto kernel = fd_tma_kernel<R, FORM, LZ, W>;
+    static bool attr_set = false;  // per instantiation, set once per process
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY, (a.Nx + a.x_block - 1) / a.x_block);
+    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(map, a, check ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Tile configurations (tile_z, tile_y) of the TMA kernel: (LZ, W) pairs.
+#define FDGB_TMA_CONFIGS(X) X(8, 8) X(16, 8) X(32, 8) X(8, 4) X(16, 4)
+
+template <int R>
+cudaError_t tma_step_r(int form, int tile_z, int tile_y, const CUtensorMap &map, const StepArgs &a,
+                       bool check, cudaStream_t s) {
+#define FDGB_TMA_CASE(LZ, W)                                                                    \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
+        return form == kFactored ? tma_launch<R, kFactored, LZ, W>(map, a, check, s)            \
+                                 : tma_launch<R, kExpanded, LZ, W>(map, a, check, s);
+    FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
+#undef FDGB_TMA_CASE
+    return cudaErrorInvalidValue;
+}
+
+// Box geometry the host needs to encode the tensor map for a configuration.
+template <int R>
+bool tma_box_r(int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
+#define FDGB_TMA_BOX(LZ, W)                                                                     \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                                    \
+        *box_w = TmaShape<R, LZ, W>::SW;                                                        \
+        *box_h = TmaShape<R, LZ, W>::SH;                                                        \
+        *rz = TmaShape<R, LZ, W>::RZ;                                                           \
+        return true;                                                                            \
+    }
+    FDGB_TMA_CONFIGS(FDGB_TMA_BOX)
+#undef FDGB_TMA_BOX
+    return false;
+}
+
+}  // namespace fdgb
+
+#define FDGB_INSTANTIATE_TMA_RADIUS(R)                                                            \
+    namespace fdgb {                                                                              \
+    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const CUtensorMap &map,     \
+                                    const StepArgs &a, bool check, cudaStream_t s) {              \
+        return tma_step_r<R>(form, tile_z, tile_y, map, a, check, s);                             \
+    }                                                                                             \
+    bool tma_box_radius_##R(int tile_z, int tile_y, int *w, int *h, int *rz) {                    \
+        return tma_box_r<R>(tile_z, tile_y, w, h, rz);                                            \
+    }                                                                                             \
+    }

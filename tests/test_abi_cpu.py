@@ -89,5 +89,6 @@ def test_version_and_error_text(built_lib):
 
 def test_options_default(built_lib):
     o = _abi.fd_options_default()
-    assert (o.storage, o.form, o.kernel, o.tile_y, o.x_block, o.check_finite) == (0, 0, 0, 0, 0, 1)
-    assert ctypes.sizeof(o) == 6 * 4
+    assert (o.storage, o.form, o.kernel, o.tile_z, o.tile_y, o.x_block, o.check_finite) == \
+        (0, 0, 0, 0, 0, 0, 1)
+    assert ctypes.sizeof(o) == 7 * 4

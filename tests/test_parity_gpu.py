@@ -49,16 +49,22 @@ def _ragged_spec(k, seed=0):
     return inputs.ShotSpec(interior, nbl, k, vel, (1, 43, 25), 25.0, 60)
 
 
+TMA_TILES = [(32, 32), (64, 16), (128, 8), (32, 16), (64, 8)]
+
+
+@pytest.mark.parametrize("kernel", ["stream", "tma"])
 @pytest.mark.parametrize("form", ["factored", "expanded"])
 @pytest.mark.parametrize("k", [2, 4, 6, 8, 10, 12, 14, 16])
-def test_every_space_order_ragged(oracle_mod, k, form):
+def test_every_space_order_ragged(oracle_mod, k, form, kernel):
     spec = _ragged_spec(k)
     dt = dt_for(spec)
     eta = eta_for(spec)
     want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
-    got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel="stream",
-                                  tile_y=8, x_block=16)
-    report(f"ragged_so{k}_{form}", rel_l2(got, want), rel_l2(got_prev, want_prev))
+    shape = dict(tile_y=8, x_block=16) if kernel == "stream" else \
+        dict(zip(("tile_z", "tile_y"), TMA_TILES[k % 5]), x_block=21)
+    got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel=kernel, **shape)
+    report(f"ragged_so{k}_{form}_{kernel}{shot.config}", rel_l2(got, want),
+           rel_l2(got_prev, want_prev))
     assert rel_l2(got, want) <= TOL
     assert rel_l2(got_prev, want_prev) <= TOL
     shot.close()
@@ -110,15 +116,24 @@ def test_chunked_forward_is_bitwise_identical():
 
 def test_launch_shape_does_not_change_results():
     """Per-point arithmetic order is independent of the tile shape and x-block,
-    so every launch shape gives the same bits."""
+    so every launch shape of a kernel gives the same bits."""
     spec = _ragged_spec(8, seed=6)
     dt = dt_for(spec)
-    ref, _, s0 = run_gpu(spec, 40, dt, tile_y=8, x_block=16)
+    ref, _, s0 = run_gpu(spec, 40, dt, kernel="stream", tile_y=8, x_block=16)
     s0.close()
     for ty, xb in ((4, 7), (16, 49), (8, 3), (4, 100)):
-        got, _, s = run_gpu(spec, 40, dt, tile_y=ty, x_block=xb)
+        got, _, s = run_gpu(spec, 40, dt, kernel="stream", tile_y=ty, x_block=xb)
         np.testing.assert_array_equal(got, ref, err_msg=f"tile_y={ty} x_block={xb}")
         s.close()
+    for form in ("factored", "expanded"):
+        ref, _, s0 = run_gpu(spec, 40, dt, form=form, kernel="tma", tile_z=32, tile_y=32,
+                             x_block=49)
+        s0.close()
+        for (tz, ty), xb in zip(TMA_TILES[1:], (5, 17, 32, 100)):
+            got, _, s = run_gpu(spec, 40, dt, form=form, kernel="tma", tile_z=tz, tile_y=ty,
+                                x_block=xb)
+            np.testing.assert_array_equal(got, ref, err_msg=f"{form} tile {tz}x{ty} x_block={xb}")
+            s.close()
 
 
 def test_load_state_resume_matches_oracle(oracle_mod):
@@ -152,7 +167,7 @@ def test_full_size_sweep_parity(oracle_mod, k):
     state = (u0, u1, 0)
     want, want_prev = run_oracle(oracle_mod, spec, 6, dt, eta, state=state)
     got, got_prev, shot = run_gpu(spec, 6, dt, None, state=state)
-    report(f"full276_so{k}_factored_autotuned{shot.config[:2]}", rel_l2(got, want),
+    report(f"full276_so{k}_factored_autotuned{shot.config}", rel_l2(got, want),
            rel_l2(got_prev, want_prev))
     assert rel_l2(got, want) <= TOL
     assert rel_l2(got_prev, want_prev) <= TOL
