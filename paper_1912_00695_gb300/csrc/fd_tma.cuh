@@ -91,7 +91,9 @@ struct TmaShape {
     static constexpr int SW = TZ + 2 * RZ;  // box width (floats)
     static constexpr int SH = TY + 2 * R;   // box height (rows)
     static constexpr int STAGE = (SW * SH + 31) / 32 * 32;  // floats per stage, 128-byte multiple
-    static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64;
+    // stages + 3 mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
+    // need a 128-byte aligned shared destination)
+    static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64 + 128;
 };
 
 template <int R, int FORM, int LZ, int W>
@@ -102,9 +104,9 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     constexpr int Q = 2 * R + 1;
     constexpr int NWIN = 4 + 2 * RZ;  // z window floats
     constexpr int S = kTmaStages;
-    extern __shared__ __align__(128) float smem[];
-    float *tiles = smem;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * G::STAGE);
+    extern __shared__ __align__(128) float smem_raw[];
+    float *tiles = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + S * G::STAGE);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -180,7 +182,8 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     const int colw = 4 * lz;  // first float of the thread's z window in a tile row
     unsigned amax_bits = 0;
     bool failed = false;
-    int issued = min(S - 1, xe - xb);
+    int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
+    int it_failed = 0;                  // first plane whose wait gave up
 
     for (int xo = xb; xo < xe; xo += Q) {
 #pragma unroll
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
             const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), uint32_t(it / S) & 1u);
             if (__syncthreads_or(!ok)) {
                 failed = true;
+                it_failed = it;
                 break;
             }
             if (tid == 0 && x + S - 1 < xe) {
@@ -314,9 +318,11 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     }
     if (failed) {
         // record the timeout, let copies still in flight land, then leave
+        // planes it_failed .. issued-1 are the only copies not yet waited for (one per stage)
         if (tid == 0) {
             if (a.status) atomicOr(a.status, kStatusTimeout);
-            for (int it = 0; it < issued; ++it) mbar_wait_bounded(smem_addr(&bars[it % S]), uint32_t(it / S) & 1u);
+            for (int it = it_failed; it < issued; ++it)
+                mbar_wait_bounded(smem_addr(&bars[it % S]), uint32_t(it / S) & 1u);
         }
         return;
     }
