@@ -94,24 +94,29 @@ def test_user_damping_everywhere_and_many_sources(oracle_mod):
         srcs.append((node, inputs.ricker(12.0 + i, dt, 40 + 3 * i, amplitude=1.0 + i)))
     want, want_prev = run_oracle(oracle_mod, spec, 50, dt, eta, sources=srcs)
     for form in ("factored", "expanded"):
-        got, got_prev, shot = run_gpu(spec, 50, dt, eta, sources=srcs, form=form, tile_y=4,
-                                      x_block=32)
-        assert rel_l2(got, want) <= TOL, form
-        assert rel_l2(got_prev, want_prev) <= TOL, form
-        shot.close()
+        for kernel, shape in (("stream", dict(tile_y=4, x_block=32)),
+                              ("tma", dict(tile_z=64, tile_y=8, x_block=19)),
+                              ("naive", {})):
+            got, got_prev, shot = run_gpu(spec, 50, dt, eta, sources=srcs, form=form,
+                                          kernel=kernel, **shape)
+            assert rel_l2(got, want) <= TOL, (form, kernel)
+            assert rel_l2(got_prev, want_prev) <= TOL, (form, kernel)
+            shot.close()
 
 
 def test_chunked_forward_is_bitwise_identical():
     spec = _ragged_spec(6, seed=5)
     dt = dt_for(spec)
-    a, ap, s1 = run_gpu(spec, 100, dt, chunks=[100], tile_y=8, x_block=16)
-    b, bp, s2 = run_gpu(spec, 100, dt, chunks=[50, 50], tile_y=8, x_block=16)
-    c, cp, s3 = run_gpu(spec, 100, dt, chunks=[1, 33, 7, 59], tile_y=8, x_block=16)
-    np.testing.assert_array_equal(a, b)
-    np.testing.assert_array_equal(ap, bp)
-    np.testing.assert_array_equal(a, c)
-    for s in (s1, s2, s3):
-        s.close()
+    for kernel, shape in (("stream", dict(tile_y=8, x_block=16)),
+                          ("tma", dict(tile_z=32, tile_y=16, x_block=30))):
+        a, ap, s1 = run_gpu(spec, 100, dt, chunks=[100], kernel=kernel, **shape)
+        b, bp, s2 = run_gpu(spec, 100, dt, chunks=[50, 50], kernel=kernel, **shape)
+        c, cp, s3 = run_gpu(spec, 100, dt, chunks=[1, 33, 7, 59], kernel=kernel, **shape)
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(ap, bp)
+        np.testing.assert_array_equal(a, c)
+        for s in (s1, s2, s3):
+            s.close()
 
 
 def test_launch_shape_does_not_change_results():
@@ -147,11 +152,13 @@ def test_load_state_resume_matches_oracle(oracle_mod):
     u1 = (u0 + 0.05 * rng.standard_normal(spec.shape)).astype(np.float32)
     state = (u0, u1, 7)
     want, want_prev = run_oracle(oracle_mod, spec, 30, dt, eta, state=state)
-    got, got_prev, shot = run_gpu(spec, 30, dt, None, state=state, tile_y=16, x_block=16)
-    assert shot.step == 37
-    assert rel_l2(got, want) <= TOL
-    assert rel_l2(got_prev, want_prev) <= TOL
-    shot.close()
+    for kernel, shape in (("stream", dict(tile_y=16, x_block=16)),
+                          ("tma", dict(tile_z=128, tile_y=8, x_block=16))):
+        got, got_prev, shot = run_gpu(spec, 30, dt, None, state=state, kernel=kernel, **shape)
+        assert shot.step == 37
+        assert rel_l2(got, want) <= TOL, kernel
+        assert rel_l2(got_prev, want_prev) <= TOL, kernel
+        shot.close()
 
 
 @pytest.mark.parametrize("k", [2, 8, 16])
