@@ -106,7 +106,7 @@ struct fd_handle {
     size_t n_pitched = 0;
     fd_options opt{};
     int tile_z = 0, tile_y = 0, x_block = 0, kernel = kStream;
-    CUtensorMap tmaps[2];  // TMA kernel: u^n read through ubuf[0] / ubuf[1]
+    TmaMaps tmaps[2];  // TMA kernel: maps of the step whose u^n is ubuf[0] / ubuf[1]
     void *ubuf[2] = {nullptr, nullptr};
     float *f1 = nullptr, *f2 = nullptr;
     float *d_wavelet = nullptr;
@@ -174,9 +174,10 @@ StepArgs make_args(const fd_handle *hd, long long step, int cur) {
     return a;
 }
 
-// One step with the given launch shape; `map` is the tensor map of a.u (TMA kernel only).
+// One step with the given launch shape; `map` holds the tensor maps of this step
+// (TMA kernel only).
 cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y,
-                          const CUtensorMap *map, bool check, cudaStream_t s) {
+                          const TmaMaps *map, bool check, cudaStream_t s) {
     if (kernel == kNaive) return launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s);
     if (kernel == kTma) return launch_tma_step(hd->r, hd->opt.form, tile_z, tile_y, *map, a, check, s);
     return launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
@@ -184,7 +185,7 @@ cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, in
 
 cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, cudaStream_t s) {
     const bool check = check_enabled(hd);
-    const CUtensorMap *map = a.u == hd->ubuf[0] ? &hd->tmaps[0] : &hd->tmaps[1];
+    const TmaMaps *map = a.u == hd->ubuf[0] ? &hd->tmaps[0] : &hd->tmaps[1];
     cudaError_t e = launch_kernel(hd, a, hd->kernel, hd->tile_z, hd->tile_y, map, check, s);
     if (e != cudaSuccess) return e;
     const int ns = int(hd->sources.size());
@@ -200,26 +201,36 @@ void destroy_graphs(fd_handle *hd) {
     hd->graphs.clear();
 }
 
-int encode_map(const fd_handle *hd, void *base, int tile_z, int tile_y, CUtensorMap *out) {
-    int bw = 0, bh = 0, rz = 0;
-    if (!tma_box(hd->r, tile_z, tile_y, &bw, &bh, &rz)) return fail(FD_ENOTSUP, "no TMA tile %dx%d", tile_z, tile_y);
+int encode_box(const fd_handle *hd, const void *base, int bw, int bh, CUtensorMap *out) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(FD_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[3] = {cuuint64_t(hd->Nz), cuuint64_t(hd->Ny), cuuint64_t(hd->Nx)};
     cuuint64_t strides[2] = {cuuint64_t(hd->pz) * 4, cuuint64_t(hd->plane) * 4};
     cuuint32_t box[3] = {cuuint32_t(bw), cuuint32_t(bh), 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return FD_OK;
 }
 
+// Maps of one step of the TMA kernel with u^n in `u` and u^{n-1} in `up`.
+int make_maps(const fd_handle *hd, const void *u, const void *up, int tile_z, int tile_y, TmaMaps *out) {
+    int bw = 0, bh = 0, rz = 0;
+    if (!tma_box(hd->r, tile_z, tile_y, &bw, &bh, &rz)) return fail(FD_ENOTSUP, "no TMA tile %dx%d", tile_z, tile_y);
+    int rc = encode_box(hd, u, bw, bh, &out->u_halo);
+    if (rc == FD_OK) rc = encode_box(hd, u, tile_z, tile_y, &out->u_pt);
+    if (rc == FD_OK) rc = encode_box(hd, up, tile_z, tile_y, &out->up_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f1, tile_z, tile_y, &out->f1_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f2, tile_z, tile_y, &out->f2_pt);
+    return rc;
+}
+
 int build_maps(fd_handle *hd) {
     if (hd->kernel != kTma) return FD_OK;
     for (int b = 0; b < 2; ++b) {
-        int rc = encode_map(hd, hd->ubuf[b], hd->tile_z, hd->tile_y, &hd->tmaps[b]);
+        int rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], hd->tile_z, hd->tile_y, &hd->tmaps[b]);
         if (rc != FD_OK) return rc;
     }
     return FD_OK;
@@ -311,8 +322,8 @@ int autotune(fd_handle *hd) {
     a.status = check_enabled(hd) ? st : nullptr;
     const bool check = check_enabled(hd);
     for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess && rc == FD_OK; ++ti) {
-        CUtensorMap map;
-        if (kernel == kTma) rc = encode_map(hd, s0, tiles[ti].first, tiles[ti].second, &map);
+        TmaMaps map;
+        if (kernel == kTma) rc = make_maps(hd, s0, s1, tiles[ti].first, tiles[ti].second, &map);
         for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess && rc == FD_OK; ++xi) {
             a.x_block = xbs[xi];
             for (int w = 0; w < 2 && e == cudaSuccess; ++w)

@@ -73,9 +73,20 @@ cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, co
 cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
                               cudaStream_t s);
 int stream_grid_x_chunks(int Nx, int x_block);
+// Tensor maps of one step of the TMA kernel: u^n with the halo box (copied into
+// the shared ring), and the point boxes (tile without halo) of u^n, u^{n-1},
+// w (m) and g (eta), used only for L2 prefetches.
+struct TmaMaps {
+    CUtensorMap u_halo;
+    CUtensorMap u_pt;
+    CUtensorMap up_pt;
+    CUtensorMap f1_pt;
+    CUtensorMap f2_pt;
+};
+
 // TMA-fed FP32 kernel (fd_tma.cuh): tile (tile_z, tile_y) in {(32,32), (64,16), (128,8),
-// (32,16), (64,8)}; `map` describes the u^n buffer with box (box_w, box_h, 1).
-cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const CUtensorMap &map,
+// (32,16), (64,8)}; the halo box of `maps.u_halo` is (box_w, box_h, 1) from tma_box.
+cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const TmaMaps &maps,
                             const StepArgs &a, bool check, cudaStream_t s);
 bool tma_box(int radius, int tile_z, int tile_y, int *box_w, int *box_h, int *rz);
 

@@ -24,7 +24,7 @@ FDGB_DECLARE_RADIUS(8)
 #undef FDGB_DECLARE_RADIUS
 
 #define FDGB_DECLARE_TMA_RADIUS(R)                                                               \
-    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const CUtensorMap &map,    \
+    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const TmaMaps &map,        \
                                     const StepArgs &a, bool check, cudaStream_t s);              \
     bool tma_box_radius_##R(int tile_z, int tile_y, int *w, int *h, int *rz);
 FDGB_DECLARE_TMA_RADIUS(1)
@@ -37,7 +37,7 @@ FDGB_DECLARE_TMA_RADIUS(7)
 FDGB_DECLARE_TMA_RADIUS(8)
 #undef FDGB_DECLARE_TMA_RADIUS
 
-cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const CUtensorMap &map,
+cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const TmaMaps &map,
                             const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {
         case 1: return tma_step_radius_1(form, tile_z, tile_y, map, a, check, s);

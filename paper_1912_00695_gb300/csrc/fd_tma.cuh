@@ -5,16 +5,18 @@
 // Schedule. A CTA of W warps owns a tile of TZ = 4*LZ points along z by
 // TY = (32/LZ)*W points along y and marches x over [x0, x0 + x_block). Each
 // thread owns 4 consecutive z points (one float4) of one y row:
-//  * x taps: a register queue of 2R+1 float4 (u^n at x-R..x+R of the thread's
-//    points); the x loop is unrolled by 2R+1 so the queue rotates by renaming
-//    instead of moving registers;
+//  * x taps: a register queue of float4 (u^n at x-R..x+R of the thread's
+//    points); the x loop is unrolled by U planes and the queue shifts by U once
+//    per U planes (2R/U float4 moves per plane, code size U bodies);
 //  * y and z taps: the current x-plane of u^n with an R-cell halo (z halo
 //    rounded up to a multiple of 4 so every TMA box starts 16-byte aligned),
 //    fetched by one tensor-map bulk copy per plane into a 3-stage shared ring
 //    guarded by mbarriers; out-of-domain boxes are zero-filled by the copy
 //    engine, which is exactly the Dirichlet halo;
 //  * the queue front u^n(x+R) and the point data u^{n-1}, w (m), g (eta) come
-//    as float4 loads one plane ahead; the result is one float4 store;
+//    as float4 loads one plane ahead; D planes further ahead the same boxes are
+//    pulled into L2 by bulk tensor prefetches, so those loads hit L2 instead of
+//    waiting on DRAM; the result is one float4 store;
 //  * the arithmetic runs on float2 pairs (FFMA2/FADD2), two points per
 //    instruction.
 // The per-point arithmetic (association order included) does not depend on
@@ -74,6 +76,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
+
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
@@ -96,12 +107,18 @@ struct TmaShape {
     static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64 + 128;
 };
 
+template <int R>
+struct TmaUnroll {
+    static constexpr int U = R <= 4 ? 4 : 2;
+};
+
 template <int R, int FORM, int LZ, int W>
-__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
                                                         const StepArgs a, int check) {
     using G = TmaShape<R, LZ, W>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
-    constexpr int Q = 2 * R + 1;
+    constexpr int U = TmaUnroll<R>::U;
+    constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window floats
     constexpr int S = kTmaStages;
     extern __shared__ __align__(128) float smem_raw[];
@@ -138,10 +155,23 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     auto issue = [&](int x, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
         mbar_expect_tx(bar, kBoxBytes);
-        tma_load_3d(smem_addr(tiles + stage * G::STAGE), &tmap, bar, z0 - RZ, y0 - R, x);
+        tma_load_3d(smem_addr(tiles + stage * G::STAGE), &maps.u_halo, bar, z0 - RZ, y0 - R, x);
     };
-    if (tid == 0)
+    // the whole y-z tile lies where the damping field vanishes (in y and z)
+    const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
+    auto prefetch = [&](int x) {
+        // point data of plane x and the queue front of plane x + R into L2
+        if (x < xe) {
+            tma_prefetch_3d(&maps.up_pt, z0, y0, x);
+            tma_prefetch_3d(&maps.f1_pt, z0, y0, x);
+            if (!(tile_yz_box && x >= a.bx0 && x < a.bx1)) tma_prefetch_3d(&maps.f2_pt, z0, y0, x);
+        }
+        if (x + R < a.Nx && x + R < xe + R) tma_prefetch_3d(&maps.u_pt, z0, y0, x + R);
+    };
+    if (tid == 0) {
         for (int s = 0; s < S - 1 && xb + s < xe; ++s) issue(xb + s, s);
+        for (int d = 1; d <= kPrefetchAhead; ++d) prefetch(xb + d);
+    }
 
     // sources among this thread's 4 points: bit s set, sub-index in src_p
     unsigned src_mask = 0;
@@ -185,9 +215,9 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
     int it_failed = 0;                  // first plane whose wait gave up
 
-    for (int xo = xb; xo < xe; xo += Q) {
+    for (int xo = xb; xo < xe; xo += U) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = 0; i < U; ++i) {
             const int x = xo + i;
             if (x >= xe) break;
             const int it = x - xb;
@@ -198,12 +228,15 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                 it_failed = it;
                 break;
             }
-            if (tid == 0 && x + S - 1 < xe) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(x + S - 1, (it + S - 1) % S);
-                ++issued;
+            if (tid == 0) {
+                if (x + S - 1 < xe) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(x + S - 1, (it + S - 1) % S);
+                    ++issued;
+                }
+                prefetch(x + 1 + kPrefetchAhead);
             }
-            q[(i + 2 * R) % Q] = nxt;
+            q[2 * R + i] = nxt;
             const float4 cum = pum, cf1 = pf1, cf2 = pf2;
             if (x + 1 < xe) {
                 nxt = load_u(x + 1 + R);
@@ -221,7 +254,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     win[4 * m + 2] = v.z;
                     win[4 * m + 3] = v.w;
                 }
-                const float4 uc = q[(i + R) % Q];
+                const float4 uc = q[R + i];
                 float2 lapA = f2(0.f, 0.f), lapB = f2(0.f, 0.f);
                 float4 out;
                 float sw[4];
@@ -231,7 +264,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     for (int j = 1; j <= R; ++j) {
                         const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
                         const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
-                        const float4 xm = q[(i + R - j) % Q], xp = q[(i + R + j) % Q];
+                        const float4 xm = q[R + i - j], xp = q[R + i + j];
                         float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
                                          add2(f2(win[RZ - j], win[RZ + 1 - j]), f2(win[RZ + j], win[RZ + 1 + j])));
                         float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym), hi2(yp))),
@@ -263,7 +296,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     for (int j = 1; j <= R; ++j) {
                         const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
                         const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
-                        const float4 xm = q[(i + R - j) % Q], xp = q[(i + R + j) % Q];
+                        const float4 xm = q[R + i - j], xp = q[R + i + j];
                         const float2 cA = mul2(cz2[j], invA), cB = mul2(cz2[j], invB);
                         lapA = fma2(cA, sub2(lo2(xm), ucA), lapA);
                         lapA = fma2(cA, sub2(lo2(xp), ucA), lapA);
@@ -315,6 +348,8 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
             }
         }
         if (failed) break;
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) q[k] = q[k + U];
     }
     if (failed) {
         // record the timeout, let copies still in flight land, then leave
@@ -330,7 +365,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
 }
 
 template <int R, int FORM, int LZ, int W>
-cudaError_t tma_launch(const CUtensorMap &map, const StepArgs &a, bool check, cudaStream_t s) {
+cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s) {
     using G = TmaShape<R, LZ, W>;
     auto kernel = fd_tma_kernel<R, FORM, LZ, W>;
     static bool attr_set = false;  // per instantiation, set once per process
@@ -340,7 +375,7 @@ cudaError_t tma_launch(const CUtensorMap &map, const StepArgs &a, bool check, cu
         attr_set = true;
     }
     const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY, (a.Nx + a.x_block - 1) / a.x_block);
-    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(map, a, check ? 1 : 0);
+    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(maps, a, check ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -348,7 +383,7 @@ cudaError_t tma_launch(const CUtensorMap &map, const StepArgs &a, bool check, cu
 #define FDGB_TMA_CONFIGS(X) X(8, 8) X(16, 8) X(32, 8) X(8, 4) X(16, 4)
 
 template <int R>
-cudaError_t tma_step_r(int form, int tile_z, int tile_y, const CUtensorMap &map, const StepArgs &a,
+cudaError_t tma_step_r(int form, int tile_z, int tile_y, const TmaMaps &map, const StepArgs &a,
                        bool check, cudaStream_t s) {
 #define FDGB_TMA_CASE(LZ, W)                                                                    \
     if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
@@ -378,7 +413,7 @@ bool tma_box_r(int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
 
 #define FDGB_INSTANTIATE_TMA_RADIUS(R)                                                            \
     namespace fdgb {                                                                              \
-    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const CUtensorMap &map,     \
+    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const TmaMaps &map,         \
                                     const StepArgs &a, bool check, cudaStream_t s) {              \
         return tma_step_r<R>(form, tile_z, tile_y, map, a, check, s);                             \
     }                                                                                             \
