@@ -107,17 +107,29 @@ struct TmaShape {
     static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64 + 128;
 };
 
-template <int R>
+template <int R, int FORM>
 struct TmaUnroll {
-    static constexpr int U = R <= 4 ? 4 : 2;
+    static constexpr int U = FORM == kFactored ? 4 : 2;
 };
+
+// Sum of the two z taps at distance j of the pair of points (p, p+1) whose
+// window index is W0 = RZ + p: (win[W0-j] + win[W0+j], win[W0+1-j] + win[W0+1+j]).
+// When W0 - j is even both operand pairs are aligned register pairs and one
+// paired add does it; otherwise two scalar adds write an aligned result pair
+// directly (cheaper than re-pairing misaligned operands).
+template <int W0>
+__device__ __forceinline__ float2 ztap_pair(const float *win, int j) {
+    if (((W0 - j) & 1) == 0)
+        return __fadd2_rn(make_float2(win[W0 - j], win[W0 + 1 - j]), make_float2(win[W0 + j], win[W0 + 1 + j]));
+    return make_float2(win[W0 - j] + win[W0 + j], win[W0 + 1 - j] + win[W0 + 1 + j]);
+}
 
 template <int R, int FORM, int LZ, int W>
 __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
                                                         const StepArgs a, int check) {
     using G = TmaShape<R, LZ, W>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
-    constexpr int U = TmaUnroll<R>::U;
+    constexpr int U = TmaUnroll<R, FORM>::U;
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window floats
     constexpr int S = kTmaStages;
@@ -259,26 +271,29 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                 float4 out;
                 float sw[4];
                 if constexpr (FORM == kFactored) {
-                    const float2 sixA = mul2(f2(6.f, 6.f), lo2(uc)), sixB = mul2(f2(6.f, 6.f), hi2(uc));
+                    // -6 u_c is added to each distance-j sum: exact zero for a constant field
+                    const float2 nsixA = mul2(f2(-6.f, -6.f), lo2(uc)), nsixB = mul2(f2(-6.f, -6.f), hi2(uc));
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
                         const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
                         const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
                         const float4 xm = q[R + i - j], xp = q[R + i + j];
-                        float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
-                                         add2(f2(win[RZ - j], win[RZ + 1 - j]), f2(win[RZ + j], win[RZ + 1 + j])));
-                        float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym), hi2(yp))),
-                                         add2(f2(win[RZ + 2 - j], win[RZ + 3 - j]), f2(win[RZ + 2 + j], win[RZ + 3 + j])));
-                        lapA = fma2(cz2[j], sub2(sA, sixA), lapA);
-                        lapB = fma2(cz2[j], sub2(sB, sixB), lapB);
+                        const float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
+                                               ztap_pair<RZ>(win, j));
+                        const float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym), hi2(yp))),
+                                               ztap_pair<RZ + 2>(win, j));
+                        lapA = fma2(cz2[j], add2(sA, nsixA), lapA);
+                        lapB = fma2(cz2[j], add2(sB, nsixB), lapB);
                     }
-                    // u+ = w L + 2u - u- - 2 g (u - u-)
-                    const float2 wA = lo2(cf1), wB = hi2(cf1), gA = lo2(cf2), gB = hi2(cf2);
+                    // u+ = w L + (2u - u-) - 2 g (u - u-)
+                    const float2 wA = lo2(cf1), wB = hi2(cf1);
                     const float2 umA = lo2(cum), umB = hi2(cum);
-                    float2 vA = fma2(wA, lapA, fma2(f2(2.f, 2.f), lo2(uc), f2(-umA.x, -umA.y)));
-                    float2 vB = fma2(wB, lapB, fma2(f2(2.f, 2.f), hi2(uc), f2(-umB.x, -umB.y)));
-                    vA = fma2(mul2(f2(-2.f, -2.f), gA), sub2(lo2(uc), umA), vA);
-                    vB = fma2(mul2(f2(-2.f, -2.f), gB), sub2(hi2(uc), umB), vB);
+                    const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2)), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2));
+                    const float2 dA = fma2(f2(-1.f, -1.f), umA, lo2(uc)), dB = fma2(f2(-1.f, -1.f), umB, hi2(uc));
+                    float2 vA = fma2(wA, lapA, add2(lo2(uc), dA));
+                    float2 vB = fma2(wB, lapB, add2(hi2(uc), dB));
+                    vA = fma2(m2gA, dA, vA);
+                    vB = fma2(m2gB, dB, vB);
                     out = make_float4(vA.x, vA.y, vB.x, vB.y);
                     sw[0] = cf1.x;
                     sw[1] = cf1.y;
