@@ -29,7 +29,13 @@
 
 namespace fdgb {
 
-constexpr int kTmaStages = 3;
+// Ring depth and register prefetch distance: short stencils have short compute
+// phases per plane, so they keep more planes in flight.
+template <int R>
+struct TmaPipe {
+    static constexpr int STAGES = R <= 4 ? 5 : 3;  // shared ring of halo tiles
+    static constexpr int PD = R <= 2 ? 2 : 1;       // planes of point data held in registers ahead
+};
 constexpr long long kMbarWaitLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -102,9 +108,9 @@ struct TmaShape {
     static constexpr int SW = TZ + 2 * RZ;  // box width (floats)
     static constexpr int SH = TY + 2 * R;   // box height (rows)
     static constexpr int STAGE = (SW * SH + 31) / 32 * 32;  // floats per stage, 128-byte multiple
-    // stages + 3 mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
+    // stages + their mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
     // need a 128-byte aligned shared destination)
-    static constexpr int SMEM_BYTES = kTmaStages * STAGE * 4 + 64 + 128;
+    static constexpr int SMEM_BYTES = TmaPipe<R>::STAGES * STAGE * 4 + 64 + 128;
 };
 
 template <int R, int FORM>
@@ -132,7 +138,9 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     constexpr int U = TmaUnroll<R, FORM>::U;
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window floats
-    constexpr int S = kTmaStages;
+    constexpr int S = TmaPipe<R>::STAGES;
+    constexpr int PD = TmaPipe<R>::PD;
+    static_assert(TmaUnroll<R, FORM>::U % PD == 0, "prefetch slots rotate within an unrolled block");
     extern __shared__ __align__(128) float smem_raw[];
     float *tiles = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + S * G::STAGE);
@@ -205,17 +213,22 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     float4 q[Q];
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
-    float4 nxt = load_u(xb + R);
-    float4 pum = zero4, pf1 = zero4, pf2 = zero4;
-    auto load_point = [&](int x) {
-        if (own) {
-            pum = up4[x * P4];
-            pf1 = __ldg(f1 + x * P4);
+    // register prefetch slots: slot (x - xb) % PD holds plane x's front u^n(x+R) and point data
+    float4 nxt[PD], pum[PD], pf1[PD], pf2[PD];
+    auto load_point = [&](int x, int slot) {
+        nxt[slot] = load_u(x + R);
+        pum[slot] = zero4;
+        pf1[slot] = zero4;
+        pf2[slot] = zero4;
+        if (own && x < xe) {
+            pum[slot] = up4[x * P4];
+            pf1[slot] = __ldg(f1 + x * P4);
             const bool in_box = yz_box && x >= a.bx0 && x < a.bx1;
-            pf2 = in_box ? zero4 : __ldg(f2p + x * P4);
+            if (!in_box) pf2[slot] = __ldg(f2p + x * P4);
         }
     };
-    load_point(xb);
+#pragma unroll
+    for (int d = 0; d < PD; ++d) load_point(xb + d, d);
 
     float2 cz2[R + 1];
 #pragma unroll
@@ -248,12 +261,10 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                 }
                 prefetch(x + 1 + kPrefetchAhead);
             }
-            q[2 * R + i] = nxt;
-            const float4 cum = pum, cf1 = pf1, cf2 = pf2;
-            if (x + 1 < xe) {
-                nxt = load_u(x + 1 + R);
-                load_point(x + 1);
-            }
+            const int slot = i % PD;  // (x - xb) % PD, since xo - xb is a multiple of U
+            q[2 * R + i] = nxt[slot];
+            const float4 cum = pum[slot], cf1 = pf1[slot], cf2 = pf2[slot];
+            if (x + PD < xe) load_point(x + PD, slot);
             if (own) {
                 const float *t = tiles + stage * G::STAGE;
                 const float *rowp = t + rowc * SW + colw;
