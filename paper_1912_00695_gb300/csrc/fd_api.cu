@@ -265,8 +265,10 @@ int autotune(fd_handle *hd) {
     if (force_xb) {
         xbs.push_back(hd->opt.x_block);
     } else {
-        for (int xb : {16, 32, 64, 128})
-            if (xb < hd->Nx && (kernel != kTma || xb >= 32)) xbs.push_back(xb);
+        const std::vector<int> cand = kernel == kTma ? std::vector<int>{12, 16, 24, 32, 48, 64, 128}
+                                                     : std::vector<int>{16, 32, 64, 128};
+        for (int xb : cand)
+            if (xb < hd->Nx) xbs.push_back(xb);
         xbs.push_back(hd->Nx);
     }
     if (tiles.size() == 1 && xbs.size() == 1) {
