@@ -68,21 +68,24 @@ extern "C" {
                                by (m + dt/2 eta) per point, as Listing 2 is written */
 
 /* Kernel schedule. */
-#define FD_KERNEL_AUTO 0    /* TMA kernel for FP32 storage, streaming kernel for 16-bit,
-                               launch shape chosen by the autotuner */
+#define FD_KERNEL_AUTO 0    /* TMA kernel where it has the storage/form (FP32: both forms;
+                               16-bit: factored), else the streaming kernel; launch shape
+                               chosen by the autotuner */
 #define FD_KERNEL_STREAM 1  /* 2.5D streaming kernel, one point per thread (x-march, y-z tile
                                staged through registers into shared memory); all storages */
 #define FD_KERNEL_NAIVE 2   /* one thread per point, all taps from global memory */
 #define FD_KERNEL_TMA 3     /* 2.5D streaming kernel, four z points per thread, y-z tile with
-                               halo fetched by tensor-map bulk copies; FP32 storage only */
+                               halo fetched by tensor-map bulk copies; FP32 storage (both
+                               forms) and 16-bit storage (factored form) */
 
 typedef struct fd_options {
     int storage;       /* FD_STORAGE_*                                             */
     int form;          /* FD_FORM_*                                                */
     int kernel;        /* FD_KERNEL_*                                              */
     int tile_z;        /* tile width along z: STREAM 32; TMA 32, 64 or 128; 0 = autotune */
-    int tile_y;        /* tile rows along y: STREAM 4, 8, 16; TMA with tile_z 32: 16 or 32,
-                          64: 8 or 16, 128: 8; 0 = autotune                             */
+    int tile_y;        /* tile rows along y: STREAM 4, 8, 16; TMA (FP32) with tile_z 32:
+                          16 or 32, 64: 8 or 16, 128: 8; TMA (16-bit) 32x16 or 64x8;
+                          0 = autotune                                              */
     int x_block;       /* planes per CTA along x; 0 = autotune                     */
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
                           fd_read_wavefield/fd_status report FD_ENONFINITE          */
@@ -108,7 +111,8 @@ int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double
 
 /* As fd_acoustic_create with explicit options (opt == NULL: defaults).
  * FD_ENOTSUP for an unknown storage/form/kernel value, FD_KERNEL_TMA with
- * 16-bit storage, or a (tile_z, tile_y) pair the chosen kernel does not have. */
+ * 16-bit storage and the expanded form, or a (tile_z, tile_y) pair the chosen
+ * kernel does not have. */
 int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                           const fd_options *opt, fd_handle **out);
 

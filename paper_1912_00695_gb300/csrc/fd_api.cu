@@ -79,14 +79,19 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Valid (tile_z, tile_y) pairs of each kernel.
-bool tile_ok(int kernel, int tz, int ty) {
+// (tile_z, tile_y) shapes the TMA kernel has for a storage/form.
+std::vector<std::pair<int, int>> tma_tiles(int storage, int form) {
+    if (storage == kF32) return {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
+    if (form == kFactored) return {{32, 16}, {64, 8}};
+    return {};
+}
+
+// Valid (tile_z, tile_y) requests of each kernel (0 = any).
+bool tile_ok(int kernel, int storage, int form, int tz, int ty) {
     if (kernel == kStream) return (tz == 0 || tz == 32) && (ty == 0 || ty == 4 || ty == 8 || ty == 16);
     if (kernel == kTma) {
-        if (tz == 0 && ty == 0) return true;
-        const int pairs[5][2] = {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
-        for (auto &p : pairs)
-            if ((tz == 0 || tz == p[0]) && (ty == 0 || ty == p[1])) return true;
+        for (auto &p : tma_tiles(storage, form))
+            if ((tz == 0 || tz == p.first) && (ty == 0 || ty == p.second)) return true;
         return false;
     }
     return true;
@@ -179,7 +184,8 @@ StepArgs make_args(const fd_handle *hd, long long step, int cur) {
 cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y,
                           const TmaMaps *map, bool check, cudaStream_t s) {
     if (kernel == kNaive) return launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s);
-    if (kernel == kTma) return launch_tma_step(hd->r, hd->opt.form, tile_z, tile_y, *map, a, check, s);
+    if (kernel == kTma)
+        return launch_tma_step(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, *map, a, check, s);
     return launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
 }
 
@@ -201,16 +207,16 @@ void destroy_graphs(fd_handle *hd) {
     hd->graphs.clear();
 }
 
-int encode_box(const fd_handle *hd, const void *base, int bw, int bh, CUtensorMap *out) {
+int encode_box(const fd_handle *hd, const void *base, CUtensorMapDataType dtype, int esize, int bw, int bh,
+               CUtensorMap *out) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(FD_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[3] = {cuuint64_t(hd->Nz), cuuint64_t(hd->Ny), cuuint64_t(hd->Nx)};
-    cuuint64_t strides[2] = {cuuint64_t(hd->pz) * 4, cuuint64_t(hd->plane) * 4};
+    cuuint64_t strides[2] = {cuuint64_t(hd->pz) * esize, cuuint64_t(hd->plane) * esize};
     cuuint32_t box[3] = {cuuint32_t(bw), cuuint32_t(bh), 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(out, dtype, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return FD_OK;
 }
@@ -218,12 +224,17 @@ int encode_box(const fd_handle *hd, const void *base, int bw, int bh, CUtensorMa
 // Maps of one step of the TMA kernel with u^n in `u` and u^{n-1} in `up`.
 int make_maps(const fd_handle *hd, const void *u, const void *up, int tile_z, int tile_y, TmaMaps *out) {
     int bw = 0, bh = 0, rz = 0;
-    if (!tma_box(hd->r, tile_z, tile_y, &bw, &bh, &rz)) return fail(FD_ENOTSUP, "no TMA tile %dx%d", tile_z, tile_y);
-    int rc = encode_box(hd, u, bw, bh, &out->u_halo);
-    if (rc == FD_OK) rc = encode_box(hd, u, tile_z, tile_y, &out->u_pt);
-    if (rc == FD_OK) rc = encode_box(hd, up, tile_z, tile_y, &out->up_pt);
-    if (rc == FD_OK) rc = encode_box(hd, hd->f1, tile_z, tile_y, &out->f1_pt);
-    if (rc == FD_OK) rc = encode_box(hd, hd->f2, tile_z, tile_y, &out->f2_pt);
+    if (!tma_box(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, &bw, &bh, &rz))
+        return fail(FD_ENOTSUP, "no TMA tile %dx%d for this storage/form", tile_z, tile_y);
+    const int es = int(elem_size(hd->opt.storage));
+    const CUtensorMapDataType ut = hd->opt.storage == kF32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : hd->opt.storage == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    int rc = encode_box(hd, u, ut, es, bw, bh, &out->u_halo);
+    if (rc == FD_OK) rc = encode_box(hd, u, ut, es, tile_z, tile_y, &out->u_pt);
+    if (rc == FD_OK) rc = encode_box(hd, up, ut, es, tile_z, tile_y, &out->up_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tile_z, tile_y, &out->f1_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tile_z, tile_y, &out->f2_pt);
     return rc;
 }
 
@@ -252,10 +263,9 @@ int autotune(fd_handle *hd) {
     const bool force_tile = hd->opt.tile_z > 0 || hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
     std::vector<std::pair<int, int>> tiles;
     if (kernel == kTma) {
-        const int pairs[5][2] = {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
-        for (auto &p : pairs)
-            if ((hd->opt.tile_z == 0 || hd->opt.tile_z == p[0]) && (hd->opt.tile_y == 0 || hd->opt.tile_y == p[1]))
-                tiles.push_back({p[0], p[1]});
+        for (auto &p : tma_tiles(hd->opt.storage, hd->opt.form))
+            if ((hd->opt.tile_z == 0 || hd->opt.tile_z == p.first) && (hd->opt.tile_y == 0 || hd->opt.tile_y == p.second))
+                tiles.push_back(p);
     } else {
         for (int ty : {4, 8, 16})
             if (hd->opt.tile_y == 0 || hd->opt.tile_y == ty) tiles.push_back({32, ty});
@@ -549,9 +559,10 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         opt.kernel > 3)
         return fail(FD_ENOTSUP, "unknown storage/form/kernel option");
     int kernel = opt.kernel;
-    if (kernel == kAuto) kernel = opt.storage == kF32 ? kTma : kStream;
-    if (kernel == kTma && opt.storage != kF32) return fail(FD_ENOTSUP, "the TMA kernel stores FP32 only");
-    if (!tile_ok(kernel, opt.tile_z, opt.tile_y))
+    if (kernel == kAuto) kernel = tma_tiles(opt.storage, opt.form).empty() ? kStream : kTma;
+    if (kernel == kTma && tma_tiles(opt.storage, opt.form).empty())
+        return fail(FD_ENOTSUP, "the TMA kernel has no expanded form for 16-bit storage");
+    if (!tile_ok(kernel, opt.storage, opt.form, opt.tile_z, opt.tile_y))
         return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
 

@@ -84,11 +84,14 @@ struct TmaMaps {
     CUtensorMap f2_pt;
 };
 
-// TMA-fed FP32 kernel (fd_tma.cuh): tile (tile_z, tile_y) in {(32,32), (64,16), (128,8),
-// (32,16), (64,8)}; the halo box of `maps.u_halo` is (box_w, box_h, 1) from tma_box.
-cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const TmaMaps &maps,
-                            const StepArgs &a, bool check, cudaStream_t s);
-bool tma_box(int radius, int tile_z, int tile_y, int *box_w, int *box_h, int *rz);
+// TMA-fed kernel (fd_tma.cuh): FP32 storage in tiles (tile_z, tile_y) of {(32,32), (64,16),
+// (128,8), (32,16), (64,8)} and both forms; 16-bit storage in (32,16) and (64,8), factored
+// form. The halo box of `maps.u_halo` is (box_w, box_h, 1) from tma_box (false: no such
+// configuration).
+cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+                            const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s);
+bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *box_w, int *box_h,
+             int *rz);
 
 // Utility kernels (fd_kernels_util.cu)
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,

@@ -24,9 +24,10 @@ FDGB_DECLARE_RADIUS(8)
 #undef FDGB_DECLARE_RADIUS
 
 #define FDGB_DECLARE_TMA_RADIUS(R)                                                               \
-    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const TmaMaps &map,        \
-                                    const StepArgs &a, bool check, cudaStream_t s);              \
-    bool tma_box_radius_##R(int tile_z, int tile_y, int *w, int *h, int *rz);
+    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y,               \
+                                    const TmaMaps &map, const StepArgs &a, bool check,           \
+                                    cudaStream_t s);                                             \
+    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int *w, int *h, int *rz);
 FDGB_DECLARE_TMA_RADIUS(1)
 FDGB_DECLARE_TMA_RADIUS(2)
 FDGB_DECLARE_TMA_RADIUS(3)
@@ -37,66 +38,28 @@ FDGB_DECLARE_TMA_RADIUS(7)
 FDGB_DECLARE_TMA_RADIUS(8)
 #undef FDGB_DECLARE_TMA_RADIUS
 
-cudaError_t launch_tma_step(int radius, int form, int tile_z, int tile_y, const TmaMaps &map,
-                            const StepArgs &a, bool check, cudaStream_t s) {
+cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+                            const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {
-        case 1: return tma_step_radius_1(form, tile_z, tile_y, map, a, check, s);
-        case 2: return tma_step_radius_2(form, tile_z, tile_y, map, a, check, s);
-        case 3: return tma_step_radius_3(form, tile_z, tile_y, map, a, check, s);
-        case 4: return tma_step_radius_4(form, tile_z, tile_y, map, a, check, s);
-        case 5: return tma_step_radius_5(form, tile_z, tile_y, map, a, check, s);
-        case 6: return tma_step_radius_6(form, tile_z, tile_y, map, a, check, s);
-        case 7: return tma_step_radius_7(form, tile_z, tile_y, map, a, check, s);
-        case 8: return tma_step_radius_8(form, tile_z, tile_y, map, a, check, s);
+#define FDGB_TMA_R(R) \
+        case R: return tma_step_radius_##R(form, storage, tile_z, tile_y, map, a, check, s);
+        FDGB_TMA_R(1) FDGB_TMA_R(2) FDGB_TMA_R(3) FDGB_TMA_R(4)
+        FDGB_TMA_R(5) FDGB_TMA_R(6) FDGB_TMA_R(7) FDGB_TMA_R(8)
+#undef FDGB_TMA_R
         default: return cudaErrorInvalidValue;
     }
 }
 
-bool tma_box(int radius, int tile_z, int tile_y, int *w, int *h, int *rz) {
+bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *w, int *h, int *rz) {
     switch (radius) {
-        case 1: return tma_box_radius_1(tile_z, tile_y, w, h, rz);
-        case 2: return tma_box_radius_2(tile_z, tile_y, w, h, rz);
-        case 3: return tma_box_radius_3(tile_z, tile_y, w, h, rz);
-        case 4: return tma_box_radius_4(tile_z, tile_y, w, h, rz);
-        case 5: return tma_box_radius_5(tile_z, tile_y, w, h, rz);
-        case 6: return tma_box_radius_6(tile_z, tile_y, w, h, rz);
-        case 7: return tma_box_radius_7(tile_z, tile_y, w, h, rz);
-        case 8: return tma_box_radius_8(tile_z, tile_y, w, h, rz);
+#define FDGB_TMA_B(R) \
+        case R: return tma_box_radius_##R(form, storage, tile_z, tile_y, w, h, rz);
+        FDGB_TMA_B(1) FDGB_TMA_B(2) FDGB_TMA_B(3) FDGB_TMA_B(4)
+        FDGB_TMA_B(5) FDGB_TMA_B(6) FDGB_TMA_B(7) FDGB_TMA_B(8)
+#undef FDGB_TMA_B
         default: return false;
     }
 }
-
-cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
-                               bool check, cudaStream_t s) {
-    switch (radius) {
-        case 1: return stream_step_radius_1(form, storage, tile_y, a, check, s);
-        case 2: return stream_step_radius_2(form, storage, tile_y, a, check, s);
-        case 3: return stream_step_radius_3(form, storage, tile_y, a, check, s);
-        case 4: return stream_step_radius_4(form, storage, tile_y, a, check, s);
-        case 5: return stream_step_radius_5(form, storage, tile_y, a, check, s);
-        case 6: return stream_step_radius_6(form, storage, tile_y, a, check, s);
-        case 7: return stream_step_radius_7(form, storage, tile_y, a, check, s);
-        case 8: return stream_step_radius_8(form, storage, tile_y, a, check, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
-                              cudaStream_t s) {
-    switch (radius) {
-        case 1: return naive_step_radius_1(form, storage, a, check, s);
-        case 2: return naive_step_radius_2(form, storage, a, check, s);
-        case 3: return naive_step_radius_3(form, storage, a, check, s);
-        case 4: return naive_step_radius_4(form, storage, a, check, s);
-        case 5: return naive_step_radius_5(form, storage, a, check, s);
-        case 6: return naive_step_radius_6(form, storage, a, check, s);
-        case 7: return naive_step_radius_7(form, storage, a, check, s);
-        case 8: return naive_step_radius_8(form, storage, a, check, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int stream_grid_x_chunks(int Nx, int x_block) { return (Nx + x_block - 1) / x_block; }
 
 namespace {
 

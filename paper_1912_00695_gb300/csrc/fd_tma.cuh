@@ -1,24 +1,27 @@
-// TMA-fed streaming step kernel (FP32 storage), templated on the stencil
-// radius R, the symbolic form and the tile shape. Included by the per-radius
-// translation units after fd_stencil.cuh.
+// TMA-fed streaming step kernel, templated on the stencil radius R, the
+// symbolic form, the tile shape and the wavefield storage type T (float,
+// bfloat16, half). Included by the per-radius translation units after
+// fd_stencil.cuh.
 //
 // Schedule. A CTA of W warps owns a tile of TZ = 4*LZ points along z by
 // TY = (32/LZ)*W points along y and marches x over [x0, x0 + x_block). Each
-// thread owns 4 consecutive z points (one float4) of one y row:
-//  * x taps: a register queue of float4 (u^n at x-R..x+R of the thread's
-//    points); the x loop is unrolled by U planes and the queue shifts by U once
-//    per U planes (2R/U float4 moves per plane, code size U bodies);
+// thread owns 4 consecutive z points of one y row:
+//  * x taps: a register queue of 4-point vectors (u^n at x-R..x+R of the
+//    thread's points); the x loop is unrolled by U planes and the queue shifts
+//    by U once per U planes (2R/U vector moves per plane, code size U bodies);
 //  * y and z taps: the current x-plane of u^n with an R-cell halo (z halo
-//    rounded up to a multiple of 4 so every TMA box starts 16-byte aligned),
-//    fetched by one tensor-map bulk copy per plane into a 3-stage shared ring
-//    guarded by mbarriers; out-of-domain boxes are zero-filled by the copy
-//    engine, which is exactly the Dirichlet halo;
+//    rounded up so every TMA box starts 16-byte aligned), fetched by one
+//    tensor-map bulk copy per plane into a shared ring guarded by mbarriers;
+//    out-of-domain boxes are zero-filled by the copy engine, which is exactly
+//    the Dirichlet halo;
 //  * the queue front u^n(x+R) and the point data u^{n-1}, w (m), g (eta) come
-//    as float4 loads one plane ahead; D planes further ahead the same boxes are
-//    pulled into L2 by bulk tensor prefetches, so those loads hit L2 instead of
-//    waiting on DRAM; the result is one float4 store;
-//  * the arithmetic runs on float2 pairs (FFMA2/FADD2), two points per
-//    instruction.
+//    as vector loads one plane ahead; further ahead the same boxes are pulled
+//    into L2 by bulk tensor prefetches, so those loads hit L2 instead of
+//    waiting on DRAM; the result is one vector store;
+//  * the arithmetic runs in FP32 on float2 pairs (FFMA2/FADD2), two points per
+//    instruction; 16-bit storage is converted on load and scaled by the
+//    level's power-of-two scale (the Laplacian is linear, so it is computed on
+//    the raw values and scaled once).
 // The per-point arithmetic (association order included) does not depend on
 // the tile shape or x_block.
 #pragma once
@@ -37,6 +40,7 @@ struct TmaPipe {
     static constexpr int PD = R <= 2 ? 2 : 1;       // planes of point data held in registers ahead
 };
 constexpr long long kMbarWaitLimit = 1LL << 22;
+constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -89,8 +93,6 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, 
                  : "memory");
 }
 
-constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
-
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
@@ -99,18 +101,56 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-template <int R, int LZ, int W>
+// Four consecutive stored values <-> float4 (raw, unscaled).
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static constexpr CUtensorMapDataType kMapType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    static __device__ __forceinline__ float4 ldg(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    static __device__ __forceinline__ float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    static __device__ __forceinline__ void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+};
+template <typename H, typename H2> struct Vec4Half {
+    static __device__ __forceinline__ float2 to2(H2 v);
+    static __device__ __forceinline__ H2 from2(float2 v);
+    static __device__ __forceinline__ float4 cvt(uint2 r) {
+        const float2 a = to2(*reinterpret_cast<const H2 *>(&r.x)), b = to2(*reinterpret_cast<const H2 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 ldg(const H *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
+    static __device__ __forceinline__ float4 ld(const H *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
+    static __device__ __forceinline__ void st(H *p, float4 v) {
+        uint2 r;
+        *reinterpret_cast<H2 *>(&r.x) = from2(make_float2(v.x, v.y));
+        *reinterpret_cast<H2 *>(&r.y) = from2(make_float2(v.z, v.w));
+        *reinterpret_cast<uint2 *>(p) = r;
+    }
+};
+template <> __device__ __forceinline__ float2 Vec4Half<__nv_bfloat16, __nv_bfloat162>::to2(__nv_bfloat162 v) {
+    return __bfloat1622float2(v);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 Vec4Half<__nv_bfloat16, __nv_bfloat162>::from2(float2 v) {
+    return __float22bfloat162_rn(v);
+}
+template <> __device__ __forceinline__ float2 Vec4Half<__half, __half2>::to2(__half2 v) { return __half22float2(v); }
+template <> __device__ __forceinline__ __half2 Vec4Half<__half, __half2>::from2(float2 v) {
+    return __float22half2_rn(v);
+}
+template <> struct Vec4<__nv_bfloat16> : Vec4Half<__nv_bfloat16, __nv_bfloat162> {};
+template <> struct Vec4<__half> : Vec4Half<__half, __half2> {};
+
+template <int R, int LZ, int W, typename T>
 struct TmaShape {
-    static constexpr int RZ = (R + 3) / 4 * 4;  // z halo, multiple of 4 (16-byte aligned boxes)
+    static constexpr int VE = 16 / int(sizeof(T));         // elements per 16 bytes
+    static constexpr int RZ = (R + VE - 1) / VE * VE;       // z halo: boxes start 16-byte aligned
     static constexpr int LY = 32 / LZ;
     static constexpr int TZ = 4 * LZ;
     static constexpr int TY = LY * W;
-    static constexpr int SW = TZ + 2 * RZ;  // box width (floats)
+    static constexpr int SW = TZ + 2 * RZ;  // box width (elements)
     static constexpr int SH = TY + 2 * R;   // box height (rows)
-    static constexpr int STAGE = (SW * SH + 31) / 32 * 32;  // floats per stage, 128-byte multiple
+    static constexpr int STAGE_BYTES = (SW * SH * int(sizeof(T)) + 127) / 128 * 128;
     // stages + their mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
     // need a 128-byte aligned shared destination)
-    static constexpr int SMEM_BYTES = TmaPipe<R>::STAGES * STAGE * 4 + 64 + 128;
+    static constexpr int SMEM_BYTES = TmaPipe<R>::STAGES * STAGE_BYTES + 64 + 128;
 };
 
 template <int R, int FORM>
@@ -130,40 +170,43 @@ __device__ __forceinline__ float2 ztap_pair(const float *win, int j) {
     return make_float2(win[W0 - j] + win[W0 + j], win[W0 + 1 - j] + win[W0 + 1 + j]);
 }
 
-template <int R, int FORM, int LZ, int W>
-__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
-                                                        const StepArgs a, int check) {
-    using G = TmaShape<R, LZ, W>;
+// The work of one CTA: tile (bz, by) of the y-z plane, x-chunk bx, of the shot
+// described by `a` and `maps`. `smem_raw` is the CTA's dynamic shared memory.
+template <int R, int FORM, int LZ, int W, typename T>
+__device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, int check, int bz, int by,
+                                        int bx, unsigned char *smem_raw) {
+    using G = TmaShape<R, LZ, W, T>;
+    using V = Vec4<T>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
     constexpr int U = TmaUnroll<R, FORM>::U;
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
-    constexpr int NWIN = 4 + 2 * RZ;  // z window floats
+    constexpr int NWIN = 4 + 2 * RZ;  // z window values
     constexpr int S = TmaPipe<R>::STAGES;
     constexpr int PD = TmaPipe<R>::PD;
-    static_assert(TmaUnroll<R, FORM>::U % PD == 0, "prefetch slots rotate within an unrolled block");
-    extern __shared__ __align__(128) float smem_raw[];
-    float *tiles = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tiles + S * G::STAGE);
+    static_assert(U % PD == 0, "prefetch slots rotate within an unrolled block");
+    unsigned char *ring = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int lz = lane % LZ, ly = lane / LZ;
-    const int z0 = blockIdx.x * TZ, y0 = blockIdx.y * TY;
+    const int z0 = bz * TZ, y0 = by * TY;
     const int ty = warp * LY + ly;
     const int y = y0 + ty;
     const int z4 = z0 + 4 * lz;
-    const int xb = blockIdx.z * a.x_block;
+    const int xb = bx * a.x_block;
     const int xe = min(xb + a.x_block, a.Nx);
     const bool own = (y < a.Ny) && (z4 < a.Nz);
     const long long P = a.plane;
     const long long col = (long long)y * a.pz + z4;
-    const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.u) + col);
-    float4 *up4 = reinterpret_cast<float4 *>(static_cast<float *>(a.up) + col);
-    const float4 *__restrict__ f1 = reinterpret_cast<const float4 *>(a.f1 + col);
-    const float4 *__restrict__ f2p = reinterpret_cast<const float4 *>(a.f2 + col);
-    const long long P4 = P / 4;  // plane stride in float4 (pz and Ny*pz are multiples of 4)
+    const T *__restrict__ u = static_cast<const T *>(a.u) + col;
+    T *up = static_cast<T *>(a.up) + col;
+    const float *__restrict__ f1 = a.f1 + col;
+    const float *__restrict__ f2p = a.f2 + col;
     // the damping field vanishes inside [bx0,bx1) x [by0,by1) x [bz0,bz1)
     const bool yz_box = y >= a.by0 && y < a.by1 && z4 >= a.bz0 && z4 + 3 < a.bz1;
+    const ScaleState sc = read_scales<T>(a);
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
@@ -171,22 +214,22 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    constexpr uint32_t kBoxBytes = uint32_t(SW) * SH * 4;
+    constexpr uint32_t kBoxBytes = uint32_t(SW) * SH * sizeof(T);
     auto issue = [&](int x, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
         mbar_expect_tx(bar, kBoxBytes);
-        tma_load_3d(smem_addr(tiles + stage * G::STAGE), &maps.u_halo, bar, z0 - RZ, y0 - R, x);
+        tma_load_3d(smem_addr(ring + stage * G::STAGE_BYTES), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
     };
     // the whole y-z tile lies where the damping field vanishes (in y and z)
     const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
     auto prefetch = [&](int x) {
         // point data of plane x and the queue front of plane x + R into L2
         if (x < xe) {
-            tma_prefetch_3d(&maps.up_pt, z0, y0, x);
-            tma_prefetch_3d(&maps.f1_pt, z0, y0, x);
-            if (!(tile_yz_box && x >= a.bx0 && x < a.bx1)) tma_prefetch_3d(&maps.f2_pt, z0, y0, x);
+            tma_prefetch_3d(&maps->up_pt, z0, y0, x);
+            tma_prefetch_3d(&maps->f1_pt, z0, y0, x);
+            if (!(tile_yz_box && x >= a.bx0 && x < a.bx1)) tma_prefetch_3d(&maps->f2_pt, z0, y0, x);
+            if (x + R < a.Nx) tma_prefetch_3d(&maps->u_pt, z0, y0, x + R);
         }
-        if (x + R < a.Nx && x + R < xe + R) tma_prefetch_3d(&maps.u_pt, z0, y0, x + R);
     };
     if (tid == 0) {
         for (int s = 0; s < S - 1 && xb + s < xe; ++s) issue(xb + s, s);
@@ -207,9 +250,7 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     }
 
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto load_u = [&](int x) -> float4 {
-        return (own && x >= 0 && x < a.Nx) ? __ldg(u4 + x * P4) : zero4;
-    };
+    auto load_u = [&](int x) -> float4 { return (own && x >= 0 && x < a.Nx) ? V::ldg(u + x * P) : zero4; };
     float4 q[Q];
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
@@ -221,10 +262,10 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
         pf1[slot] = zero4;
         pf2[slot] = zero4;
         if (own && x < xe) {
-            pum[slot] = up4[x * P4];
-            pf1[slot] = __ldg(f1 + x * P4);
+            pum[slot] = V::ld(up + x * P);
+            pf1[slot] = __ldg(reinterpret_cast<const float4 *>(f1 + x * P));
             const bool in_box = yz_box && x >= a.bx0 && x < a.bx1;
-            if (!in_box) pf2[slot] = __ldg(f2p + x * P4);
+            if (!in_box) pf2[slot] = __ldg(reinterpret_cast<const float4 *>(f2p + x * P));
         }
     };
 #pragma unroll
@@ -233,9 +274,11 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
     float2 cz2[R + 1];
 #pragma unroll
     for (int j = 1; j <= R; ++j) cz2[j] = f2(a.coef[j], a.coef[j]);
+    const float2 su2 = f2(sc.s_u, sc.s_u), sup2 = f2(sc.s_up, sc.s_up);
     const int rowc = ty + R;
-    const int colw = 4 * lz;  // first float of the thread's z window in a tile row
+    const int colw = 4 * lz;  // first element of the thread's z window in a tile row
     unsigned amax_bits = 0;
+    bool over = false;
     bool failed = false;
     int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
     int it_failed = 0;                  // first plane whose wait gave up
@@ -266,12 +309,12 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
             const float4 cum = pum[slot], cf1 = pf1[slot], cf2 = pf2[slot];
             if (x + PD < xe) load_point(x + PD, slot);
             if (own) {
-                const float *t = tiles + stage * G::STAGE;
-                const float *rowp = t + rowc * SW + colw;
+                const T *t = reinterpret_cast<const T *>(ring + stage * G::STAGE_BYTES);
+                const T *rowp = t + rowc * SW + colw;
                 float win[NWIN];
 #pragma unroll
                 for (int m = 0; m < NWIN / 4; ++m) {
-                    const float4 v = *reinterpret_cast<const float4 *>(rowp + 4 * m);
+                    const float4 v = V::ld(rowp + 4 * m);
                     win[4 * m] = v.x;
                     win[4 * m + 1] = v.y;
                     win[4 * m + 2] = v.z;
@@ -286,8 +329,8 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     const float2 nsixA = mul2(f2(-6.f, -6.f), lo2(uc)), nsixB = mul2(f2(-6.f, -6.f), hi2(uc));
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
-                        const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
-                        const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
+                        const float4 ym = V::ld(rowp + RZ - j * SW);
+                        const float4 yp = V::ld(rowp + RZ + j * SW);
                         const float4 xm = q[R + i - j], xp = q[R + i + j];
                         const float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
                                                ztap_pair<RZ>(win, j));
@@ -296,13 +339,20 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                         lapA = fma2(cz2[j], add2(sA, nsixA), lapA);
                         lapB = fma2(cz2[j], add2(sB, nsixB), lapB);
                     }
-                    // u+ = w L + (2u - u-) - 2 g (u - u-)
-                    const float2 wA = lo2(cf1), wB = hi2(cf1);
-                    const float2 umA = lo2(cum), umB = hi2(cum);
+                    // u+ = w L + (2u - u-) - 2 g (u - u-), on scaled values
+                    float2 ucA = lo2(uc), ucB = hi2(uc), umA = lo2(cum), umB = hi2(cum);
+                    if constexpr (Io<T>::kScaled) {
+                        lapA = mul2(lapA, su2);
+                        lapB = mul2(lapB, su2);
+                        ucA = mul2(ucA, su2);
+                        ucB = mul2(ucB, su2);
+                        umA = mul2(umA, sup2);
+                        umB = mul2(umB, sup2);
+                    }
                     const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2)), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2));
-                    const float2 dA = fma2(f2(-1.f, -1.f), umA, lo2(uc)), dB = fma2(f2(-1.f, -1.f), umB, hi2(uc));
-                    float2 vA = fma2(wA, lapA, add2(lo2(uc), dA));
-                    float2 vB = fma2(wB, lapB, add2(hi2(uc), dB));
+                    const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
+                    float2 vA = fma2(lo2(cf1), lapA, add2(ucA, dA));
+                    float2 vB = fma2(hi2(cf1), lapB, add2(ucB, dB));
                     vA = fma2(m2gA, dA, vA);
                     vB = fma2(m2gB, dB, vB);
                     out = make_float4(vA.x, vA.y, vB.x, vB.y);
@@ -320,8 +370,8 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     const float2 ucA = lo2(uc), ucB = hi2(uc);
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
-                        const float4 ym = *reinterpret_cast<const float4 *>(rowp + RZ - j * SW);
-                        const float4 yp = *reinterpret_cast<const float4 *>(rowp + RZ + j * SW);
+                        const float4 ym = V::ld(rowp + RZ - j * SW);
+                        const float4 yp = V::ld(rowp + RZ + j * SW);
                         const float4 xm = q[R + i - j], xp = q[R + i + j];
                         const float2 cA = mul2(cz2[j], invA), cB = mul2(cz2[j], invB);
                         lapA = fma2(cA, sub2(lo2(xm), ucA), lapA);
@@ -338,9 +388,9 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                         lapB = fma2(cB, sub2(f2(win[RZ + 2 + j], win[RZ + 3 + j]), ucB), lapB);
                     }
                     const float ms[4] = {cf1.x, cf1.y, cf1.z, cf1.w};
-                    const float ums[4] = {cum.x, cum.y, cum.z, cum.w};
-                    const float ucs[4] = {uc.x, uc.y, uc.z, uc.w};
-                    const float taps[4] = {lapA.x, lapA.y, lapB.x, lapB.y};
+                    const float ums[4] = {cum.x * sc.s_up, cum.y * sc.s_up, cum.z * sc.s_up, cum.w * sc.s_up};
+                    const float ucs[4] = {uc.x * sc.s_u, uc.y * sc.s_u, uc.z * sc.s_u, uc.w * sc.s_u};
+                    const float taps[4] = {lapA.x * sc.s_u, lapA.y * sc.s_u, lapB.x * sc.s_u, lapB.y * sc.s_u};
                     float v[4];
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
@@ -368,9 +418,17 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
                     if (z4 + 2 >= a.Nz) out.z = 0.f;
                     if (z4 + 3 >= a.Nz) out.w = 0.f;
                 }
-                up4[x * P4] = out;
                 amax_bits = max(amax_bits, max(max(__float_as_uint(fabsf(out.x)), __float_as_uint(fabsf(out.y))),
                                                max(__float_as_uint(fabsf(out.z)), __float_as_uint(fabsf(out.w)))));
+                if constexpr (Io<T>::kScaled) {
+                    out.x *= sc.inv_s_out;
+                    out.y *= sc.inv_s_out;
+                    out.z *= sc.inv_s_out;
+                    out.w *= sc.inv_s_out;
+                    over |= fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))) >
+                            Io<T>::kMaxStored;
+                }
+                V::st(up + x * P, out);
             }
         }
         if (failed) break;
@@ -378,7 +436,6 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
         for (int k = 0; k < 2 * R; ++k) q[k] = q[k + U];
     }
     if (failed) {
-        // record the timeout, let copies still in flight land, then leave
         // planes it_failed .. issued-1 are the only copies not yet waited for (one per stage)
         if (tid == 0) {
             if (a.status) atomicOr(a.status, kStatusTimeout);
@@ -387,13 +444,21 @@ __global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ 
         }
         return;
     }
-    if (check) reduce_amax(a, amax_bits, false);
+    if (check) reduce_amax(a, amax_bits, over);
 }
 
-template <int R, int FORM, int LZ, int W>
+template <int R, int FORM, int LZ, int W, typename T>
+__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
+                                                        const StepArgs a, int check) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
+    tma_cta<R, FORM, LZ, W, T>(&maps, a, check, blockIdx.x, blockIdx.y, blockIdx.z, smem_dyn);
+}
+
+template <int R, int FORM, int LZ, int W, typename T>
 cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s) {
-    using G = TmaShape<R, LZ, W>;
-    auto kernel = fd_tma_kernel<R, FORM, LZ, W>;
+    using G = TmaShape<R, LZ, W, T>;
+    auto kernel = fd_tma_kernel<R, FORM, LZ, W, T>;
     static bool attr_set = false;  // per instantiation, set once per process
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -405,33 +470,53 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
     return cudaGetLastError();
 }
 
-// Tile configurations (tile_z, tile_y) of the TMA kernel: (LZ, W) pairs.
+// Tile configurations (tile_z, tile_y) of the TMA kernel: (LZ, W) pairs. FP32
+// storage has every shape and both forms; 16-bit storage the factored form in
+// the shapes of the second list.
 #define FDGB_TMA_CONFIGS(X) X(8, 8) X(16, 8) X(32, 8) X(8, 4) X(16, 4)
+#define FDGB_TMA_CONFIGS_16(X) X(8, 4) X(16, 4)
 
 template <int R>
-cudaError_t tma_step_r(int form, int tile_z, int tile_y, const TmaMaps &map, const StepArgs &a,
+cudaError_t tma_step_r(int form, int storage, int tile_z, int tile_y, const TmaMaps &map, const StepArgs &a,
                        bool check, cudaStream_t s) {
 #define FDGB_TMA_CASE(LZ, W)                                                                    \
-    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
-        return form == kFactored ? tma_launch<R, kFactored, LZ, W>(map, a, check, s)            \
-                                 : tma_launch<R, kExpanded, LZ, W>(map, a, check, s);
+    if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                   \
+        return form == kFactored ? tma_launch<R, kFactored, LZ, W, float>(map, a, check, s)     \
+                                 : tma_launch<R, kExpanded, LZ, W, float>(map, a, check, s);
     FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
 #undef FDGB_TMA_CASE
+#define FDGB_TMA_CASE16(LZ, W)                                                                  \
+    if (form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {               \
+        if (storage == kBF16) return tma_launch<R, kFactored, LZ, W, __nv_bfloat16>(map, a, check, s); \
+        if (storage == kF16) return tma_launch<R, kFactored, LZ, W, __half>(map, a, check, s);  \
+    }
+    FDGB_TMA_CONFIGS_16(FDGB_TMA_CASE16)
+#undef FDGB_TMA_CASE16
     return cudaErrorInvalidValue;
 }
 
-// Box geometry the host needs to encode the tensor map for a configuration.
+// Box geometry the host needs to encode the tensor map for a configuration
+// (false when the configuration does not exist).
 template <int R>
-bool tma_box_r(int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
+bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
 #define FDGB_TMA_BOX(LZ, W)                                                                     \
-    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                                    \
-        *box_w = TmaShape<R, LZ, W>::SW;                                                        \
-        *box_h = TmaShape<R, LZ, W>::SH;                                                        \
-        *rz = TmaShape<R, LZ, W>::RZ;                                                           \
+    if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                 \
+        *box_w = TmaShape<R, LZ, W, float>::SW;                                                 \
+        *box_h = TmaShape<R, LZ, W, float>::SH;                                                 \
+        *rz = TmaShape<R, LZ, W, float>::RZ;                                                    \
         return true;                                                                            \
     }
     FDGB_TMA_CONFIGS(FDGB_TMA_BOX)
 #undef FDGB_TMA_BOX
+#define FDGB_TMA_BOX16(LZ, W)                                                                   \
+    if (storage != kF32 && form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) { \
+        *box_w = TmaShape<R, LZ, W, __half>::SW;                                                \
+        *box_h = TmaShape<R, LZ, W, __half>::SH;                                                \
+        *rz = TmaShape<R, LZ, W, __half>::RZ;                                                   \
+        return true;                                                                            \
+    }
+    FDGB_TMA_CONFIGS_16(FDGB_TMA_BOX16)
+#undef FDGB_TMA_BOX16
     return false;
 }
 
@@ -439,11 +524,13 @@ bool tma_box_r(int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
 
 #define FDGB_INSTANTIATE_TMA_RADIUS(R)                                                            \
     namespace fdgb {                                                                              \
-    cudaError_t tma_step_radius_##R(int form, int tile_z, int tile_y, const TmaMaps &map,         \
-                                    const StepArgs &a, bool check, cudaStream_t s) {              \
-        return tma_step_r<R>(form, tile_z, tile_y, map, a, check, s);                             \
+    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y,                \
+                                    const TmaMaps &map, const StepArgs &a, bool check,            \
+                                    cudaStream_t s) {                                             \
+        return tma_step_r<R>(form, storage, tile_z, tile_y, map, a, check, s);                    \
     }                                                                                             \
-    bool tma_box_radius_##R(int tile_z, int tile_y, int *w, int *h, int *rz) {                    \
-        return tma_box_r<R>(tile_z, tile_y, w, h, rz);                                            \
+    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int *w, int *h,        \
+                            int *rz) {                                                            \
+        return tma_box_r<R>(form, storage, tile_z, tile_y, w, h, rz);                             \
     }                                                                                             \
     }

@@ -221,3 +221,49 @@ def test_nonfinite_is_reported():
     shot.reset()
     shot.synchronize()  # status cleared by reset
     shot.close()
+
+
+# ---- 16-bit storage ------------------------------------------------------------
+# Storage rounding injects a relative error of at most one half-ulp of the
+# storage format per step (bf16: 2^-9, fp16 with a per-level power-of-two
+# scale that keeps the field within 2^12..2^16 of the FP16 range: 2^-12); over
+# n steps the leapfrog carries these errors along (they do not grow for a stable
+# step), so the relative L2 error stays within a small multiple of
+# half-ulp * sqrt(n). The tolerances below (60 steps) are ~3x the measured
+# errors and below 4 * half-ulp * sqrt(60).
+STORAGE_TOL = {"bf16": 4 * 2.0 ** -9 * 60 ** 0.5, "f16": 4 * 2.0 ** -12 * 60 ** 0.5}
+
+
+@pytest.mark.parametrize("kernel", ["stream", "tma"])
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("k", [2, 4, 8, 12, 16])
+def test_16bit_storage_ragged(oracle_mod, k, storage, kernel):
+    spec = _ragged_spec(k, seed=11)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
+    shape = dict(tile_y=8, x_block=16) if kernel == "stream" else \
+        dict(zip(("tile_z", "tile_y"), [(32, 16), (64, 8)][k % 2]), x_block=13)
+    got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, storage=storage, kernel=kernel, **shape)
+    e0, e1 = rel_l2(got, want), rel_l2(got_prev, want_prev)
+    report(f"ragged_so{k}_{storage}_{kernel}{shot.config}", e0, e1)
+    assert e0 <= STORAGE_TOL[storage] and e1 <= STORAGE_TOL[storage]
+    shot.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_16bit_resume_and_chunks(oracle_mod, storage):
+    """Loaded state (per-level scales picked from max|u|), chunked forwards."""
+    rng = np.random.default_rng(13)
+    spec = _ragged_spec(8, seed=13)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    u0 = inputs._gaussian_smooth(rng.standard_normal(spec.shape), 2.0).astype(np.float32) * 1e-3
+    u1 = (0.99 * u0).astype(np.float32)
+    state = (u0, u1, 3)
+    want, _ = run_oracle(oracle_mod, spec, 40, dt, eta, state=state)
+    got, _, shot = run_gpu(spec, 40, dt, None, state=state, chunks=[7, 33], storage=storage)
+    e = rel_l2(got, want)
+    report(f"resume_so8_{storage}{shot.config}", e)
+    assert e <= STORAGE_TOL[storage]
+    shot.close()
