@@ -77,7 +77,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     if force or todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcuda"]
+        # -z defs: every symbol the library uses must resolve at link time
+        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xlinker", "-z,defs"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -23,6 +23,38 @@ FDGB_DECLARE_RADIUS(7)
 FDGB_DECLARE_RADIUS(8)
 #undef FDGB_DECLARE_RADIUS
 
+cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
+                               bool check, cudaStream_t s) {
+    switch (radius) {
+        case 1: return stream_step_radius_1(form, storage, tile_y, a, check, s);
+        case 2: return stream_step_radius_2(form, storage, tile_y, a, check, s);
+        case 3: return stream_step_radius_3(form, storage, tile_y, a, check, s);
+        case 4: return stream_step_radius_4(form, storage, tile_y, a, check, s);
+        case 5: return stream_step_radius_5(form, storage, tile_y, a, check, s);
+        case 6: return stream_step_radius_6(form, storage, tile_y, a, check, s);
+        case 7: return stream_step_radius_7(form, storage, tile_y, a, check, s);
+        case 8: return stream_step_radius_8(form, storage, tile_y, a, check, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
+                              cudaStream_t s) {
+    switch (radius) {
+        case 1: return naive_step_radius_1(form, storage, a, check, s);
+        case 2: return naive_step_radius_2(form, storage, a, check, s);
+        case 3: return naive_step_radius_3(form, storage, a, check, s);
+        case 4: return naive_step_radius_4(form, storage, a, check, s);
+        case 5: return naive_step_radius_5(form, storage, a, check, s);
+        case 6: return naive_step_radius_6(form, storage, a, check, s);
+        case 7: return naive_step_radius_7(form, storage, a, check, s);
+        case 8: return naive_step_radius_8(form, storage, a, check, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int stream_grid_x_chunks(int Nx, int x_block) { return (Nx + x_block - 1) / x_block; }
+
 #define FDGB_DECLARE_TMA_RADIUS(R)                                                               \
     cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y,               \
                                     const TmaMaps &map, const StepArgs &a, bool check,           \
