@@ -270,6 +270,100 @@ def run_ours(args, rank: int, world: int):
         shot.close()
 
 
+def run_batched(args, rank: int, world: int):
+    """64 uneven shots (each axis U{96..256} + 10, smooth random velocity, k=8,
+    300 steps): the batch (one launch per step over all shots) against the same
+    shots run one after another through the single-shot path."""
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    specs = inputs.batched_shots(count=args.shots, nt=args.nt_batched)
+    k = specs[0].space_order
+    batch = fd.Batch(k, inputs.H)
+    batch.set_stream(stream.cuda_stream)
+    singles, ms = [], []
+    for spec in specs:
+        spec.dt = 0.9 * fd.fd_dt_max(k, inputs.H, spec.vmax)
+        m = spec.m
+        wav = inputs.ricker(spec.f0, spec.dt, spec.nt)
+        s = batch.add(spec.interior, spec.nbl, spec.dt, m)
+        batch.inject(s, *spec.source, wav)
+        shot = fd.Shot(spec.interior, k, inputs.H, spec.dt, spec.nbl)
+        shot.set_model(m)
+        shot.inject(*spec.source, wav)
+        shot.set_stream(stream.cuda_stream)
+        singles.append(shot)
+    nt = args.nt_batched
+    pts = sum(spec.points for spec in specs) * nt
+
+    def plain_step():
+        for shot in singles:
+            shot.reset()
+            shot.forward(nt)
+
+    def batch_step():
+        batch.reset()
+        batch.forward(nt)
+
+    def timed(fn, steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        plain_step()
+        batch_step()
+    torch.cuda.synchronize()
+    plain_ms = timed(plain_step, args.steps)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    batch_ms = timed(batch_step, args.steps)
+    clk = clocks.stop()
+    value = pts * args.steps * world / (batch_ms * 1e-3) / 1e9
+    plain = pts * args.steps / (plain_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    alg = sum(algorithmic_bytes_per_step(spec) for spec in specs) * nt * args.steps
+    achieved = alg / (batch_ms * 1e-3) / 1e9
+    active, items = batch.size()
+    line = {
+        "metric": "Gpts/s, 64 uneven shots advanced as one batch (one launch per step over "
+                  "all shots) vs the same shots one by one",
+        "value": round(value, 3), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(batch_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded smooth random velocity models, Ricker sources)",
+        "config": {"workload": f"batched: {len(specs)} shots, interiors U{{96..256}} per axis + 10, "
+                               f"space order {k}, {nt} steps, factored, FP32",
+                   "points": sum(spec.points for spec in specs), "work_items_per_step": items,
+                   "l2": "inputs larger than L2 (7.8 GB of fields)",
+                   "parallelism": f"replicas x{world}"},
+        "plain_one_by_one": {"value": round(plain, 3), "unit": "Gpts/s",
+                             "ms_per_step": round(plain_ms / args.steps, 3)},
+        "speedup_vs_plain": round(value / world / plain, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "fd_tma_batch_kernel", "peak_source": peak_kind},
+        "gpu_launches": nt * args.steps + 2 * len(specs) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for shot in singles:
+        shot.close()
+
+
 def run_e2e(args, shots, stream, world):
     """Same metric through the public C-ABI calls with host buffers: per shot,
     set the model from host memory, inject the host wavelet, reset, run, and
@@ -371,7 +465,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "batched"])
+    ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
+    ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -389,6 +485,8 @@ def main():
         tdist.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -205,6 +205,67 @@ int fd_last_forward_ms(fd_handle *hd, float *ms);
 /* Release every device buffer and the handle. NULL is accepted (no-op). */
 int fd_destroy(fd_handle *hd);
 
+/* ---- batches of uneven shots ---------------------------------------------- */
+/* A batch advances many independent shots (each its own grid, model, dt and
+ * sources; all with the same space order, h, storage and form) together: one
+ * kernel launch per time step covers every shot's tiles, and the launches are
+ * replayed from a CUDA graph. Shots keep their own step counters, so shots
+ * added later run behind the others; a shot's result does not depend on which
+ * other shots share the batch (same arithmetic per point as fd_forward). Each
+ * shot is the time step of Sec. 2.1, Eq. 1 (see the top of this header). */
+typedef struct fd_batch fd_batch;
+
+/* Device bytes one shot of this size needs (wavefields, model fields, small
+ * buffers), for admission by memory budget. storage: FD_STORAGE_*. */
+int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long *out);
+
+/* Create an empty batch. opt: storage/form as for fd_acoustic_create_ex
+ * (16-bit storage needs the factored form), tile_z/tile_y 0 (= 32x16) or one
+ * of 32x16, 64x8; kernel and x_block are ignored (per-shot x_block is
+ * autotuned). FD_ENOTSUP for other shapes. */
+int fd_batch_create(int space_order, double h, const fd_options *opt, fd_batch **out);
+
+/* Add a shot: interior nx*ny*nz, layer nbl, time step dt, HOST model m and
+ * eta (eta NULL: default profile) exactly as fd_acoustic_create +
+ * fd_set_model (same errors). Allocates its device state (see
+ * fd_shot_device_bytes). *slot receives its id (slots of removed shots are
+ * reused). The shot starts at step 0 with zero wavefields. */
+int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const float *m,
+                 const float *eta, int *slot);
+
+/* Source of a shot, as fd_inject (at most 4 sources per batched shot:
+ * FD_ENOTSUP beyond). */
+int fd_batch_inject(fd_batch *b, int slot, int ix, int iy, int iz, const float *wavelet, int nt);
+
+/* Remove a shot and free its device memory (waits for queued work). */
+int fd_batch_remove(fd_batch *b, int slot);
+
+/* Advance every shot in the batch by nt steps (asynchronous, on the batch's
+ * stream). */
+int fd_batch_forward(fd_batch *b, int nt);
+
+/* Read a shot's wavefield level (as fd_read_wavefield / _device). */
+int fd_batch_read(fd_batch *b, int slot, float *out, int level);
+int fd_batch_read_device(fd_batch *b, int slot, float *d_out, int level);
+
+/* A shot's global step counter; a shot's device status (as fd_status). */
+int fd_batch_shot_step(fd_batch *b, int slot, long long *step);
+int fd_batch_shot_status(fd_batch *b, int slot);
+
+/* Number of shots in the batch and work items (CTAs) per step (-1 until the
+ * next fd_batch_forward rebuilds the work list). */
+int fd_batch_size(fd_batch *b, int *active, int *work_items);
+
+/* Zero every shot's wavefields, step counter and status (as fd_reset). */
+int fd_batch_reset(fd_batch *b);
+
+/* Stream binding and synchronisation of the batch (as for handles). */
+int fd_batch_set_stream(fd_batch *b, void *cuda_stream);
+int fd_batch_synchronize(fd_batch *b);
+
+/* Free every shot and the batch. NULL is accepted. */
+int fd_batch_destroy(fd_batch *b);
+
 /* ---- allocation-free stepping -------------------------------------------- */
 
 /* nt time steps on CALLER-OWNED device buffers, allocating no device memory.

@@ -12,6 +12,10 @@ from __future__ import annotations
 
 import numpy as np
 
+from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_forward,  # noqa: F401
+                   fd_batch_inject, fd_batch_read, fd_batch_read_device, fd_batch_remove, fd_batch_reset,
+                   fd_batch_set_stream, fd_batch_shot_status, fd_batch_shot_step, fd_batch_size,
+                   fd_batch_synchronize, fd_shot_device_bytes)
 from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD_EUNSTABLE,  # noqa: F401
                    FD_ERANGE, FD_ESTATE, FD_ETIMEOUT, FD_FORM_EXPANDED, FD_FORM_FACTORED,
                    FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
@@ -39,6 +43,73 @@ def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x
     o.x_block = int(x_block)
     o.check_finite = int(bool(check_finite))
     return o
+
+
+class Batch:
+    """A batch of uneven shots advanced together (owns its device state)."""
+
+    def __init__(self, space_order, h, storage="f32", form="factored", tile_z=0, tile_y=0):
+        self.space_order = int(space_order)
+        self.h = float(h)
+        self.handle = fd_batch_create(space_order, h, options(storage=storage, form=form,
+                                                              tile_z=tile_z, tile_y=tile_y))
+        self.shapes = {}
+
+    def add(self, interior, nbl, dt, m, eta=None) -> int:
+        nx, ny, nz = interior
+        slot = fd_batch_add(self.handle, nx, ny, nz, nbl, dt, m, eta)
+        self.shapes[slot] = tuple(n + 2 * nbl for n in interior)
+        return slot
+
+    def inject(self, slot, ix, iy, iz, wavelet):
+        fd_batch_inject(self.handle, slot, ix, iy, iz, wavelet)
+
+    def remove(self, slot):
+        fd_batch_remove(self.handle, slot)
+        self.shapes.pop(slot, None)
+
+    def forward(self, nt):
+        fd_batch_forward(self.handle, nt)
+
+    def wavefield(self, slot, level=0, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shapes[slot], dtype=np.float32)
+        return fd_batch_read(self.handle, slot, out, level)
+
+    def step(self, slot) -> int:
+        return fd_batch_shot_step(self.handle, slot)
+
+    def status(self, slot) -> int:
+        return fd_batch_shot_status(self.handle, slot)
+
+    def size(self):
+        return fd_batch_size(self.handle)
+
+    def reset(self):
+        fd_batch_reset(self.handle)
+
+    def set_stream(self, stream_ptr):
+        fd_batch_set_stream(self.handle, stream_ptr)
+
+    def synchronize(self):
+        fd_batch_synchronize(self.handle)
+
+    def close(self):
+        if self.handle:
+            fd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Shot:

@@ -88,6 +88,21 @@ _SIGNATURES = {
     "fd_default_damping": (_i, [_i, _i, _i, _i, _d, _vp, _vp]),
     "fd_forward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _i, _vp, _vp, _i,
                                ctypes.c_longlong, _i, _vp, _fp]),
+    "fd_shot_device_bytes": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_batch_create": (_i, [_i, _d, ctypes.POINTER(fd_options), ctypes.POINTER(_vp)]),
+    "fd_batch_add": (_i, [_vp, _i, _i, _i, _i, _d, _vp, _vp, _ip]),
+    "fd_batch_inject": (_i, [_vp, _i, _i, _i, _i, _vp, _i]),
+    "fd_batch_remove": (_i, [_vp, _i]),
+    "fd_batch_forward": (_i, [_vp, _i]),
+    "fd_batch_read": (_i, [_vp, _i, _vp, _i]),
+    "fd_batch_read_device": (_i, [_vp, _i, _vp, _i]),
+    "fd_batch_shot_step": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_batch_shot_status": (_i, [_vp, _i]),
+    "fd_batch_size": (_i, [_vp, _ip, _ip]),
+    "fd_batch_reset": (_i, [_vp]),
+    "fd_batch_set_stream": (_i, [_vp, _vp]),
+    "fd_batch_synchronize": (_i, [_vp]),
+    "fd_batch_destroy": (_i, [_vp]),
     "fd_last_error": (ctypes.c_char_p, []),
     "fd_version": (ctypes.c_char_p, []),
 }
@@ -277,6 +292,84 @@ def fd_forward_noalloc(d_u, d_u_prev, d_m, d_eta, dims, space_order, h, dt, sour
                                   ctypes.byref(amax) if want_amax else None)
     _check(rc, "fd_forward_noalloc")
     return amax.value if want_amax else None
+
+
+def fd_shot_device_bytes(nx, ny, nz, nbl, storage) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().fd_shot_device_bytes(nx, ny, nz, nbl, storage, ctypes.byref(v)),
+           "fd_shot_device_bytes")
+    return v.value
+
+
+def fd_batch_create(space_order, h, opt: fd_options | None = None) -> int:
+    out = _vp()
+    _check(lib().fd_batch_create(space_order, h, ctypes.byref(opt) if opt is not None else None,
+                                 ctypes.byref(out)), "fd_batch_create")
+    return out.value
+
+
+def fd_batch_add(b, nx, ny, nz, nbl, dt, m, eta=None) -> int:
+    m = _host_f32(m)
+    eta = None if eta is None else _host_f32(eta)
+    slot = _i()
+    _check(lib().fd_batch_add(b, nx, ny, nz, nbl, dt, _ptr(m), _ptr(eta), ctypes.byref(slot)),
+           "fd_batch_add")
+    return slot.value
+
+
+def fd_batch_inject(b, slot, ix, iy, iz, wavelet):
+    w = _host_f32(wavelet)
+    _check(lib().fd_batch_inject(b, slot, ix, iy, iz, _ptr(w), int(w.size)), "fd_batch_inject")
+
+
+def fd_batch_remove(b, slot):
+    _check(lib().fd_batch_remove(b, slot), "fd_batch_remove")
+
+
+def fd_batch_forward(b, nt):
+    _check(lib().fd_batch_forward(b, nt), "fd_batch_forward")
+
+
+def fd_batch_read(b, slot, out: np.ndarray, level: int = 0):
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _check(lib().fd_batch_read(b, slot, _ptr(out), level), "fd_batch_read")
+    return out
+
+
+def fd_batch_read_device(b, slot, d_out, level: int = 0):
+    _check(lib().fd_batch_read_device(b, slot, _ptr(d_out), level), "fd_batch_read_device")
+
+
+def fd_batch_shot_step(b, slot) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().fd_batch_shot_step(b, slot, ctypes.byref(v)), "fd_batch_shot_step")
+    return v.value
+
+
+def fd_batch_shot_status(b, slot) -> int:
+    return lib().fd_batch_shot_status(b, slot)
+
+
+def fd_batch_size(b):
+    a, w = _i(), _i()
+    _check(lib().fd_batch_size(b, ctypes.byref(a), ctypes.byref(w)), "fd_batch_size")
+    return a.value, w.value
+
+
+def fd_batch_reset(b):
+    _check(lib().fd_batch_reset(b), "fd_batch_reset")
+
+
+def fd_batch_set_stream(b, stream_ptr):
+    _check(lib().fd_batch_set_stream(b, stream_ptr), "fd_batch_set_stream")
+
+
+def fd_batch_synchronize(b):
+    _check(lib().fd_batch_synchronize(b), "fd_batch_synchronize")
+
+
+def fd_batch_destroy(b):
+    _check(lib().fd_batch_destroy(b), "fd_batch_destroy")
 
 
 def fd_last_error() -> str:

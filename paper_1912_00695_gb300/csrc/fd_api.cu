@@ -897,3 +897,335 @@ int fd_destroy(fd_handle *hd) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many shots (different grids, same space order / h / storage / form)
+// advanced together, one launch per time step over every shot's work items,
+// replayed from a CUDA graph.
+// ---------------------------------------------------------------------------
+
+struct fd_batch {
+    int k = 0, r = 0;
+    double h = 0;
+    fd_options opt{};
+    int tile_z = 0, tile_y = 0;
+    std::vector<fd_handle *> slots;  // slot id -> shot (nullptr when free)
+    BatchShot *d_shots = nullptr;
+    size_t cap_shots = 0;
+    int4 *d_items = nullptr;
+    size_t cap_items = 0;
+    int n_items = 0;
+    std::vector<int> order;  // active slots in table order
+    bool dirty = true;
+    unsigned long long gen = 1;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int nt = 0;
+        unsigned long long gen = 0;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    std::vector<BatchShot> host_table;
+};
+
+namespace {
+
+int batch_rebuild(fd_batch *b) {
+    b->order.clear();
+    std::vector<int4> items;
+    for (size_t s = 0; s < b->slots.size(); ++s) {
+        fd_handle *hd = b->slots[s];
+        if (!hd) continue;
+        const int idx = int(b->order.size());
+        b->order.push_back(int(s));
+        const int tz = (hd->Nz + b->tile_z - 1) / b->tile_z, ty = (hd->Ny + b->tile_y - 1) / b->tile_y;
+        const int tx = (hd->Nx + hd->x_block - 1) / hd->x_block;
+        for (int x = 0; x < tx; ++x)
+            for (int y = 0; y < ty; ++y)
+                for (int z = 0; z < tz; ++z) items.push_back(make_int4(idx, z, y, x));
+    }
+    const size_t ns = b->order.size();
+    if (ns > b->cap_shots) {
+        if (b->d_shots) cudaFree(b->d_shots);
+        b->d_shots = nullptr;
+        b->cap_shots = 0;
+        if (cudaMalloc(&b->d_shots, ns * sizeof(BatchShot)) != cudaSuccess)
+            return fail(FD_ENOMEM, "cannot allocate the batch table");
+        b->cap_shots = ns;
+    }
+    if (items.size() > b->cap_items) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->cap_items = 0;
+        if (cudaMalloc(&b->d_items, items.size() * sizeof(int4)) != cudaSuccess)
+            return fail(FD_ENOMEM, "cannot allocate the batch work list");
+        b->cap_items = items.size();
+    }
+    if (!items.empty())
+        FD_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                b->stream));
+    FD_CUDA(cudaStreamSynchronize(b->stream));
+    b->n_items = int(items.size());
+    for (auto &g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    b->dirty = false;
+    b->gen++;
+    return FD_OK;
+}
+
+int batch_upload_table(fd_batch *b) {
+    b->host_table.resize(b->order.size());
+    for (size_t i = 0; i < b->order.size(); ++i) {
+        fd_handle *hd = b->slots[b->order[i]];
+        BatchShot &t = b->host_table[i];
+        for (int p = 0; p < 2; ++p) {
+            t.args[p] = make_args(hd, hd->step, p);
+            t.maps[p] = hd->tmaps[p];
+        }
+        t.cur0 = hd->cur;
+        t.step0 = hd->step;
+    }
+    if (!b->host_table.empty())
+        FD_CUDA(cudaMemcpyAsync(b->d_shots, b->host_table.data(), b->host_table.size() * sizeof(BatchShot),
+                                cudaMemcpyHostToDevice, b->stream));
+    // the host table may be rewritten by the next call: let this copy finish
+    FD_CUDA(cudaStreamSynchronize(b->stream));
+    return FD_OK;
+}
+
+fd_handle *batch_shot(fd_batch *b, int slot) {
+    if (!b || slot < 0 || size_t(slot) >= b->slots.size()) return nullptr;
+    return b->slots[slot];
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long *out) {
+    if (!out || nx < 1 || ny < 1 || nz < 1 || nbl < 0 || storage < 0 || storage > 2)
+        return fail(FD_EINVAL, "bad extents or storage");
+    const long long Nx = nx + 2LL * nbl, Ny = ny + 2LL * nbl, Nz = nz + 2LL * nbl;
+    const long long pz = (Nz + 63) / 64 * 64;
+    const long long n = Nx * Ny * pz;
+    *out = 2 * n * (long long)elem_size(storage) + 2 * n * 4 + (1 << 16);
+    return FD_OK;
+}
+
+int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batch **out) {
+    if (!out) return fail(FD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (space_order < 2 || space_order > 2 * kMaxRadius || space_order % 2)
+        return fail(FD_EINVAL, "space_order must be even in [2, 16], got %d", space_order);
+    if (!(h > 0) || !std::isfinite(h)) return fail(FD_EINVAL, "h must be positive and finite");
+    fd_options opt;
+    fd_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.storage < 0 || opt.storage > 2 || opt.form < 0 || opt.form > 1)
+        return fail(FD_ENOTSUP, "unknown storage/form option");
+    if (opt.storage != kF32 && opt.form != kFactored)
+        return fail(FD_ENOTSUP, "batches with 16-bit storage use the factored form");
+    int tz = opt.tile_z, ty = opt.tile_y;
+    if (tz == 0 && ty == 0) {
+        tz = kBatchTiles[0][0];
+        ty = kBatchTiles[0][1];
+    }
+    bool ok = false;
+    for (auto &t : kBatchTiles) ok |= (t[0] == tz && t[1] == ty);
+    if (!ok) return fail(FD_ENOTSUP, "batch tile must be 32x16 or 64x8");
+    fd_batch *b = new fd_batch();
+    b->k = space_order;
+    b->r = space_order / 2;
+    b->h = h;
+    b->opt = opt;
+    b->opt.kernel = kTma;
+    b->opt.tile_z = tz;
+    b->opt.tile_y = ty;
+    b->opt.check_finite = 1;
+    b->tile_z = tz;
+    b->tile_y = ty;
+    if (cudaStreamCreate(&b->own_stream) != cudaSuccess) {
+        delete b;
+        return fail(FD_ECUDA, "cudaStreamCreate failed");
+    }
+    b->stream = b->own_stream;
+    *out = b;
+    return FD_OK;
+}
+
+int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const float *m, const float *eta,
+                 int *slot) {
+    if (!b || !m || !slot) return fail(FD_EINVAL, "batch, m or slot is NULL");
+    fd_options opt = b->opt;
+    opt.x_block = 0;  // per-shot x_block from the autotuner, tile fixed by the batch
+    fd_handle *hd = nullptr;
+    int rc = fd_acoustic_create_ex(nx, ny, nz, b->k, b->h, dt, nbl, &opt, &hd);
+    if (rc != FD_OK) return rc;
+    rc = fd_set_stream(hd, b->stream);
+    if (rc == FD_OK) rc = fd_set_model(hd, m, eta);
+    if (rc == FD_OK) rc = autotune(hd);
+    if (rc == FD_OK) rc = build_maps(hd);
+    if (rc != FD_OK) {
+        std::string msg = g_last_error;
+        fd_destroy(hd);
+        return fail(rc, "%s", msg.c_str());
+    }
+    int s = -1;
+    for (size_t i = 0; i < b->slots.size(); ++i)
+        if (!b->slots[i]) {
+            s = int(i);
+            break;
+        }
+    if (s < 0) {
+        s = int(b->slots.size());
+        b->slots.push_back(nullptr);
+    }
+    b->slots[s] = hd;
+    b->dirty = true;
+    *slot = s;
+    return FD_OK;
+}
+
+int fd_batch_inject(fd_batch *b, int slot, int ix, int iy, int iz, const float *wavelet, int nt) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    if (int(hd->sources.size()) >= kFusedSources)
+        return fail(FD_ENOTSUP, "a batched shot holds at most %d sources", kFusedSources);
+    int rc = fd_inject(hd, ix, iy, iz, wavelet, nt);
+    if (rc == FD_OK) b->dirty = true;  // argument tables carry the sources
+    return rc;
+}
+
+int fd_batch_remove(fd_batch *b, int slot) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    FD_CUDA(cudaStreamSynchronize(b->stream));
+    b->slots[slot] = nullptr;
+    b->dirty = true;
+    // the handle's stream is the batch stream, which fd_destroy must not destroy
+    hd->stream = hd->own_stream;
+    return fd_destroy(hd);
+}
+
+int fd_batch_forward(fd_batch *b, int nt) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (b->dirty) {
+        int rc = batch_rebuild(b);
+        if (rc != FD_OK) return rc;
+    }
+    if (nt == 0 || b->order.empty()) return FD_OK;
+    int rc = batch_upload_table(b);
+    if (rc != FD_OK) return rc;
+    fd_batch::Graph *g = nullptr;
+    for (auto &e : b->graphs)
+        if (e.nt == nt && e.gen == b->gen) g = &e;
+    if (!g) {
+        cudaGraph_t graph = nullptr;
+        FD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < nt && err == cudaSuccess; ++i)
+            err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y, b->d_shots,
+                                        b->d_items, b->n_items, i, b->stream);
+        cudaError_t cap = cudaStreamEndCapture(b->stream, &graph);
+        if (err != cudaSuccess || cap != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(FD_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : cap));
+        }
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(FD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+        if (b->graphs.size() >= 8) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back({exec, nt, b->gen});
+        g = &b->graphs.back();
+    }
+    FD_CUDA(cudaGraphLaunch(g->exec, b->stream));
+    for (int s : b->order) {
+        fd_handle *hd = b->slots[s];
+        hd->step += nt;
+        hd->cur ^= (nt & 1);
+    }
+    return FD_OK;
+}
+
+int fd_batch_read(fd_batch *b, int slot, float *out, int level) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    return fd_read_wavefield(hd, out, level);
+}
+
+int fd_batch_read_device(fd_batch *b, int slot, float *d_out, int level) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    return fd_read_wavefield_device(hd, d_out, level);
+}
+
+int fd_batch_shot_step(fd_batch *b, int slot, long long *step) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    return fd_get_step(hd, step);
+}
+
+int fd_batch_shot_status(fd_batch *b, int slot) {
+    fd_handle *hd = batch_shot(b, slot);
+    if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
+    return fd_status(hd);
+}
+
+int fd_batch_size(fd_batch *b, int *active, int *work_items) {
+    if (!b || !active || !work_items) return fail(FD_EINVAL, "NULL argument");
+    int n = 0;
+    for (auto *hd : b->slots) n += hd != nullptr;
+    *active = n;
+    *work_items = b->dirty ? -1 : b->n_items;
+    return FD_OK;
+}
+
+int fd_batch_reset(fd_batch *b) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    for (auto *hd : b->slots)
+        if (hd) {
+            int rc = fd_reset(hd);
+            if (rc != FD_OK) return rc;
+        }
+    return FD_OK;
+}
+
+int fd_batch_set_stream(fd_batch *b, void *cuda_stream) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    FD_CUDA(cudaStreamSynchronize(b->stream));
+    b->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : b->own_stream;
+    for (auto *hd : b->slots)
+        if (hd) hd->stream = b->stream;
+    return FD_OK;
+}
+
+int fd_batch_synchronize(fd_batch *b) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    FD_CUDA(cudaStreamSynchronize(b->stream));
+    return FD_OK;
+}
+
+int fd_batch_destroy(fd_batch *b) {
+    if (!b) return FD_OK;
+    cudaStreamSynchronize(b->stream);
+    for (auto *hd : b->slots)
+        if (hd) {
+            hd->stream = hd->own_stream;
+            fd_destroy(hd);
+        }
+    for (auto &g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (b->d_shots) cudaFree(b->d_shots);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+    return FD_OK;
+}
+
+}  // extern "C"

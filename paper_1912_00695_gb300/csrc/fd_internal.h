@@ -84,6 +84,25 @@ struct TmaMaps {
     CUtensorMap f2_pt;
 };
 
+// One shot of a batch as the batched kernel sees it (device memory): the step
+// arguments and tensor maps for both buffer parities (index p: u^n in buffer
+// p), the parity and global step of u^n at the start of the launch sequence.
+struct BatchShot {
+    StepArgs args[2];
+    TmaMaps maps[2];
+    int cur0;
+    long long step0;
+};
+
+// Tile shapes of the batched kernel (every storage and form).
+constexpr int kBatchTiles[2][2] = {{32, 16}, {64, 8}};
+
+// Batched TMA kernel (fd_tma.cuh): one CTA per work item (shot, tile_z index,
+// tile_y index, x chunk); `offset` is the step's index within the launch sequence.
+cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z, int tile_y,
+                                  const BatchShot *shots, const int4 *items, int n_items, int offset,
+                                  cudaStream_t s);
+
 // TMA-fed kernel (fd_tma.cuh): FP32 storage in tiles (tile_z, tile_y) of {(32,32), (64,16),
 // (128,8), (32,16), (64,8)} and both forms; 16-bit storage in (32,16) and (64,8), factored
 // form. The halo box of `maps.u_halo` is (box_w, box_h, 1) from tma_box (false: no such

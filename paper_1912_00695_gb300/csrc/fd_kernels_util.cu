@@ -70,6 +70,33 @@ FDGB_DECLARE_TMA_RADIUS(7)
 FDGB_DECLARE_TMA_RADIUS(8)
 #undef FDGB_DECLARE_TMA_RADIUS
 
+#define FDGB_DECLARE_BATCH_RADIUS(R)                                                             \
+    cudaError_t tma_batch_step_radius_##R(int form, int storage, int tile_z, int tile_y,         \
+                                          const BatchShot *shots, const int4 *items, int n_items, \
+                                          int offset, cudaStream_t s);
+FDGB_DECLARE_BATCH_RADIUS(1)
+FDGB_DECLARE_BATCH_RADIUS(2)
+FDGB_DECLARE_BATCH_RADIUS(3)
+FDGB_DECLARE_BATCH_RADIUS(4)
+FDGB_DECLARE_BATCH_RADIUS(5)
+FDGB_DECLARE_BATCH_RADIUS(6)
+FDGB_DECLARE_BATCH_RADIUS(7)
+FDGB_DECLARE_BATCH_RADIUS(8)
+#undef FDGB_DECLARE_BATCH_RADIUS
+
+cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z, int tile_y,
+                                  const BatchShot *shots, const int4 *items, int n_items, int offset,
+                                  cudaStream_t s) {
+    switch (radius) {
+#define FDGB_BATCH_R(R) \
+        case R: return tma_batch_step_radius_##R(form, storage, tile_z, tile_y, shots, items, n_items, offset, s);
+        FDGB_BATCH_R(1) FDGB_BATCH_R(2) FDGB_BATCH_R(3) FDGB_BATCH_R(4)
+        FDGB_BATCH_R(5) FDGB_BATCH_R(6) FDGB_BATCH_R(7) FDGB_BATCH_R(8)
+#undef FDGB_BATCH_R
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {

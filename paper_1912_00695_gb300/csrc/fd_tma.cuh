@@ -470,6 +470,69 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
     return cudaGetLastError();
 }
 
+// Batched form: one CTA per work item (shot, bz, by, bx) of a device table, so
+// many uneven shots advance in one launch. Each CTA copies its shot's step
+// arguments into shared memory (with the step index of this launch) and runs
+// the same per-CTA schedule as the single-shot kernel.
+template <int R, int FORM, int LZ, int W, typename T>
+__global__ void __launch_bounds__(32 * W) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
+                                                              const int4 *__restrict__ items, int offset) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ StepArgs sa;
+    const int4 it = items[blockIdx.x];  // (shot, bz, by, bx)
+    const BatchShot &sh = shots[it.x];
+    const int p = (sh.cur0 + offset) & 1;
+    const TmaMaps *maps = &sh.maps[p];
+    if (threadIdx.x == 0) {
+        sa = sh.args[p];
+        sa.step = sh.step0 + offset;
+        // the maps were written to global memory by the host: acquire them for the copy engine
+        const CUtensorMap *m[5] = {&maps->u_halo, &maps->u_pt, &maps->up_pt, &maps->f1_pt, &maps->f2_pt};
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                             reinterpret_cast<uint64_t>(m[k]))
+                         : "memory");
+    }
+    __syncthreads();
+    publish_scales<T>(sa, it.y == 0 && it.z == 0 && it.w == 0 && threadIdx.x == 0);
+    tma_cta<R, FORM, LZ, W, T>(maps, sa, 1, it.y, it.z, it.w, smem_dyn);
+}
+
+template <int R, int FORM, int LZ, int W, typename T>
+cudaError_t tma_batch_launch(const BatchShot *shots, const int4 *items, int n_items, int offset, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W, T>;
+    auto kernel = fd_tma_batch_kernel<R, FORM, LZ, W, T>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (n_items <= 0) return cudaSuccess;
+    kernel<<<n_items, 32 * W, G::SMEM_BYTES, s>>>(shots, items, offset);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t tma_batch_step_r(int form, int storage, int tile_z, int tile_y, const BatchShot *shots,
+                             const int4 *items, int n_items, int offset, cudaStream_t s) {
+#define FDGB_BATCH_CASE(LZ, W)                                                                          \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                                            \
+        if (storage == kF32)                                                                            \
+            return form == kFactored ? tma_batch_launch<R, kFactored, LZ, W, float>(shots, items, n_items, offset, s) \
+                                     : tma_batch_launch<R, kExpanded, LZ, W, float>(shots, items, n_items, offset, s); \
+        if (form == kFactored && storage == kBF16)                                                      \
+            return tma_batch_launch<R, kFactored, LZ, W, __nv_bfloat16>(shots, items, n_items, offset, s); \
+        if (form == kFactored && storage == kF16)                                                       \
+            return tma_batch_launch<R, kFactored, LZ, W, __half>(shots, items, n_items, offset, s);    \
+    }
+    FDGB_BATCH_CASE(8, 4)
+    FDGB_BATCH_CASE(16, 4)
+#undef FDGB_BATCH_CASE
+    return cudaErrorInvalidValue;
+}
+
 // Tile configurations (tile_z, tile_y) of the TMA kernel: (LZ, W) pairs. FP32
 // storage has every shape and both forms; 16-bit storage the factored form in
 // the shapes of the second list.
@@ -532,5 +595,10 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
     bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int *w, int *h,        \
                             int *rz) {                                                            \
         return tma_box_r<R>(form, storage, tile_z, tile_y, w, h, rz);                             \
+    }                                                                                             \
+    cudaError_t tma_batch_step_radius_##R(int form, int storage, int tile_z, int tile_y,          \
+                                          const BatchShot *shots, const int4 *items, int n_items, \
+                                          int offset, cudaStream_t s) {                           \
+        return tma_batch_step_r<R>(form, storage, tile_z, tile_y, shots, items, n_items, offset, s); \
     }                                                                                             \
     }

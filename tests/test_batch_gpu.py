@@ -1,0 +1,124 @@
+"""GPU tests of batches: uneven shots advanced together in one launch per step.
+
+Each shot's result must be the same alone (its own handle, fd_forward) and in
+the mix (bit for bit: the per-point arithmetic does not depend on which other
+shots share the launch), including shots added and removed between forwards
+(continuous batching), and must match the FP64 oracle within the FP32
+tolerance.
+"""
+import numpy as np
+import pytest
+
+import paper_1912_00695_gb300 as fd
+from paper_1912_00695_gb300 import inputs
+from harness import rel_l2, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+H = inputs.H
+
+
+def _shots(k, seed, count=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        interior = tuple(int(v) for v in rng.integers(20, 60, size=3))
+        nbl = int(rng.integers(3, 8))
+        vel = inputs.smooth_random_velocity(interior, nbl, rng, sigma=3.0)
+        src = tuple(int(rng.integers(0, n)) for n in interior)
+        spec = inputs.ShotSpec(interior, nbl, k, vel, src, float(rng.uniform(8, 30)), 200)
+        spec.dt = 0.9 * fd.fd_dt_max(k, H, spec.vmax)
+        out.append(spec)
+    return out
+
+
+def _alone(spec, nt, storage="f32", form="factored"):
+    with fd.Shot(spec.interior, spec.space_order, H, spec.dt, spec.nbl, storage=storage,
+                 form=form, kernel="tma", tile_z=32, tile_y=16) as shot:
+        shot.set_model(spec.m)
+        shot.inject(*spec.source, inputs.ricker(spec.f0, spec.dt, spec.nt))
+        shot.forward(nt)
+        return shot.wavefield(0), shot.wavefield(1)
+
+
+@pytest.mark.parametrize("storage,form", [("f32", "factored"), ("f32", "expanded"),
+                                          ("bf16", "factored")])
+@pytest.mark.parametrize("k", [4, 8, 16])
+def test_batch_equals_alone(k, storage, form):
+    specs = _shots(k, seed=k)
+    with fd.Batch(k, H, storage=storage, form=form) as b:
+        slots = []
+        for spec in specs:
+            s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
+            b.inject(s, *spec.source, inputs.ricker(spec.f0, spec.dt, spec.nt))
+            slots.append(s)
+        b.forward(17)
+        b.forward(23)
+        for spec, s in zip(specs, slots):
+            want, want_prev = _alone(spec, 40, storage, form)
+            assert b.step(s) == 40
+            np.testing.assert_array_equal(b.wavefield(s, 0), want)
+            np.testing.assert_array_equal(b.wavefield(s, 1), want_prev)
+
+
+def test_batch_matches_oracle(oracle_mod):
+    specs = _shots(8, seed=3, count=3)
+    with fd.Batch(8, H) as b:
+        slots = []
+        for spec in specs:
+            s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
+            b.inject(s, *spec.source, inputs.ricker(spec.f0, spec.dt, spec.nt))
+            slots.append(s)
+        b.forward(60)
+        for spec, s in zip(specs, slots):
+            eta = fd.fd_default_damping(spec.m, spec.nbl, H)
+            want, _ = run_oracle(oracle_mod, spec, 60, spec.dt, eta)
+            e = rel_l2(b.wavefield(s, 0), want)
+            print(f"PARITY batch_so8_{spec.interior} {e:.3e}")
+            assert e <= 1e-5
+
+
+def test_continuous_batching_add_remove():
+    """Shots join and leave between forwards; each still equals its run alone."""
+    specs = _shots(8, seed=9, count=4)
+    with fd.Batch(8, H) as b:
+        def add(spec):
+            s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
+            b.inject(s, *spec.source, inputs.ricker(spec.f0, spec.dt, spec.nt))
+            return s
+        s0 = add(specs[0])
+        b.forward(10)
+        s1 = add(specs[1])
+        s2 = add(specs[2])
+        b.forward(15)
+        u0 = b.wavefield(s0)
+        b.remove(s0)
+        s3 = add(specs[3])  # reuses the freed slot
+        assert s3 == s0
+        b.forward(8)
+        b.remove(s2)
+        b.forward(5)
+        np.testing.assert_array_equal(u0, _alone(specs[0], 25)[0])
+        np.testing.assert_array_equal(b.wavefield(s1), _alone(specs[1], 28)[0])
+        np.testing.assert_array_equal(b.wavefield(s3), _alone(specs[3], 13)[0])
+        assert b.step(s1) == 28 and b.step(s3) == 13
+        assert b.size()[0] == 2
+
+
+def test_batch_errors():
+    with pytest.raises(fd.FdError) as e:
+        fd.Batch(8, H, storage="bf16", form="expanded")
+    assert e.value.code == fd.FD_ENOTSUP
+    with fd.Batch(4, H) as b:
+        spec = _shots(4, seed=1, count=1)[0]
+        s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
+        for _ in range(4):
+            b.inject(s, 0, 0, 0, np.ones(3, np.float32))
+        with pytest.raises(fd.FdError) as e:
+            b.inject(s, 0, 0, 0, np.ones(3, np.float32))
+        assert e.value.code == fd.FD_ENOTSUP
+        with pytest.raises(fd.FdError):
+            b.remove(s + 5)
+        with pytest.raises(fd.FdError) as e:
+            b.add(spec.interior, spec.nbl, 10 * spec.dt, spec.m)
+        assert e.value.code == fd.FD_EUNSTABLE
