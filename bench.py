@@ -282,9 +282,11 @@ def run_batched(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    specs = inputs.batched_shots(count=args.shots, nt=args.nt_batched)
+    specs = inputs.batched_shots(count=args.shots, nt=args.nt_batched, lo=args.shot_range[0],
+                                 hi=args.shot_range[1])
     k = specs[0].space_order
-    batch = fd.Batch(k, inputs.H)
+    batch = fd.Batch(k, inputs.H, tile_z=args.batch_tile[0], tile_y=args.batch_tile[1],
+                     x_block=args.batch_xb)
     batch.set_stream(stream.cuda_stream)
     singles, ms = [], []
     for spec in specs:
@@ -343,8 +345,10 @@ def run_batched(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(batch_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded smooth random velocity models, Ricker sources)",
-        "config": {"workload": f"batched: {len(specs)} shots, interiors U{{96..256}} per axis + 10, "
-                               f"space order {k}, {nt} steps, factored, FP32",
+        "config": {"workload": f"batched: {len(specs)} shots, interiors U{{{args.shot_range[0]}.."
+                               f"{args.shot_range[1]}}} per axis + 10, space order {k}, {nt} steps, "
+                               "factored, FP32",
+                   "batch_tile": list(args.batch_tile), "batch_x_block": args.batch_xb,
                    "points": sum(spec.points for spec in specs), "work_items_per_step": items,
                    "l2": "inputs larger than L2 (7.8 GB of fields)",
                    "parallelism": f"replicas x{world}"},
@@ -468,6 +472,11 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "batched"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
+    ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = autotuned per shot)")
+    ap.add_argument("--batch-tile", type=lambda v: tuple(int(x) for x in v.split("x")), default=(0, 0),
+                    help="batched workload: tile as ZxY (32x16 or 64x8; default 32x16)")
+    ap.add_argument("--shot-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(96, 256),
+                    help="batched workload: interior size range lo,hi per axis")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")

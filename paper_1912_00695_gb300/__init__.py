@@ -48,11 +48,13 @@ def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x
 class Batch:
     """A batch of uneven shots advanced together (owns its device state)."""
 
-    def __init__(self, space_order, h, storage="f32", form="factored", tile_z=0, tile_y=0):
+    def __init__(self, space_order, h, storage="f32", form="factored", tile_z=0, tile_y=0,
+                 x_block=0):
         self.space_order = int(space_order)
         self.h = float(h)
         self.handle = fd_batch_create(space_order, h, options(storage=storage, form=form,
-                                                              tile_z=tile_z, tile_y=tile_y))
+                                                              tile_z=tile_z, tile_y=tile_y,
+                                                              x_block=x_block))
         self.shapes = {}
 
     def add(self, interior, nbl, dt, m, eta=None) -> int:

@@ -1057,8 +1057,7 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
 int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const float *m, const float *eta,
                  int *slot) {
     if (!b || !m || !slot) return fail(FD_EINVAL, "batch, m or slot is NULL");
-    fd_options opt = b->opt;
-    opt.x_block = 0;  // per-shot x_block from the autotuner, tile fixed by the batch
+    fd_options opt = b->opt;  // tile fixed by the batch; x_block forced or per-shot autotuned
     fd_handle *hd = nullptr;
     int rc = fd_acoustic_create_ex(nx, ny, nz, b->k, b->h, dt, nbl, &opt, &hd);
     if (rc != FD_OK) return rc;
