@@ -368,6 +368,77 @@ def run_batched(args, rank: int, world: int):
         shot.close()
 
 
+def run_precision(args, rank: int, world: int):
+    """384^3 + 20 (424^3 points), space order 12, 4-layer model: the same shot
+    with FP32, BF16 and FP16 wavefield storage (per-level power-of-two scales,
+    FP32 arithmetic). The errors against the FP64 oracle are measured by the
+    precision test at a size the oracle finishes (96^3 + 20, 1000 steps)."""
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    spec = inputs.precision_shot(n=args.n_precision, nt=args.nt_precision)
+    dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+    m = spec.m
+    wav = inputs.ricker(spec.f0, dt, spec.nt)
+    res = {}
+    peak, peak_kind = _peaks()
+    clk = None
+    for st in ("f32", "bf16", "f16"):
+        shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, storage=st)
+        shot.set_model(m)
+        shot.inject(*spec.source, wav)
+        shot.set_stream(stream.cuda_stream)
+        for _ in range(args.warmup):
+            shot.reset()
+            shot.forward(spec.nt)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(dev)
+        if st == "bf16":
+            clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            shot.reset()
+            shot.forward(spec.nt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if st == "bf16":
+            clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        gpts = spec.points * spec.nt * args.steps / (ms * 1e-3) / 1e9
+        alg = algorithmic_bytes_per_step(spec, st) * spec.nt * args.steps
+        res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / args.steps, 3),
+                   "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config)}
+        shot.close()
+    line = {
+        "metric": "Gpts/s with BF16 wavefield storage (per-level scale, FP32 arithmetic) vs FP32 "
+                  "storage, 384^3+20, space order 12",
+        "value": round(res["bf16"]["gpts"] * world, 3), "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["bf16"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 storage, f32 math",
+        "data": "synthetic (seeded layered velocity model, Ricker source)",
+        "config": {"workload": f"precision: {args.n_precision}^3+20, space order 12, 4-layer model, "
+                               f"{spec.nt} steps", "points": spec.points,
+                   "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+        "by_storage": res,
+        "speedup_bf16_vs_f32": round(res["bf16"]["gpts"] / res["f32"]["gpts"], 3),
+        "speedup_f16_vs_f32": round(res["f16"]["gpts"] / res["f32"]["gpts"], 3),
+        "roofline": {"bound": "hbm", "achieved": round(res["bf16"]["hbm_frac"] * peak, 1), "peak": peak,
+                     "unit": "GB/s", "frac": res["bf16"]["hbm_frac"], "traffic": None,
+                     "kernel": "fd_tma_kernel (bf16)", "peak_source": peak_kind},
+        "gpu_launches": 3 * spec.nt * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_e2e(args, shots, stream, world):
     """Same metric through the public C-ABI calls with host buffers: per shot,
     set the model from host memory, inject the host wavelet, reset, run, and
@@ -469,7 +540,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "batched"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "batched", "precision"])
+    ap.add_argument("--n-precision", type=int, default=384, help="precision workload: interior size")
+    ap.add_argument("--nt-precision", type=int, default=1000, help="precision workload: steps")
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
     ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = autotuned per shot)")
@@ -496,6 +569,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world)
+    elif args.workload == "precision":
+        run_precision(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -267,3 +267,45 @@ def test_16bit_resume_and_chunks(oracle_mod, storage):
     report(f"resume_so8_{storage}{shot.config}", e)
     assert e <= STORAGE_TOL[storage]
     shot.close()
+
+
+def test_precision_error_report(oracle_mod):
+    """The precision workload shape (space order 12, 4-layer model, 20-cell
+    layer, 1000 steps) on a 96^3 interior where the FP64 oracle finishes in
+    seconds: every 100 steps, the relative L2 error on the 64^3 crop around the
+    source and the relative error of the discrete energy E^{n+1/2}, for FP32,
+    BF16 and FP16 storage."""
+    spec = inputs.precision_shot(n=96, nbl=20, nt=1000)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    m64 = spec.m.astype(np.float64)
+    k = spec.space_order
+    wav = inputs.ricker(spec.f0, dt, spec.nt)
+    src = [tuple(c + spec.nbl for c in spec.source)]
+    c = [s + spec.nbl for s in spec.source]
+    crop = tuple(slice(max(ci - 32, 0), max(ci - 32, 0) + 64) for ci in c)
+    shots = {st: fd.Shot(spec.interior, k, inputs.H, dt, spec.nbl, storage=st)
+             for st in ("f32", "bf16", "f16")}
+    for shot in shots.values():
+        shot.set_model(spec.m, eta)
+        shot.inject(*spec.source, wav)
+    u = up = None
+    worst = {st: 0.0 for st in shots}
+    for chunk in range(10):
+        u, up = oracle_mod.forward(m64, eta.astype(np.float64), k, inputs.H, dt, 100, src,
+                                   wav.astype(np.float64)[None, :], u0=u, u_prev0=up,
+                                   step0=100 * chunk)
+        e_ref = oracle_mod.energy(u, up, m64, k, inputs.H, dt)
+        for st, shot in shots.items():
+            shot.forward(100)
+            g0, g1 = shot.wavefield(0), shot.wavefield(1)
+            ecrop = rel_l2(g0[crop], u[crop])
+            e_en = abs(oracle_mod.energy(g0, g1, m64, k, inputs.H, dt) - e_ref) / abs(e_ref)
+            worst[st] = max(worst[st], ecrop)
+            print(f"PRECISION step {100 * (chunk + 1)} {st} crop_rel_l2 {ecrop:.3e} "
+                  f"energy_rel {e_en:.3e}")
+    for shot in shots.values():
+        shot.close()
+    assert worst["f32"] <= 1e-4
+    assert worst["f16"] <= 2e-2
+    assert worst["bf16"] <= 1e-1
