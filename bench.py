@@ -545,7 +545,7 @@ def main():
     ap.add_argument("--nt-precision", type=int, default=1000, help="precision workload: steps")
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
-    ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = autotuned per shot)")
+    ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = the library default)")
     ap.add_argument("--batch-tile", type=lambda v: tuple(int(x) for x in v.split("x")), default=(0, 0),
                     help="batched workload: tile as ZxY (32x16 or 64x8; default 32x16)")
     ap.add_argument("--shot-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(96, 256),

@@ -221,8 +221,8 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
 
 /* Create an empty batch. opt: storage/form as for fd_acoustic_create_ex
  * (16-bit storage needs the factored form), tile_z/tile_y 0 (= 32x16) or one
- * of 32x16, 64x8; x_block 0 = autotuned per shot, else used for every shot;
- * kernel is ignored. FD_ENOTSUP for other shapes. */
+ * of 32x16, 64x8; x_block 0 = 96 planes (or the whole extent if shorter),
+ * else used for every shot; kernel is ignored. FD_ENOTSUP for other shapes. */
 int fd_batch_create(int space_order, double h, const fd_options *opt, fd_batch **out);
 
 /* Add a shot: interior nx*ny*nz, layer nbl, time step dt, HOST model m and

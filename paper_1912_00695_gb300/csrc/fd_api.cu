@@ -930,6 +930,8 @@ struct fd_batch {
 
 namespace {
 
+constexpr int kBatchXBlock = 96;
+
 int batch_rebuild(fd_batch *b) {
     b->order.clear();
     std::vector<int4> items;
@@ -1057,7 +1059,10 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
 int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const float *m, const float *eta,
                  int *slot) {
     if (!b || !m || !slot) return fail(FD_EINVAL, "batch, m or slot is NULL");
-    fd_options opt = b->opt;  // tile fixed by the batch; x_block forced or per-shot autotuned
+    // tile fixed by the batch; x_block forced, else long x-runs: a batch has work items to
+    // spare, so it trades CTA count for fewer queue warm-ups (measured best near 96 planes)
+    fd_options opt = b->opt;
+    if (opt.x_block == 0) opt.x_block = std::min(kBatchXBlock, nx + 2 * nbl);
     fd_handle *hd = nullptr;
     int rc = fd_acoustic_create_ex(nx, ny, nz, b->k, b->h, dt, nbl, &opt, &hd);
     if (rc != FD_OK) return rc;
