@@ -54,11 +54,17 @@ extern "C" {
 #define FD_EFULL (-10)      /* batch/server: no slot or memory budget left        */
 
 /* ---- options -------------------------------------------------------------- */
-/* Storage precision of the wavefields u^n, u^{n-1} (the Laplacian and the
- * update are always accumulated in FP32; m and eta stay FP32). */
+/* Storage precision of the wavefields (the Laplacian and the update are
+ * always computed in FP32; m and eta stay FP32). FP32 keeps the two leapfrog
+ * levels u^n, u^{n-1}. The 16-bit formats keep u^n and the increment
+ * d^n = u^n - u^{n-1}, each with its own per-level power-of-two scale, and
+ * step d^{n+1} = dt^2/(m + dt/2 eta) (L u^n + q) + (1 - dt eta/(m + dt/2 eta)) d^n,
+ * u^{n+1} = u^n + d^{n+1} (the same scheme, rearranged): rounding both levels
+ * instead would lose the small difference u^n - u^{n-1} and drift without
+ * bound over long runs. 16-bit storage needs the factored form. */
 #define FD_STORAGE_F32 0
-#define FD_STORAGE_BF16 1   /* bfloat16 with a per-field power-of-two scale */
-#define FD_STORAGE_F16 2    /* float16 with a per-field power-of-two scale  */
+#define FD_STORAGE_BF16 1   /* bfloat16 u and increment, per-level power-of-two scales */
+#define FD_STORAGE_F16 2    /* float16 u and increment, per-level power-of-two scales  */
 
 /* Symbolic form of the stencil expression (Sec. 4: Devito's "basic" versus
  * "aggressive" symbolic optimisation). Both compute the same update. */
@@ -68,12 +74,10 @@ extern "C" {
                                by (m + dt/2 eta) per point, as Listing 2 is written */
 
 /* Kernel schedule. */
-#define FD_KERNEL_AUTO 0    /* TMA kernel where it has the storage/form (FP32: both forms;
-                               16-bit: factored), else the streaming kernel; launch shape
-                               chosen by the autotuner */
+#define FD_KERNEL_AUTO 0    /* the TMA kernel, launch shape chosen by the autotuner */
 #define FD_KERNEL_STREAM 1  /* 2.5D streaming kernel, one point per thread (x-march, y-z tile
-                               staged through registers into shared memory); all storages */
-#define FD_KERNEL_NAIVE 2   /* one thread per point, all taps from global memory */
+                               staged through registers into shared memory); FP32 only */
+#define FD_KERNEL_NAIVE 2   /* one thread per point, all taps from global memory; FP32 only */
 #define FD_KERNEL_TMA 3     /* 2.5D streaming kernel, four z points per thread, y-z tile with
                                halo fetched by tensor-map bulk copies; FP32 storage (both
                                forms) and 16-bit storage (factored form) */
@@ -110,9 +114,9 @@ int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double
                        fd_handle **out);
 
 /* As fd_acoustic_create with explicit options (opt == NULL: defaults).
- * FD_ENOTSUP for an unknown storage/form/kernel value, FD_KERNEL_TMA with
- * 16-bit storage and the expanded form, or a (tile_z, tile_y) pair the chosen
- * kernel does not have. */
+ * FD_ENOTSUP for an unknown storage/form/kernel value, 16-bit storage with
+ * the expanded form or a kernel other than TMA/AUTO, or a (tile_z, tile_y)
+ * pair the chosen kernel does not have. */
 int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                           const fd_options *opt, fd_handle **out);
 
@@ -177,8 +181,9 @@ int fd_status(fd_handle *hd);
  * (N_x*N_y*N_z floats each, dense C-order): u = u^step (level 0) and
  * u_prev = u^{step-1} (level 1), and set the global step counter to `step`
  * (>= 0; it indexes the source wavelets). Together with fd_read_wavefield and
- * fd_get_step this is checkpoint/resume. 16-bit storage picks each level's
- * power-of-two scale from its max |u|. Clears the device status.
+ * fd_get_step this is checkpoint/resume. 16-bit storage stores u and
+ * u - u_prev with power-of-two scales picked from their max magnitudes. Clears
+ * the device status.
  * FD_EINVAL for NULL arrays, non-finite values or step < 0. */
 int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long step);
 

@@ -113,6 +113,7 @@ struct fd_handle {
     int tile_z = 0, tile_y = 0, x_block = 0, kernel = kStream;
     TmaMaps tmaps[2];  // TMA kernel: maps of the step whose u^n is ubuf[0] / ubuf[1]
     void *ubuf[2] = {nullptr, nullptr};
+    void *dbuf = nullptr;  // 16-bit storage: the increment d^n = u^n - u^{n-1}
     float *f1 = nullptr, *f2 = nullptr;
     float *d_wavelet = nullptr;
     int *d_src = nullptr;  // 3 * ns ints: x[], y[], z[]
@@ -141,7 +142,13 @@ bool check_enabled(const fd_handle *hd) { return hd->opt.check_finite != 0 || hd
 StepArgs make_args(const fd_handle *hd, long long step, int cur) {
     StepArgs a{};
     a.u = hd->ubuf[cur];
-    a.up = hd->ubuf[cur ^ 1];
+    if (hd->opt.storage == kF32) {
+        a.up = hd->ubuf[cur ^ 1];
+        a.un = nullptr;
+    } else {
+        a.up = hd->dbuf;
+        a.un = hd->ubuf[cur ^ 1];
+    }
     a.f1 = hd->f1;
     a.f2 = hd->f2;
     a.Nx = hd->Nx;
@@ -241,7 +248,8 @@ int make_maps(const fd_handle *hd, const void *u, const void *up, int tile_z, in
 int build_maps(fd_handle *hd) {
     if (hd->kernel != kTma) return FD_OK;
     for (int b = 0; b < 2; ++b) {
-        int rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], hd->tile_z, hd->tile_y, &hd->tmaps[b]);
+        const void *up = hd->opt.storage == kF32 ? hd->ubuf[b ^ 1] : hd->dbuf;
+        int rc = make_maps(hd, hd->ubuf[b], up, hd->tile_z, hd->tile_y, &hd->tmaps[b]);
         if (rc != FD_OK) return rc;
     }
     return FD_OK;
@@ -305,12 +313,14 @@ int autotune(fd_handle *hd) {
         return FD_OK;
     }
     const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
-    void *s0 = nullptr, *s1 = nullptr, *aux = nullptr;
+    const bool inc = hd->opt.storage != kF32;  // increment form needs a third field
+    void *s0 = nullptr, *s1 = nullptr, *s2 = nullptr, *aux = nullptr;
     if (cudaMalloc(&s0, ub) != cudaSuccess || cudaMalloc(&s1, ub) != cudaSuccess ||
-        cudaMalloc(&aux, 256) != cudaSuccess) {
+        (inc && cudaMalloc(&s2, ub) != cudaSuccess) || cudaMalloc(&aux, 256) != cudaSuccess) {
         cudaGetLastError();
         if (s0) cudaFree(s0);
         if (s1) cudaFree(s1);
+        if (s2) cudaFree(s2);
         // not enough memory for scratch fields: take the first shape, heuristic x_block
         hd->tile_z = tiles[0].first;
         hd->tile_y = tiles[0].second;
@@ -324,11 +334,13 @@ int autotune(fd_handle *hd) {
     int best_t = 0, best_xb = xbs[0];
     cudaError_t e = cudaMemsetAsync(s0, 0, ub, hd->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s1, 0, ub, hd->stream);
+    if (e == cudaSuccess && inc) e = cudaMemsetAsync(s2, 0, ub, hd->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(aux, 0, 256, hd->stream);
     if (e == cudaSuccess) e = launch_init_scales(ls, hd->stream);
     StepArgs a = make_args(hd, 0, 0);
     a.u = s0;
     a.up = s1;
+    a.un = inc ? s2 : nullptr;
     a.ns = 0;
     a.scales = hd->opt.storage != kF32 ? ls : nullptr;
     a.status = check_enabled(hd) ? st : nullptr;
@@ -358,6 +370,7 @@ int autotune(fd_handle *hd) {
     cudaStreamSynchronize(hd->stream);
     cudaFree(s0);
     cudaFree(s1);
+    if (s2) cudaFree(s2);
     cudaFree(aux);
     if (rc != FD_OK) return rc;
     hd->tile_z = tiles[best_t].first;
@@ -484,6 +497,19 @@ int set_model_host(fd_handle *hd, const float *m, const float *eta_in) {
     return update_src_bound(hd);
 }
 
+// Level 0 (u^n) or 1 (u^{n-1}) as dense FP32 into a device buffer.
+cudaError_t unpack_to(fd_handle *hd, int level, float *dst) {
+    const int slot = int(((hd->step % 3) + 3) % 3);
+    if (hd->opt.storage == kF32)
+        return launch_unpack_level(hd->ubuf[level == 0 ? hd->cur : hd->cur ^ 1], dst, hd->Nx, hd->Ny, hd->Nz,
+                                   hd->pz, kF32, nullptr, slot, hd->stream);
+    if (level == 0)
+        return launch_unpack_level(hd->ubuf[hd->cur], dst, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
+                                   hd->d_scales, slot, hd->stream);
+    return launch_unpack_prev(hd->ubuf[hd->cur], hd->dbuf, dst, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
+                              hd->d_scales, slot, hd->stream);
+}
+
 int read_status(fd_handle *hd) {
     unsigned st = 0;
     FD_CUDA(cudaMemcpyAsync(&st, hd->d_status, sizeof st, cudaMemcpyDeviceToHost, hd->stream));
@@ -559,9 +585,12 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         opt.kernel > 3)
         return fail(FD_ENOTSUP, "unknown storage/form/kernel option");
     int kernel = opt.kernel;
-    if (kernel == kAuto) kernel = tma_tiles(opt.storage, opt.form).empty() ? kStream : kTma;
-    if (kernel == kTma && tma_tiles(opt.storage, opt.form).empty())
-        return fail(FD_ENOTSUP, "the TMA kernel has no expanded form for 16-bit storage");
+    if (opt.storage != kF32) {
+        // 16-bit storage is the increment form, computed by the TMA kernel, factored form
+        if (opt.form != kFactored) return fail(FD_ENOTSUP, "16-bit storage needs the factored form");
+        if (kernel != kAuto && kernel != kTma) return fail(FD_ENOTSUP, "16-bit storage runs on the TMA kernel");
+    }
+    if (kernel == kAuto) kernel = kTma;
     if (!tile_ok(kernel, opt.storage, opt.form, opt.tile_z, opt.tile_y))
         return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
@@ -595,6 +624,7 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         return bail(FD_ECUDA, "cudaEventCreate failed");
     const size_t ub = hd->n_pitched * elem_size(opt.storage), fb = hd->n_pitched * sizeof(float);
     if (cudaMalloc(&hd->ubuf[0], ub) != cudaSuccess || cudaMalloc(&hd->ubuf[1], ub) != cudaSuccess ||
+        (opt.storage != kF32 && cudaMalloc(&hd->dbuf, ub) != cudaSuccess) ||
         cudaMalloc(&hd->f1, fb) != cudaSuccess || cudaMalloc(&hd->f2, fb) != cudaSuccess ||
         cudaMalloc(&hd->d_status, sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&hd->d_scales, sizeof(LevelScales)) != cudaSuccess) {
@@ -753,10 +783,7 @@ int fd_read_wavefield(fd_handle *hd, float *out, int level) {
         const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
         if (!hd->d_unpack && cudaMalloc(&hd->d_unpack, n * sizeof(float)) != cudaSuccess)
             return fail(FD_ENOMEM, "cannot allocate the read-back buffer");
-        const long long lvl_step = level == 0 ? hd->step : hd->step - 1;
-        const int slot = int(((lvl_step % 3) + 3) % 3);
-        FD_CUDA(launch_unpack_level(hd->ubuf[buf], hd->d_unpack, hd->Nx, hd->Ny, hd->Nz, hd->pz,
-                                    hd->opt.storage, hd->d_scales, slot, hd->stream));
+        FD_CUDA(unpack_to(hd, level, hd->d_unpack));
         FD_CUDA(cudaMemcpyAsync(out, hd->d_unpack, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
     }
     FD_CUDA(cudaStreamSynchronize(hd->stream));
@@ -766,11 +793,7 @@ int fd_read_wavefield(fd_handle *hd, float *out, int level) {
 int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level) {
     if (!hd || !d_out) return fail(FD_EINVAL, "handle or out is NULL");
     if (level != 0 && level != 1) return fail(FD_EINVAL, "level must be 0 or 1");
-    const int buf = level == 0 ? hd->cur : hd->cur ^ 1;
-    const long long lvl_step = level == 0 ? hd->step : hd->step - 1;
-    const int slot = int(((lvl_step % 3) + 3) % 3);
-    FD_CUDA(launch_unpack_level(hd->ubuf[buf], d_out, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
-                                hd->opt.storage == kF32 ? nullptr : hd->d_scales, slot, hd->stream));
+    FD_CUDA(unpack_to(hd, level, d_out));
     return FD_OK;
 }
 
@@ -794,48 +817,51 @@ int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long 
     if (!hd || !u || !u_prev) return fail(FD_EINVAL, "handle or arrays are NULL");
     if (step < 0) return fail(FD_EINVAL, "step must be >= 0");
     const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
+    const bool inc = hd->opt.storage != kF32;
+    // levels as stored: FP32 (u^n, u^{n-1}); 16-bit (u^n, d^n = u^n - u^{n-1})
+    std::vector<float> dvec;
+    if (inc) dvec.resize(n);
     float amax[2] = {0.0f, 0.0f};
-    const float *lv[2] = {u, u_prev};
+    for (size_t i = 0; i < n; ++i) {
+        if (!std::isfinite(u[i]) || !std::isfinite(u_prev[i]))
+            return fail(FD_EINVAL, "state value %zu is not finite", i);
+        amax[0] = std::max(amax[0], std::fabs(u[i]));
+        const float second = inc ? (dvec[i] = u[i] - u_prev[i]) : u_prev[i];
+        amax[1] = std::max(amax[1], std::fabs(second));
+    }
+    const float *lv[2] = {u, inc ? dvec.data() : u_prev};
+    void *dst[2] = {hd->ubuf[0], inc ? hd->dbuf : hd->ubuf[1]};
+    float scale[2] = {1.0f, 1.0f};
     for (int l = 0; l < 2; ++l)
-        for (size_t i = 0; i < n; ++i) {
-            if (!std::isfinite(lv[l][i])) return fail(FD_EINVAL, "state value %zu of level %d is not finite", i, l);
-            amax[l] = std::max(amax[l], std::fabs(lv[l][i]));
+        if (inc && amax[l] > 0.0f) {
+            int e;
+            std::frexp(double(amax[l]) / 4096.0, &e);
+            scale[l] = std::ldexp(1.0f, e);
         }
     float *tmp = nullptr;
     if (cudaMalloc(&tmp, n * sizeof(float)) != cudaSuccess) return fail(FD_ENOMEM, "cannot allocate staging buffer");
-    int rc = FD_OK;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+        e = cudaMemcpyAsync(tmp, lv[l], n * sizeof(float), cudaMemcpyHostToDevice, hd->stream);
+        if (e == cudaSuccess)
+            e = launch_pack_level(tmp, dst[l], hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage, 1.0f / scale[l],
+                                  hd->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
+    }
+    unsigned bits[2];
+    std::memcpy(bits, amax, sizeof bits);
+    const int slot = int(((step % 3) + 3) % 3), next = int(((step + 1) % 3 + 3) % 3);
+    if (e == cudaSuccess) e = launch_init_scales(hd->d_scales, hd->stream);
+    if (e == cudaSuccess) e = launch_set_level_scale(hd->d_scales, slot, scale[0], bits[0], scale[1], bits[1], hd->stream);
+    // the accumulators of the level the next step writes start at zero
+    if (e == cudaSuccess) e = launch_set_level_scale(hd->d_scales, next, 1.0f, 0u, 1.0f, 0u, hd->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
     hd->step = step;
     hd->cur = 0;
-    for (int l = 0; l < 2 && rc == FD_OK; ++l) {
-        // level 0 -> ubuf[cur], level 1 -> ubuf[cur ^ 1]
-        float scale = 1.0f;
-        if (hd->opt.storage != kF32 && amax[l] > 0.0f) {
-            int e;
-            std::frexp(double(amax[l]) / 4096.0, &e);
-            scale = std::ldexp(1.0f, e);
-        }
-        const long long lvl_step = step - l;
-        const int slot = int(((lvl_step % 3) + 3) % 3);
-        unsigned bits;
-        std::memcpy(&bits, &amax[l], sizeof bits);
-        cudaError_t e = cudaMemcpyAsync(tmp, lv[l], n * sizeof(float), cudaMemcpyHostToDevice, hd->stream);
-        if (e == cudaSuccess)
-            e = launch_pack_level(tmp, hd->ubuf[l], hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
-                                  1.0f / scale, hd->stream);
-        if (e == cudaSuccess) e = launch_set_level_scale(hd->d_scales, slot, scale, bits, hd->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
-        if (e != cudaSuccess) rc = fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
-    }
-    if (rc == FD_OK) {
-        // the accumulator of the level the next step writes starts at zero
-        const int next = int(((step + 1) % 3 + 3) % 3);
-        cudaError_t e = launch_set_level_scale(hd->d_scales, next, 1.0f, 0u, hd->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
-        if (e != cudaSuccess) rc = fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
-    }
-    cudaFree(tmp);
-    return rc;
+    return FD_OK;
 }
 
 int fd_reset(fd_handle *hd) {
@@ -843,6 +869,7 @@ int fd_reset(fd_handle *hd) {
     const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
     FD_CUDA(cudaMemsetAsync(hd->ubuf[0], 0, ub, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->ubuf[1], 0, ub, hd->stream));
+    if (hd->dbuf) FD_CUDA(cudaMemsetAsync(hd->dbuf, 0, ub, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream));
     FD_CUDA(launch_init_scales(hd->d_scales, hd->stream));
     hd->step = 0;
@@ -885,8 +912,8 @@ int fd_destroy(fd_handle *hd) {
     if (!hd) return FD_OK;
     if (hd->stream) cudaStreamSynchronize(hd->stream);
     destroy_graphs(hd);
-    void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->f1, hd->f2, hd->d_wavelet, hd->d_src, hd->d_status,
-                    hd->d_scales, hd->d_unpack};
+    void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
+                    hd->d_status, hd->d_scales, hd->d_unpack};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (hd->ev0) cudaEventDestroy(hd->ev0);
@@ -1011,7 +1038,8 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
     const long long Nx = nx + 2LL * nbl, Ny = ny + 2LL * nbl, Nz = nz + 2LL * nbl;
     const long long pz = (Nz + 63) / 64 * 64;
     const long long n = Nx * Ny * pz;
-    *out = 2 * n * (long long)elem_size(storage) + 2 * n * 4 + (1 << 16);
+    const int fields = storage == kF32 ? 2 : 3;  // 16-bit keeps u in two buffers plus the increment
+    *out = fields * n * (long long)elem_size(storage) + 2 * n * 4 + (1 << 16);
     return FD_OK;
 }
 

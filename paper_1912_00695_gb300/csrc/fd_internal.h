@@ -24,19 +24,24 @@ enum KernelKind : int { kAuto = 0, kStream = 1, kNaive = 2, kTma = 3 };
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;  // a bounded device-side wait gave up
 
-// Per-level scale bookkeeping for 16-bit storage: value = stored * scale.
-// Three rotating slots, indexed by global step modulo 3: slot (n % 3) holds the
-// scale of u^n and the max |u^n| accumulated while u^n was written.
+// Per-level scale bookkeeping for 16-bit storage, which keeps u^n and the
+// increment d^n = u^n - u^{n-1} (value = stored * scale). Three rotating slots,
+// indexed by global step modulo 3: slot (n % 3) holds the scales of u^n and d^n
+// and the max |u^n|, |d^n| accumulated while they were written.
 struct LevelScales {
-    float scale[3];
-    unsigned amax_bits[3];  // max |u| as float bits (non-negative floats order as uints)
+    float scale[3];          // u^n
+    float dscale[3];         // d^n
+    unsigned amax_bits[3];   // max |u| as float bits (non-negative floats order as uints)
+    unsigned damax_bits[3];  // max |d|
 };
 
 // Arguments of one time step of one shot. Passed by value (kernel parameter
 // space) for the single-shot kernels and stored in device memory for batches.
 struct StepArgs {
     const void *u;      // u^n, storage type, pitched [Nx][Ny][pz]
-    void *up;           // u^{n-1} on entry, overwritten by u^{n+1}
+    void *up;           // FP32: u^{n-1} on entry, overwritten by u^{n+1};
+                        // 16-bit: the increment d^n on entry, overwritten by d^{n+1}
+    void *un;           // 16-bit: receives u^{n+1} (the buffer that held u^{n-1}); FP32: null
     const float *f1;    // factored: w = dt^2/(m + dt/2 eta); expanded: m
     const float *f2;    // factored: g = (dt/2 eta)/(m + dt/2 eta); expanded: eta
     int Nx, Ny, Nz;     // computational domain
@@ -121,7 +126,10 @@ cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int
 cudaError_t launch_init_scales(LevelScales *scales, cudaStream_t s);
 cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int Nz, int pz,
                               int storage, float inv_scale, cudaStream_t s);
+// u^{n-1} = u^n - d^n of a 16-bit shot into dense FP32
+cudaError_t launch_unpack_prev(const void *u, const void *d, float *dst, int Nx, int Ny, int Nz, int pz,
+                               int storage, const LevelScales *scales, int slot, cudaStream_t s);
 cudaError_t launch_set_level_scale(LevelScales *scales, int slot, float scale, unsigned amax_bits,
-                                   cudaStream_t s);
+                                   float dscale, unsigned damax_bits, cudaStream_t s);
 
 }  // namespace fdgb

@@ -139,21 +139,29 @@ template <> __device__ __forceinline__ __half from_f<__half>(float v) { return _
 
 // Sources beyond the ones fused into the step kernel, added after the step in
 // one thread (in order, so duplicates of a node add up deterministically). The
-// step kernel already wrote u^{n+1} with the scale of slot n+1.
+// step kernel already wrote level n+1 with the scales of slot n+1; 16-bit shots
+// add the source to both the increment d^{n+1} and u^{n+1} = u^n + d^{n+1}.
 template <typename T>
 __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *sy, const int *sz,
                                     int first, int count, int expanded) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (a.step < 0 || a.step >= a.ld) return;
     T *up = static_cast<T *>(a.up);
-    const float s_out = a.scales ? a.scales->scale[slot_of(a.step + 1)] : 1.0f;
+    T *un = static_cast<T *>(a.un);
+    const int n1 = slot_of(a.step + 1);
+    const float s_u = a.scales ? a.scales->scale[n1] : 1.0f;
+    const float s_d = a.scales ? a.scales->dscale[n1] : 1.0f;
     for (int i = first; i < first + count; ++i) {
         const long long p = (long long)sx[i] * a.plane + (long long)sy[i] * a.pz + sz[i];
         const float q = a.wavelet[(long long)i * a.ld + a.step];
         const float f1 = a.f1[p], f2 = a.f2[p];
         const float w = expanded ? a.dt2 * __frcp_rn(fmaf(a.half_dt, f2, f1)) : f1;
-        const float v = to_f<T>(up[p]) * s_out + w * q;
-        up[p] = from_f<T>(v / s_out);
+        if (un) {
+            up[p] = from_f<T>((to_f<T>(up[p]) * s_d + w * q) / s_d);
+            un[p] = from_f<T>((to_f<T>(un[p]) * s_u + w * q) / s_u);
+        } else {
+            up[p] = from_f<T>(to_f<T>(up[p]) * s_u + w * q);
+        }
     }
 }
 
@@ -183,10 +191,27 @@ __global__ void pack_kernel(const float *src, T *dst, int Nx, int Ny, int Nz, in
     }
 }
 
-__global__ void set_level_scale_kernel(LevelScales *ls, int slot, float scale, unsigned amax_bits) {
+// u^{n-1} = u^n * s_u - d^n * s_d of a 16-bit shot, pitched -> dense FP32.
+template <typename T>
+__global__ void unpack_prev_kernel(const T *u, const T *d, float *dst, int Nx, int Ny, int Nz, int pz,
+                                   const LevelScales *scales, int slot) {
+    const float su = scales->scale[slot], sd = scales->dscale[slot];
+    const long long n = (long long)Nx * Ny * Nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long z = i % Nz;
+        const long long xy = i / Nz;
+        dst[i] = to_f<T>(u[xy * pz + z]) * su - to_f<T>(d[xy * pz + z]) * sd;
+    }
+}
+
+__global__ void set_level_scale_kernel(LevelScales *ls, int slot, float scale, unsigned amax_bits,
+                                       float dscale, unsigned damax_bits) {
     if (threadIdx.x == 0) {
         ls->scale[slot] = scale;
         ls->amax_bits[slot] = amax_bits;
+        ls->dscale[slot] = dscale;
+        ls->damax_bits[slot] = damax_bits;
     }
 }
 
@@ -194,6 +219,8 @@ __global__ void init_scales_kernel(LevelScales *ls) {
     if (threadIdx.x < 3) {
         ls->scale[threadIdx.x] = 1.0f;
         ls->amax_bits[threadIdx.x] = 0u;
+        ls->dscale[threadIdx.x] = 1.0f;
+        ls->damax_bits[threadIdx.x] = 0u;
     }
 }
 
@@ -243,8 +270,23 @@ cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int N
 }
 
 cudaError_t launch_set_level_scale(LevelScales *scales, int slot, float scale, unsigned amax_bits,
-                                   cudaStream_t s) {
-    set_level_scale_kernel<<<1, 32, 0, s>>>(scales, slot, scale, amax_bits);
+                                   float dscale, unsigned damax_bits, cudaStream_t s) {
+    set_level_scale_kernel<<<1, 32, 0, s>>>(scales, slot, scale, amax_bits, dscale, damax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_prev(const void *u, const void *d, float *dst, int Nx, int Ny, int Nz, int pz,
+                               int storage, const LevelScales *scales, int slot, cudaStream_t s) {
+    const int blocks = 1024, threads = 256;
+    if (storage == kBF16)
+        unpack_prev_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(
+            static_cast<const __nv_bfloat16 *>(u), static_cast<const __nv_bfloat16 *>(d), dst, Nx, Ny, Nz, pz,
+            scales, slot);
+    else if (storage == kF16)
+        unpack_prev_kernel<__half><<<blocks, threads, 0, s>>>(static_cast<const __half *>(u),
+                                                              static_cast<const __half *>(d), dst, Nx, Ny, Nz,
+                                                              pz, scales, slot);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -46,58 +46,82 @@ template <> struct Io<__half> {
 
 __device__ __forceinline__ int level_slot(long long n) { return int(((n % 3) + 3) % 3); }
 
-// Power-of-two scale for the next level of a 16-bit field: the largest value
-// expected in u^{n+1} (a bound from max|u^n| and the source term) maps to about
-// 2^12, leaving 16x headroom below the FP16 maximum.
-__device__ __forceinline__ float next_scale(float amax_n, float src_bound) {
-    float bound = 6.5f * amax_n + src_bound;
+// Power-of-two scale mapping `bound` (the largest value expected in the next
+// level) to about 2^12, leaving 16x headroom below the FP16 maximum.
+__device__ __forceinline__ float pow2_scale(float bound) {
     bound = fmaxf(bound * (1.0f / 4096.0f), 1e-30f);
     int e;
     frexpf(bound, &e);
     return ldexpf(1.0f, e);
 }
 
+// Scales of the next levels of a 16-bit shot from max|u^n|, max|d^n| and the
+// source bound: d^{n+1} = w L u^n + (1 - 2g) d^n + w q with w L bounded by 4 in
+// magnitude below the stability limit, and u^{n+1} = u^n + d^{n+1}.
+__device__ __forceinline__ float next_u_scale(float amax_u, float amax_d, float src) {
+    return pow2_scale(5.0f * amax_u + amax_d + src);
+}
+__device__ __forceinline__ float next_d_scale(float amax_u, float amax_d, float src) {
+    return pow2_scale(4.0f * amax_u + amax_d + src);
+}
+
+// s_u, s_d: scales of the stored u^n and d^n (16-bit) — s_up of u^{n-1} is 1
+// for FP32, the only storage of the two-level kernels; inv_s_out, inv_s_d_out:
+// reciprocal scales of u^{n+1}, d^{n+1}.
 struct ScaleState {
-    float s_u, s_up, inv_s_out;
+    float s_u, s_up, inv_s_out, s_d, inv_s_d_out;
 };
 
 template <typename T>
 __device__ __forceinline__ ScaleState read_scales(const StepArgs &a) {
-    ScaleState st{1.0f, 1.0f, 1.0f};
+    ScaleState st{1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
     if constexpr (Io<T>::kScaled) {
         const LevelScales *ls = a.scales;
-        st.s_u = ls->scale[level_slot(a.step)];
-        st.s_up = ls->scale[level_slot(a.step - 1)];
-        const float amax = __uint_as_float(ls->amax_bits[level_slot(a.step)]);
-        const float s_out = next_scale(amax, a.src_bound);
-        st.inv_s_out = 1.0f / s_out;
+        const int n = level_slot(a.step);
+        st.s_u = ls->scale[n];
+        st.s_d = ls->dscale[n];
+        const float au = __uint_as_float(ls->amax_bits[n]), ad = __uint_as_float(ls->damax_bits[n]);
+        st.inv_s_out = 1.0f / next_u_scale(au, ad, a.src_bound);
+        st.inv_s_d_out = 1.0f / next_d_scale(au, ad, a.src_bound);
     }
     return st;
 }
 
-// One CTA of every launch publishes the scale of u^{n+1} and clears the max
-// accumulator that the next launch (writing u^{n+2}) will use.
+// One CTA of every launch publishes the scales of u^{n+1}, d^{n+1} and clears
+// the max accumulators that the next launch (writing level n+2) will use.
 template <typename T>
 __device__ __forceinline__ void publish_scales(const StepArgs &a, bool leader) {
     if constexpr (Io<T>::kScaled) {
         if (leader) {
             LevelScales *ls = a.scales;
-            const float amax = __uint_as_float(ls->amax_bits[level_slot(a.step)]);
-            ls->scale[level_slot(a.step + 1)] = next_scale(amax, a.src_bound);
-            ls->amax_bits[level_slot(a.step + 2)] = 0u;
+            const int n = level_slot(a.step), n1 = level_slot(a.step + 1), n2 = level_slot(a.step + 2);
+            const float au = __uint_as_float(ls->amax_bits[n]), ad = __uint_as_float(ls->damax_bits[n]);
+            ls->scale[n1] = next_u_scale(au, ad, a.src_bound);
+            ls->dscale[n1] = next_d_scale(au, ad, a.src_bound);
+            ls->amax_bits[n2] = 0u;
+            ls->damax_bits[n2] = 0u;
         }
     }
 }
 
-// Warp-level max of |u^{n+1}| (float bits, so NaN > Inf > finite) folded into
-// the level's accumulator and the sticky non-finite status bit.
-__device__ __forceinline__ void reduce_amax(const StepArgs &a, unsigned bits, bool overflow) {
+// Warp-level max of |u^{n+1}| (and |d^{n+1}| for 16-bit storage) as float bits
+// (so NaN > Inf > finite), folded into the level's accumulators and the sticky
+// non-finite status bit.
+__device__ __forceinline__ void reduce_amax(const StepArgs &a, unsigned bits, bool overflow,
+                                            unsigned dbits = 0u) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+        dbits = max(dbits, __shfl_xor_sync(0xffffffffu, dbits, o));
+    }
     const unsigned any_over = __any_sync(0xffffffffu, overflow);
     if ((threadIdx.x & 31) == 0) {
-        if (a.scales) atomicMax(&a.scales->amax_bits[level_slot(a.step + 1)], bits);
-        if (a.status && (bits >= 0x7f800000u || any_over)) atomicOr(a.status, kStatusNonFinite);
+        if (a.scales) {
+            atomicMax(&a.scales->amax_bits[level_slot(a.step + 1)], bits);
+            atomicMax(&a.scales->damax_bits[level_slot(a.step + 1)], dbits);
+        }
+        if (a.status && (bits >= 0x7f800000u || dbits >= 0x7f800000u || any_over))
+            atomicOr(a.status, kStatusNonFinite);
     }
 }
 
@@ -145,6 +169,7 @@ template <> struct Update<kExpanded> {
 // ---- naive kernel: one thread per point, every tap from global memory ------
 template <int R, int FORM, typename T>
 __global__ void __launch_bounds__(256) fd_naive_kernel(const StepArgs a, int check) {
+    static_assert(!Io<T>::kScaled, "16-bit storage runs on the TMA kernel (increment form)");
     const int z = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
     const int x = blockIdx.z;
@@ -213,6 +238,7 @@ __global__ void __launch_bounds__(256) fd_naive_kernel(const StepArgs a, int che
 // one plane ahead, so each plane costs one barrier.
 template <int R, int FORM, int TY, typename T>
 __global__ void __launch_bounds__(32 * TY) fd_stream_kernel(const StepArgs a, int check) {
+    static_assert(!Io<T>::kScaled, "16-bit storage runs on the TMA kernel (increment form)");
     constexpr int TZ = kTileZ;
     constexpr int SW = TZ + 2 * R;
     constexpr int SH = TY + 2 * R;
@@ -379,14 +405,11 @@ cudaError_t stream_step_r(int form, int storage, int tile_y, const StepArgs &a, 
         case 16: return go(fd_stream_kernel<R, FORM, 16, T>, 16);                        \
         default: return cudaErrorInvalidValue;                                           \
     }
+    if (storage != kF32) return cudaErrorInvalidValue;
     if (form == kFactored) {
-        if (storage == kF32) { FDGB_STREAM_CASE(kFactored, float) }
-        if (storage == kBF16) { FDGB_STREAM_CASE(kFactored, __nv_bfloat16) }
-        if (storage == kF16) { FDGB_STREAM_CASE(kFactored, __half) }
+        FDGB_STREAM_CASE(kFactored, float)
     } else {
-        if (storage == kF32) { FDGB_STREAM_CASE(kExpanded, float) }
-        if (storage == kBF16) { FDGB_STREAM_CASE(kExpanded, __nv_bfloat16) }
-        if (storage == kF16) { FDGB_STREAM_CASE(kExpanded, __half) }
+        FDGB_STREAM_CASE(kExpanded, float)
     }
 #undef FDGB_STREAM_CASE
     return cudaErrorInvalidValue;
@@ -397,17 +420,9 @@ cudaError_t naive_step_r(int form, int storage, const StepArgs &a, bool check, c
     const dim3 grid((a.Nz + 31) / 32, (a.Ny + 7) / 8, a.Nx);
     const dim3 block(32, 8);
     const int c = check ? 1 : 0;
-    if (form == kFactored) {
-        if (storage == kF32) fd_naive_kernel<R, kFactored, float><<<grid, block, 0, s>>>(a, c);
-        else if (storage == kBF16) fd_naive_kernel<R, kFactored, __nv_bfloat16><<<grid, block, 0, s>>>(a, c);
-        else if (storage == kF16) fd_naive_kernel<R, kFactored, __half><<<grid, block, 0, s>>>(a, c);
-        else return cudaErrorInvalidValue;
-    } else {
-        if (storage == kF32) fd_naive_kernel<R, kExpanded, float><<<grid, block, 0, s>>>(a, c);
-        else if (storage == kBF16) fd_naive_kernel<R, kExpanded, __nv_bfloat16><<<grid, block, 0, s>>>(a, c);
-        else if (storage == kF16) fd_naive_kernel<R, kExpanded, __half><<<grid, block, 0, s>>>(a, c);
-        else return cudaErrorInvalidValue;
-    }
+    if (storage != kF32) return cudaErrorInvalidValue;
+    if (form == kFactored) fd_naive_kernel<R, kFactored, float><<<grid, block, 0, s>>>(a, c);
+    else fd_naive_kernel<R, kExpanded, float><<<grid, block, 0, s>>>(a, c);
     return cudaGetLastError();
 }
 

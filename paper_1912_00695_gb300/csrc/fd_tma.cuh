@@ -19,9 +19,14 @@
 //    into L2 by bulk tensor prefetches, so those loads hit L2 instead of
 //    waiting on DRAM; the result is one vector store;
 //  * the arithmetic runs in FP32 on float2 pairs (FFMA2/FADD2), two points per
-//    instruction; 16-bit storage is converted on load and scaled by the
-//    level's power-of-two scale (the Laplacian is linear, so it is computed on
-//    the raw values and scaled once).
+//    instruction;
+//  * 16-bit storage keeps u^n and the increment d^n = u^n - u^{n-1} (the
+//    discrete velocity times dt), each with its own per-level power-of-two
+//    scale: d^{n+1} = w L u^n + (1 - 2g) d^n + w q, u^{n+1} = u^n + d^{n+1}.
+//    Rounding both leapfrog levels instead would cost the velocity u - u^{-}
+//    about ulp/(omega dt) of relative precision per step, which grows without
+//    bound over long runs. Values are converted on load and scaled; the
+//    Laplacian is linear, so it is computed on the raw values and scaled once.
 // The per-point arithmetic (association order included) does not depend on
 // the tile shape or x_block.
 #pragma once
@@ -201,7 +206,8 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     const long long P = a.plane;
     const long long col = (long long)y * a.pz + z4;
     const T *__restrict__ u = static_cast<const T *>(a.u) + col;
-    T *up = static_cast<T *>(a.up) + col;
+    T *up = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
+    T *un = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
     const float *__restrict__ f1 = a.f1 + col;
     const float *__restrict__ f2p = a.f2 + col;
     // the damping field vanishes inside [bx0,bx1) x [by0,by1) x [bz0,bz1)
@@ -274,10 +280,10 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     float2 cz2[R + 1];
 #pragma unroll
     for (int j = 1; j <= R; ++j) cz2[j] = f2(a.coef[j], a.coef[j]);
-    const float2 su2 = f2(sc.s_u, sc.s_u), sup2 = f2(sc.s_up, sc.s_up);
+    const float2 su2 = f2(sc.s_u, sc.s_u), sd2 = f2(sc.s_d, sc.s_d);
     const int rowc = ty + R;
     const int colw = 4 * lz;  // first element of the thread's z window in a tile row
-    unsigned amax_bits = 0;
+    unsigned amax_bits = 0, damax_bits = 0;
     bool over = false;
     bool failed = false;
     int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
@@ -339,23 +345,27 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
                         lapA = fma2(cz2[j], add2(sA, nsixA), lapA);
                         lapB = fma2(cz2[j], add2(sB, nsixB), lapB);
                     }
-                    // u+ = w L + (2u - u-) - 2 g (u - u-), on scaled values
-                    float2 ucA = lo2(uc), ucB = hi2(uc), umA = lo2(cum), umB = hi2(cum);
                     if constexpr (Io<T>::kScaled) {
+                        // increment form: d+ = w L u + (1 - 2g) d, u+ = u + d+ (formed below,
+                        // after the source), on scaled values
                         lapA = mul2(lapA, su2);
                         lapB = mul2(lapB, su2);
-                        ucA = mul2(ucA, su2);
-                        ucB = mul2(ucB, su2);
-                        umA = mul2(umA, sup2);
-                        umB = mul2(umB, sup2);
+                        const float2 omA = fma2(f2(-2.f, -2.f), lo2(cf2), f2(1.f, 1.f));
+                        const float2 omB = fma2(f2(-2.f, -2.f), hi2(cf2), f2(1.f, 1.f));
+                        const float2 dA = fma2(lo2(cf1), lapA, mul2(omA, mul2(lo2(cum), sd2)));
+                        const float2 dB = fma2(hi2(cf1), lapB, mul2(omB, mul2(hi2(cum), sd2)));
+                        out = make_float4(dA.x, dA.y, dB.x, dB.y);
+                    } else {
+                        // u+ = w L + (2u - u-) - 2 g (u - u-)
+                        const float2 ucA = lo2(uc), ucB = hi2(uc), umA = lo2(cum), umB = hi2(cum);
+                        const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2)), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2));
+                        const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
+                        float2 vA = fma2(lo2(cf1), lapA, add2(ucA, dA));
+                        float2 vB = fma2(hi2(cf1), lapB, add2(ucB, dB));
+                        vA = fma2(m2gA, dA, vA);
+                        vB = fma2(m2gB, dB, vB);
+                        out = make_float4(vA.x, vA.y, vB.x, vB.y);
                     }
-                    const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2)), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2));
-                    const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
-                    float2 vA = fma2(lo2(cf1), lapA, add2(ucA, dA));
-                    float2 vB = fma2(hi2(cf1), lapB, add2(ucB, dB));
-                    vA = fma2(m2gA, dA, vA);
-                    vB = fma2(m2gB, dB, vB);
-                    out = make_float4(vA.x, vA.y, vB.x, vB.y);
                     sw[0] = cf1.x;
                     sw[1] = cf1.y;
                     sw[2] = cf1.z;
@@ -387,10 +397,11 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
                         lapB = fma2(cB, sub2(f2(win[RZ + 2 - j], win[RZ + 3 - j]), ucB), lapB);
                         lapB = fma2(cB, sub2(f2(win[RZ + 2 + j], win[RZ + 3 + j]), ucB), lapB);
                     }
+                    static_assert(!Io<T>::kScaled, "16-bit storage uses the factored form");
                     const float ms[4] = {cf1.x, cf1.y, cf1.z, cf1.w};
-                    const float ums[4] = {cum.x * sc.s_up, cum.y * sc.s_up, cum.z * sc.s_up, cum.w * sc.s_up};
-                    const float ucs[4] = {uc.x * sc.s_u, uc.y * sc.s_u, uc.z * sc.s_u, uc.w * sc.s_u};
-                    const float taps[4] = {lapA.x * sc.s_u, lapA.y * sc.s_u, lapB.x * sc.s_u, lapB.y * sc.s_u};
+                    const float ums[4] = {cum.x, cum.y, cum.z, cum.w};
+                    const float ucs[4] = {uc.x, uc.y, uc.z, uc.w};
+                    const float taps[4] = {lapA.x, lapA.y, lapB.x, lapB.y};
                     float v[4];
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
@@ -418,15 +429,26 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
                     if (z4 + 2 >= a.Nz) out.z = 0.f;
                     if (z4 + 3 >= a.Nz) out.w = 0.f;
                 }
-                amax_bits = max(amax_bits, max(max(__float_as_uint(fabsf(out.x)), __float_as_uint(fabsf(out.y))),
-                                               max(__float_as_uint(fabsf(out.z)), __float_as_uint(fabsf(out.w)))));
+                auto bits4 = [](const float4 &v) {
+                    return max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
+                               max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w))));
+                };
                 if constexpr (Io<T>::kScaled) {
-                    out.x *= sc.inv_s_out;
-                    out.y *= sc.inv_s_out;
-                    out.z *= sc.inv_s_out;
-                    out.w *= sc.inv_s_out;
-                    over |= fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))) >
-                            Io<T>::kMaxStored;
+                    // out is d^{n+1}; u^{n+1} = u^n + d^{n+1} (padding stays zero: both terms are)
+                    float4 unew = make_float4(fmaf(uc.x, sc.s_u, out.x), fmaf(uc.y, sc.s_u, out.y),
+                                              fmaf(uc.z, sc.s_u, out.z), fmaf(uc.w, sc.s_u, out.w));
+                    damax_bits = max(damax_bits, bits4(out));
+                    amax_bits = max(amax_bits, bits4(unew));
+                    out = make_float4(out.x * sc.inv_s_d_out, out.y * sc.inv_s_d_out, out.z * sc.inv_s_d_out,
+                                      out.w * sc.inv_s_d_out);
+                    unew = make_float4(unew.x * sc.inv_s_out, unew.y * sc.inv_s_out, unew.z * sc.inv_s_out,
+                                       unew.w * sc.inv_s_out);
+                    const float mx = fmaxf(fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))),
+                                           fmaxf(fmaxf(fabsf(unew.x), fabsf(unew.y)), fmaxf(fabsf(unew.z), fabsf(unew.w))));
+                    over |= mx > Io<T>::kMaxStored;
+                    V::st(un + x * P, unew);
+                } else {
+                    amax_bits = max(amax_bits, bits4(out));
                 }
                 V::st(up + x * P, out);
             }
@@ -444,7 +466,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
         }
         return;
     }
-    if (check) reduce_amax(a, amax_bits, over);
+    if (check) reduce_amax(a, amax_bits, over, damax_bits);
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
