@@ -439,6 +439,78 @@ def run_precision(args, rank: int, world: int):
         print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank: int, world: int):
+    """Continuous-batching server (paper_1912_00695_gb300.serve) on a Poisson
+    trace of shot requests: cubic interiors U{lo..hi} + 10, space order 8 or 16,
+    FP32 or BF16 storage (50/50), steps U{steps}, smooth random velocity.
+    Two runs of the same requests: at the trace's Poisson rate, and at 70 % of
+    the capacity measured by an offline pass (all requests present at t=0), so
+    that the latency percentiles are also reported below saturation."""
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+    from paper_1912_00695_gb300.serve import Request, Server
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    trace = inputs.serving_trace(count=args.requests, rate=args.rate, lo=args.serve_range[0],
+                                 hi=args.serve_range[1], steps=args.serve_steps)
+
+    def make_requests(rate_scale=1.0):
+        reqs = []
+        for i, spec in enumerate(trace):
+            vel = models[i]
+            dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, float(vel.max()))
+            reqs.append(Request(i, spec.arrival * rate_scale, spec.interior, spec.nbl, spec.space_order,
+                                spec.storage, dt, ms[i], spec.source,
+                                inputs.ricker(spec.f0, dt, spec.nt), spec.nt))
+        return reqs
+
+    models = [inputs.velocity_for(spec) for spec in trace]
+    ms = [inputs.slowness2(v) for v in models]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(args.serve_budget * free)
+
+    def serve(reqs, realtime):
+        srv = Server(inputs.H, budget, chunk=args.chunk, keep_results=False)
+        stats = srv.run(reqs, realtime=realtime)
+        srv.close()
+        return stats
+
+    serve(make_requests()[: min(4, len(trace))], realtime=False)  # warm-up: tuner, graphs
+    offline = serve(make_requests(), realtime=False)
+    capacity = offline["gpts"]
+    mean_work = np.mean([spec.points * spec.nt for spec in trace])
+    offered = args.rate * mean_work / 1e9
+    clocks = ClockSampler(dev)
+    clocks.start()
+    at_rate = serve(make_requests(), realtime=True)
+    clk = clocks.stop()
+    scale70 = offered / (0.7 * capacity) if capacity > 0 else 1.0
+    at70 = serve(make_requests(scale70), realtime=True)
+    line = {
+        "metric": "served Gpts/s and p50/p99 request latency, continuous batching of shot requests",
+        "value": round(at_rate["gpts"] * world, 3), "unit": "Gpts/s", "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": round(at_rate["makespan_s"] * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 / bf16 storage per request",
+        "data": "synthetic (seeded smooth random velocity models, Ricker sources, Poisson arrivals)",
+        "config": {"workload": f"serving: {len(trace)} requests, Poisson {args.rate}/s, cubic interiors "
+                               f"U{{{args.serve_range[0]}..{args.serve_range[1]}}} + 10, space order 8/16, "
+                               f"FP32/BF16, steps U{{{args.serve_steps[0]}..{args.serve_steps[1]}}}",
+                   "chunk": args.chunk, "budget_bytes": budget, "parallelism": f"replicas x{world}"},
+        "offered_gpts": round(offered, 2),
+        "capacity_offline_gpts": round(capacity, 2),
+        "at_trace_rate": {k: round(v, 4) if isinstance(v, float) else v for k, v in at_rate.items()},
+        "at_70pct_capacity": dict({k: round(v, 4) if isinstance(v, float) else v for k, v in at70.items()},
+                                  rate_per_s=round(args.rate / scale70, 3)),
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_e2e(args, shots, stream, world):
     """Same metric through the public C-ABI calls with host buffers: per shot,
     set the model from host memory, inject the host wavelet, reset, run, and
@@ -540,7 +612,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "batched", "precision"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "plain", "batched", "precision", "serving"])
+    ap.add_argument("--requests", type=int, default=40, help="serving: requests in the trace")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrivals per second")
+    ap.add_argument("--serve-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(128, 256),
+                    help="serving: cubic interior size range lo,hi")
+    ap.add_argument("--serve-steps", type=lambda v: tuple(int(x) for x in v.split(",")), default=(200, 1000),
+                    help="serving: steps range lo,hi")
+    ap.add_argument("--serve-budget", type=float, default=0.8, help="serving: fraction of free HBM to admit into")
+    ap.add_argument("--chunk", type=int, default=50, help="serving: steps per scheduling chunk")
     ap.add_argument("--n-precision", type=int, default=384, help="precision workload: interior size")
     ap.add_argument("--nt-precision", type=int, default=1000, help="precision workload: steps")
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
@@ -571,6 +652,8 @@ def main():
         run_batched(args, rank, world)
     elif args.workload == "precision":
         run_precision(args, rank, world)
+    elif args.workload == "serving":
+        run_serving(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:
