@@ -14,10 +14,12 @@
 //    tensor-map bulk copy per plane into a shared ring guarded by mbarriers;
 //    out-of-domain boxes are zero-filled by the copy engine, which is exactly
 //    the Dirichlet halo;
-//  * the queue front u^n(x+R) and the point data u^{n-1}, w (m), g (eta) come
-//    as vector loads one plane ahead; further ahead the same boxes are pulled
-//    into L2 by bulk tensor prefetches, so those loads hit L2 instead of
-//    waiting on DRAM; the result is one vector store;
+//  * the queue front u^n(x+R) and the point data u^{n-1}, w (m), g (eta) of
+//    plane x arrive in the same ring stage as its halo tile (one bulk tensor
+//    copy each, several planes ahead, g skipped where the damping vanishes),
+//    so no thread waits on a global load inside the loop; further ahead the
+//    same boxes are pulled into L2 by bulk tensor prefetches; the result is
+//    one vector store;
 //  * the arithmetic runs in FP32 on float2 pairs (FFMA2/FADD2), two points per
 //    instruction;
 //  * 16-bit storage keeps u^n and the increment d^n = u^n - u^{n-1} (the
@@ -37,12 +39,10 @@
 
 namespace fdgb {
 
-// Ring depth and register prefetch distance: short stencils have short compute
-// phases per plane, so they keep more planes in flight.
+// Ring depth: planes whose inputs are in flight or resident in shared memory.
 template <int R>
 struct TmaPipe {
-    static constexpr int STAGES = R <= 4 ? 5 : 3;  // shared ring of halo tiles
-    static constexpr int PD = R <= 2 ? 2 : 1;       // planes of point data held in registers ahead
+    static constexpr int STAGES = R <= 2 ? 5 : 4;
 };
 constexpr long long kMbarWaitLimit = 1LL << 22;
 constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
@@ -152,7 +152,17 @@ struct TmaShape {
     static constexpr int TY = LY * W;
     static constexpr int SW = TZ + 2 * RZ;  // box width (elements)
     static constexpr int SH = TY + 2 * R;   // box height (rows)
-    static constexpr int STAGE_BYTES = (SW * SH * int(sizeof(T)) + 127) / 128 * 128;
+    // one ring stage: the halo tile of u^n(x), then the point tiles (TZ x TY, no halo)
+    // of the queue front u^n(x+R), of u^{n-1}(x) (16-bit: d^n(x)), w(x) and g(x)
+    static constexpr int HALO_RAW = SW * SH * int(sizeof(T));
+    static constexpr int PT_T_RAW = TZ * TY * int(sizeof(T));
+    static constexpr int PT_F_RAW = TZ * TY * 4;
+    static constexpr int HALO = (HALO_RAW + 127) / 128 * 128;
+    static constexpr int PT_T = (PT_T_RAW + 127) / 128 * 128;
+    static constexpr int PT_F = (PT_F_RAW + 127) / 128 * 128;
+    static constexpr int OFF_FRONT = HALO, OFF_UP = HALO + PT_T, OFF_F1 = HALO + 2 * PT_T,
+                         OFF_F2 = HALO + 2 * PT_T + PT_F;
+    static constexpr int STAGE_BYTES = HALO + 2 * PT_T + 2 * PT_F;
     // stages + their mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
     // need a 128-byte aligned shared destination)
     static constexpr int SMEM_BYTES = TmaPipe<R>::STAGES * STAGE_BYTES + 64 + 128;
@@ -187,8 +197,6 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window values
     constexpr int S = TmaPipe<R>::STAGES;
-    constexpr int PD = TmaPipe<R>::PD;
-    static_assert(U % PD == 0, "prefetch slots rotate within an unrolled block");
     unsigned char *ring = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
@@ -208,10 +216,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     const T *__restrict__ u = static_cast<const T *>(a.u) + col;
     T *up = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
     T *un = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
-    const float *__restrict__ f1 = a.f1 + col;
-    const float *__restrict__ f2p = a.f2 + col;
     // the damping field vanishes inside [bx0,bx1) x [by0,by1) x [bz0,bz1)
-    const bool yz_box = y >= a.by0 && y < a.by1 && z4 >= a.bz0 && z4 + 3 < a.bz1;
     const ScaleState sc = read_scales<T>(a);
 
     if (tid == 0) {
@@ -220,20 +225,28 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    constexpr uint32_t kBoxBytes = uint32_t(SW) * SH * sizeof(T);
+    // the whole y-z tile lies where the damping field vanishes (in y and z): such planes
+    // inside the box's x range need no g tile
+    const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
+    auto g_free = [&](int x) { return tile_yz_box && x >= a.bx0 && x < a.bx1; };
+    // every input of plane x arrives in its ring stage by bulk tensor copies
     auto issue = [&](int x, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
-        mbar_expect_tx(bar, kBoxBytes);
-        tma_load_3d(smem_addr(ring + stage * G::STAGE_BYTES), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
+        unsigned char *st = ring + stage * G::STAGE_BYTES;
+        const bool need_g = !g_free(x);
+        mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW + (need_g ? 2 : 1) * G::PT_F_RAW));
+        tma_load_3d(smem_addr(st), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
+        tma_load_3d(smem_addr(st + G::OFF_FRONT), &maps->u_pt, bar, z0, y0, x + R);  // zero past Nx
+        tma_load_3d(smem_addr(st + G::OFF_UP), &maps->up_pt, bar, z0, y0, x);
+        tma_load_3d(smem_addr(st + G::OFF_F1), &maps->f1_pt, bar, z0, y0, x);
+        if (need_g) tma_load_3d(smem_addr(st + G::OFF_F2), &maps->f2_pt, bar, z0, y0, x);
     };
-    // the whole y-z tile lies where the damping field vanishes (in y and z)
-    const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
     auto prefetch = [&](int x) {
         // point data of plane x and the queue front of plane x + R into L2
         if (x < xe) {
             tma_prefetch_3d(&maps->up_pt, z0, y0, x);
             tma_prefetch_3d(&maps->f1_pt, z0, y0, x);
-            if (!(tile_yz_box && x >= a.bx0 && x < a.bx1)) tma_prefetch_3d(&maps->f2_pt, z0, y0, x);
+            if (!g_free(x)) tma_prefetch_3d(&maps->f2_pt, z0, y0, x);
             if (x + R < a.Nx) tma_prefetch_3d(&maps->u_pt, z0, y0, x + R);
         }
     };
@@ -260,22 +273,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     float4 q[Q];
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
-    // register prefetch slots: slot (x - xb) % PD holds plane x's front u^n(x+R) and point data
-    float4 nxt[PD], pum[PD], pf1[PD], pf2[PD];
-    auto load_point = [&](int x, int slot) {
-        nxt[slot] = load_u(x + R);
-        pum[slot] = zero4;
-        pf1[slot] = zero4;
-        pf2[slot] = zero4;
-        if (own && x < xe) {
-            pum[slot] = V::ld(up + x * P);
-            pf1[slot] = __ldg(reinterpret_cast<const float4 *>(f1 + x * P));
-            const bool in_box = yz_box && x >= a.bx0 && x < a.bx1;
-            if (!in_box) pf2[slot] = __ldg(reinterpret_cast<const float4 *>(f2p + x * P));
-        }
-    };
-#pragma unroll
-    for (int d = 0; d < PD; ++d) load_point(xb + d, d);
+    const int pt_off = ty * TZ + 4 * lz;  // the thread's 4 points in a point tile
 
     float2 cz2[R + 1];
 #pragma unroll
@@ -310,12 +308,15 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
                 }
                 prefetch(x + 1 + kPrefetchAhead);
             }
-            const int slot = i % PD;  // (x - xb) % PD, since xo - xb is a multiple of U
-            q[2 * R + i] = nxt[slot];
-            const float4 cum = pum[slot], cf1 = pf1[slot], cf2 = pf2[slot];
-            if (x + PD < xe) load_point(x + PD, slot);
+            const unsigned char *st = ring + stage * G::STAGE_BYTES;
+            q[2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + pt_off);
             if (own) {
-                const T *t = reinterpret_cast<const T *>(ring + stage * G::STAGE_BYTES);
+                const float4 cum = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + pt_off);
+                const float4 cf1 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + pt_off);
+                const float4 cf2 = g_free(x) ? zero4
+                                             : *reinterpret_cast<const float4 *>(
+                                                   reinterpret_cast<const float *>(st + G::OFF_F2) + pt_off);
+                const T *t = reinterpret_cast<const T *>(st);
                 const T *rowp = t + rowc * SW + colw;
                 float win[NWIN];
 #pragma unroll
