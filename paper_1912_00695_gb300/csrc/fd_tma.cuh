@@ -39,11 +39,16 @@
 
 namespace fdgb {
 
-// Ring depth: planes whose inputs are in flight or resident in shared memory.
+// Ring depth: planes whose inputs are in flight or resident in shared memory,
+// sized so that four 128-thread CTAs (16 warps) fit an SM's shared memory with
+// the 32x16 tile.
 template <int R>
 struct TmaPipe {
-    static constexpr int STAGES = R <= 2 ? 5 : 4;
+    static constexpr int STAGES = R >= 7 ? 3 : 4;
 };
+// Registers capped for 16 resident warps per SM (the kernel is latency-bound:
+// occupancy is worth more than the few spill slots this costs at R = 8).
+constexpr int kTmaWarpsPerSM = 16;
 constexpr long long kMbarWaitLimit = 1LL << 22;
 constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
 
@@ -471,7 +476,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
-__global__ void __launch_bounds__(32 * W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
+__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
                                                         const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
@@ -498,7 +503,7 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
 // arguments into shared memory (with the step index of this launch) and runs
 // the same per-CTA schedule as the single-shot kernel.
 template <int R, int FORM, int LZ, int W, typename T>
-__global__ void __launch_bounds__(32 * W) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
+__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
                                                               const int4 *__restrict__ items, int offset) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ StepArgs sa;
