@@ -128,13 +128,14 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
  * (a convention: the paper names absorbing boundaries but gives no profile).
  * Checks stability: FD_EUNSTABLE when dt > fd_dt_max(k, h, v_max).
  * FD_EINVAL for non-positive or non-finite m, negative or non-finite eta.
- * Resets nothing: the wavefields keep their state. */
+ * Validation, the default profile and the derived per-point coefficients run
+ * on the device after one copy of m (and eta); on failure the handle has no
+ * model (fd_forward returns FD_ESTATE) until a valid one is set. Resets
+ * nothing: the wavefields keep their state. */
 int fd_set_model(fd_handle *hd, const float *m, const float *eta);
 
 /* As fd_set_model, from DEVICE arrays of the same layout (e.g. a torch
- * tensor's data_ptr()). The arrays are read back once (validation, stability
- * check and the derived per-point coefficients run on the host); setting a
- * model is not on the time-stepping path. */
+ * tensor's data_ptr()), copied device-to-device on the handle's stream. */
 int fd_set_model_device(fd_handle *hd, const float *d_m, const float *d_eta);
 
 /* Add a point source at INTERIOR node (ix, iy, iz) (offset by nbl internally)

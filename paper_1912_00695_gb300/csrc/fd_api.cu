@@ -121,6 +121,7 @@ struct fd_handle {
     std::vector<Source> sources;
     unsigned *d_status = nullptr;
     LevelScales *d_scales = nullptr;
+    ModelCheck *d_check = nullptr;
     float *d_unpack = nullptr;
     long long step = 0;
     int cur = 0;  // ubuf[cur] holds u^step
@@ -431,66 +432,51 @@ int update_src_bound(fd_handle *hd) {
     return FD_OK;
 }
 
-int set_model_host(fd_handle *hd, const float *m, const float *eta_in) {
-    const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
-    double mmin = INFINITY;
-    for (size_t i = 0; i < n; ++i) {
-        const float v = m[i];
-        if (!(v > 0.0f) || !std::isfinite(v)) return fail(FD_EINVAL, "m[%zu] = %g is not positive finite", i, v);
-        mmin = std::min(mmin, double(v));
-    }
-    std::vector<float> eta_default;
-    const float *eta = eta_in;
-    const double vmax = 1.0 / std::sqrt(mmin);
-    if (!eta) {
-        eta_default.resize(n);
-        default_damping(m, eta_default.data(), hd->Nx, hd->Ny, hd->Nz, hd->nbl, hd->h, vmax);
-        eta = eta_default.data();
-    } else {
-        for (size_t i = 0; i < n; ++i)
-            if (!(eta[i] >= 0.0f) || !std::isfinite(eta[i]))
-                return fail(FD_EINVAL, "eta[%zu] = %g is not non-negative finite", i, eta[i]);
-    }
+// Model upload and set-up, all O(n) work on the device: copy m (and eta) into the
+// handle's fields, validate and reduce min(m) in one pass, check stability,
+// build the default damping when eta is absent, then derive the factored
+// form's per-point coefficients. On failure the handle has no model until a
+// valid one is set.
+int set_model_common(fd_handle *hd, const float *m, const float *eta, cudaMemcpyKind kind) {
+    hd->has_model = false;
+    const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
+    const size_t pitch = size_t(hd->pz) * sizeof(float);
+    const size_t rows = size_t(hd->Nx) * hd->Ny;
+    FD_CUDA(cudaMemcpy2DAsync(hd->f1, pitch, m, row_bytes, row_bytes, rows, kind, hd->stream));
+    if (eta) FD_CUDA(cudaMemcpy2DAsync(hd->f2, pitch, eta, row_bytes, row_bytes, rows, kind, hd->stream));
+    const ModelCheck init{0u, 0u, 0x7f800000u, 0u};
+    FD_CUDA(cudaMemcpyAsync(hd->d_check, &init, sizeof init, cudaMemcpyHostToDevice, hd->stream));
+    FD_CUDA(launch_model_check(hd->f1, eta ? hd->f2 : nullptr, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->nbl,
+                               hd->d_check, hd->stream));
+    ModelCheck chk;
+    FD_CUDA(cudaMemcpyAsync(&chk, hd->d_check, sizeof chk, cudaMemcpyDeviceToHost, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    if (chk.bad_m) return fail(FD_EINVAL, "m must be positive and finite everywhere");
+    if (chk.bad_eta) return fail(FD_EINVAL, "eta must be non-negative and finite everywhere");
+    float mmin;
+    std::memcpy(&mmin, &chk.min_m_bits, sizeof mmin);
+    const double vmax = 1.0 / std::sqrt(double(mmin));
     const double dtm = stability_limit(hd->k, hd->h, vmax);
     if (hd->dt > dtm)
         return fail(FD_EUNSTABLE, "dt = %g exceeds the stability limit %g for v_max = %g", hd->dt, dtm, vmax);
-    // box where eta vanishes: the interior, when that holds; else nothing
     bool interior_zero = true;
+    if (!eta) {
+        const double dmax = hd->nbl > 0 ? 3.0 * vmax * std::log(1000.0) / (2.0 * double(hd->nbl) * hd->h) : 0.0;
+        FD_CUDA(launch_default_damping(hd->f1, hd->f2, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->nbl, float(dmax),
+                                       hd->stream));
+    } else {
+        interior_zero = chk.eta_interior_nonzero == 0;
+    }
     const int lo = hd->nbl;
-    for (int x = lo; x < hd->Nx - lo && interior_zero; ++x)
-        for (int y = lo; y < hd->Ny - lo && interior_zero; ++y) {
-            const size_t row = (size_t(x) * hd->Ny + y) * hd->Nz;
-            for (int z = lo; z < hd->Nz - lo; ++z)
-                if (eta[row + z] != 0.0f) {
-                    interior_zero = false;
-                    break;
-                }
-        }
     if (interior_zero) {
         const int b[6] = {lo, hd->Nx - lo, lo, hd->Ny - lo, lo, hd->Nz - lo};
         std::memcpy(hd->box, b, sizeof b);
     } else {
         std::memset(hd->box, 0, sizeof hd->box);
     }
-    // derived per-point fields
-    std::vector<float> f1(n), f2(n);
-    const double half_dt = 0.5 * hd->dt, dt2 = hd->dt * hd->dt;
-    for (size_t i = 0; i < n; ++i) {
-        if (hd->opt.form == kExpanded) {
-            f1[i] = m[i];
-            f2[i] = eta[i];
-        } else {
-            const double r0 = double(m[i]) + half_dt * double(eta[i]);
-            f1[i] = float(dt2 / r0);
-            f2[i] = float(half_dt * double(eta[i]) / r0);
-        }
-    }
-    const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
-    const size_t pitch = size_t(hd->pz) * sizeof(float);
-    FD_CUDA(cudaMemcpy2DAsync(hd->f1, pitch, f1.data(), row_bytes, row_bytes, size_t(hd->Nx) * hd->Ny,
-                              cudaMemcpyHostToDevice, hd->stream));
-    FD_CUDA(cudaMemcpy2DAsync(hd->f2, pitch, f2.data(), row_bytes, row_bytes, size_t(hd->Nx) * hd->Ny,
-                              cudaMemcpyHostToDevice, hd->stream));
+    if (hd->opt.form == kFactored)
+        FD_CUDA(launch_prepare_factored(hd->f1, hd->f2, (long long)hd->n_pitched, float(0.5 * hd->dt),
+                                        float(hd->dt * hd->dt), hd->stream));
     FD_CUDA(cudaStreamSynchronize(hd->stream));
     hd->has_model = true;
     hd->gen++;
@@ -627,7 +613,8 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         (opt.storage != kF32 && cudaMalloc(&hd->dbuf, ub) != cudaSuccess) ||
         cudaMalloc(&hd->f1, fb) != cudaSuccess || cudaMalloc(&hd->f2, fb) != cudaSuccess ||
         cudaMalloc(&hd->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&hd->d_scales, sizeof(LevelScales)) != cudaSuccess) {
+        cudaMalloc(&hd->d_scales, sizeof(LevelScales)) != cudaSuccess ||
+        cudaMalloc(&hd->d_check, sizeof(ModelCheck)) != cudaSuccess) {
         cudaGetLastError();
         return bail(FD_ENOMEM, "device allocation failed");
     }
@@ -651,20 +638,12 @@ int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double
 
 int fd_set_model(fd_handle *hd, const float *m, const float *eta) {
     if (!hd || !m) return fail(FD_EINVAL, "handle or m is NULL");
-    return set_model_host(hd, m, eta);
+    return set_model_common(hd, m, eta, cudaMemcpyHostToDevice);
 }
 
 int fd_set_model_device(fd_handle *hd, const float *d_m, const float *d_eta) {
     if (!hd || !d_m) return fail(FD_EINVAL, "handle or m is NULL");
-    const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
-    std::vector<float> m(n), eta;
-    FD_CUDA(cudaMemcpyAsync(m.data(), d_m, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
-    if (d_eta) {
-        eta.resize(n);
-        FD_CUDA(cudaMemcpyAsync(eta.data(), d_eta, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
-    }
-    FD_CUDA(cudaStreamSynchronize(hd->stream));
-    return set_model_host(hd, m.data(), d_eta ? eta.data() : nullptr);
+    return set_model_common(hd, d_m, d_eta, cudaMemcpyDeviceToDevice);
 }
 
 int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int nt) {
@@ -913,7 +892,7 @@ int fd_destroy(fd_handle *hd) {
     if (hd->stream) cudaStreamSynchronize(hd->stream);
     destroy_graphs(hd);
     void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
-                    hd->d_status, hd->d_scales, hd->d_unpack};
+                    hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (hd->ev0) cudaEventDestroy(hd->ev0);

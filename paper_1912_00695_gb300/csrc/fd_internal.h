@@ -124,6 +124,21 @@ cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int
                                 int storage, const LevelScales *scales, int slot,
                                 cudaStream_t s);
 cudaError_t launch_init_scales(LevelScales *scales, cudaStream_t s);
+
+// Model set-up on the device (fd_set_model*): validation and min(m) in one pass,
+// the default damping profile, and the factored form's derived coefficients.
+struct ModelCheck {
+    unsigned bad_m;                 // some m is not positive finite
+    unsigned bad_eta;               // some eta is negative or not finite
+    unsigned min_m_bits;            // min m as float bits (positive floats order as uints)
+    unsigned eta_interior_nonzero;  // eta != 0 somewhere inside the interior box
+};
+cudaError_t launch_model_check(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                               ModelCheck *out, cudaStream_t s);
+cudaError_t launch_default_damping(const float *m, float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                                   float dmax, cudaStream_t s);
+cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, float half_dt, float dt2,
+                                    cudaStream_t s);
 cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int Nz, int pz,
                               int storage, float inv_scale, cudaStream_t s);
 // u^{n-1} = u^n - d^n of a 16-bit shot into dense FP32

@@ -224,7 +224,97 @@ __global__ void init_scales_kernel(LevelScales *ls) {
     }
 }
 
+// One pass over the model: validation flags, min(m), and whether eta vanishes
+// inside the interior box [nbl, N - nbl)^3 (the kernels then skip its loads there).
+__global__ void model_check_kernel(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                                   ModelCheck *out) {
+    const long long n = (long long)Nx * Ny * Nz;
+    unsigned bad_m = 0, bad_eta = 0, inner = 0, mn = 0x7f800000u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int z = int(i % Nz);
+        const long long xy = i / Nz;
+        const int y = int(xy % Ny), x = int(xy / Ny);
+        const long long p = xy * pz + z;
+        const float mv = m[p];
+        if (!(mv > 0.0f) || !isfinite(mv)) bad_m = 1;
+        else mn = min(mn, __float_as_uint(mv));
+        if (eta) {
+            const float e = eta[p];
+            if (!(e >= 0.0f) || !isfinite(e)) bad_eta = 1;
+            if (e != 0.0f && x >= nbl && x < Nx - nbl && y >= nbl && y < Ny - nbl && z >= nbl && z < Nz - nbl)
+                inner = 1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad_m |= __shfl_xor_sync(0xffffffffu, bad_m, o);
+        bad_eta |= __shfl_xor_sync(0xffffffffu, bad_eta, o);
+        inner |= __shfl_xor_sync(0xffffffffu, inner, o);
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad_m) atomicOr(&out->bad_m, 1u);
+        if (bad_eta) atomicOr(&out->bad_eta, 1u);
+        if (inner) atomicOr(&out->eta_interior_nonzero, 1u);
+        atomicMin(&out->min_m_bits, mn);
+    }
+}
+
+// eta = m * d_max * sum_a (l_a / nbl)^2, l_a the depth into the layer along axis a.
+__global__ void default_damping_kernel(const float *m, float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                                       float dmax) {
+    const long long n = (long long)Nx * Ny * Nz;
+    const float inv = nbl > 0 ? 1.0f / float(nbl) : 0.0f;
+    auto frac2 = [&](int i, int N) {
+        const int d = max(max(nbl - i, i - (N - 1 - nbl)), 0);
+        const float f = float(d) * inv;
+        return f * f;
+    };
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int z = int(i % Nz);
+        const long long xy = i / Nz;
+        const int y = int(xy % Ny), x = int(xy / Ny);
+        const long long p = xy * pz + z;
+        eta[p] = nbl > 0 ? m[p] * (dmax * (frac2(x, Nx) + frac2(y, Ny) + frac2(z, Nz))) : 0.0f;
+    }
+}
+
+// Factored form's per-point coefficients, in place: (m, eta) -> (w, g) with
+// w = dt^2 / (m + dt/2 eta), g = (dt/2 eta) / (m + dt/2 eta) (correctly rounded
+// divisions; padding elements are zero in both and stay zero).
+__global__ void prepare_factored_kernel(float *f1, float *f2, long long n, float half_dt, float dt2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float mv = f1[i], he = half_dt * f2[i];
+        const float r0 = mv + he;
+        if (r0 > 0.0f) {
+            f1[i] = __fdiv_rn(dt2, r0);
+            f2[i] = __fdiv_rn(he, r0);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_model_check(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                               ModelCheck *out, cudaStream_t s) {
+    model_check_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_default_damping(const float *m, float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
+                                   float dmax, cudaStream_t s) {
+    default_damping_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, dmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, float half_dt, float dt2,
+                                    cudaStream_t s) {
+    prepare_factored_kernel<<<1216, 256, 0, s>>>(f1, f2, n_pitched, half_dt, dt2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
                                 int first, int count, int storage, int expanded, cudaStream_t s) {
