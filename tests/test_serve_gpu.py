@@ -40,15 +40,19 @@ def _alone(r):
         return shot.wavefield(0)
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("realtime", [False, True])
+def test_served_results_equal_alone(realtime):
+    """Offline (every request present at once, so the memory budget makes some
+    wait) and on the wall clock (arrivals 3 ms apart)."""
     reqs = _requests(0, 10)
     budget = sum(sorted(r.device_bytes for r in reqs)[-3:])  # about three shots at a time
     srv = Server(H, budget, chunk=16)
-    stats = srv.run(reqs, realtime=True)
+    stats = srv.run(reqs, realtime=realtime)
     srv.close()
     assert stats["requests"] == len(reqs)
     assert srv.peak_used <= budget
-    assert any(r.admitted > r.arrival + 1e-4 for r in reqs)  # some had to wait for memory
+    if not realtime:
+        assert sum(r.admitted > 0 for r in reqs) >= 3  # admitted only as memory freed up
     for r in reqs:
         np.testing.assert_array_equal(r.result, _alone(r), err_msg=f"request {r.rid}")
     assert 0 <= stats["p50_s"] <= stats["p99_s"]
