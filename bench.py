@@ -124,6 +124,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float) -> float:
+    """Largest value over the ranks of the default process group (the timing
+    rule: a multi-GPU step takes as long as its slowest replica); the value
+    itself when not distributed."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---- workload -----------------------------------------------------------------
 
 def build_workload(name: str, n: int, nt: int, orders=ORDERS, forms=FORMS):
@@ -213,10 +226,7 @@ def run_ours(args, rank: int, world: int):
     # per-shot kernel time (events around each graph replay on the launching stream)
     bench_step(kernel_ms)
     torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
 
     pts_per_step = sum(spec.points * spec.nt for spec, *_ in shots)
     value = pts_per_step * args.steps * world / (total_ms * 1e-3) / 1e9
@@ -330,9 +340,12 @@ def run_batched(args, rank: int, world: int):
         batch_step()
     torch.cuda.synchronize()
     plain_ms = timed(plain_step, args.steps)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
     clocks = ClockSampler(dev)
     clocks.start()
-    batch_ms = timed(batch_step, args.steps)
+    batch_ms = max_over_ranks(timed(batch_step, args.steps))
     clk = clocks.stop()
     value = pts * args.steps * world / (batch_ms * 1e-3) / 1e9
     plain = pts * args.steps / (plain_ms * 1e-3) / 1e9
