@@ -90,7 +90,8 @@ typedef struct fd_options {
     int tile_y;        /* tile rows along y: STREAM 4, 8, 16; TMA (FP32) with tile_z 32:
                           16 or 32, 64: 8 or 16, 128: 8; TMA (16-bit) 32x16 or 64x8;
                           0 = autotune                                              */
-    int x_block;       /* planes per CTA along x; 0 = autotune                     */
+    int x_block;       /* planes per CTA along x (each CTA streams x_block
+                          consecutive planes of one y-z tile); 0 = autotune         */
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
                           fd_read_wavefield/fd_status report FD_ENONFINITE          */
 } fd_options;

@@ -290,7 +290,30 @@ int autotune(fd_handle *hd) {
             if (xb < hd->Nx) xbs.push_back(xb);
         xbs.push_back(hd->Nx);
     }
-    if (tiles.size() == 1 && xbs.size() == 1) {
+    // TMA kernel: add the x_block whose CTA count (tiles x chunks) just fits the GPU's
+    // resident CTA slots once, twice or three times
+    auto tile_xbs = [&](int tz, int ty) {
+        std::vector<int> v = xbs;
+        if (kernel != kTma || force_xb) return v;
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            cudaGetLastError();
+            return v;
+        }
+        const long long warps = (long long)tz * ty / 128;  // 4 points per thread
+        const long long slots = (long long)sms * std::max(1LL, kTmaWarpsPerSM / warps);
+        const long long tiles = (long long)((hd->Nz + tz - 1) / tz) * ((hd->Ny + ty - 1) / ty);
+        for (int waves = 1; waves <= 3; ++waves) {
+            const long long chunks = slots * waves / tiles;  // chunks per tile that still fit
+            if (chunks < 1) continue;
+            const long long xb = (hd->Nx + chunks - 1) / chunks;
+            if (xb >= 4 && xb < hd->Nx && std::find(v.begin(), v.end(), int(xb)) == v.end())
+                v.push_back(int(xb));
+        }
+        return v;
+    };
+    if (tiles.size() == 1 && tile_xbs(tiles[0].first, tiles[0].second).size() == 1) {
         hd->tile_z = tiles[0].first;
         hd->tile_y = tiles[0].second;
         hd->x_block = xbs[0];
@@ -349,6 +372,7 @@ int autotune(fd_handle *hd) {
     for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess && rc == FD_OK; ++ti) {
         TmaMaps map;
         if (kernel == kTma) rc = make_maps(hd, s0, s1, tiles[ti].first, tiles[ti].second, &map);
+        const std::vector<int> xbs = tile_xbs(tiles[ti].first, tiles[ti].second);
         for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess && rc == FD_OK; ++xi) {
             a.x_block = xbs[xi];
             for (int w = 0; w < 2 && e == cudaSuccess; ++w)

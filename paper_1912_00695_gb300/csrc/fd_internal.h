@@ -13,6 +13,10 @@ namespace fdgb {
 constexpr int kMaxRadius = 8;       // space order 16
 constexpr int kMaxRadiusHost = 12;  // host weight generator reaches space order 24
 constexpr int kFusedSources = 4;    // sources injected inside the step kernel
+// TMA kernel: registers capped for 16 resident warps per SM (the kernel is
+// latency-bound: occupancy is worth more than the few spill slots this costs
+// at R = 8).
+constexpr int kTmaWarpsPerSM = 16;
 constexpr int kTileZ = 32;          // streaming tile width along z (one warp)
 constexpr int kMaxDim = 65535;  // keeps every launch grid dimension within limits
 

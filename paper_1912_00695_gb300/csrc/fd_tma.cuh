@@ -46,9 +46,6 @@ template <int R>
 struct TmaPipe {
     static constexpr int STAGES = R >= 7 ? 3 : 4;
 };
-// Registers capped for 16 resident warps per SM (the kernel is latency-bound:
-// occupancy is worth more than the few spill slots this costs at R = 8).
-constexpr int kTmaWarpsPerSM = 16;
 constexpr long long kMbarWaitLimit = 1LL << 22;
 constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
 
@@ -190,11 +187,38 @@ __device__ __forceinline__ float2 ztap_pair(const float *win, int j) {
     return make_float2(win[W0 - j] + win[W0 + j], win[W0 + 1 - j] + win[W0 + 1 + j]);
 }
 
-// The work of one CTA: tile (bz, by) of the y-z plane, x-chunk bx, of the shot
-// described by `a` and `maps`. `smem_raw` is the CTA's dynamic shared memory.
+// Per-CTA accumulators of the max-|value| reduction, carried across segments.
+struct TmaAcc {
+    unsigned amax_bits = 0, damax_bits = 0;
+    bool over = false;
+};
+
+// The ring of stages in dynamic shared memory (128-byte aligned) and its S
+// mbarriers; thread 0 initialises the barriers once per CTA.
+template <int R, int LZ, int W, typename T>
+__device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw) {
+    using G = TmaShape<R, LZ, W, T>;
+    constexpr int S = TmaPipe<R>::STAGES;
+    unsigned char *ring = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    if (threadIdx.x == 0) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
+        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    return ring;
+}
+
+// One segment of a CTA's work: planes [xb, xe) of tile (bz, by) of the y-z plane
+// of the shot described by `a` and `maps`. `g` counts the planes the CTA has
+// already streamed through its ring (it selects the stage and the mbarrier
+// phase, so consecutive segments share one ring without re-initialising it).
+// Returns false if a wait gave up (status set, copies in flight drained).
 template <int R, int FORM, int LZ, int W, typename T>
-__device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, int check, int bz, int by,
-                                        int bx, unsigned char *smem_raw) {
+__device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs &a, const ScaleState &sc, int bz,
+                                            int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc) {
     using G = TmaShape<R, LZ, W, T>;
     using V = Vec4<T>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
@@ -202,8 +226,6 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window values
     constexpr int S = TmaPipe<R>::STAGES;
-    unsigned char *ring = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
 
     const int tid = threadIdx.x;
@@ -213,23 +235,15 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     const int ty = warp * LY + ly;
     const int y = y0 + ty;
     const int z4 = z0 + 4 * lz;
-    const int xb = bx * a.x_block;
-    const int xe = min(xb + a.x_block, a.Nx);
     const bool own = (y < a.Ny) && (z4 < a.Nz);
     const long long P = a.plane;
     const long long col = (long long)y * a.pz + z4;
     const T *__restrict__ u = static_cast<const T *>(a.u) + col;
     T *up = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
     T *un = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
-    // the damping field vanishes inside [bx0,bx1) x [by0,by1) x [bz0,bz1)
-    const ScaleState sc = read_scales<T>(a);
+    const int g0 = g;
+    g += xe - xb;
 
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
     // the whole y-z tile lies where the damping field vanishes (in y and z): such planes
     // inside the box's x range need no g tile
     const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
@@ -256,7 +270,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
         }
     };
     if (tid == 0) {
-        for (int s = 0; s < S - 1 && xb + s < xe; ++s) issue(xb + s, s);
+        for (int s = 0; s < S - 1 && xb + s < xe; ++s) issue(xb + s, (g0 + s) % S);
         for (int d = 1; d <= kPrefetchAhead; ++d) prefetch(xb + d);
     }
 
@@ -286,11 +300,13 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
     const float2 su2 = f2(sc.s_u, sc.s_u), sd2 = f2(sc.s_d, sc.s_d);
     const int rowc = ty + R;
     const int colw = 4 * lz;  // first element of the thread's z window in a tile row
-    unsigned amax_bits = 0, damax_bits = 0;
-    bool over = false;
+    unsigned amax_bits = acc.amax_bits, damax_bits = acc.damax_bits;
+    bool over = acc.over;
     bool failed = false;
     int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
     int it_failed = 0;                  // first plane whose wait gave up
+    int stage = g0 % S;                 // ring stage and mbarrier phase of the current plane
+    uint32_t phase = uint32_t(g0 / S) & 1u;
 
     for (int xo = xb; xo < xe; xo += U) {
 #pragma unroll
@@ -298,8 +314,7 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
             const int x = xo + i;
             if (x >= xe) break;
             const int it = x - xb;
-            const int stage = it % S;
-            const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), uint32_t(it / S) & 1u);
+            const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), phase);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 it_failed = it;
@@ -307,8 +322,10 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
             }
             if (tid == 0) {
                 if (x + S - 1 < xe) {
+                    // plane x + S - 1 takes the stage of plane x - 1, which every thread has
+                    // finished reading (it passed the barrier above)
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(x + S - 1, (it + S - 1) % S);
+                    issue(x + S - 1, stage == 0 ? S - 1 : stage - 1);
                     ++issued;
                 }
                 prefetch(x + 1 + kPrefetchAhead);
@@ -458,6 +475,10 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
                 }
                 V::st(up + x * P, out);
             }
+            if (++stage == S) {
+                stage = 0;
+                phase ^= 1u;
+            }
         }
         if (failed) break;
 #pragma unroll
@@ -468,19 +489,34 @@ __device__ __forceinline__ void tma_cta(const TmaMaps *maps, const StepArgs &a, 
         if (tid == 0) {
             if (a.status) atomicOr(a.status, kStatusTimeout);
             for (int it = it_failed; it < issued; ++it)
-                mbar_wait_bounded(smem_addr(&bars[it % S]), uint32_t(it / S) & 1u);
+                mbar_wait_bounded(smem_addr(&bars[(g0 + it) % S]), uint32_t((g0 + it) / S) & 1u);
         }
-        return;
+        return false;
     }
-    if (check) reduce_amax(a, amax_bits, over, damax_bits);
+    acc.amax_bits = amax_bits;
+    acc.damax_bits = damax_bits;
+    acc.over = over;
+    return true;
 }
 
+// Single-shot step: CTA (bz, by, bx) streams planes [bx x_block, (bx+1) x_block)
+// of tile (bz, by). The grid runs z-tiles fastest and x-chunks slowest, so the
+// CTAs resident at any moment cover neighbouring tiles at the same planes and
+// share their halo rows in L2.
 template <int R, int FORM, int LZ, int W, typename T>
 __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
                                                         const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
-    tma_cta<R, FORM, LZ, W, T>(&maps, a, check, blockIdx.x, blockIdx.y, blockIdx.z, smem_dyn);
+    unsigned char *ring = tma_ring_init<R, LZ, W, T>(smem_dyn);
+    const ScaleState sc = read_scales<T>(a);
+    const int xb = blockIdx.z * a.x_block;
+    int g = 0;
+    TmaAcc acc;
+    if (tma_segment<R, FORM, LZ, W, T>(&maps, a, sc, blockIdx.x, blockIdx.y, xb, min(xb + a.x_block, a.Nx), ring,
+                                       g, acc) &&
+        check)
+        reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
@@ -501,7 +537,8 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
 // Batched form: one CTA per work item (shot, bz, by, bx) of a device table, so
 // many uneven shots advance in one launch. Each CTA copies its shot's step
 // arguments into shared memory (with the step index of this launch) and runs
-// the same per-CTA schedule as the single-shot kernel.
+// one segment (planes [bx x_block, (bx+1) x_block) of tile (bz, by)) of the
+// single-shot kernel's schedule.
 template <int R, int FORM, int LZ, int W, typename T>
 __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
                                                               const int4 *__restrict__ items, int offset) {
@@ -524,7 +561,13 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_batch_kerne
     }
     __syncthreads();
     publish_scales<T>(sa, it.y == 0 && it.z == 0 && it.w == 0 && threadIdx.x == 0);
-    tma_cta<R, FORM, LZ, W, T>(maps, sa, 1, it.y, it.z, it.w, smem_dyn);
+    unsigned char *ring = tma_ring_init<R, LZ, W, T>(smem_dyn);
+    const ScaleState sc = read_scales<T>(sa);
+    const int xb = it.w * sa.x_block;
+    int g = 0;
+    TmaAcc acc;
+    if (tma_segment<R, FORM, LZ, W, T>(maps, sa, sc, it.y, it.z, xb, min(xb + sa.x_block, sa.Nx), ring, g, acc))
+        reduce_amax(sa, acc.amax_bits, acc.over, acc.damax_bits);
 }
 
 template <int R, int FORM, int LZ, int W, typename T>

@@ -43,6 +43,7 @@ class Request:
     result: np.ndarray | None = field(default=None, repr=False)
     admitted: float = -1.0
     completed: float = -1.0
+    visible: float = 0.0      # when the server could first see it (latency is measured from here)
 
     @property
     def points(self) -> int:
@@ -131,7 +132,8 @@ class Server:
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         """Serve a trace. With realtime, requests become visible at their arrival
-        times on the wall clock; otherwise all are visible at once (offline)."""
+        times on the wall clock; otherwise all are visible at once (offline) and
+        latencies count from the start of the run."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         waiting: deque[Request] = deque()
         finished: list[Request] = []
@@ -140,7 +142,9 @@ class Server:
         while pending or waiting or self.active:
             now = now_fn()
             while pending and (not realtime or pending[0].arrival <= now):
-                waiting.append(pending.popleft())
+                r = pending.popleft()
+                r.visible = r.arrival if realtime else 0.0
+                waiting.append(r)
             while waiting and self.admit(waiting[0], now):
                 waiting.popleft()
             if waiting and not self.active:
@@ -161,7 +165,7 @@ class Server:
 
 
 def summarize(finished: list[Request], makespan: float) -> dict:
-    lat = np.array([r.completed - r.arrival for r in finished]) if finished else np.zeros(1)
+    lat = np.array([r.completed - r.visible for r in finished]) if finished else np.zeros(1)
     pts = sum(r.points * r.nt for r in finished)
     return {"requests": len(finished), "makespan_s": makespan,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
