@@ -519,7 +519,7 @@ def run_serving(args, rank: int, world: int):
         "at_trace_rate": {k: round(v, 4) if isinstance(v, float) else v for k, v in at_rate.items()},
         "at_70pct_capacity": dict({k: round(v, 4) if isinstance(v, float) else v for k, v in at70.items()},
                                   rate_per_s=round(args.rate / scale70, 3)),
-        "gpu_launches": None,
+        "gpu_launches": at_rate["gpu_launches"],
         "clocks": clk,
     }
     if rank == 0:

@@ -45,17 +45,43 @@ def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x
     return o
 
 
+class PendingRead:
+    """A shot's wavefield on its way to pinned host memory (stream-ordered after
+    the launches queued before it); ``ready()`` polls, ``result()`` waits."""
+
+    def __init__(self, host, event, keep):
+        self._host = host
+        self._event = event
+        self._keep = keep  # device staging, alive until the copy ran
+
+    def ready(self) -> bool:
+        return self._event.query()
+
+    def result(self) -> np.ndarray:
+        self._event.synchronize()
+        self._keep = None
+        return self._host.numpy()
+
+
 class Batch:
-    """A batch of uneven shots advanced together (owns its device state)."""
+    """A batch of uneven shots advanced together (owns its device state).
+
+    With ``stream`` (a ``torch.cuda.Stream``) every launch, upload and read of
+    the batch is queued on that stream; ``read_async`` and ``mark`` then give
+    stream-ordered completion handles, so a host loop can keep several chunks
+    queued per batch without synchronising."""
 
     def __init__(self, space_order, h, storage="f32", form="factored", tile_z=0, tile_y=0,
-                 x_block=0):
+                 x_block=0, stream=None):
         self.space_order = int(space_order)
         self.h = float(h)
         self.handle = fd_batch_create(space_order, h, options(storage=storage, form=form,
                                                               tile_z=tile_z, tile_y=tile_y,
                                                               x_block=x_block))
         self.shapes = {}
+        self.stream = stream
+        if stream is not None:
+            fd_batch_set_stream(self.handle, stream.cuda_stream)
 
     def add(self, interior, nbl, dt, m, eta=None) -> int:
         nx, ny, nz = interior
@@ -77,6 +103,32 @@ class Batch:
         if out is None:
             out = np.empty(self.shapes[slot], dtype=np.float32)
         return fd_batch_read(self.handle, slot, out, level)
+
+    def read_async(self, slot, level=0) -> PendingRead:
+        """Start copying the shot's wavefield (dense FP32) to pinned host memory
+        without waiting; the shot may be removed right after this call."""
+        import torch
+        if self.stream is None:
+            raise RuntimeError("read_async needs a batch created with a torch stream")
+        shape = self.shapes[slot]
+        with torch.cuda.stream(self.stream):
+            dev = torch.empty(shape, dtype=torch.float32, device="cuda")
+            fd_batch_read_device(self.handle, slot, dev.data_ptr(), level)
+            host = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+            host.copy_(dev, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        dev.record_stream(self.stream)
+        return PendingRead(host, ev, dev)
+
+    def mark(self):
+        """An event recorded after the work queued so far (``ready()``/``wait()``)."""
+        import torch
+        if self.stream is None:
+            raise RuntimeError("mark needs a batch created with a torch stream")
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return _Mark(ev)
 
     def step(self, slot) -> int:
         return fd_batch_shot_step(self.handle, slot)
@@ -112,6 +164,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class _Mark:
+    def __init__(self, ev):
+        self._ev = ev
+
+    def ready(self) -> bool:
+        return self._ev.query()
+
+    def wait(self):
+        self._ev.synchronize()
 
 
 class Shot:

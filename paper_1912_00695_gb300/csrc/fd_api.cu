@@ -58,6 +58,49 @@ struct GraphEntry {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync) from the
+// device's default pool, whose release threshold is raised once per device so
+// that freed blocks stay cached: shots created and retired at a high rate (a
+// serving loop) reuse memory without driver allocations, and freeing a shot's
+// fields never synchronises the device (a plain cudaFree would stall every
+// stream, including other batches' launches).
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool_ready[dev]) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                cuuint64_t thr = ~cuuint64_t(0);
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            cudaGetLastError();
+            g_pool_ready[dev] = true;
+        }
+    }
+    e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {  // the bulk tensor copies need aligned bases
+        cudaFreeAsync(*p, s);
+        *p = nullptr;
+        return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -339,12 +382,13 @@ int autotune(fd_handle *hd) {
     const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
     const bool inc = hd->opt.storage != kF32;  // increment form needs a third field
     void *s0 = nullptr, *s1 = nullptr, *s2 = nullptr, *aux = nullptr;
-    if (cudaMalloc(&s0, ub) != cudaSuccess || cudaMalloc(&s1, ub) != cudaSuccess ||
-        (inc && cudaMalloc(&s2, ub) != cudaSuccess) || cudaMalloc(&aux, 256) != cudaSuccess) {
+    if (dev_alloc(&s0, ub, hd->stream) != cudaSuccess || dev_alloc(&s1, ub, hd->stream) != cudaSuccess ||
+        (inc && dev_alloc(&s2, ub, hd->stream) != cudaSuccess) || dev_alloc(&aux, 256, hd->stream) != cudaSuccess) {
         cudaGetLastError();
-        if (s0) cudaFree(s0);
-        if (s1) cudaFree(s1);
-        if (s2) cudaFree(s2);
+        dev_free(s0, hd->stream);
+        dev_free(s1, hd->stream);
+        dev_free(s2, hd->stream);
+        dev_free(aux, hd->stream);
         // not enough memory for scratch fields: take the first shape, heuristic x_block
         hd->tile_z = tiles[0].first;
         hd->tile_y = tiles[0].second;
@@ -392,11 +436,11 @@ int autotune(fd_handle *hd) {
         }
     }
     if (e != cudaSuccess && rc == FD_OK) rc = fail(FD_ECUDA, "autotune launch failed: %s", cudaGetErrorString(e));
+    dev_free(s0, hd->stream);
+    dev_free(s1, hd->stream);
+    dev_free(s2, hd->stream);
+    dev_free(aux, hd->stream);
     cudaStreamSynchronize(hd->stream);
-    cudaFree(s0);
-    cudaFree(s1);
-    if (s2) cudaFree(s2);
-    cudaFree(aux);
     if (rc != FD_OK) return rc;
     hd->tile_z = tiles[best_t].first;
     hd->tile_y = tiles[best_t].second;
@@ -409,8 +453,8 @@ int autotune(fd_handle *hd) {
 }
 
 int upload_sources(fd_handle *hd) {
-    if (hd->d_wavelet) cudaFree(hd->d_wavelet);
-    if (hd->d_src) cudaFree(hd->d_src);
+    dev_free(hd->d_wavelet, hd->stream);
+    dev_free(hd->d_src, hd->stream);
     hd->d_wavelet = nullptr;
     hd->d_src = nullptr;
     const int ns = int(hd->sources.size());
@@ -426,8 +470,8 @@ int upload_sources(fd_handle *hd) {
         xyz[ns + s] = hd->sources[s].y;
         xyz[2 * ns + s] = hd->sources[s].z;
     }
-    if (cudaMalloc(&hd->d_wavelet, w.size() * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&hd->d_src, xyz.size() * sizeof(int)) != cudaSuccess)
+    if (dev_alloc(reinterpret_cast<void **>(&hd->d_wavelet), w.size() * sizeof(float), hd->stream) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_src), xyz.size() * sizeof(int), hd->stream) != cudaSuccess)
         return fail(FD_ENOMEM, "cannot allocate source arrays");
     FD_CUDA(cudaMemcpyAsync(hd->d_wavelet, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice,
                             hd->stream));
@@ -444,8 +488,9 @@ int update_src_bound(fd_handle *hd) {
         for (auto &s : hd->sources) {
             const size_t p = size_t(s.x) * hd->plane + size_t(s.y) * hd->pz + s.z;
             float f1 = 0, f2 = 0;
-            FD_CUDA(cudaMemcpy(&f1, hd->f1 + p, sizeof(float), cudaMemcpyDeviceToHost));
-            FD_CUDA(cudaMemcpy(&f2, hd->f2 + p, sizeof(float), cudaMemcpyDeviceToHost));
+            FD_CUDA(cudaMemcpyAsync(&f1, hd->f1 + p, sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
+            FD_CUDA(cudaMemcpyAsync(&f2, hd->f2 + p, sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
+            FD_CUDA(cudaStreamSynchronize(hd->stream));
             const double w = hd->opt.form == kExpanded ? hd->dt * hd->dt / (f1 + 0.5 * hd->dt * f2) : f1;
             double qmax = 0.0;
             for (float q : s.wavelet) qmax = std::max(qmax, std::fabs(double(q)));
@@ -518,6 +563,22 @@ cudaError_t unpack_to(fd_handle *hd, int level, float *dst) {
                                    hd->d_scales, slot, hd->stream);
     return launch_unpack_prev(hd->ubuf[hd->cur], hd->dbuf, dst, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->opt.storage,
                               hd->d_scales, slot, hd->stream);
+}
+
+// Free a handle's device memory in the order of its stream (after the work
+// already queued there) and its host resources, without waiting for the device.
+void release_handle(fd_handle *hd) {
+    for (auto &g : hd->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    hd->graphs.clear();
+    cudaStream_t st = hd->stream ? hd->stream : hd->own_stream;
+    void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
+                    hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack};
+    for (void *p : bufs) dev_free(p, st);
+    if (hd->ev0) cudaEventDestroy(hd->ev0);
+    if (hd->ev1) cudaEventDestroy(hd->ev1);
+    if (hd->own_stream) cudaStreamDestroy(hd->own_stream);  // released once its work completes
+    delete hd;
 }
 
 int read_status(fd_handle *hd) {
@@ -628,17 +689,20 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         fd_destroy(hd);
         return fail(code, "%s", msg);
     };
-    if (cudaStreamCreate(&hd->own_stream) != cudaSuccess) return bail(FD_ECUDA, "cudaStreamCreate failed");
+    if (cudaStreamCreateWithFlags(&hd->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(FD_ECUDA, "cudaStreamCreate failed");
     hd->stream = hd->own_stream;
     if (cudaEventCreate(&hd->ev0) != cudaSuccess || cudaEventCreate(&hd->ev1) != cudaSuccess)
         return bail(FD_ECUDA, "cudaEventCreate failed");
     const size_t ub = hd->n_pitched * elem_size(opt.storage), fb = hd->n_pitched * sizeof(float);
-    if (cudaMalloc(&hd->ubuf[0], ub) != cudaSuccess || cudaMalloc(&hd->ubuf[1], ub) != cudaSuccess ||
-        (opt.storage != kF32 && cudaMalloc(&hd->dbuf, ub) != cudaSuccess) ||
-        cudaMalloc(&hd->f1, fb) != cudaSuccess || cudaMalloc(&hd->f2, fb) != cudaSuccess ||
-        cudaMalloc(&hd->d_status, sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&hd->d_scales, sizeof(LevelScales)) != cudaSuccess ||
-        cudaMalloc(&hd->d_check, sizeof(ModelCheck)) != cudaSuccess) {
+    cudaStream_t st = hd->stream;
+    if (dev_alloc(&hd->ubuf[0], ub, st) != cudaSuccess || dev_alloc(&hd->ubuf[1], ub, st) != cudaSuccess ||
+        (opt.storage != kF32 && dev_alloc(&hd->dbuf, ub, st) != cudaSuccess) ||
+        dev_alloc(reinterpret_cast<void **>(&hd->f1), fb, st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->f2), fb, st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_status), sizeof(unsigned), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_scales), sizeof(LevelScales), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_check), sizeof(ModelCheck), st) != cudaSuccess) {
         cudaGetLastError();
         return bail(FD_ENOMEM, "device allocation failed");
     }
@@ -784,7 +848,8 @@ int fd_read_wavefield(fd_handle *hd, float *out, int level) {
                                   size_t(hd->Nx) * hd->Ny, cudaMemcpyDeviceToHost, hd->stream));
     } else {
         const size_t n = size_t(hd->Nx) * hd->Ny * hd->Nz;
-        if (!hd->d_unpack && cudaMalloc(&hd->d_unpack, n * sizeof(float)) != cudaSuccess)
+        if (!hd->d_unpack &&
+            dev_alloc(reinterpret_cast<void **>(&hd->d_unpack), n * sizeof(float), hd->stream) != cudaSuccess)
             return fail(FD_ENOMEM, "cannot allocate the read-back buffer");
         FD_CUDA(unpack_to(hd, level, hd->d_unpack));
         FD_CUDA(cudaMemcpyAsync(out, hd->d_unpack, n * sizeof(float), cudaMemcpyDeviceToHost, hd->stream));
@@ -842,7 +907,8 @@ int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long 
             scale[l] = std::ldexp(1.0f, e);
         }
     float *tmp = nullptr;
-    if (cudaMalloc(&tmp, n * sizeof(float)) != cudaSuccess) return fail(FD_ENOMEM, "cannot allocate staging buffer");
+    if (dev_alloc(reinterpret_cast<void **>(&tmp), n * sizeof(float), hd->stream) != cudaSuccess)
+        return fail(FD_ENOMEM, "cannot allocate staging buffer");
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
         e = cudaMemcpyAsync(tmp, lv[l], n * sizeof(float), cudaMemcpyHostToDevice, hd->stream);
@@ -859,8 +925,8 @@ int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long 
     // the accumulators of the level the next step writes start at zero
     if (e == cudaSuccess) e = launch_set_level_scale(hd->d_scales, next, 1.0f, 0u, 1.0f, 0u, hd->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream);
+    dev_free(tmp, hd->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
     hd->step = step;
     hd->cur = 0;
@@ -914,15 +980,7 @@ int fd_last_forward_ms(fd_handle *hd, float *ms) {
 int fd_destroy(fd_handle *hd) {
     if (!hd) return FD_OK;
     if (hd->stream) cudaStreamSynchronize(hd->stream);
-    destroy_graphs(hd);
-    void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
-                    hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack};
-    for (void *p : bufs)
-        if (p) cudaFree(p);
-    if (hd->ev0) cudaEventDestroy(hd->ev0);
-    if (hd->ev1) cudaEventDestroy(hd->ev1);
-    if (hd->own_stream) cudaStreamDestroy(hd->own_stream);
-    delete hd;
+    release_handle(hd);
     return FD_OK;
 }
 
@@ -954,13 +1012,70 @@ struct fd_batch {
         unsigned long long gen = 0;
     };
     std::vector<Graph> graphs;
-    cudaStream_t own_stream = nullptr, stream = nullptr;
+    std::vector<int> seen_nt;              // chunk lengths launched once with this work list
+    std::vector<cudaGraphExec_t> retired;  // replaced graphs, destroyed once the stream is idle
     std::vector<BatchShot> host_table;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    cudaEvent_t join_ev = nullptr;
+    // pinned staging for the argument table and the work list: uploads are
+    // asynchronous, a buffer is rewritten only after its previous copy ran
+    static constexpr int kStaging = 4;
+    struct Staging {
+        void *host = nullptr;
+        size_t cap = 0;
+        cudaEvent_t done = nullptr;
+    };
+    Staging staging[kStaging];
+    int next_staging = 0;
 };
 
 namespace {
 
 constexpr int kBatchXBlock = 96;
+
+// Copy `bytes` from host memory to `dst` on the batch stream through the next
+// pinned staging buffer (no host synchronisation unless that buffer's previous
+// copy has not run yet).
+int batch_stage_upload(fd_batch *b, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return FD_OK;
+    fd_batch::Staging &sg = b->staging[b->next_staging];
+    b->next_staging = (b->next_staging + 1) % fd_batch::kStaging;
+    if (sg.done) FD_CUDA(cudaEventSynchronize(sg.done));
+    if (sg.cap < bytes) {
+        if (sg.host) cudaFreeHost(sg.host);
+        sg.host = nullptr;
+        sg.cap = 0;
+        const size_t cap = std::max<size_t>(bytes, 4096) * 2;
+        if (cudaMallocHost(&sg.host, cap) != cudaSuccess) return fail(FD_ENOMEM, "cannot allocate pinned staging");
+        sg.cap = cap;
+    }
+    if (!sg.done) FD_CUDA(cudaEventCreateWithFlags(&sg.done, cudaEventDisableTiming));
+    std::memcpy(sg.host, src, bytes);
+    FD_CUDA(cudaMemcpyAsync(dst, sg.host, bytes, cudaMemcpyHostToDevice, b->stream));
+    FD_CUDA(cudaEventRecord(sg.done, b->stream));
+    return FD_OK;
+}
+
+// Grow a device array of the batch (stream-ordered: the old one is freed after
+// the launches already queued that read it).
+int batch_reserve(fd_batch *b, void **ptr, size_t *cap, size_t need, size_t elem) {
+    if (need <= *cap) return FD_OK;
+    dev_free(*ptr, b->stream);
+    *ptr = nullptr;
+    *cap = 0;
+    const size_t n = std::max<size_t>(need, 2 * *cap);
+    if (dev_alloc(ptr, n * elem, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FD_ENOMEM, "cannot allocate a batch table");
+    }
+    *cap = n;
+    return FD_OK;
+}
+
+void batch_destroy_retired(fd_batch *b) {
+    for (auto e : b->retired) cudaGraphExecDestroy(e);
+    b->retired.clear();
+}
 
 int batch_rebuild(fd_batch *b) {
     b->order.clear();
@@ -968,6 +1083,13 @@ int batch_rebuild(fd_batch *b) {
     for (size_t s = 0; s < b->slots.size(); ++s) {
         fd_handle *hd = b->slots[s];
         if (!hd) continue;
+        if (hd->stream != b->stream) {
+            // a shot set up on its own stream joins the batch stream: the batch's next
+            // launches wait for its set-up work (already finished in the usual case)
+            FD_CUDA(cudaEventRecord(b->join_ev, hd->stream));
+            FD_CUDA(cudaStreamWaitEvent(b->stream, b->join_ev, 0));
+            hd->stream = b->stream;
+        }
         const int idx = int(b->order.size());
         b->order.push_back(int(s));
         const int tz = (hd->Nz + b->tile_z - 1) / b->tile_z, ty = (hd->Ny + b->tile_y - 1) / b->tile_y;
@@ -976,31 +1098,22 @@ int batch_rebuild(fd_batch *b) {
             for (int y = 0; y < ty; ++y)
                 for (int z = 0; z < tz; ++z) items.push_back(make_int4(idx, z, y, x));
     }
-    const size_t ns = b->order.size();
-    if (ns > b->cap_shots) {
-        if (b->d_shots) cudaFree(b->d_shots);
-        b->d_shots = nullptr;
-        b->cap_shots = 0;
-        if (cudaMalloc(&b->d_shots, ns * sizeof(BatchShot)) != cudaSuccess)
-            return fail(FD_ENOMEM, "cannot allocate the batch table");
-        b->cap_shots = ns;
-    }
-    if (items.size() > b->cap_items) {
-        if (b->d_items) cudaFree(b->d_items);
-        b->d_items = nullptr;
-        b->cap_items = 0;
-        if (cudaMalloc(&b->d_items, items.size() * sizeof(int4)) != cudaSuccess)
-            return fail(FD_ENOMEM, "cannot allocate the batch work list");
-        b->cap_items = items.size();
-    }
-    if (!items.empty())
-        FD_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                                b->stream));
-    FD_CUDA(cudaStreamSynchronize(b->stream));
+    int rc = batch_reserve(b, reinterpret_cast<void **>(&b->d_shots), &b->cap_shots, b->order.size(),
+                           sizeof(BatchShot));
+    if (rc == FD_OK)
+        rc = batch_reserve(b, reinterpret_cast<void **>(&b->d_items), &b->cap_items, items.size(), sizeof(int4));
+    if (rc == FD_OK) rc = batch_stage_upload(b, b->d_items, items.data(), items.size() * sizeof(int4));
+    if (rc != FD_OK) return rc;
     b->n_items = int(items.size());
+    // graphs of the old work list may still be queued: retire them, destroy them later
     for (auto &g : b->graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.exec) b->retired.push_back(g.exec);
     b->graphs.clear();
+    b->seen_nt.clear();
+    if (b->retired.size() > 64) {
+        FD_CUDA(cudaStreamSynchronize(b->stream));
+        batch_destroy_retired(b);
+    }
     b->dirty = false;
     b->gen++;
     return FD_OK;
@@ -1018,12 +1131,7 @@ int batch_upload_table(fd_batch *b) {
         t.cur0 = hd->cur;
         t.step0 = hd->step;
     }
-    if (!b->host_table.empty())
-        FD_CUDA(cudaMemcpyAsync(b->d_shots, b->host_table.data(), b->host_table.size() * sizeof(BatchShot),
-                                cudaMemcpyHostToDevice, b->stream));
-    // the host table may be rewritten by the next call: let this copy finish
-    FD_CUDA(cudaStreamSynchronize(b->stream));
-    return FD_OK;
+    return batch_stage_upload(b, b->d_shots, b->host_table.data(), b->host_table.size() * sizeof(BatchShot));
 }
 
 fd_handle *batch_shot(fd_batch *b, int slot) {
@@ -1078,7 +1186,9 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
     b->opt.check_finite = 1;
     b->tile_z = tz;
     b->tile_y = ty;
-    if (cudaStreamCreate(&b->own_stream) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (b->own_stream) cudaStreamDestroy(b->own_stream);
         delete b;
         return fail(FD_ECUDA, "cudaStreamCreate failed");
     }
@@ -1097,8 +1207,10 @@ int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const 
     fd_handle *hd = nullptr;
     int rc = fd_acoustic_create_ex(nx, ny, nz, b->k, b->h, dt, nbl, &opt, &hd);
     if (rc != FD_OK) return rc;
-    rc = fd_set_stream(hd, b->stream);
-    if (rc == FD_OK) rc = fd_set_model(hd, m, eta);
+    // set-up (model upload and checks, sources) runs on the shot's own stream, so it
+    // neither waits for nor stalls the batch's launches; the shot moves to the batch
+    // stream when the next forward rebuilds the work list
+    rc = fd_set_model(hd, m, eta);
     if (rc == FD_OK) rc = autotune(hd);
     if (rc == FD_OK) rc = build_maps(hd);
     if (rc != FD_OK) {
@@ -1135,12 +1247,11 @@ int fd_batch_inject(fd_batch *b, int slot, int ix, int iy, int iz, const float *
 int fd_batch_remove(fd_batch *b, int slot) {
     fd_handle *hd = batch_shot(b, slot);
     if (!hd) return fail(FD_EINVAL, "no shot in slot %d", slot);
-    FD_CUDA(cudaStreamSynchronize(b->stream));
     b->slots[slot] = nullptr;
     b->dirty = true;
-    // the handle's stream is the batch stream, which fd_destroy must not destroy
-    hd->stream = hd->own_stream;
-    return fd_destroy(hd);
+    // its fields are freed in stream order, after the launches already queued that use them
+    release_handle(hd);
+    return FD_OK;
 }
 
 int fd_batch_forward(fd_batch *b, int nt) {
@@ -1156,7 +1267,18 @@ int fd_batch_forward(fd_batch *b, int nt) {
     fd_batch::Graph *g = nullptr;
     for (auto &e : b->graphs)
         if (e.nt == nt && e.gen == b->gen) g = &e;
-    if (!g) {
+    // a chunk length seen for the first time with this work list is launched
+    // directly (capturing a graph costs more than one replay saves); the second
+    // time it is captured and replayed from then on
+    const bool first = std::find(b->seen_nt.begin(), b->seen_nt.end(), nt) == b->seen_nt.end();
+    if (!g && first) {
+        b->seen_nt.push_back(nt);
+        for (int i = 0; i < nt; ++i) {
+            cudaError_t err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y,
+                                                    b->d_shots, b->d_items, b->n_items, i, b->stream);
+            if (err != cudaSuccess) return fail(FD_ECUDA, "batch launch failed: %s", cudaGetErrorString(err));
+        }
+    } else if (!g) {
         cudaGraph_t graph = nullptr;
         FD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
@@ -1173,13 +1295,13 @@ int fd_batch_forward(fd_batch *b, int nt) {
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) return fail(FD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
         if (b->graphs.size() >= 8) {
-            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->retired.push_back(b->graphs.front().exec);  // may still be queued
             b->graphs.erase(b->graphs.begin());
         }
         b->graphs.push_back({exec, nt, b->gen});
         g = &b->graphs.back();
     }
-    FD_CUDA(cudaGraphLaunch(g->exec, b->stream));
+    if (g) FD_CUDA(cudaGraphLaunch(g->exec, b->stream));
     for (int s : b->order) {
         fd_handle *hd = b->slots[s];
         hd->step += nt;
@@ -1243,6 +1365,7 @@ int fd_batch_set_stream(fd_batch *b, void *cuda_stream) {
 int fd_batch_synchronize(fd_batch *b) {
     if (!b) return fail(FD_EINVAL, "batch is NULL");
     FD_CUDA(cudaStreamSynchronize(b->stream));
+    batch_destroy_retired(b);
     return FD_OK;
 }
 
@@ -1251,13 +1374,20 @@ int fd_batch_destroy(fd_batch *b) {
     cudaStreamSynchronize(b->stream);
     for (auto *hd : b->slots)
         if (hd) {
-            hd->stream = hd->own_stream;
-            fd_destroy(hd);
+            cudaStreamSynchronize(hd->stream);
+            release_handle(hd);
         }
     for (auto &g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (b->d_shots) cudaFree(b->d_shots);
-    if (b->d_items) cudaFree(b->d_items);
+    batch_destroy_retired(b);
+    dev_free(b->d_shots, b->stream);
+    dev_free(b->d_items, b->stream);
+    cudaStreamSynchronize(b->stream);
+    for (auto &sg : b->staging) {
+        if (sg.done) cudaEventDestroy(sg.done);
+        if (sg.host) cudaFreeHost(sg.host);
+    }
+    if (b->join_ev) cudaEventDestroy(b->join_ev);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
     return FD_OK;

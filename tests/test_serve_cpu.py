@@ -6,6 +6,22 @@ import numpy as np
 from paper_1912_00695_gb300.serve import Request, Server
 
 
+class _Done:
+    """A completion handle that is ready at once (the fake batch is synchronous)."""
+
+    def __init__(self, value):
+        self.value = value
+
+    def ready(self):
+        return True
+
+    def result(self):
+        return self.value
+
+    def wait(self):
+        pass
+
+
 class FakeBatch:
     def __init__(self, k, h, storage):
         self.steps = {}
@@ -31,8 +47,11 @@ class FakeBatch:
     def synchronize(self):
         pass
 
-    def wavefield(self, slot):
-        return np.full(3, float(self.steps[slot]))
+    def read_async(self, slot):
+        return _Done(np.full(3, float(self.steps[slot])))
+
+    def mark(self):
+        return _Done(None)
 
     def remove(self, slot):
         del self.steps[slot]
@@ -54,7 +73,7 @@ def test_admission_budget_fifo_and_exact_steps():
                  bytes_fn=lambda r: r.size)
     stats = srv.run(reqs, realtime=False)
     assert stats["requests"] == 5
-    assert srv.peak_used <= 5 and srv.used == 0 and not srv.active
+    assert srv.peak_used <= 5 and srv.used == 0 and not srv.active and not srv.reads
     for r in reqs:
         assert r.result[0] == r.nt  # every shot took exactly its steps
         assert r.completed >= r.admitted >= 0
