@@ -396,41 +396,55 @@ def run_precision(args, rank: int, world: int):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    spec = inputs.precision_shot(n=args.n_precision, nt=args.nt_precision)
-    dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
-    m = spec.m
-    wav = inputs.ricker(spec.f0, dt, spec.nt)
-    res = {}
     peak, peak_kind = _peaks()
     clk = None
-    for st in ("f32", "bf16", "f16"):
-        shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, storage=st)
-        shot.set_model(m)
-        shot.inject(*spec.source, wav)
-        shot.set_stream(stream.cuda_stream)
-        for _ in range(args.warmup):
-            shot.reset()
-            shot.forward(spec.nt)
-        torch.cuda.synchronize()
-        clocks = ClockSampler(dev)
-        if st == "bf16":
-            clocks.start()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            shot.reset()
-            shot.forward(spec.nt)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        if st == "bf16":
-            clk = clocks.stop()
-        ms = ev0.elapsed_time(ev1)
-        gpts = spec.points * spec.nt * args.steps / (ms * 1e-3) / 1e9
-        alg = algorithmic_bytes_per_step(spec, st) * spec.nt * args.steps
-        res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / args.steps, 3),
-                   "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config)}
-        shot.close()
+
+    def measure(spec, sample_clocks):
+        nonlocal clk
+        dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+        m = spec.m
+        wav = inputs.ricker(spec.f0, dt, spec.nt)
+        res = {}
+        for st in ("f32", "bf16", "f16"):
+            shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, storage=st)
+            shot.set_model(m)
+            shot.inject(*spec.source, wav)
+            shot.set_stream(stream.cuda_stream)
+            for _ in range(args.warmup):
+                shot.reset()
+                shot.forward(spec.nt)
+            torch.cuda.synchronize()
+            clocks = ClockSampler(dev)
+            if sample_clocks and st == "bf16":
+                clocks.start()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                shot.reset()
+                shot.forward(spec.nt)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if sample_clocks and st == "bf16":
+                clk = clocks.stop()
+            ms = ev0.elapsed_time(ev1)
+            gpts = spec.points * spec.nt * args.steps / (ms * 1e-3) / 1e9
+            alg = algorithmic_bytes_per_step(spec, st) * spec.nt * args.steps
+            res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / args.steps, 3),
+                       "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config)}
+            shot.close()
+        return res
+
+    spec = inputs.precision_shot(n=args.n_precision, nt=args.nt_precision)
+    res = measure(spec, True)
+    # the same storages on the 256^3 + 10 sweep shot at every requested space order
+    by_order = {}
+    for k in args.precision_orders:
+        sp = inputs.sweep_shot(k, n=args.n, nt=min(args.nt, args.nt_precision))
+        r = measure(sp, False)
+        by_order[f"so{k}"] = {st: {"gpts": v["gpts"], "hbm_frac": v["hbm_frac"]} for st, v in r.items()}
+        by_order[f"so{k}"]["bf16_vs_f32"] = round(r["bf16"]["gpts"] / r["f32"]["gpts"], 3)
+        by_order[f"so{k}"]["f16_vs_f32"] = round(r["f16"]["gpts"] / r["f32"]["gpts"], 3)
     line = {
         "metric": "Gpts/s with BF16 wavefield storage (per-level scale, FP32 arithmetic) vs FP32 "
                   "storage, 384^3+20, space order 12",
@@ -444,6 +458,7 @@ def run_precision(args, rank: int, world: int):
         "by_storage": res,
         "speedup_bf16_vs_f32": round(res["bf16"]["gpts"] / res["f32"]["gpts"], 3),
         "speedup_f16_vs_f32": round(res["f16"]["gpts"] / res["f32"]["gpts"], 3),
+        "sweep_shot_by_order": by_order,
         "roofline": {"bound": "hbm", "achieved": round(res["bf16"]["hbm_frac"] * peak, 1), "peak": peak,
                      "unit": "GB/s", "frac": res["bf16"]["hbm_frac"], "traffic": None,
                      "kernel": "fd_tma_kernel (bf16)", "peak_source": peak_kind},
@@ -639,6 +654,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=50, help="serving: steps per scheduling chunk")
     ap.add_argument("--n-precision", type=int, default=384, help="precision workload: interior size")
     ap.add_argument("--nt-precision", type=int, default=1000, help="precision workload: steps")
+    ap.add_argument("--precision-orders", type=lambda v: tuple(int(x) for x in v.split(",") if x), default=(),
+                    help="precision workload: also compare the storages on the sweep shot at these orders")
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
     ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = the library default)")

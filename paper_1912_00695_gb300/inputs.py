@@ -164,10 +164,10 @@ def batched_shots(seed: int = 0, count: int = 64, lo: int = 96, hi: int = 256, n
     return out
 
 
-def precision_shot(n: int = 384, nbl: int = 20, nt: int = 1000) -> ShotSpec:
-    """n^3 interior + nbl layer, space order 12, 4-layer model (n/4-cell layers)."""
+def precision_shot(n: int = 384, nbl: int = 20, nt: int = 1000, space_order: int = 12) -> ShotSpec:
+    """n^3 interior + nbl layer, space order 12 (by default), 4-layer model (n/4-cell layers)."""
     interior = (n, n, n)
-    return ShotSpec(interior, nbl, 12, layered_velocity(interior, nbl),
+    return ShotSpec(interior, nbl, space_order, layered_velocity(interior, nbl),
                     (n // 2, n // 2, max(1, (20 * n) // 256)), 15.0, nt)
 
 
