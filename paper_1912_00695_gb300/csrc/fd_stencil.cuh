@@ -69,20 +69,22 @@ __device__ __forceinline__ float next_d_scale(float amax_u, float amax_d, float 
 // for FP32, the only storage of the two-level kernels; inv_s_out, inv_s_d_out:
 // reciprocal scales of u^{n+1}, d^{n+1}.
 struct ScaleState {
-    float s_u, s_up, inv_s_out, s_d, inv_s_d_out;
+    float s_u, s_up, inv_s_out, s_d, inv_s_d_out, s_out, s_d_out;
 };
 
 template <typename T>
 __device__ __forceinline__ ScaleState read_scales(const StepArgs &a) {
-    ScaleState st{1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
+    ScaleState st{1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
     if constexpr (Io<T>::kScaled) {
         const LevelScales *ls = a.scales;
         const int n = level_slot(a.step);
         st.s_u = ls->scale[n];
         st.s_d = ls->dscale[n];
         const float au = __uint_as_float(ls->amax_bits[n]), ad = __uint_as_float(ls->damax_bits[n]);
-        st.inv_s_out = 1.0f / next_u_scale(au, ad, a.src_bound);
-        st.inv_s_d_out = 1.0f / next_d_scale(au, ad, a.src_bound);
+        st.s_out = next_u_scale(au, ad, a.src_bound);
+        st.s_d_out = next_d_scale(au, ad, a.src_bound);
+        st.inv_s_out = 1.0f / st.s_out;  // powers of two: exact
+        st.inv_s_d_out = 1.0f / st.s_d_out;
     }
     return st;
 }

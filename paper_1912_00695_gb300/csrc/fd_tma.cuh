@@ -299,7 +299,14 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     float2 cz2[R + 1];
 #pragma unroll
     for (int j = 1; j <= R; ++j) cz2[j] = f2(a.coef[j], a.coef[j]);
-    const float2 su2 = f2(sc.s_u, sc.s_u), sd2 = f2(sc.s_d, sc.s_d);
+    // 16-bit storage: every factor below is a power of two, so folding the output
+    // scales into the input scales changes no rounding (barring subnormals):
+    // d_st = w (L u_raw) s_u/s_d' + (1 - 2g) d_raw s_d/s_d' and
+    // u_st = u_raw s_u/s_u' + d_st s_d'/s_u' are the stored (scaled) values directly
+    const float kd = sc.inv_s_d_out;
+    const float2 su2 = f2(sc.s_u * kd, sc.s_u * kd), sd2 = f2(sc.s_d * kd, sc.s_d * kd);
+    const float2 uu2 = f2(sc.s_u * sc.inv_s_out, sc.s_u * sc.inv_s_out);
+    const float2 rr2 = f2(sc.s_d_out * sc.inv_s_out, sc.s_d_out * sc.inv_s_out);
     const int rowc = ty + R;
     const int colw = 4 * lz;  // first element of the thread's z window in a tile row
     unsigned amax_bits = acc.amax_bits, damax_bits = acc.damax_bits;
@@ -372,7 +379,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     }
                     if constexpr (Io<T>::kScaled) {
                         // increment form: d+ = w L u + (1 - 2g) d, u+ = u + d+ (formed below,
-                        // after the source), on scaled values
+                        // after the source), directly in the output scales
                         lapA = mul2(lapA, su2);
                         lapB = mul2(lapB, su2);
                         const float2 omA = fma2(f2(-2.f, -2.f), lo2(cf2), f2(1.f, 1.f));
@@ -391,10 +398,10 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         vB = fma2(m2gB, dB, vB);
                         out = make_float4(vA.x, vA.y, vB.x, vB.y);
                     }
-                    sw[0] = cf1.x;
-                    sw[1] = cf1.y;
-                    sw[2] = cf1.z;
-                    sw[3] = cf1.w;
+                    sw[0] = cf1.x * kd;  // kd = 1 for FP32 storage
+                    sw[1] = cf1.y * kd;
+                    sw[2] = cf1.z * kd;
+                    sw[3] = cf1.w * kd;
                 } else {
                     // expanded: every tap (u_tap - u_c) times (c_j dt^2/h^2)/r0
                     const float r0[4] = {fmaf(a.half_dt, cf2.x, cf1.x), fmaf(a.half_dt, cf2.y, cf1.y),
@@ -459,18 +466,14 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                                max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w))));
                 };
                 if constexpr (Io<T>::kScaled) {
-                    // out is d^{n+1}; u^{n+1} = u^n + d^{n+1} (padding stays zero: both terms are)
-                    float4 unew = make_float4(fmaf(uc.x, sc.s_u, out.x), fmaf(uc.y, sc.s_u, out.y),
-                                              fmaf(uc.z, sc.s_u, out.z), fmaf(uc.w, sc.s_u, out.w));
+                    // out is the stored d^{n+1}; u^{n+1} = u^n + d^{n+1}, stored (padding
+                    // stays zero: both terms are). The maxima are of stored values (scaled
+                    // back once, after the loop); the 16-bit range is checked there too.
+                    const float2 nA = fma2(lo2(uc), uu2, mul2(f2(out.x, out.y), rr2));
+                    const float2 nB = fma2(hi2(uc), uu2, mul2(f2(out.z, out.w), rr2));
+                    const float4 unew = make_float4(nA.x, nA.y, nB.x, nB.y);
                     damax_bits = max(damax_bits, bits4(out));
                     amax_bits = max(amax_bits, bits4(unew));
-                    out = make_float4(out.x * sc.inv_s_d_out, out.y * sc.inv_s_d_out, out.z * sc.inv_s_d_out,
-                                      out.w * sc.inv_s_d_out);
-                    unew = make_float4(unew.x * sc.inv_s_out, unew.y * sc.inv_s_out, unew.z * sc.inv_s_out,
-                                       unew.w * sc.inv_s_out);
-                    const float mx = fmaxf(fmaxf(fmaxf(fabsf(out.x), fabsf(out.y)), fmaxf(fabsf(out.z), fabsf(out.w))),
-                                           fmaxf(fmaxf(fabsf(unew.x), fabsf(unew.y)), fmaxf(fabsf(unew.z), fabsf(unew.w))));
-                    over |= mx > Io<T>::kMaxStored;
                     V::st(un + x * P, unew);
                 } else {
                     amax_bits = max(amax_bits, bits4(out));
@@ -501,6 +504,19 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     return true;
 }
 
+// 16-bit storage: the per-thread maxima were taken over stored (scaled) values;
+// check them against the format's range and scale them back to true values
+// (powers of two: exact) for the next level's scale selection.
+template <typename T>
+__device__ __forceinline__ void tma_finish(TmaAcc &acc, const ScaleState &sc) {
+    if constexpr (Io<T>::kScaled) {
+        const float dmax = __uint_as_float(acc.damax_bits), umax = __uint_as_float(acc.amax_bits);
+        acc.over |= dmax > Io<T>::kMaxStored || umax > Io<T>::kMaxStored;
+        acc.damax_bits = __float_as_uint(dmax * sc.s_d_out);
+        acc.amax_bits = __float_as_uint(umax * sc.s_out);
+    }
+}
+
 // Single-shot step: CTA (bz, by, bx) streams planes [bx x_block, (bx+1) x_block)
 // of tile (bz, by). The grid runs z-tiles fastest and x-chunks slowest, so the
 // CTAs resident at any moment cover neighbouring tiles at the same planes and
@@ -517,8 +533,10 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(cons
     TmaAcc acc;
     if (tma_segment<R, FORM, LZ, W, T>(&maps, a, sc, blockIdx.x, blockIdx.y, xb, min(xb + a.x_block, a.Nx), ring,
                                        g, acc) &&
-        check)
+        check) {
+        tma_finish<T>(acc, sc);
         reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
+    }
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
@@ -568,8 +586,10 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_batch_kerne
     const int xb = it.w * sa.x_block;
     int g = 0;
     TmaAcc acc;
-    if (tma_segment<R, FORM, LZ, W, T>(maps, sa, sc, it.y, it.z, xb, min(xb + sa.x_block, sa.Nx), ring, g, acc))
+    if (tma_segment<R, FORM, LZ, W, T>(maps, sa, sc, it.y, it.z, xb, min(xb + sa.x_block, sa.Nx), ring, g, acc)) {
+        tma_finish<T>(acc, sc);
         reduce_amax(sa, acc.amax_bits, acc.over, acc.damax_bits);
+    }
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
