@@ -12,7 +12,8 @@ passage it follows (arXiv 1912.00695, Sec. 2.1 Eq. 1, Listing 1, Listing 2),
 is stated in the C source beside the function.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
-closed forms, invariants, Listing 2 or a dense brute force, except the default
+closed forms, invariants, Listing 2, a library interpolator or a dense brute
+force, except the default
 damping profile, whose formula is a convention the paper does not give
 (parity unpinned as a formula; its invariants are tested).
 """
@@ -79,6 +80,16 @@ def _load():
         lib.oracle_default_damping.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_long,
                                                ctypes.c_long, ctypes.c_int, ctypes.c_double]
         lib.oracle_default_damping.restype = ctypes.c_int
+        _lp = ctypes.POINTER(ctypes.c_long)
+        lib.oracle_trilinear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_long, ctypes.c_long, ctypes.c_long, _lp, _dp]
+        lib.oracle_trilinear.restype = ctypes.c_int
+        lib.oracle_forward_offgrid.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_long, ctypes.c_long,
+                                               ctypes.c_long, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                               ctypes.c_long, ctypes.c_int, _dp, _dp, ctypes.c_long,
+                                               ctypes.c_long]
+        lib.oracle_forward_offgrid.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -161,6 +172,48 @@ def forward(m, eta, space_order: int, h: float, dt: float, nt: int, sources=(), 
     if rc != 0:
         raise ValueError(f"oracle forward failed ({rc})")
     return u, up
+
+
+def trilinear(point, shape):
+    """The 8 nodes (8x3 int array) and weights of a continuous domain point."""
+    nodes = np.zeros((8, 3), dtype=np.int64)
+    w = np.zeros(8)
+    rc = _load().oracle_trilinear(float(point[0]), float(point[1]), float(point[2]), *map(int, shape),
+                                  nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _ptr(w))
+    if rc != 0:
+        raise ValueError(f"point {tuple(point)} outside a {tuple(shape)} domain")
+    return nodes, w
+
+
+def forward_offgrid(m, eta, space_order: int, h: float, dt: float, nt: int, sources=(),
+                    wavelets=None, receivers=(), u0=None, u_prev0=None, step0: int = 0,
+                    periodic: bool = False):
+    """Advance nt steps with off-grid sources (continuous domain coordinates,
+    trilinear spreading) and receivers (trilinear sampling of each new level).
+    Returns (u^{step0+nt}, u^{step0+nt-1}, traces[nr, nt])."""
+    m = _f64(m)
+    shape = m.shape
+    u = np.zeros(shape) if u0 is None else _f64(u0).copy()
+    up = np.zeros(shape) if u_prev0 is None else _f64(u_prev0).copy()
+    eta_a = None if eta is None else _f64(eta)
+    ns, nr = len(sources), len(receivers)
+    src = _f64(np.asarray(sources, dtype=np.float64).reshape(ns, 3)) if ns else np.zeros((1, 3))
+    rec = _f64(np.asarray(receivers, dtype=np.float64).reshape(nr, 3)) if nr else np.zeros((1, 3))
+    if ns:
+        w = _f64(np.asarray(wavelets).reshape(ns, -1))
+        ld = w.shape[1]
+    else:
+        w = np.zeros((1, 1))
+        ld = 0
+    traces = np.zeros((max(nr, 1), max(int(nt), 1)))
+    nx, ny, nz = shape
+    rc = _load().oracle_forward_offgrid(_ptr(u), _ptr(up), _ptr(m), None if eta_a is None else _ptr(eta_a),
+                                        nx, ny, nz, int(space_order), float(h), float(dt), int(periodic),
+                                        ns, _ptr(src), _ptr(w), ld, nr, _ptr(rec), _ptr(traces), int(step0),
+                                        int(nt))
+    if rc != 0:
+        raise ValueError(f"oracle forward_offgrid failed ({rc})")
+    return u, up, traces[:nr, :nt]
 
 
 def energy(u_new, u_old, m, space_order: int, h: float, dt: float,

@@ -26,7 +26,10 @@
  * solve and polynomial exactness; the Laplacian against the closed-form plane
  * wave symbol and symmetry; the step against the literal Listing 2 algebra
  * (k=2, h=1), a dense-matrix brute force, the exact discrete plane-wave
- * solution and discrete energy conservation; dt_max against power iteration.
+ * solution and discrete energy conservation; dt_max against power iteration;
+ * off-grid sampling against a library interpolator and affine exactness,
+ * off-grid spreading against integer-node sources combined by linearity and a
+ * dense brute force, and reciprocity between off-grid points.
  * The default damping profile is a convention the paper does not give
  * (parity unpinned as a formula; pinned only by its invariants).
  */
@@ -182,6 +185,112 @@ int oracle_forward(double *u, double *u_prev, const double *m, const double *eta
     }
     free(next);
     return 0;
+}
+
+/*
+ * Off-grid points (sources and receivers between nodes). The paper names
+ * receivers and off-grid sources as the next step of the workflow (Sec. 5) but
+ * gives no formula; the reading taken is multilinear (trilinear)
+ * interpolation in the computational-domain index space, node (i, j, l) at
+ * coordinates (i, j, l):
+ *
+ *   sampling:  v(p) = sum over the 8 nodes c of the cell holding p of W_c u[c],
+ *   spreading: a source q at p adds W_c q to the right-hand side at node c,
+ *   W_c = prod over axes a of (1 - |p_a - c_a|),
+ *
+ * so spreading is the adjoint (transpose) of sampling. The cell of a
+ * coordinate t on an axis of n nodes is [i0, i0 + 1] with
+ * i0 = min(floor(t), n - 2), so t = n - 1 lies in the last cell with weight 1 on
+ * its upper node. Coordinates must lie in [0, n - 1] on every axis.
+ *
+ * Writes the 8 nodes (x, y, z triples, x slowest over the 2x2x2 corners) and
+ * weights; returns 0, or -1 if the point lies outside the domain or an axis
+ * has fewer than 2 nodes.
+ */
+int oracle_trilinear(double x, double y, double z, long nx, long ny, long nz, long *nodes,
+                     double *w) {
+    const double p[3] = {x, y, z};
+    const long n[3] = {nx, ny, nz};
+    long i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 2 || !(p[a] >= 0.0) || !(p[a] <= (double)(n[a] - 1))) return -1;
+        long i = (long)floor(p[a]);
+        if (i > n[a] - 2) i = n[a] - 2;
+        i0[a] = i;
+        f[a] = p[a] - (double)i;
+    }
+    int c = 0;
+    for (int dx = 0; dx < 2; ++dx)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dz = 0; dz < 2; ++dz, ++c) {
+                nodes[3 * c] = i0[0] + dx;
+                nodes[3 * c + 1] = i0[1] + dy;
+                nodes[3 * c + 2] = i0[2] + dz;
+                w[c] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+            }
+    return 0;
+}
+
+/*
+ * oracle_forward with off-grid sources and receivers. Source s sits at the
+ * continuous domain coordinates src[3s..3s+2] and is spread onto its 8 nodes:
+ *   u^{n+1}[c] += W_c dt^2 q / (m[c] + dt/2 eta[c]),  q = wavelet[s*ld + n];
+ * receiver r at rec[3r..3r+2] records, after each step (sources included),
+ *   traces[r*nt + it] = sum_c W_c u^{step0+it+1}[c].
+ * Returns 0, -1 on bad arguments (a point outside the domain), -2 on
+ * allocation failure.
+ */
+int oracle_forward_offgrid(double *u, double *u_prev, const double *m, const double *eta, long nx,
+                           long ny, long nz, int k, double h, double dt, int periodic, int ns,
+                           const double *src, const double *wavelet, long ld, int nr,
+                           const double *rec, double *traces, long step0, long nt) {
+    size_t n = (size_t)nx * (size_t)ny * (size_t)nz;
+    long *snodes = (long *)malloc(sizeof(long) * 24 * (size_t)(ns > 0 ? ns : 1));
+    double *sw = (double *)malloc(sizeof(double) * 8 * (size_t)(ns > 0 ? ns : 1));
+    long *rnodes = (long *)malloc(sizeof(long) * 24 * (size_t)(nr > 0 ? nr : 1));
+    double *rw = (double *)malloc(sizeof(double) * 8 * (size_t)(nr > 0 ? nr : 1));
+    double *next = (double *)malloc(n * sizeof(double));
+    int rc = 0;
+    if (!snodes || !sw || !rnodes || !rw || !next) rc = -2;
+    for (int s = 0; s < ns && rc == 0; ++s)
+        if (oracle_trilinear(src[3 * s], src[3 * s + 1], src[3 * s + 2], nx, ny, nz, snodes + 24 * s,
+                             sw + 8 * s) != 0)
+            rc = -1;
+    for (int r = 0; r < nr && rc == 0; ++r)
+        if (oracle_trilinear(rec[3 * r], rec[3 * r + 1], rec[3 * r + 2], nx, ny, nz, rnodes + 24 * r,
+                             rw + 8 * r) != 0)
+            rc = -1;
+    for (long it = 0; it < nt && rc == 0; ++it) {
+        long step = step0 + it;
+        rc = oracle_step(u, u_prev, next, m, eta, nx, ny, nz, k, h, dt, periodic);
+        if (rc != 0) break;
+        for (int s = 0; s < ns; ++s) {
+            double q = (step >= 0 && step < ld) ? wavelet[(size_t)s * (size_t)ld + (size_t)step] : 0.0;
+            for (int c = 0; c < 8; ++c) {
+                const long *nd = snodes + 24 * s + 3 * c;
+                size_t p = idx3(nd[0], nd[1], nd[2], ny, nz);
+                double e = eta ? eta[p] : 0.0;
+                next[p] += sw[8 * s + c] * dt * dt * q / (m[p] + 0.5 * dt * e);
+            }
+        }
+        for (int r = 0; r < nr; ++r) {
+            double v = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                const long *nd = rnodes + 24 * r + 3 * c;
+                v += rw[8 * r + c] * next[idx3(nd[0], nd[1], nd[2], ny, nz)];
+            }
+            traces[(size_t)r * (size_t)nt + (size_t)it] = v;
+        }
+        memcpy(u_prev, u, n * sizeof(double));
+        memcpy(u, next, n * sizeof(double));
+    }
+    free(snodes);
+    free(sw);
+    free(rnodes);
+    free(rw);
+    free(next);
+    return rc;
 }
 
 /*
