@@ -149,6 +149,41 @@ int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int n
 /* Remove every source. */
 int fd_clear_sources(fd_handle *hd);
 
+/* Sources and receivers between nodes: the next step of the workflow after
+ * the forward step (Sec. 5 names receivers and the imaging workflow as future
+ * work; no formula is given). Coordinates are continuous INTERIOR coordinates
+ * in grid units: interior node (i, j, l) sits at (i, j, l), and each
+ * coordinate must lie in [0, n_a - 1] of its axis (FD_ERANGE otherwise; NaN
+ * included). A point belongs to the cell with lower node
+ * i0 = min(floor(t), N - 2) on each axis (domain index t = coordinate + nbl),
+ * and its 8 corner weights are the trilinear W_c = prod_a (1 - |t_a - c_a|).
+ *
+ * fd_inject_at: an off-grid point source, spread onto the nodes of its cell:
+ * each corner with W_c > 0 becomes one point source (as fd_inject) whose
+ * wavelet is W_c times the given one, rounded to FP32 (so up to 8 sources per
+ * call). Spreading is the transpose of the receivers' sampling, which keeps
+ * source-receiver reciprocity. Same errors as fd_inject. */
+int fd_inject_at(fd_handle *hd, double x, double y, double z, const float *wavelet, int nt);
+
+/* Receivers: n points at xyz[3r], xyz[3r+1], xyz[3r+2] (host array, copied),
+ * replacing any earlier set (n = 0 removes them). From the handle's current
+ * step s0 on, every step records per receiver the trilinear interpolation
+ * sum_c W_c u^{n+1}[c] of the level it has just written (after source
+ * injection; 16-bit storage: dequantised with that level's scale): sample i of
+ * receiver r is u^{s0+i+1} there, stored at traces[r * nt_max + i], for
+ * i < nt_max; later steps are not recorded. fd_reset restarts the traces at
+ * step 0, fd_load_state at the loaded step. Device memory: 8 (offset, weight)
+ * pairs per receiver and n * nt_max floats, owned by the handle. FD_EINVAL for
+ * n < 0, a NULL xyz or nt_max < 1 with n > 0, or n * nt_max > 2^31; FD_ERANGE
+ * for a point outside the interior; FD_ENOMEM. */
+int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max);
+
+/* Copy the traces into HOST memory out[n * nt_max] (r-major; samples not yet
+ * recorded are zero) and the number of recorded samples per receiver into
+ * *recorded. Synchronises the handle's stream; returns the device status like
+ * fd_synchronize. FD_ESTATE when no receivers are set. */
+int fd_read_traces(fd_handle *hd, float *out, int *recorded);
+
 /* Queue nt time steps on the handle's stream (asynchronous; returns before
  * the GPU finishes). The global step counter persists across calls, so
  * fd_forward(a) followed by fd_forward(b) equals fd_forward(a + b) bit for

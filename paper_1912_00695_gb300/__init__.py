@@ -21,7 +21,8 @@ from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD
                    FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
-                   fd_forward, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_load_state,
+                   fd_forward, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
+                   fd_load_state, fd_read_traces, fd_set_receivers,
                    fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
                    fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
                    fd_set_model_device, fd_set_stream, fd_status, fd_synchronize, fd_version)
@@ -201,6 +202,24 @@ class Shot:
 
     def forward(self, nt):
         fd_forward(self.handle, nt)
+
+    def inject_at(self, x, y, z, wavelet):
+        """Off-grid source at continuous interior coordinates (trilinear spreading)."""
+        fd_inject_at(self.handle, x, y, z, wavelet)
+
+    def set_receivers(self, xyz, nt_max):
+        """Receivers at continuous interior coordinates xyz (n, 3), recording up
+        to nt_max samples from the current step on."""
+        p = np.asarray(xyz, dtype=np.float64).reshape(-1, 3)
+        fd_set_receivers(self.handle, p, nt_max)
+        self._rec = (p.shape[0], int(nt_max))
+
+    def traces(self) -> np.ndarray:
+        """Recorded traces, shape (n, recorded samples)."""
+        n, nt_max = self._rec
+        out = np.empty(n * nt_max, dtype=np.float32)
+        done = fd_read_traces(self.handle, out)
+        return out.reshape(n, nt_max)[:, :done]
 
     def wavefield(self, level=0, out=None) -> np.ndarray:
         if out is None:

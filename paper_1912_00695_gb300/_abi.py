@@ -70,6 +70,9 @@ _SIGNATURES = {
     "fd_set_model_device": (_i, [_vp, _vp, _vp]),
     "fd_inject": (_i, [_vp, _i, _i, _i, _vp, _i]),
     "fd_clear_sources": (_i, [_vp]),
+    "fd_inject_at": (_i, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _i]),
+    "fd_set_receivers": (_i, [_vp, _i, _vp, _i]),
+    "fd_read_traces": (_i, [_vp, _vp, _ip]),
     "fd_forward": (_i, [_vp, _i]),
     "fd_read_wavefield": (_i, [_vp, _vp, _i]),
     "fd_read_wavefield_device": (_i, [_vp, _vp, _i]),
@@ -190,6 +193,26 @@ def fd_inject(hd, ix, iy, iz, wavelet):
 
 def fd_clear_sources(hd):
     _check(lib().fd_clear_sources(hd), "fd_clear_sources")
+
+
+def fd_inject_at(hd, x, y, z, wavelet):
+    w = _host_f32(wavelet)
+    _check(lib().fd_inject_at(hd, float(x), float(y), float(z), _ptr(w), int(w.size)), "fd_inject_at")
+
+
+def fd_set_receivers(hd, xyz, nt_max):
+    """xyz: (n, 3) continuous interior coordinates (copied); n = 0 removes them."""
+    p = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    n = int(p.shape[0])
+    _check(lib().fd_set_receivers(hd, n, _ptr(p) if n else None, int(nt_max)), "fd_set_receivers")
+
+
+def fd_read_traces(hd, out: np.ndarray) -> int:
+    """Fill out (float32, n * nt_max, receiver-major); returns the recorded samples."""
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    rec = ctypes.c_int()
+    _check(lib().fd_read_traces(hd, _ptr(out), ctypes.byref(rec)), "fd_read_traces")
+    return rec.value
 
 
 def fd_forward(hd, nt):

@@ -177,6 +177,12 @@ struct fd_handle {
     unsigned long long gen = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
+    // receivers: 8 (pitched offset, weight) pairs each; traces [n_rec][rec_nt_max]
+    int n_rec = 0, rec_nt_max = 0;
+    long long rec_step0 = 0;
+    long long *d_rec_off = nullptr;
+    float *d_rec_w = nullptr;
+    float *d_traces = nullptr;
 };
 
 namespace {
@@ -249,6 +255,15 @@ cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, cudaStream_t s)
     if (ns > kFusedSources)
         e = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources,
                                 ns - kFusedSources, hd->opt.storage, hd->opt.form == kExpanded, s);
+    if (e == cudaSuccess && hd->n_rec > 0) {
+        // receivers sample the level this step wrote (u^{n+1}: over u^{n-1} for FP32 storage,
+        // the other u buffer for 16-bit storage, whose scale is that of level n+1)
+        const long long smp = a.step - hd->rec_step0;
+        if (smp >= 0 && smp < hd->rec_nt_max)
+            e = launch_sample_receivers(hd->opt.storage == kF32 ? a.up : a.un, hd->opt.storage, hd->d_scales,
+                                        int(((a.step + 1) % 3 + 3) % 3), hd->d_rec_off, hd->d_rec_w, hd->n_rec,
+                                        hd->d_traces + smp, hd->rec_nt_max, s);
+    }
     return e;
 }
 
@@ -565,6 +580,39 @@ cudaError_t unpack_to(fd_handle *hd, int level, float *dst) {
                               hd->d_scales, slot, hd->stream);
 }
 
+// Trilinear cell of a continuous domain coordinate t on an axis of n >= 2
+// nodes: lower node i0 = min(floor(t), n - 2) and fraction t - i0 (t in [0, n-1]).
+void trilinear_axis(double t, int n, int *i0, double *f) {
+    int i = int(std::floor(t));
+    if (i > n - 2) i = n - 2;
+    if (i < 0) i = 0;
+    *i0 = i;
+    *f = t - double(i);
+}
+
+bool interior_point_ok(const fd_handle *hd, double x, double y, double z) {
+    return std::isfinite(x) && std::isfinite(y) && std::isfinite(z) && x >= 0.0 && y >= 0.0 && z >= 0.0 &&
+           x <= double(hd->nx - 1) && y <= double(hd->ny - 1) && z <= double(hd->nz - 1);
+}
+
+// The 8 nodes (domain indices) and weights of an interior point (x, y, z).
+void trilinear_nodes(const fd_handle *hd, double x, double y, double z, int nodes[8][3], double w[8]) {
+    const double p[3] = {x + hd->nbl, y + hd->nbl, z + hd->nbl};
+    const int n[3] = {hd->Nx, hd->Ny, hd->Nz};
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) trilinear_axis(p[a], n[a], &i0[a], &f[a]);
+    int c = 0;
+    for (int dx = 0; dx < 2; ++dx)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dz = 0; dz < 2; ++dz, ++c) {
+                nodes[c][0] = i0[0] + dx;
+                nodes[c][1] = i0[1] + dy;
+                nodes[c][2] = i0[2] + dz;
+                w[c] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+            }
+}
+
 // Free a handle's device memory in the order of its stream (after the work
 // already queued there) and its host resources, without waiting for the device.
 void release_handle(fd_handle *hd) {
@@ -573,7 +621,8 @@ void release_handle(fd_handle *hd) {
     hd->graphs.clear();
     cudaStream_t st = hd->stream ? hd->stream : hd->own_stream;
     void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
-                    hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack};
+                    hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack, hd->d_rec_off, hd->d_rec_w,
+                    hd->d_traces};
     for (void *p : bufs) dev_free(p, st);
     if (hd->ev0) cudaEventDestroy(hd->ev0);
     if (hd->ev1) cudaEventDestroy(hd->ev1);
@@ -753,6 +802,99 @@ int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int n
     return update_src_bound(hd);
 }
 
+int fd_inject_at(fd_handle *hd, double x, double y, double z, const float *wavelet, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (!wavelet || nt < 1) return fail(FD_EINVAL, "wavelet is NULL or nt < 1");
+    if (!interior_point_ok(hd, x, y, z))
+        return fail(FD_ERANGE, "source (%g,%g,%g) outside the [0,%d]x[0,%d]x[0,%d] interior", x, y, z, hd->nx - 1,
+                    hd->ny - 1, hd->nz - 1);
+    for (int i = 0; i < nt; ++i)
+        if (!std::isfinite(wavelet[i])) return fail(FD_EINVAL, "wavelet[%d] is not finite", i);
+    int nodes[8][3];
+    double w[8];
+    trilinear_nodes(hd, x, y, z, nodes, w);
+    const size_t before = hd->sources.size();
+    for (int c = 0; c < 8; ++c) {
+        if (w[c] <= 0.0) continue;
+        Source s{nodes[c][0], nodes[c][1], nodes[c][2], std::vector<float>(size_t(nt))};
+        for (int i = 0; i < nt; ++i) s.wavelet[size_t(i)] = float(w[c] * double(wavelet[i]));
+        hd->sources.push_back(std::move(s));
+    }
+    int rc = upload_sources(hd);
+    if (rc != FD_OK) {
+        hd->sources.resize(before);
+        return rc;
+    }
+    hd->gen++;
+    return update_src_bound(hd);
+}
+
+int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (n < 0 || (n > 0 && (!xyz || nt_max < 1))) return fail(FD_EINVAL, "bad receiver count, positions or nt_max");
+    if (n > 0 && (long long)n * nt_max > (1LL << 31))
+        return fail(FD_EINVAL, "n * nt_max above 2^31 samples");
+    for (int r = 0; r < n; ++r)
+        if (!interior_point_ok(hd, xyz[3 * r], xyz[3 * r + 1], xyz[3 * r + 2]))
+            return fail(FD_ERANGE, "receiver %d (%g,%g,%g) outside the interior", r, xyz[3 * r], xyz[3 * r + 1],
+                        xyz[3 * r + 2]);
+    // queued steps may still write the old traces: the old arrays are freed behind them
+    dev_free(hd->d_rec_off, hd->stream);
+    dev_free(hd->d_rec_w, hd->stream);
+    dev_free(hd->d_traces, hd->stream);
+    hd->d_rec_off = nullptr;
+    hd->d_rec_w = nullptr;
+    hd->d_traces = nullptr;
+    hd->n_rec = 0;
+    hd->rec_nt_max = 0;
+    hd->gen++;
+    if (n == 0) return FD_OK;
+    std::vector<long long> off(size_t(n) * 8);
+    std::vector<float> w(size_t(n) * 8);
+    for (int r = 0; r < n; ++r) {
+        int nodes[8][3];
+        double wd[8];
+        trilinear_nodes(hd, xyz[3 * r], xyz[3 * r + 1], xyz[3 * r + 2], nodes, wd);
+        for (int c = 0; c < 8; ++c) {
+            off[size_t(r) * 8 + c] = (long long)nodes[c][0] * hd->plane + (long long)nodes[c][1] * hd->pz + nodes[c][2];
+            w[size_t(r) * 8 + c] = float(wd[c]);
+        }
+    }
+    const size_t nsamp = size_t(n) * size_t(nt_max);
+    if (dev_alloc(reinterpret_cast<void **>(&hd->d_rec_off), off.size() * sizeof(long long), hd->stream) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_rec_w), w.size() * sizeof(float), hd->stream) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&hd->d_traces), nsamp * sizeof(float), hd->stream) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(hd->d_rec_off, hd->stream);
+        dev_free(hd->d_rec_w, hd->stream);
+        dev_free(hd->d_traces, hd->stream);
+        hd->d_rec_off = nullptr;
+        hd->d_rec_w = nullptr;
+        hd->d_traces = nullptr;
+        return fail(FD_ENOMEM, "cannot allocate receivers");
+    }
+    FD_CUDA(cudaMemcpyAsync(hd->d_rec_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                            hd->stream));
+    FD_CUDA(cudaMemcpyAsync(hd->d_rec_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, hd->stream));
+    FD_CUDA(cudaMemsetAsync(hd->d_traces, 0, nsamp * sizeof(float), hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));  // the host vectors go out of scope
+    hd->n_rec = n;
+    hd->rec_nt_max = nt_max;
+    hd->rec_step0 = hd->step;
+    return FD_OK;
+}
+
+int fd_read_traces(fd_handle *hd, float *out, int *recorded) {
+    if (!hd || !out || !recorded) return fail(FD_EINVAL, "NULL argument");
+    if (hd->n_rec == 0) return fail(FD_ESTATE, "no receivers set");
+    const long long done = std::max(0LL, std::min<long long>(hd->step - hd->rec_step0, hd->rec_nt_max));
+    FD_CUDA(cudaMemcpyAsync(out, hd->d_traces, size_t(hd->n_rec) * hd->rec_nt_max * sizeof(float),
+                            cudaMemcpyDeviceToHost, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));
+    *recorded = int(done);
+    return check_enabled(hd) ? read_status(hd) : FD_OK;
+}
+
 int fd_clear_sources(fd_handle *hd) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
     hd->sources.clear();
@@ -815,6 +957,7 @@ int fd_forward(fd_handle *hd, int nt) {
             }
             if (!entry) {
                 if (hd->graphs.size() >= 8) {
+                    cudaStreamSynchronize(hd->stream);  // the oldest graph may still be queued
                     cudaGraphExecDestroy(hd->graphs.front().exec);
                     hd->graphs.erase(hd->graphs.begin());
                 }
@@ -928,6 +1071,11 @@ int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long 
     dev_free(tmp, hd->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(hd->stream);
     if (e != cudaSuccess) return fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
+    if (hd->n_rec > 0) {  // traces restart at the loaded step
+        e = cudaMemsetAsync(hd->d_traces, 0, size_t(hd->n_rec) * hd->rec_nt_max * sizeof(float), hd->stream);
+        if (e != cudaSuccess) return fail(FD_ECUDA, "loading state failed: %s", cudaGetErrorString(e));
+    }
+    hd->rec_step0 = step;
     hd->step = step;
     hd->cur = 0;
     return FD_OK;
@@ -941,6 +1089,9 @@ int fd_reset(fd_handle *hd) {
     if (hd->dbuf) FD_CUDA(cudaMemsetAsync(hd->dbuf, 0, ub, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->d_status, 0, sizeof(unsigned), hd->stream));
     FD_CUDA(launch_init_scales(hd->d_scales, hd->stream));
+    if (hd->n_rec > 0)  // receivers keep their positions; their traces restart at step 0
+        FD_CUDA(cudaMemsetAsync(hd->d_traces, 0, size_t(hd->n_rec) * hd->rec_nt_max * sizeof(float), hd->stream));
+    hd->rec_step0 = 0;
     hd->step = 0;
     hd->cur = 0;
     return FD_OK;

@@ -124,6 +124,9 @@ bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *box
 // Utility kernels (fd_kernels_util.cu)
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
                                 int first, int count, int storage, int expanded, cudaStream_t s);
+cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
+                                    const long long *off, const float *w, int n, float *out, int stride,
+                                    cudaStream_t s);
 cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int Nz, int pz,
                                 int storage, const LevelScales *scales, int slot,
                                 cudaStream_t s);

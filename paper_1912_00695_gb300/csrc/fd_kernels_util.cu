@@ -165,6 +165,20 @@ __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *
     }
 }
 
+// Receivers: trilinear interpolation of the new level u^{n+1} (stored values
+// times the level's scale) at each receiver, one thread per receiver, the 8
+// corner terms summed in a fixed order (deterministic). off/w: 8 per receiver.
+template <typename T>
+__global__ void sample_receivers_kernel(const T *u, const LevelScales *scales, int slot, const long long *off,
+                                        const float *w, int n, float *out, int stride) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float v = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v = fmaf(w[8 * r + c], to_f<T>(u[off[8 * r + c]]), v);
+    out[(long long)r * stride] = scales ? v * scales->scale[slot] : v;
+}
+
 // Pitched storage-type level -> dense FP32 [Nx][Ny][Nz], times the level scale.
 template <typename T>
 __global__ void unpack_kernel(const T *src, float *dst, int Nx, int Ny, int Nz, int pz,
@@ -325,6 +339,25 @@ cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy,
     else if (storage == kF16)
         inject_extra_kernel<__half><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
+                                    const long long *off, const float *w, int n, float *out, int stride,
+                                    cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 128, blocks = (n + threads - 1) / threads;
+    if (storage == kF32)
+        sample_receivers_kernel<float><<<blocks, threads, 0, s>>>(static_cast<const float *>(u), nullptr, slot,
+                                                                   off, w, n, out, stride);
+    else if (storage == kBF16)
+        sample_receivers_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(
+            static_cast<const __nv_bfloat16 *>(u), scales, slot, off, w, n, out, stride);
+    else if (storage == kF16)
+        sample_receivers_kernel<__half><<<blocks, threads, 0, s>>>(static_cast<const __half *>(u), scales, slot,
+                                                                    off, w, n, out, stride);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
