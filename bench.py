@@ -282,6 +282,107 @@ def run_ours(args, rank: int, world: int):
         shot.close()
 
 
+def run_receivers(args, rank: int, world: int):
+    """Off-grid source and a surface receiver array on the sweep shot: 256^3 + 10,
+    space order 8 (factored), 4-layer model, 500 steps, the source at
+    (127.3, 128.6, 20.25) spread onto its 8 nodes and (n-1)^2 receivers at
+    (i + 1/2, j + 1/2, 10.5) sampled every step, against the same shot with the
+    integer-node source and no receivers."""
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    spec = inputs.sweep_shot(args.rec_order, n=args.n, nt=args.nt)
+    dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+    m = spec.m
+    wav = inputs.ricker(spec.f0, dt, spec.nt)
+    n = args.n
+    g = np.arange(n - 1, dtype=np.float64) + 0.5
+    rx, ry = np.meshgrid(g, g, indexing="ij")
+    recs = np.stack([rx.ravel(), ry.ravel(), np.full(rx.size, 10.5)], axis=1)
+    src_at = (n / 2 - 0.7, n / 2 + 0.6, 20.25)
+
+    plain = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl)
+    plain.set_model(m)
+    plain.inject(*spec.source, wav)
+    plain.set_stream(stream.cuda_stream)
+    rshot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl)
+    rshot.set_model(m)
+    rshot.inject_at(*src_at, wav)
+    rshot.set_receivers(recs, spec.nt)
+    rshot.set_stream(stream.cuda_stream)
+
+    def timed(shot):
+        for _ in range(args.warmup):
+            shot.reset()
+            shot.forward(spec.nt)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            shot.reset()
+            shot.forward(spec.nt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    ms_plain = max_over_ranks(timed(plain))
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms_rec = max_over_ranks(timed(rshot))
+    clk = clocks.stop()
+    pts = spec.points * spec.nt * args.steps * world
+    gpts, gpts_plain = pts / (ms_rec * 1e-3) / 1e9, pts / (ms_plain * 1e-3) / 1e9
+    tr = rshot.traces()
+    # end to end through the public API with host buffers: model upload, source,
+    # receivers, the run, read-back of the traces and the final field
+    h2d = m.nbytes + wav.nbytes + recs.nbytes
+    d2h = tr.nbytes + m.nbytes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl)
+        s.set_model(m)
+        s.inject_at(*src_at, wav)
+        s.set_receivers(recs, spec.nt)
+        s.forward(spec.nt)
+        s.traces()
+        s.wavefield(0)
+        s.close()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) * 1e3) * 1e-3
+    peak, peak_kind = _peaks()
+    alg = algorithmic_bytes_per_step(spec) * spec.nt * args.steps
+    line = {
+        "metric": "Gpts/s with an off-grid source and a surface receiver array sampled every step "
+                  "(256^3+10, space order 8) vs the integer-node source alone",
+        "value": round(gpts, 3), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_rec / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered velocity model, Ricker source)",
+        "config": {"workload": f"receivers: {n}^3+10, space order {spec.space_order}, {spec.nt} steps, "
+                               f"{len(recs)} receivers at depth 10.5, off-grid source {src_at}",
+                   "receivers": len(recs), "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+        "plain_gpts": round(gpts_plain, 3),
+        "receiver_cost_frac": round(ms_rec / ms_plain - 1.0, 4),
+        "roofline": {"bound": "hbm", "achieved": round(alg / (ms_rec * 1e-3) / 1e9, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(alg / (ms_rec * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                     "kernel": "fd_tma_kernel + sample_receivers_kernel", "peak_source": peak_kind},
+        "e2e": {"value": round(spec.points * spec.nt * args.steps * world / e2e_s / 1e9, 3), "unit": "Gpts/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 3 * spec.nt * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plain.close()
+    rshot.close()
+
+
 def run_batched(args, rank: int, world: int):
     """64 uneven shots (each axis U{96..256} + 10, smooth random velocity, k=8,
     300 steps): the batch (one launch per step over all shots) against the same
@@ -643,7 +744,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "plain", "batched", "precision", "serving"])
+                    choices=["sweep", "plain", "batched", "precision", "serving", "receivers"])
     ap.add_argument("--requests", type=int, default=40, help="serving: requests in the trace")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--serve-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(128, 256),
@@ -663,6 +764,7 @@ def main():
                     help="batched workload: tile as ZxY (32x16 or 64x8; default 32x16)")
     ap.add_argument("--shot-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(96, 256),
                     help="batched workload: interior size range lo,hi per axis")
+    ap.add_argument("--rec-order", type=int, default=8, help="receivers workload: space order")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -686,6 +788,8 @@ def main():
         run_precision(args, rank, world)
     elif args.workload == "serving":
         run_serving(args, rank, world)
+    elif args.workload == "receivers":
+        run_receivers(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -177,6 +177,7 @@ struct fd_handle {
     unsigned long long gen = 1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
+    bool extra_distinct = true;  // sources beyond the fused ones sit at pairwise distinct nodes
     // receivers: 8 (pitched offset, weight) pairs each; traces [n_rec][rec_nt_max]
     int n_rec = 0, rec_nt_max = 0;
     long long rec_step0 = 0;
@@ -233,7 +234,23 @@ StepArgs make_args(const fd_handle *hd, long long step, int cur) {
     a.status = check_enabled(hd) ? hd->d_status : nullptr;
     a.scales = hd->opt.storage != kF32 ? hd->d_scales : nullptr;
     a.src_bound = hd->src_bound;
+    // receivers: the TMA kernel samples its input level u^step (sample step - s0 - 1)
+    a.rec_off = hd->d_rec_off;
+    a.rec_w = hd->d_rec_w;
+    a.traces = hd->d_traces;
+    a.n_rec = hd->kernel == kTma ? hd->n_rec : 0;
+    a.rec_stride = hd->rec_nt_max;
+    const long long smp = step - hd->rec_step0 - 1;
+    a.rec_sample = (a.n_rec > 0 && smp >= 0 && smp < hd->rec_nt_max) ? int(smp) : -1;
     return a;
+}
+
+// Standalone sample of level `level` (stored in buffer u) into the traces.
+cudaError_t sample_level(const fd_handle *hd, const void *u, long long level, cudaStream_t s) {
+    const long long smp = level - hd->rec_step0 - 1;
+    if (hd->n_rec <= 0 || smp < 0 || smp >= hd->rec_nt_max) return cudaSuccess;
+    return launch_sample_receivers(u, hd->opt.storage, hd->d_scales, int((level % 3 + 3) % 3), hd->d_rec_off,
+                                   hd->d_rec_w, hd->n_rec, hd->d_traces + smp, hd->rec_nt_max, s);
 }
 
 // One step with the given launch shape; `map` holds the tensor maps of this step
@@ -254,16 +271,11 @@ cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, cudaStream_t s)
     const int ns = int(hd->sources.size());
     if (ns > kFusedSources)
         e = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources,
-                                ns - kFusedSources, hd->opt.storage, hd->opt.form == kExpanded, s);
-    if (e == cudaSuccess && hd->n_rec > 0) {
-        // receivers sample the level this step wrote (u^{n+1}: over u^{n-1} for FP32 storage,
-        // the other u buffer for 16-bit storage, whose scale is that of level n+1)
-        const long long smp = a.step - hd->rec_step0;
-        if (smp >= 0 && smp < hd->rec_nt_max)
-            e = launch_sample_receivers(hd->opt.storage == kF32 ? a.up : a.un, hd->opt.storage, hd->d_scales,
-                                        int(((a.step + 1) % 3 + 3) % 3), hd->d_rec_off, hd->d_rec_w, hd->n_rec,
-                                        hd->d_traces + smp, hd->rec_nt_max, s);
-    }
+                                ns - kFusedSources, hd->opt.storage, hd->opt.form == kExpanded,
+                                hd->extra_distinct, s);
+    if (e == cudaSuccess && hd->n_rec > 0 && hd->kernel != kTma)
+        // kernels without fused sampling: sample the level this step wrote (FP32: over u^{n-1})
+        e = sample_level(hd, a.up, a.step + 1, s);
     return e;
 }
 
@@ -425,6 +437,8 @@ int autotune(fd_handle *hd) {
     a.up = s1;
     a.un = inc ? s2 : nullptr;
     a.ns = 0;
+    a.n_rec = 0;
+    a.rec_sample = -1;
     a.scales = hd->opt.storage != kF32 ? ls : nullptr;
     a.status = check_enabled(hd) ? st : nullptr;
     const bool check = check_enabled(hd);
@@ -473,6 +487,12 @@ int upload_sources(fd_handle *hd) {
     hd->d_wavelet = nullptr;
     hd->d_src = nullptr;
     const int ns = int(hd->sources.size());
+    hd->extra_distinct = true;
+    for (int i = kFusedSources; i < ns; ++i)
+        for (int j = kFusedSources; j < i; ++j)
+            if (hd->sources[i].x == hd->sources[j].x && hd->sources[i].y == hd->sources[j].y &&
+                hd->sources[i].z == hd->sources[j].z)
+                hd->extra_distinct = false;
     hd->ld = 0;
     for (auto &s : hd->sources) hd->ld = std::max<int>(hd->ld, int(s.wavelet.size()));
     if (ns == 0) return FD_OK;
@@ -931,6 +951,10 @@ int fd_forward(fd_handle *hd, int nt) {
             err = enqueue_step(hd, a, hd->stream);
             cur ^= 1;
         }
+        // the TMA kernel samples its input level: the last level of this forward is
+        // sampled here (the next forward's first step samples it again, same values)
+        if (err == cudaSuccess && hd->n_rec > 0 && hd->kernel == kTma)
+            err = sample_level(hd, hd->ubuf[cur], hd->step + nt, hd->stream);
         cudaError_t cap = cudaStreamEndCapture(hd->stream, &graph);
         if (err != cudaSuccess || cap != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

@@ -12,7 +12,7 @@ namespace fdgb {
 
 constexpr int kMaxRadius = 8;       // space order 16
 constexpr int kMaxRadiusHost = 12;  // host weight generator reaches space order 24
-constexpr int kFusedSources = 4;    // sources injected inside the step kernel
+constexpr int kFusedSources = 4;    // sources injected inside the step kernel (more: one extra kernel)
 // TMA kernel: registers capped for 16 resident warps per SM (the kernel is
 // latency-bound: occupancy is worth more than the few spill slots this costs
 // at R = 8).
@@ -68,6 +68,12 @@ struct StepArgs {
     unsigned *status;
     LevelScales *scales;
     float src_bound;       // max_s |w_s q_s| bound used by 16-bit scale selection
+    // receivers (single-shot TMA kernel): the step samples its input level u^n
+    // into traces[r * rec_stride + rec_sample]; rec_sample < 0: no sample
+    const long long *rec_off;  // 8 pitched offsets per receiver
+    const float *rec_w;        // 8 trilinear weights per receiver
+    float *traces;
+    int n_rec, rec_stride, rec_sample;
 };
 
 // Host numerics (fd_numerics.cpp)
@@ -123,7 +129,7 @@ bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *box
 
 // Utility kernels (fd_kernels_util.cu)
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
-                                int first, int count, int storage, int expanded, cudaStream_t s);
+                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s);
 cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
                                     const long long *off, const float *w, int n, float *out, int stride,
                                     cudaStream_t s);

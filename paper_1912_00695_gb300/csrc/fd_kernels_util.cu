@@ -143,15 +143,19 @@ template <> __device__ __forceinline__ __half from_f<__half>(float v) { return _
 // add the source to both the increment d^{n+1} and u^{n+1} = u^n + d^{n+1}.
 template <typename T>
 __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *sy, const int *sz,
-                                    int first, int count, int expanded) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                                    int first, int count, int expanded, int distinct) {
+    // distinct nodes: one thread per source (no two threads touch one point);
+    // otherwise one thread adds them all in order
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (distinct ? t >= count : t != 0) return;
     if (a.step < 0 || a.step >= a.ld) return;
     T *up = static_cast<T *>(a.up);
     T *un = static_cast<T *>(a.un);
     const int n1 = slot_of(a.step + 1);
     const float s_u = a.scales ? a.scales->scale[n1] : 1.0f;
     const float s_d = a.scales ? a.scales->dscale[n1] : 1.0f;
-    for (int i = first; i < first + count; ++i) {
+    const int i0 = distinct ? first + t : first, i1 = distinct ? first + t + 1 : first + count;
+    for (int i = i0; i < i1; ++i) {
         const long long p = (long long)sx[i] * a.plane + (long long)sy[i] * a.pz + sz[i];
         const float q = a.wavelet[(long long)i * a.ld + a.step];
         const float f1 = a.f1[p], f2 = a.f2[p];
@@ -331,13 +335,16 @@ cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, f
 }
 
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
-                                int first, int count, int storage, int expanded, cudaStream_t s) {
+                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (storage == kF32) inject_extra_kernel<float><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+    const int threads = 64, blocks = distinct ? (count + threads - 1) / threads : 1;
+    const int d = distinct ? 1 : 0;
+    if (storage == kF32)
+        inject_extra_kernel<float><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
     else if (storage == kBF16)
-        inject_extra_kernel<__nv_bfloat16><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+        inject_extra_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
     else if (storage == kF16)
-        inject_extra_kernel<__half><<<1, 32, 0, s>>>(a, sx, sy, sz, first, count, expanded);
+        inject_extra_kernel<__half><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

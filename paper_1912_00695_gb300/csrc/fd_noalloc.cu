@@ -12,6 +12,9 @@
 #include "../../include/fd_acoustic.h"
 #include "fd_stencil.cuh"
 
+// sources this entry point accepts (its documented limit)
+constexpr int kNoallocSources = 4;
+
 namespace fdgb {
 void set_last_error(const char *msg);  // fd_api.cu: the fd_last_error() text
 
@@ -260,7 +263,7 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
     if (!weights_on_stack(space_order, c)) return fail(FD_EINVAL, "space_order must be even in [2, 16]");
     if (!(h > 0) || !std::isfinite(h) || !(dt > 0) || !std::isfinite(dt))
         return fail(FD_EINVAL, "h and dt must be positive and finite");
-    if (ns < 0 || ns > kFusedSources) return fail(FD_EINVAL, "ns must be in [0, 4]");
+    if (ns < 0 || ns > kNoallocSources) return fail(FD_EINVAL, "ns must be in [0, 4]");
     if (ns > 0 && (!src_xyz || !d_wavelet || ld < 1)) return fail(FD_EINVAL, "sources need src_xyz, wavelet, ld >= 1");
     if (nt < 0 || step0 < 0) return fail(FD_EINVAL, "nt and step0 must be >= 0");
     const int r = space_order / 2;

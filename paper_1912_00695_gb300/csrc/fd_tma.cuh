@@ -517,6 +517,23 @@ __device__ __forceinline__ void tma_finish(TmaAcc &acc, const ScaleState &sc) {
     }
 }
 
+// Receivers of a single-shot step: every thread of the grid samples at most a
+// few receivers from the step's input level u^n (read-only during the step),
+// trilinear, corners summed in a fixed order and dequantised with the level's
+// scale, as the standalone sampling kernel does (same values bit for bit).
+template <typename T>
+__device__ __forceinline__ void tma_sample_receivers(const StepArgs &a, float scale) {
+    const long long nthreads = (long long)gridDim.x * gridDim.y * gridDim.z * blockDim.x;
+    const long long cta = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    const T *u = static_cast<const T *>(a.u);
+    for (long long r = cta * blockDim.x + threadIdx.x; r < a.n_rec; r += nthreads) {
+        float v = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v = fmaf(a.rec_w[8 * r + c], Io<T>::to_f(u[a.rec_off[8 * r + c]]), v);
+        a.traces[r * a.rec_stride + a.rec_sample] = Io<T>::kScaled ? v * scale : v;
+    }
+}
+
 // Single-shot step: CTA (bz, by, bx) streams planes [bx x_block, (bx+1) x_block)
 // of tile (bz, by). The grid runs z-tiles fastest and x-chunks slowest, so the
 // CTAs resident at any moment cover neighbouring tiles at the same planes and
@@ -528,6 +545,7 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(cons
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
     unsigned char *ring = tma_ring_init<R, LZ, W, T>(smem_dyn);
     const ScaleState sc = read_scales<T>(a);
+    if (a.rec_sample >= 0 && a.n_rec > 0) tma_sample_receivers<T>(a, sc.s_u);
     const int xb = blockIdx.z * a.x_block;
     int g = 0;
     TmaAcc acc;

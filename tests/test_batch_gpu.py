@@ -112,7 +112,7 @@ def test_batch_errors():
     with fd.Batch(4, H) as b:
         spec = _shots(4, seed=1, count=1)[0]
         s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
-        for _ in range(4):
+        for _ in range(4):  # a batched shot holds at most 4 sources
             b.inject(s, 0, 0, 0, np.ones(3, np.float32))
         with pytest.raises(fd.FdError) as e:
             b.inject(s, 0, 0, 0, np.ones(3, np.float32))
