@@ -90,6 +90,11 @@ def _load():
                                                ctypes.c_long, ctypes.c_int, _dp, _dp, ctypes.c_long,
                                                ctypes.c_long]
         lib.oracle_forward_offgrid.restype = ctypes.c_int
+        lib.oracle_fwi_gradient.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                                            ctypes.c_long, ctypes.c_int, _dp, _dp, ctypes.c_long, _dp, _dp, _dp,
+                                            _dp]
+        lib.oracle_fwi_gradient.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -214,6 +219,35 @@ def forward_offgrid(m, eta, space_order: int, h: float, dt: float, nt: int, sour
     if rc != 0:
         raise ValueError(f"oracle forward_offgrid failed ({rc})")
     return u, up, traces[:nr, :nt]
+
+
+def fwi_gradient(m, eta, space_order: int, h: float, dt: float, nt: int, sources, wavelets, receivers,
+                 d_obs, adjoint: bool = False):
+    """Misfit J = 1/2 |d - d_obs|^2 of one shot (off-grid sources and receivers,
+    traces d^n = R u^{n+1}) and its exact discrete gradient dJ/dm.
+    Returns (grad, syn traces [nr, nt], J) and, with adjoint=True, also the
+    adjoint of the source-to-traces map applied to d_obs, [ns, nt]."""
+    m = _f64(m)
+    nx, ny, nz = m.shape
+    eta_a = None if eta is None else _f64(eta)
+    ns, nr = len(sources), len(receivers)
+    src = _f64(np.asarray(sources, dtype=np.float64).reshape(ns, 3)) if ns else np.zeros((1, 3))
+    rec = _f64(np.asarray(receivers, dtype=np.float64).reshape(nr, 3))
+    w = _f64(np.asarray(wavelets).reshape(ns, -1)) if ns else np.zeros((1, 1))
+    ld = w.shape[1] if ns else 0
+    obs = _f64(np.asarray(d_obs).reshape(nr, nt))
+    grad = np.zeros(m.shape)
+    syn = np.zeros((nr, nt))
+    J = np.zeros(1)
+    adj = np.zeros((max(ns, 1), nt)) if adjoint else None
+    rc = _load().oracle_fwi_gradient(_ptr(m), None if eta_a is None else _ptr(eta_a), nx, ny, nz, int(space_order),
+                                     float(h), float(dt), ns, _ptr(src), _ptr(w), ld, nr, _ptr(rec), _ptr(obs),
+                                     int(nt), _ptr(grad), _ptr(syn), _ptr(J), None if adj is None else _ptr(adj))
+    if rc != 0:
+        raise ValueError(f"oracle fwi_gradient failed ({rc})")
+    if adjoint:
+        return grad, syn, float(J[0]), adj[:ns]
+    return grad, syn, float(J[0])
 
 
 def energy(u_new, u_old, m, space_order: int, h: float, dt: float,

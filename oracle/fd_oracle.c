@@ -294,6 +294,154 @@ int oracle_forward_offgrid(double *u, double *u_prev, const double *m, const dou
 }
 
 /*
+ * Adjoint propagation and the FWI gradient (the paper's motivating workloads,
+ * Sec. 1 and Sec. 5; not formulated there). The forward map of one shot is the
+ * block lower-triangular system, for n = 0..nt-1 (u^0 = u^{-1} = 0),
+ *   A u^{n+1} - (dt^2 L + 2M) u^n + (M - dt/2 E) u^{n-1} = dt^2 S q^n,
+ *   A = M + dt/2 E (M = diag m, E = diag eta, S the source spreading),
+ * with traces d^n = R u^{n+1} (R the receivers' sampling). L, M, E and A are
+ * symmetric, so the transposed system is solved backward in time:
+ *   A w^{n+1} = (dt^2 L + 2M) w^{n+2} - (M - dt/2 E) w^{n+3} + R^T r^n,
+ * n = nt-1..0, w^{nt+1} = w^{nt+2} = 0, for the data-space vector r. For the
+ * misfit J(m) = 1/2 sum_{r,n} (d^n - d_obs^n)^2, r = d - d_obs and, since only
+ * the system matrix depends on m (dA/dm = dM/dm = I),
+ *   dJ/dm = - sum_{n=0}^{nt-1} w^{n+1} * (u^{n+1} - 2u^n + u^{n-1})   (pointwise).
+ * The adjoint of q -> d is (F^T r)^n = dt^2 S^T w^{n+1}.
+ *
+ * oracle_fwi_gradient: forward run keeping every level, traces, misfit, the
+ * backward recursion written out as above, the gradient. src/rec: continuous
+ * domain coordinates (trilinear spreading/sampling as oracle_forward_offgrid).
+ * Outputs: grad[nx*ny*nz], syn[nr*nt] (synthetic traces), *misfit; adj_src
+ * (if not NULL) receives (F^T d_obs)^n at each source, [ns*nt] (with r = d_obs).
+ * Returns 0, -1 on bad arguments, -2 on allocation failure.
+ */
+int oracle_fwi_gradient(const double *m, const double *eta, long nx, long ny, long nz, int k, double h,
+                        double dt, int ns, const double *src, const double *wavelet, long ld, int nr,
+                        const double *rec, const double *d_obs, long nt, double *grad, double *syn,
+                        double *misfit, double *adj_src) {
+    size_t n = (size_t)nx * (size_t)ny * (size_t)nz;
+    if (nt < 1 || nr < 1) return -1;
+    double *hist = (double *)calloc(n * (size_t)(nt + 2), sizeof(double)); /* u^{-1}, u^0, ..., u^nt */
+    double *u = (double *)calloc(n, sizeof(double));
+    double *up = (double *)calloc(n, sizeof(double));
+    double *w1 = (double *)calloc(n, sizeof(double)); /* w^{j+1} */
+    double *w2 = (double *)calloc(n, sizeof(double)); /* w^{j+2} */
+    double *lap = (double *)malloc(n * sizeof(double));
+    double *wn = (double *)malloc(n * sizeof(double));
+    long *rnodes = (long *)malloc(sizeof(long) * 24 * (size_t)nr);
+    double *rw = (double *)malloc(sizeof(double) * 8 * (size_t)nr);
+    long *snodes = (long *)malloc(sizeof(long) * 24 * (size_t)(ns > 0 ? ns : 1));
+    double *sw = (double *)malloc(sizeof(double) * 8 * (size_t)(ns > 0 ? ns : 1));
+    int rc = 0;
+    if (!hist || !u || !up || !w1 || !w2 || !lap || !wn || !rnodes || !rw || !snodes || !sw) rc = -2;
+    for (int r = 0; r < nr && rc == 0; ++r)
+        if (oracle_trilinear(rec[3 * r], rec[3 * r + 1], rec[3 * r + 2], nx, ny, nz, rnodes + 24 * r, rw + 8 * r))
+            rc = -1;
+    for (int s = 0; s < ns && rc == 0; ++s)
+        if (oracle_trilinear(src[3 * s], src[3 * s + 1], src[3 * s + 2], nx, ny, nz, snodes + 24 * s, sw + 8 * s))
+            rc = -1;
+    /* forward one step at a time, every level kept: hist slot j + 1 holds u^j */
+    for (long it = 0; it < nt && rc == 0; ++it) {
+        rc = oracle_forward_offgrid(u, up, m, eta, nx, ny, nz, k, h, dt, 0, ns, src, wavelet, ld, 0, rec, NULL,
+                                    it, 1);
+        if (rc == 0) memcpy(hist + n * (size_t)(it + 2), u, n * sizeof(double));
+    }
+    /* traces d^n = R u^{n+1} and the misfit */
+    double J = 0.0;
+    for (int r = 0; r < nr && rc == 0; ++r)
+        for (long it = 0; it < nt; ++it) {
+            const double *un = hist + n * (size_t)(it + 2);
+            double v = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                const long *nd = rnodes + 24 * r + 3 * c;
+                v += rw[8 * r + c] * un[idx3(nd[0], nd[1], nd[2], ny, nz)];
+            }
+            syn[(size_t)r * (size_t)nt + (size_t)it] = v;
+            const double res = v - d_obs[(size_t)r * (size_t)nt + (size_t)it];
+            J += 0.5 * res * res;
+        }
+    if (rc == 0) *misfit = J;
+    /* backward recursion for r = syn - d_obs, and the gradient */
+    if (rc == 0) {
+        memset(grad, 0, n * sizeof(double));
+        if (adj_src) memset(adj_src, 0, sizeof(double) * (size_t)(ns > 0 ? ns : 0) * (size_t)nt);
+    }
+    for (long it = nt - 1; it >= 0 && rc == 0; --it) {
+        /* w^{it+1} from w1 = w^{it+2}, w2 = w^{it+3} */
+        rc = oracle_laplacian(w1, lap, nx, ny, nz, k, h, 0);
+        if (rc != 0) break;
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)n; ++i) {
+            double e = eta ? eta[i] : 0.0;
+            wn[i] = dt * dt * lap[i] + 2.0 * m[i] * w1[i] - (m[i] - 0.5 * dt * e) * w2[i];
+        }
+        for (int r = 0; r < nr; ++r) {
+            const double res = syn[(size_t)r * (size_t)nt + (size_t)it] - d_obs[(size_t)r * (size_t)nt + (size_t)it];
+            for (int c = 0; c < 8; ++c) {
+                const long *nd = rnodes + 24 * r + 3 * c;
+                wn[idx3(nd[0], nd[1], nd[2], ny, nz)] += rw[8 * r + c] * res;
+            }
+        }
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)n; ++i) {
+            double e = eta ? eta[i] : 0.0;
+            wn[i] /= m[i] + 0.5 * dt * e;
+        }
+        /* gradient term n = it: - w^{it+1} (u^{it+1} - 2u^{it} + u^{it-1}) */
+        const double *a = hist + n * (size_t)(it + 2), *b = hist + n * (size_t)(it + 1), *c0 = hist + n * (size_t)it;
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)n; ++i) grad[i] -= wn[i] * (a[i] - 2.0 * b[i] + c0[i]);
+        memcpy(w2, w1, n * sizeof(double));
+        memcpy(w1, wn, n * sizeof(double));
+    }
+    /* adjoint of q -> d applied to d_obs: a second backward sweep with r = d_obs */
+    if (rc == 0 && adj_src && ns > 0) {
+        memset(w1, 0, n * sizeof(double));
+        memset(w2, 0, n * sizeof(double));
+        for (long it = nt - 1; it >= 0 && rc == 0; --it) {
+            rc = oracle_laplacian(w1, lap, nx, ny, nz, k, h, 0);
+            if (rc != 0) break;
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < (long)n; ++i) {
+                double e = eta ? eta[i] : 0.0;
+                wn[i] = dt * dt * lap[i] + 2.0 * m[i] * w1[i] - (m[i] - 0.5 * dt * e) * w2[i];
+            }
+            for (int r = 0; r < nr; ++r)
+                for (int c = 0; c < 8; ++c) {
+                    const long *nd = rnodes + 24 * r + 3 * c;
+                    wn[idx3(nd[0], nd[1], nd[2], ny, nz)] += rw[8 * r + c] * d_obs[(size_t)r * (size_t)nt + (size_t)it];
+                }
+            for (long i = 0; i < (long)n; ++i) {
+                double e = eta ? eta[i] : 0.0;
+                wn[i] /= m[i] + 0.5 * dt * e;
+            }
+            for (int s = 0; s < ns; ++s) {
+                double v = 0.0;
+                for (int c = 0; c < 8; ++c) {
+                    const long *nd = snodes + 24 * s + 3 * c;
+                    v += sw[8 * s + c] * wn[idx3(nd[0], nd[1], nd[2], ny, nz)];
+                }
+                adj_src[(size_t)s * (size_t)nt + (size_t)it] = dt * dt * v;
+            }
+            memcpy(w2, w1, n * sizeof(double));
+            memcpy(w1, wn, n * sizeof(double));
+        }
+    }
+    free(hist);
+    free(u);
+    free(up);
+    free(w1);
+    free(w2);
+    free(lap);
+    free(wn);
+    free(rnodes);
+    free(rw);
+    free(snodes);
+    free(sw);
+    return rc;
+}
+
+/*
  * Discrete energy between levels n and n+1 of the undamped, source-free scheme:
  *   E^{n+1/2} = sum m ((u^{n+1} - u^n)/dt)^2 - sum u^{n+1} (L u^n).
  * Multiplying the scheme by (u^{n+1} - u^{n-1}) and using the symmetry of L
