@@ -383,6 +383,74 @@ def run_receivers(args, rank: int, world: int):
     rshot.close()
 
 
+def run_gradient(args, rank: int, world: int):
+    """FWI gradient of one shot (forward pass storing the second time difference
+    of every step, adjoint pass backward in time with the residuals injected at
+    the receivers and the gradient accumulated in its step kernel): the sweep
+    shot (256^3 + 10, 4-layer model, 15 Hz Ricker at (128,128,20)), space order 8,
+    500 steps, (n-1)^2 receivers at (i + 1/2, j + 1/2, 10.5), d_obs = 0 (the
+    residual is the synthetic data; the cost does not depend on it)."""
+    import torch
+
+    import paper_1912_00695_gb300 as fd
+    from paper_1912_00695_gb300 import inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    spec = inputs.sweep_shot(args.rec_order, n=args.n, nt=args.nt)
+    dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+    m = spec.m
+    wav = inputs.ricker(spec.f0, dt, spec.nt)
+    n = args.n
+    g = np.arange(n - 1, dtype=np.float64) + 0.5
+    rx, ry = np.meshgrid(g, g, indexing="ij")
+    recs = np.stack([rx.ravel(), ry.ravel(), np.full(rx.size, 10.5)], axis=1)
+    obs = np.zeros((len(recs), spec.nt), np.float32)
+    shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl)
+    shot.set_model(m)
+    shot.inject(*spec.source, wav)
+    for _ in range(args.warmup):
+        shot.fwi_gradient(recs, obs)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    dev_ms, wall = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        shot.fwi_gradient(recs, obs)
+        wall.append(time.perf_counter() - t0)
+        dev_ms.append(shot.last_forward_ms())
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(dev_ms))
+    wall_s = max_over_ranks(sum(wall) * 1e3) * 1e-3
+    updates = 2 * spec.points * spec.nt * args.steps * world
+    peak, peak_kind = _peaks()
+    layer = layer_points(spec)
+    # forward: u^n, u^{n-1}, w read, u^{n+1} and D written (16 + 4 B); adjoint: the same
+    # step (16 B) plus D read and the gradient read and written (12 B); g in the layer
+    alg = (spec.points * (20 + 28) + 2 * layer * 4) * spec.nt * args.steps
+    line = {
+        "metric": "FWI gradient Gpts/s (forward + adjoint point updates per second), 256^3+10, space order 8",
+        "value": round(updates / (ms * 1e-3) / 1e9, 3), "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered velocity model, Ricker source, zero observed data)",
+        "config": {"workload": f"fwi gradient: {n}^3+10, space order {spec.space_order}, {spec.nt} steps, "
+                               f"{len(recs)} receivers at depth 10.5, history {spec.nt} x "
+                               f"{spec.points * 4 / 1e6:.0f} MB in HBM",
+                   "receivers": len(recs), "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                     "kernel": "fd_tma_grad_kernel (forward D / adjoint gradient)", "peak_source": peak_kind},
+        "e2e": {"value": round(updates / wall_s / 1e9, 3), "unit": "Gpts/s",
+                "h2d_bytes_per_step": int(obs.nbytes), "d2h_bytes_per_step": int(m.nbytes + obs.nbytes)},
+        "gpu_launches": (3 * spec.nt + 2) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    shot.close()
+
+
 def run_batched(args, rank: int, world: int):
     """64 uneven shots (each axis U{96..256} + 10, smooth random velocity, k=8,
     300 steps): the batch (one launch per step over all shots) against the same
@@ -744,7 +812,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "plain", "batched", "precision", "serving", "receivers"])
+                    choices=["sweep", "plain", "batched", "precision", "serving", "receivers", "gradient"])
     ap.add_argument("--requests", type=int, default=40, help="serving: requests in the trace")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--serve-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(128, 256),
@@ -764,7 +832,7 @@ def main():
                     help="batched workload: tile as ZxY (32x16 or 64x8; default 32x16)")
     ap.add_argument("--shot-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(96, 256),
                     help="batched workload: interior size range lo,hi per axis")
-    ap.add_argument("--rec-order", type=int, default=8, help="receivers workload: space order")
+    ap.add_argument("--rec-order", type=int, default=8, help="receivers/gradient workloads: space order")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -790,6 +858,8 @@ def main():
         run_serving(args, rank, world)
     elif args.workload == "receivers":
         run_receivers(args, rank, world)
+    elif args.workload == "gradient":
+        run_gradient(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -178,6 +178,29 @@ int fd_inject_at(fd_handle *hd, double x, double y, double z, const float *wavel
  * for a point outside the interior; FD_ENOMEM. */
 int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max);
 
+/* FWI gradient of one shot (the adjoint workflow the paper names as its
+ * motivation, Sec. 1 and Sec. 5; FP32 storage, factored form, TMA kernel).
+ * Runs the handle's shot (its sources, from step 0: the handle is reset and
+ * ends at step nt with these receivers set) for nt steps, records the traces
+ * d^n = R u^{n+1} at the nrec receivers (rec_xyz as fd_set_receivers), and
+ * returns the misfit J = 1/2 sum (d - d_obs)^2 (FP64 sum) and its exact
+ * discrete gradient with respect to m (eta held fixed):
+ *   dJ/dm = - sum_{n<nt} w^{n+1} (u^{n+1} - 2u^n + u^{n-1}),
+ * w the adjoint field: the same step run backward in time from
+ * w^{nt+1} = w^{nt+2} = 0 with the residuals injected at the receivers
+ * (spreading = transpose of the sampling). The forward pass stores the second
+ * time difference of every step in device memory (nt fields of the pitched
+ * size: FD_ENOMEM if it does not fit), fused into the step kernel; the adjoint
+ * pass accumulates the gradient in its step kernel. d_obs: HOST [nrec][nt];
+ * grad_out: HOST N_x*N_y*N_z floats (C-order, whole domain); syn_out: HOST
+ * [nrec][nt] synthetic traces or NULL. FD_EINVAL/FD_ERANGE for bad
+ * arguments, FD_ESTATE without a model, FD_ENOTSUP for other storage/form/
+ * kernel choices. Synchronises; fd_last_forward_ms then returns the device
+ * time of the two passes (which run back to back: the residual is formed on
+ * the device). */
+int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt, float *grad_out,
+                    float *syn_out, double *misfit);
+
 /* Copy the traces into HOST memory out[n * nt_max] (r-major; samples not yet
  * recorded are zero) and the number of recorded samples per receiver into
  * *recorded. Synchronises the handle's stream; returns the device status like

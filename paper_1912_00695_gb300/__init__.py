@@ -22,7 +22,7 @@ from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
                    fd_forward, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
-                   fd_load_state, fd_read_traces, fd_set_receivers,
+                   fd_load_state, fd_read_traces, fd_set_receivers, fd_fwi_gradient,
                    fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
                    fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
                    fd_set_model_device, fd_set_stream, fd_status, fd_synchronize, fd_version)
@@ -220,6 +220,15 @@ class Shot:
         out = np.empty(n * nt_max, dtype=np.float32)
         done = fd_read_traces(self.handle, out)
         return out.reshape(n, nt_max)[:, :done]
+
+    def fwi_gradient(self, receivers, d_obs):
+        """(dJ/dm over the domain, synthetic traces [nrec, nt], misfit J) of this
+        shot against observed traces d_obs [nrec, nt] at the receivers."""
+        d_obs = np.asarray(d_obs, dtype=np.float32)
+        grad = np.empty(self.shape, dtype=np.float32)
+        syn = np.empty(d_obs.shape, dtype=np.float32)
+        J = fd_fwi_gradient(self.handle, receivers, d_obs, grad, syn)
+        return grad, syn, J
 
     def wavefield(self, level=0, out=None) -> np.ndarray:
         if out is None:

@@ -915,6 +915,165 @@ int fd_read_traces(fd_handle *hd, float *out, int *recorded) {
     return check_enabled(hd) ? read_status(hd) : FD_OK;
 }
 
+int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt, float *grad_out,
+                    float *syn_out, double *misfit) {
+    if (!hd || nrec < 1 || !rec_xyz || !d_obs || nt < 1 || !grad_out || !misfit)
+        return fail(FD_EINVAL, "bad receivers, data, nt or output pointers");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_fwi_gradient before fd_set_model");
+    if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->kernel != kTma)
+        return fail(FD_ENOTSUP, "the FWI gradient runs on FP32 storage, factored form, TMA kernel");
+    if ((long long)nrec * nt > (1LL << 31)) return fail(FD_EINVAL, "nrec * nt above 2^31 samples");
+    for (int r = 0; r < nrec; ++r)
+        if (!interior_point_ok(hd, rec_xyz[3 * r], rec_xyz[3 * r + 1], rec_xyz[3 * r + 2]))
+            return fail(FD_ERANGE, "receiver %d outside the interior", r);
+    const int tz = 32, ty = 16;  // the gradient passes' tile
+    const int xb = (hd->tile_z == tz && hd->tile_y == ty && hd->x_block > 0) ? hd->x_block
+                                                                              : heuristic_x_block(hd, tz, ty);
+    cudaStream_t st = hd->stream;
+    const size_t np = hd->n_pitched;
+    // workspace: the second-time-difference history (one level per step), the gradient,
+    // two adjoint fields, the residuals and the receivers' node lists
+    float *hist = nullptr, *grad = nullptr, *w[2] = {nullptr, nullptr}, *resid = nullptr;
+    long long *node_off = nullptr;
+    int *row = nullptr, *rec_idx = nullptr;
+    float *rec_w = nullptr;
+    auto release = [&]() {
+        void *bufs[] = {hist, grad, w[0], w[1], resid, node_off, row, rec_idx, rec_w};
+        for (void *p : bufs) dev_free(p, st);
+    };
+    // the receivers' spreading as a node-major list (fixed order within a node)
+    struct Entry {
+        long long off;
+        int rec;
+        float w;
+    };
+    std::vector<Entry> ent;
+    for (int r = 0; r < nrec; ++r) {
+        int nodes[8][3];
+        double wd[8];
+        trilinear_nodes(hd, rec_xyz[3 * r], rec_xyz[3 * r + 1], rec_xyz[3 * r + 2], nodes, wd);
+        for (int c = 0; c < 8; ++c)
+            if (wd[c] > 0.0)
+                ent.push_back({(long long)nodes[c][0] * hd->plane + (long long)nodes[c][1] * hd->pz + nodes[c][2], r,
+                               float(wd[c])});
+    }
+    std::stable_sort(ent.begin(), ent.end(), [](const Entry &a, const Entry &b) { return a.off < b.off; });
+    std::vector<long long> h_node;
+    std::vector<int> h_row, h_rec;
+    std::vector<float> h_w;
+    for (size_t e = 0; e < ent.size(); ++e) {
+        if (e == 0 || ent[e].off != ent[e - 1].off) {
+            h_node.push_back(ent[e].off);
+            h_row.push_back(int(e));
+        }
+        h_rec.push_back(ent[e].rec);
+        h_w.push_back(ent[e].w);
+    }
+    h_row.push_back(int(ent.size()));
+    const int n_nodes = int(h_node.size());
+    if (dev_alloc(reinterpret_cast<void **>(&hist), size_t(nt) * np * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&grad), np * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&w[0]), np * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&w[1]), np * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&resid), size_t(nrec) * nt * sizeof(float), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&node_off), h_node.size() * sizeof(long long), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&row), h_row.size() * sizeof(int), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&rec_idx), h_rec.size() * sizeof(int), st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&rec_w), h_w.size() * sizeof(float), st) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(FD_ENOMEM, "cannot allocate the gradient workspace (%.1f GB of history)",
+                    double(nt) * double(np) * 4e-9);
+    }
+    auto cuda_fail = [&](cudaError_t e) {
+        release();
+        return fail(FD_ECUDA, "fd_fwi_gradient: %s", cudaGetErrorString(e));
+    };
+    // d_obs goes to the residual buffer now; the residual is formed on the device after
+    // the forward pass, so that the two passes run back to back
+    cudaError_t e = cudaMemcpyAsync(resid, d_obs, size_t(nrec) * nt * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(node_off, h_node.data(), h_node.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(row, h_row.data(), h_row.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rec_idx, h_rec.data(), h_rec.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rec_w, h_w.data(), h_w.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // forward pass: every step also stores D^n = u^{n+1} - 2u^n + u^{n-1}; receivers record the traces
+    int rc = fd_reset(hd);
+    if (rc == FD_OK) rc = fd_set_receivers(hd, nrec, rec_xyz, nt);
+    TmaMaps fm[2], am[2];
+    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], tz, ty, &fm[b]);
+    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, w[b], w[b ^ 1], tz, ty, &am[b]);
+    if (rc != FD_OK) {
+        release();
+        return rc;
+    }
+    const bool check = check_enabled(hd);
+    const int ns = int(hd->sources.size());
+    int cur = hd->cur;
+    e = cudaEventRecord(hd->ev0, st);  // device time of both passes: fd_last_forward_ms
+    for (int n = 0; n < nt && e == cudaSuccess; ++n) {
+        StepArgs a = make_args(hd, n, cur);
+        a.x_block = xb;
+        a.hist = hist + size_t(n) * np;
+        e = launch_tma_grad_step(hd->r, kModeForwardD, fm[cur], a, check, st);
+        if (e == cudaSuccess && ns > kFusedSources)
+            e = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources, ns - kFusedSources,
+                                    kF32, 0, hd->extra_distinct, st, a.hist);
+        cur ^= 1;
+    }
+    if (e == cudaSuccess) e = sample_level(hd, hd->ubuf[cur], nt, st);
+    hd->step = nt;
+    hd->cur = cur;
+    // residual r = d - d_obs (in place over d_obs)
+    if (e == cudaSuccess) e = launch_residual(hd->d_traces, resid, size_t(nrec) * nt, st);
+    // adjoint pass, backward in time: w^k over w^{k+2} from w^{k+1}, the residual of
+    // step k-1 injected at the receivers' nodes, gradient -= w^k D^{k-1}
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w[0], 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w[1], 0, np * sizeof(float), st);
+    const float inv_dt2 = float(1.0 / (hd->dt * hd->dt));
+    int c = 0;  // w[c] holds w^{k+1}, w[c^1] w^{k+2}
+    for (int s = 0; s < nt && e == cudaSuccess; ++s) {
+        const int k = nt - s;
+        StepArgs a = make_args(hd, 0, 0);
+        a.u = w[c];
+        a.up = w[c ^ 1];
+        a.ns = 0;
+        a.n_rec = 0;
+        a.rec_sample = -1;
+        a.x_block = xb;
+        a.hist = hist + size_t(k - 1) * np;
+        a.grad = grad;
+        e = launch_tma_grad_step(hd->r, kModeAdjointGrad, am[c], a, check, st);
+        if (e == cudaSuccess)
+            e = launch_adjoint_inject(w[c ^ 1], grad, a.hist, hd->f1, node_off, row, rec_idx, rec_w, resid, nt, k - 1,
+                                      inv_dt2, n_nodes, st);
+        c ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, st);
+    hd->timed = e == cudaSuccess;
+    // the traces (synthetic data) and the misfit (FP64 sum on the host) while the copies run
+    std::vector<float> syn(size_t(nrec) * nt);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(syn.data(), hd->d_traces, syn.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+    const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(grad_out, row_bytes, grad, size_t(hd->pz) * sizeof(float), row_bytes,
+                              size_t(hd->Nx) * hd->Ny, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    double J = 0.0;
+    for (size_t i = 0; i < syn.size(); ++i) {
+        const double d = double(syn[i]) - double(d_obs[i]);
+        J += 0.5 * d * d;
+    }
+    if (syn_out) std::memcpy(syn_out, syn.data(), syn.size() * sizeof(float));
+    *misfit = J;
+    release();
+    return check ? read_status(hd) : FD_OK;
+}
+
 int fd_clear_sources(fd_handle *hd) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
     hd->sources.clear();

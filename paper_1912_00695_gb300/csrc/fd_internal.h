@@ -13,6 +13,13 @@ namespace fdgb {
 constexpr int kMaxRadius = 8;       // space order 16
 constexpr int kMaxRadiusHost = 12;  // host weight generator reaches space order 24
 constexpr int kFusedSources = 4;    // sources injected inside the step kernel (more: one extra kernel)
+// Epilogue modes of the FP32 factored TMA step (the FWI gradient's two passes):
+// kModeStep the plain step; kModeForwardD also stores the second time
+// difference D^n = u^{n+1} - 2u^n + u^{n-1} (this step's fused sources
+// included) into StepArgs::hist; kModeAdjointGrad (the adjoint field w^k
+// computed over w^{k+2} from w^{k+1}) accumulates grad -= w^k * D^{k-1}, D
+// read from StepArgs::hist.
+constexpr int kModeStep = 0, kModeForwardD = 1, kModeAdjointGrad = 2;
 // TMA kernel: registers capped for 16 resident warps per SM (the kernel is
 // latency-bound: occupancy is worth more than the few spill slots this costs
 // at R = 8).
@@ -74,6 +81,10 @@ struct StepArgs {
     const float *rec_w;        // 8 trilinear weights per receiver
     float *traces;
     int n_rec, rec_stride, rec_sample;
+    // FWI gradient passes: this step's slot of the second-time-difference
+    // history (forward: written; adjoint: read) and the gradient (adjoint)
+    float *hist;
+    float *grad;
 };
 
 // Host numerics (fd_numerics.cpp)
@@ -129,7 +140,14 @@ bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *box
 
 // Utility kernels (fd_kernels_util.cu)
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
-                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s);
+                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s,
+                                float *hist = nullptr);
+cudaError_t launch_residual(const float *syn, float *obs_to_res, size_t n, cudaStream_t s);
+cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, const float *f1,
+                                  const long long *node_off, const int *row, const int *rec_idx, const float *rec_w,
+                                  const float *resid, int nt, int t, float inv_dt2, int n_nodes, cudaStream_t s);
+cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
+                                 cudaStream_t s);
 cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
                                     const long long *off, const float *w, int n, float *out, int stride,
                                     cudaStream_t s);

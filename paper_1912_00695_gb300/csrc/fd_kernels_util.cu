@@ -97,6 +97,31 @@ cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z,
     }
 }
 
+#define FDGB_DECLARE_GRAD_RADIUS(R)                                                              \
+    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const StepArgs &a, bool check, \
+                                         cudaStream_t s);
+FDGB_DECLARE_GRAD_RADIUS(1)
+FDGB_DECLARE_GRAD_RADIUS(2)
+FDGB_DECLARE_GRAD_RADIUS(3)
+FDGB_DECLARE_GRAD_RADIUS(4)
+FDGB_DECLARE_GRAD_RADIUS(5)
+FDGB_DECLARE_GRAD_RADIUS(6)
+FDGB_DECLARE_GRAD_RADIUS(7)
+FDGB_DECLARE_GRAD_RADIUS(8)
+#undef FDGB_DECLARE_GRAD_RADIUS
+
+cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
+                                 cudaStream_t s) {
+    switch (radius) {
+#define FDGB_GRAD_R(R) \
+        case R: return tma_grad_step_radius_##R(mode, map, a, check, s);
+        FDGB_GRAD_R(1) FDGB_GRAD_R(2) FDGB_GRAD_R(3) FDGB_GRAD_R(4)
+        FDGB_GRAD_R(5) FDGB_GRAD_R(6) FDGB_GRAD_R(7) FDGB_GRAD_R(8)
+#undef FDGB_GRAD_R
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {
@@ -143,7 +168,7 @@ template <> __device__ __forceinline__ __half from_f<__half>(float v) { return _
 // add the source to both the increment d^{n+1} and u^{n+1} = u^n + d^{n+1}.
 template <typename T>
 __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *sy, const int *sz,
-                                    int first, int count, int expanded, int distinct) {
+                                    int first, int count, int expanded, int distinct, float *hist) {
     // distinct nodes: one thread per source (no two threads touch one point);
     // otherwise one thread adds them all in order
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,8 +190,27 @@ __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *
             un[p] = from_f<T>((to_f<T>(un[p]) * s_u + w * q) / s_u);
         } else {
             up[p] = from_f<T>(to_f<T>(up[p]) * s_u + w * q);
+            if (hist) hist[p] += w * q;  // the stored second time difference includes the source
         }
     }
+}
+
+// Adjoint sources of the FWI gradient: receiver residuals r^t spread onto
+// their nodes (the transpose of the trilinear sampling), gathered per node in a
+// fixed order (CSR: node i takes entries row[i]..row[i+1]); the node gets
+// w += inc = (dt^2/A) (R^T r)/dt^2 and the gradient its share -inc * D.
+__global__ void adjoint_inject_kernel(float *w, float *grad, const float *dhist, const float *f1,
+                                      const long long *node_off, const int *row, const int *rec_idx,
+                                      const float *rec_w, const float *resid, int nt, int t, float inv_dt2,
+                                      int n_nodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    float s = 0.0f;
+    for (int e = row[i]; e < row[i + 1]; ++e) s = fmaf(rec_w[e], resid[(long long)rec_idx[e] * nt + t], s);
+    const long long p = node_off[i];
+    const float inc = f1[p] * (s * inv_dt2);
+    w[p] += inc;
+    grad[p] = fmaf(-inc, dhist[p], grad[p]);
 }
 
 // Receivers: trilinear interpolation of the new level u^{n+1} (stored values
@@ -335,17 +379,40 @@ cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, f
 }
 
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
-                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s) {
+                                int first, int count, int storage, int expanded, bool distinct, cudaStream_t s,
+                                float *hist) {
     if (count <= 0) return cudaSuccess;
     const int threads = 64, blocks = distinct ? (count + threads - 1) / threads : 1;
     const int d = distinct ? 1 : 0;
     if (storage == kF32)
-        inject_extra_kernel<float><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
+        inject_extra_kernel<float><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d, hist);
     else if (storage == kBF16)
-        inject_extra_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
+        inject_extra_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d,
+                                                                      nullptr);
     else if (storage == kF16)
-        inject_extra_kernel<__half><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d);
+        inject_extra_kernel<__half><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d, nullptr);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, const float *f1,
+                                  const long long *node_off, const int *row, const int *rec_idx, const float *rec_w,
+                                  const float *resid, int nt, int t, float inv_dt2, int n_nodes, cudaStream_t s) {
+    if (n_nodes <= 0) return cudaSuccess;
+    const int threads = 128, blocks = (n_nodes + threads - 1) / threads;
+    adjoint_inject_kernel<<<blocks, threads, 0, s>>>(w, grad, dhist, f1, node_off, row, rec_idx, rec_w, resid, nt, t,
+                                                     inv_dt2, n_nodes);
+    return cudaGetLastError();
+}
+
+__global__ void residual_kernel(const float *syn, float *obs_to_res, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        obs_to_res[i] = syn[i] - obs_to_res[i];
+}
+
+cudaError_t launch_residual(const float *syn, float *obs_to_res, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    residual_kernel<<<608, 256, 0, s>>>(syn, obs_to_res, (long long)n);
     return cudaGetLastError();
 }
 

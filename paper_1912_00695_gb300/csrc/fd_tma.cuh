@@ -218,7 +218,7 @@ __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw)
 // already streamed through its ring (it selects the stage and the mbarrier
 // phase, so consecutive segments share one ring without re-initialising it).
 // Returns false if a wait gave up (status set, copies in flight drained).
-template <int R, int FORM, int LZ, int W, typename T>
+template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep>
 __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs &a, const ScaleState &sc, int bz,
                                             int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc) {
     using G = TmaShape<R, LZ, W, T>;
@@ -243,6 +243,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     const T *__restrict__ u = static_cast<const T *>(a.u) + col;
     T *up = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
     T *un = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
+    static_assert(MODE == kModeStep || (FORM == kFactored && !Io<T>::kScaled), "gradient modes: FP32 factored");
+    float *hist = MODE != kModeStep ? a.hist + col : nullptr;
+    float *grad = MODE == kModeAdjointGrad ? a.grad + col : nullptr;
     const int g0 = g;
     g += xe - xb;
 
@@ -341,6 +344,13 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
             }
             const unsigned char *st = ring + stage * G::STAGE_BYTES;
             q[2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + pt_off);
+            float4 dv, gv;  // adjoint pass: D^{k-1} and the gradient at this plane, loaded early
+            if constexpr (MODE == kModeAdjointGrad) {
+                if (own) {
+                    dv = __ldcs(reinterpret_cast<const float4 *>(hist + x * P));
+                    gv = *reinterpret_cast<const float4 *>(grad + x * P);
+                }
+            }
             if (own) {
                 const float4 cum = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + pt_off);
                 const float4 cf1 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + pt_off);
@@ -479,6 +489,17 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     amax_bits = max(amax_bits, bits4(out));
                 }
                 V::st(up + x * P, out);
+                if constexpr (MODE == kModeForwardD) {
+                    // D = (u^{n+1} - 2u^n) + u^{n-1}; FP32 factored: cum is u^{n-1}
+                    const float4 d4 = make_float4(fmaf(-2.0f, uc.x, out.x) + cum.x, fmaf(-2.0f, uc.y, out.y) + cum.y,
+                                                  fmaf(-2.0f, uc.z, out.z) + cum.z, fmaf(-2.0f, uc.w, out.w) + cum.w);
+                    __stcs(reinterpret_cast<float4 *>(hist + x * P), d4);
+                }
+                if constexpr (MODE == kModeAdjointGrad) {
+                    gv = make_float4(fmaf(-out.x, dv.x, gv.x), fmaf(-out.y, dv.y, gv.y), fmaf(-out.z, dv.z, gv.z),
+                                     fmaf(-out.w, dv.w, gv.w));
+                    *reinterpret_cast<float4 *>(grad + x * P) = gv;
+                }
             }
             if (++stage == S) {
                 stage = 0;
@@ -555,6 +576,46 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(cons
         tma_finish<T>(acc, sc);
         reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
     }
+}
+
+// The FWI gradient's passes (FP32 factored; sources and receivers as the step).
+template <int R, int LZ, int W, int MODE>
+__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_grad_kernel(const __grid_constant__ TmaMaps maps,
+                                                             const StepArgs a, int check) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *ring = tma_ring_init<R, LZ, W, float>(smem_dyn);
+    const ScaleState sc = read_scales<float>(a);
+    if (a.rec_sample >= 0 && a.n_rec > 0) tma_sample_receivers<float>(a, 1.0f);
+    const int xb = blockIdx.z * a.x_block;
+    int g = 0;
+    TmaAcc acc;
+    if (tma_segment<R, kFactored, LZ, W, float, MODE>(&maps, a, sc, blockIdx.x, blockIdx.y, xb,
+                                                      min(xb + a.x_block, a.Nx), ring, g, acc) &&
+        check)
+        reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
+}
+
+template <int R, int LZ, int W, int MODE>
+cudaError_t tma_grad_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W, float>;
+    auto kernel = fd_tma_grad_kernel<R, LZ, W, MODE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY, (a.Nx + a.x_block - 1) / a.x_block);
+    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(maps, a, check ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Gradient passes exist for the 32x16 tile (LZ 8, W 4) only.
+template <int R>
+cudaError_t tma_grad_step_r(int mode, const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
+    if (mode == kModeForwardD) return tma_grad_launch<R, 8, 4, kModeForwardD>(map, a, check, s);
+    if (mode == kModeAdjointGrad) return tma_grad_launch<R, 8, 4, kModeAdjointGrad>(map, a, check, s);
+    return cudaErrorInvalidValue;
 }
 
 template <int R, int FORM, int LZ, int W, typename T>
@@ -711,5 +772,9 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
                                           const BatchShot *shots, const int4 *items, int n_items, \
                                           int offset, cudaStream_t s) {                           \
         return tma_batch_step_r<R>(form, storage, tile_z, tile_y, shots, items, n_items, offset, s); \
+    }                                                                                             \
+    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const StepArgs &a, bool check, \
+                                         cudaStream_t s) {                                        \
+        return tma_grad_step_r<R>(mode, map, a, check, s);                                        \
     }                                                                                             \
     }
