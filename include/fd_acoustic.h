@@ -197,9 +197,22 @@ int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max);
  * arguments, FD_ESTATE without a model, FD_ENOTSUP for other storage/form/
  * kernel choices. Synchronises; fd_last_forward_ms then returns the device
  * time of the two passes (which run back to back: the residual is formed on
- * the device). */
+ * the device). When the history does not fit in 80 % of the free device
+ * memory, the call checkpoints instead (as fd_fwi_gradient_checkpointed with
+ * segment = ceil(sqrt(nt))). */
 int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt, float *grad_out,
                     float *syn_out, double *misfit);
+
+/* As fd_fwi_gradient with wavefield checkpointing: the forward pass keeps only
+ * the states (u^j, u^{j-1}) at j = 0, segment, 2 segment, ...; the adjoint
+ * pass recomputes each segment's history from its checkpoint just before it
+ * is needed (one extra forward pass; device memory about 2 nt/segment +
+ * segment + 4 fields instead of nt + 4). The recomputation repeats the same
+ * per-point arithmetic, so the gradient, traces and misfit equal those of
+ * fd_fwi_gradient bit for bit. segment >= nt is the full history; FD_EINVAL
+ * for segment < 1. */
+int fd_fwi_gradient_checkpointed(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt,
+                                 int segment, float *grad_out, float *syn_out, double *misfit);
 
 /* Copy the traces into HOST memory out[n * nt_max] (r-major; samples not yet
  * recorded are zero) and the number of recorded samples per receiver into

@@ -221,13 +221,14 @@ class Shot:
         done = fd_read_traces(self.handle, out)
         return out.reshape(n, nt_max)[:, :done]
 
-    def fwi_gradient(self, receivers, d_obs):
+    def fwi_gradient(self, receivers, d_obs, segment=0):
         """(dJ/dm over the domain, synthetic traces [nrec, nt], misfit J) of this
-        shot against observed traces d_obs [nrec, nt] at the receivers."""
+        shot against observed traces d_obs [nrec, nt] at the receivers;
+        segment > 0 checkpoints every `segment` steps."""
         d_obs = np.asarray(d_obs, dtype=np.float32)
         grad = np.empty(self.shape, dtype=np.float32)
         syn = np.empty(d_obs.shape, dtype=np.float32)
-        J = fd_fwi_gradient(self.handle, receivers, d_obs, grad, syn)
+        J = fd_fwi_gradient(self.handle, receivers, d_obs, grad, syn, segment=segment)
         return grad, syn, J
 
     def wavefield(self, level=0, out=None) -> np.ndarray:

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "fd_set_receivers": (_i, [_vp, _i, _vp, _i]),
     "fd_read_traces": (_i, [_vp, _vp, _ip]),
     "fd_fwi_gradient": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "fd_fwi_gradient_checkpointed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "fd_forward": (_i, [_vp, _i]),
     "fd_read_wavefield": (_i, [_vp, _vp, _i]),
     "fd_read_wavefield_device": (_i, [_vp, _vp, _i]),
@@ -208,9 +209,10 @@ def fd_set_receivers(hd, xyz, nt_max):
     _check(lib().fd_set_receivers(hd, n, _ptr(p) if n else None, int(nt_max)), "fd_set_receivers")
 
 
-def fd_fwi_gradient(hd, rec_xyz, d_obs, grad_out: np.ndarray, syn_out=None) -> float:
+def fd_fwi_gradient(hd, rec_xyz, d_obs, grad_out: np.ndarray, syn_out=None, segment: int = 0) -> float:
     """Fill grad_out (float32, domain shape) with dJ/dm; optionally syn_out
-    (float32 [nrec, nt]); returns the misfit J."""
+    (float32 [nrec, nt]); returns the misfit J. segment > 0: checkpointed
+    (fd_fwi_gradient_checkpointed)."""
     p = np.ascontiguousarray(np.asarray(rec_xyz, dtype=np.float64).reshape(-1, 3))
     obs = np.ascontiguousarray(np.asarray(d_obs, dtype=np.float32))
     nrec, nt = obs.shape
@@ -219,8 +221,12 @@ def fd_fwi_gradient(hd, rec_xyz, d_obs, grad_out: np.ndarray, syn_out=None) -> f
     if syn_out is not None:
         assert syn_out.dtype == np.float32 and syn_out.flags.c_contiguous and syn_out.shape == obs.shape
     j = ctypes.c_double()
-    _check(lib().fd_fwi_gradient(hd, nrec, _ptr(p), _ptr(obs), nt, _ptr(grad_out), _ptr(syn_out),
-                                 ctypes.byref(j)), "fd_fwi_gradient")
+    if segment:
+        _check(lib().fd_fwi_gradient_checkpointed(hd, nrec, _ptr(p), _ptr(obs), nt, int(segment), _ptr(grad_out),
+                                                  _ptr(syn_out), ctypes.byref(j)), "fd_fwi_gradient_checkpointed")
+    else:
+        _check(lib().fd_fwi_gradient(hd, nrec, _ptr(p), _ptr(obs), nt, _ptr(grad_out), _ptr(syn_out),
+                                     ctypes.byref(j)), "fd_fwi_gradient")
     return j.value
 
 

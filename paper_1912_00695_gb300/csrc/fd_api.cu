@@ -915,10 +915,17 @@ int fd_read_traces(fd_handle *hd, float *out, int *recorded) {
     return check_enabled(hd) ? read_status(hd) : FD_OK;
 }
 
-int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt, float *grad_out,
-                    float *syn_out, double *misfit) {
-    if (!hd || nrec < 1 || !rec_xyz || !d_obs || nt < 1 || !grad_out || !misfit)
-        return fail(FD_EINVAL, "bad receivers, data, nt or output pointers");
+// The FWI gradient (see fd_fwi_gradient in the header). segment >= nt keeps the
+// second time difference of every step in device memory; a shorter segment
+// keeps only the states (u^j, u^{j-1}) at every segment-th step during the
+// forward pass and, during the adjoint pass, recomputes each segment's
+// history from its checkpoint (one extra forward pass; memory ~ 2 nt/segment +
+// segment fields). The recomputation uses the same per-point arithmetic, so
+// both give the same bits.
+static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt,
+                             int segment, float *grad_out, float *syn_out, double *misfit) {
+    if (!hd || nrec < 1 || !rec_xyz || !d_obs || nt < 1 || !grad_out || !misfit || segment < 0)
+        return fail(FD_EINVAL, "bad receivers, data, nt, segment or output pointers");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_fwi_gradient before fd_set_model");
     if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->kernel != kTma)
         return fail(FD_ENOTSUP, "the FWI gradient runs on FP32 storage, factored form, TMA kernel");
@@ -926,19 +933,39 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
     for (int r = 0; r < nrec; ++r)
         if (!interior_point_ok(hd, rec_xyz[3 * r], rec_xyz[3 * r + 1], rec_xyz[3 * r + 2]))
             return fail(FD_ERANGE, "receiver %d outside the interior", r);
+    if (hd->tile_y == 0 || hd->x_block == 0) {  // the plain steps of the checkpointed pass use the tuned shape
+        int rc = autotune(hd);
+        if (rc == FD_OK) rc = build_maps(hd);
+        if (rc != FD_OK) {
+            hd->tile_y = hd->x_block = 0;
+            return rc;
+        }
+        hd->gen++;
+    }
+    cudaStream_t st = hd->stream;
+    const size_t np = hd->n_pitched;
+    const size_t fbytes = np * sizeof(float);
+    if (segment == 0) {
+        // automatic: the full history if it fits in 80 % of the free memory, else segments of sqrt(nt)
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const double need = double(nt + 4) * double(fbytes) + double(nrec) * nt * 8.0;
+        segment = need <= 0.8 * double(free_b) ? nt : std::max(1, int(std::ceil(std::sqrt(double(nt)))));
+    }
+    segment = std::min(segment, nt);
+    const int nseg = (nt + segment - 1) / segment;
+    const bool ckpt = nseg > 1;
     const int tz = 32, ty = 16;  // the gradient passes' tile
     const int xb = (hd->tile_z == tz && hd->tile_y == ty && hd->x_block > 0) ? hd->x_block
                                                                               : heuristic_x_block(hd, tz, ty);
-    cudaStream_t st = hd->stream;
-    const size_t np = hd->n_pitched;
-    // workspace: the second-time-difference history (one level per step), the gradient,
-    // two adjoint fields, the residuals and the receivers' node lists
-    float *hist = nullptr, *grad = nullptr, *w[2] = {nullptr, nullptr}, *resid = nullptr;
+    // workspace: the history of one segment (all steps without checkpoints), the
+    // checkpoints, the gradient, two adjoint fields, the residuals, the receivers' node lists
+    float *hist = nullptr, *ckp = nullptr, *grad = nullptr, *w[2] = {nullptr, nullptr}, *resid = nullptr;
     long long *node_off = nullptr;
     int *row = nullptr, *rec_idx = nullptr;
     float *rec_w = nullptr;
     auto release = [&]() {
-        void *bufs[] = {hist, grad, w[0], w[1], resid, node_off, row, rec_idx, rec_w};
+        void *bufs[] = {hist, ckp, grad, w[0], w[1], resid, node_off, row, rec_idx, rec_w};
         for (void *p : bufs) dev_free(p, st);
     };
     // the receivers' spreading as a node-major list (fixed order within a node)
@@ -971,10 +998,11 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
     }
     h_row.push_back(int(ent.size()));
     const int n_nodes = int(h_node.size());
-    if (dev_alloc(reinterpret_cast<void **>(&hist), size_t(nt) * np * sizeof(float), st) != cudaSuccess ||
-        dev_alloc(reinterpret_cast<void **>(&grad), np * sizeof(float), st) != cudaSuccess ||
-        dev_alloc(reinterpret_cast<void **>(&w[0]), np * sizeof(float), st) != cudaSuccess ||
-        dev_alloc(reinterpret_cast<void **>(&w[1]), np * sizeof(float), st) != cudaSuccess ||
+    if (dev_alloc(reinterpret_cast<void **>(&hist), size_t(segment) * fbytes, st) != cudaSuccess ||
+        (ckpt && dev_alloc(reinterpret_cast<void **>(&ckp), size_t(2 * nseg) * fbytes, st) != cudaSuccess) ||
+        dev_alloc(reinterpret_cast<void **>(&grad), fbytes, st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&w[0]), fbytes, st) != cudaSuccess ||
+        dev_alloc(reinterpret_cast<void **>(&w[1]), fbytes, st) != cudaSuccess ||
         dev_alloc(reinterpret_cast<void **>(&resid), size_t(nrec) * nt * sizeof(float), st) != cudaSuccess ||
         dev_alloc(reinterpret_cast<void **>(&node_off), h_node.size() * sizeof(long long), st) != cudaSuccess ||
         dev_alloc(reinterpret_cast<void **>(&row), h_row.size() * sizeof(int), st) != cudaSuccess ||
@@ -982,15 +1010,15 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
         dev_alloc(reinterpret_cast<void **>(&rec_w), h_w.size() * sizeof(float), st) != cudaSuccess) {
         cudaGetLastError();
         release();
-        return fail(FD_ENOMEM, "cannot allocate the gradient workspace (%.1f GB of history)",
-                    double(nt) * double(np) * 4e-9);
+        return fail(FD_ENOMEM, "cannot allocate the gradient workspace (%d history levels, %d checkpoints)", segment,
+                    ckpt ? nseg : 0);
     }
     auto cuda_fail = [&](cudaError_t e) {
         release();
         return fail(FD_ECUDA, "fd_fwi_gradient: %s", cudaGetErrorString(e));
     };
     // d_obs goes to the residual buffer now; the residual is formed on the device after
-    // the forward pass, so that the two passes run back to back
+    // the forward pass, so that the passes run back to back
     cudaError_t e = cudaMemcpyAsync(resid, d_obs, size_t(nrec) * nt * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(node_off, h_node.data(), h_node.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
@@ -998,7 +1026,6 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
     if (e == cudaSuccess) e = cudaMemcpyAsync(rec_idx, h_rec.data(), h_rec.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rec_w, h_w.data(), h_w.size() * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    // forward pass: every step also stores D^n = u^{n+1} - 2u^n + u^{n-1}; receivers record the traces
     int rc = fd_reset(hd);
     if (rc == FD_OK) rc = fd_set_receivers(hd, nrec, rec_xyz, nt);
     TmaMaps fm[2], am[2];
@@ -1010,50 +1037,105 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
     }
     const bool check = check_enabled(hd);
     const int ns = int(hd->sources.size());
+    // forward steps [n0, n1) from the handle's fields (cur), storing D^n at hist[n - n0]
+    // (with_receivers: the traces of those steps are recorded)
+    auto forward_d = [&](int n0, int n1, int &cur, bool with_receivers) {
+        cudaError_t err = cudaSuccess;
+        for (int n = n0; n < n1 && err == cudaSuccess; ++n) {
+            StepArgs a = make_args(hd, n, cur);
+            a.x_block = xb;
+            a.hist = hist + size_t(n - n0) * np;
+            if (!with_receivers) {
+                a.n_rec = 0;
+                a.rec_sample = -1;
+            }
+            err = launch_tma_grad_step(hd->r, kModeForwardD, fm[cur], a, check, st);
+            if (err == cudaSuccess && ns > kFusedSources)
+                err = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources,
+                                          ns - kFusedSources, kF32, 0, hd->extra_distinct, st, a.hist);
+            cur ^= 1;
+        }
+        return err;
+    };
     int cur = hd->cur;
-    e = cudaEventRecord(hd->ev0, st);  // device time of both passes: fd_last_forward_ms
-    for (int n = 0; n < nt && e == cudaSuccess; ++n) {
-        StepArgs a = make_args(hd, n, cur);
-        a.x_block = xb;
-        a.hist = hist + size_t(n) * np;
-        e = launch_tma_grad_step(hd->r, kModeForwardD, fm[cur], a, check, st);
-        if (e == cudaSuccess && ns > kFusedSources)
-            e = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources, ns - kFusedSources,
-                                    kF32, 0, hd->extra_distinct, st, a.hist);
-        cur ^= 1;
+    e = cudaEventRecord(hd->ev0, st);  // device time of the passes: fd_last_forward_ms
+    if (!ckpt) {
+        if (e == cudaSuccess) e = forward_d(0, nt, cur, true);
+    } else {
+        // plain steps; the states (u^j, u^{j-1}) at j = 0, segment, 2 segment, ... are kept
+        for (int n = 0; n < nt && e == cudaSuccess; ++n) {
+            if (n % segment == 0) {
+                const size_t slot = size_t(2 * (n / segment));
+                e = cudaMemcpyAsync(ckp + slot * np, hd->ubuf[cur], fbytes, cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(ckp + (slot + 1) * np, hd->ubuf[cur ^ 1], fbytes, cudaMemcpyDeviceToDevice, st);
+            }
+            if (e == cudaSuccess) e = enqueue_step(hd, make_args(hd, n, cur), st);
+            cur ^= 1;
+        }
     }
     if (e == cudaSuccess) e = sample_level(hd, hd->ubuf[cur], nt, st);
-    hd->step = nt;
-    hd->cur = cur;
+    const int cur_end = cur;
     // residual r = d - d_obs (in place over d_obs)
     if (e == cudaSuccess) e = launch_residual(hd->d_traces, resid, size_t(nrec) * nt, st);
     // adjoint pass, backward in time: w^k over w^{k+2} from w^{k+1}, the residual of
     // step k-1 injected at the receivers' nodes, gradient -= w^k D^{k-1}
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, np * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w[0], 0, np * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w[1], 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, fbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w[0], 0, fbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w[1], 0, fbytes, st);
     const float inv_dt2 = float(1.0 / (hd->dt * hd->dt));
     int c = 0;  // w[c] holds w^{k+1}, w[c^1] w^{k+2}
-    for (int s = 0; s < nt && e == cudaSuccess; ++s) {
-        const int k = nt - s;
-        StepArgs a = make_args(hd, 0, 0);
-        a.u = w[c];
-        a.up = w[c ^ 1];
-        a.ns = 0;
-        a.n_rec = 0;
-        a.rec_sample = -1;
-        a.x_block = xb;
-        a.hist = hist + size_t(k - 1) * np;
-        a.grad = grad;
-        e = launch_tma_grad_step(hd->r, kModeAdjointGrad, am[c], a, check, st);
-        if (e == cudaSuccess)
-            e = launch_adjoint_inject(w[c ^ 1], grad, a.hist, hd->f1, node_off, row, rec_idx, rec_w, resid, nt, k - 1,
-                                      inv_dt2, n_nodes, st);
-        c ^= 1;
+    for (int sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+        const int n0 = sg * segment, n1 = std::min(nt, n0 + segment);
+        if (ckpt) {
+            // recompute this segment's history from its checkpoint
+            const size_t slot = size_t(2 * sg);
+            int rcur = 0;
+            e = cudaMemcpyAsync(hd->ubuf[0], ckp + slot * np, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hd->ubuf[1], ckp + (slot + 1) * np, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = forward_d(n0, n1, rcur, false);
+        }
+        for (int k = n1; k > n0 && e == cudaSuccess; --k) {
+            StepArgs a = make_args(hd, 0, 0);
+            a.u = w[c];
+            a.up = w[c ^ 1];
+            a.ns = 0;
+            a.n_rec = 0;
+            a.rec_sample = -1;
+            a.x_block = xb;
+            a.hist = hist + size_t(k - 1 - n0) * np;
+            a.grad = grad;
+            e = launch_tma_grad_step(hd->r, kModeAdjointGrad, am[c], a, check, st);
+            if (e == cudaSuccess)
+                e = launch_adjoint_inject(w[c ^ 1], grad, a.hist, hd->f1, node_off, row, rec_idx, rec_w, resid, nt,
+                                          k - 1, inv_dt2, n_nodes, st);
+            c ^= 1;
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, st);
     hd->timed = e == cudaSuccess;
-    // the traces (synthetic data) and the misfit (FP64 sum on the host) while the copies run
+    // the handle ends at step nt (with checkpoints its fields hold a recomputed early state:
+    // the last state is restored from the end of the forward pass only without them)
+    hd->step = nt;
+    hd->cur = cur_end;
+    if (ckpt && e == cudaSuccess) {
+        // put u^nt, u^{nt-1} back: recompute the last segment's end state from its checkpoint
+        const int sg = nseg - 1, n0 = sg * segment;
+        const size_t slot = size_t(2 * sg);
+        int rcur = 0;
+        e = cudaMemcpyAsync(hd->ubuf[0], ckp + slot * np, fbytes, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hd->ubuf[1], ckp + (slot + 1) * np, fbytes, cudaMemcpyDeviceToDevice, st);
+        for (int n = n0; n < nt && e == cudaSuccess; ++n) {
+            StepArgs a = make_args(hd, n, rcur);
+            a.n_rec = 0;
+            a.rec_sample = -1;
+            e = enqueue_step(hd, a, st);
+            rcur ^= 1;
+        }
+        hd->cur = rcur;
+    }
+    // the traces (synthetic data) and the misfit (FP64 sum on the host)
     std::vector<float> syn(size_t(nrec) * nt);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(syn.data(), hd->d_traces, syn.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -1072,6 +1154,17 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
     *misfit = J;
     release();
     return check ? read_status(hd) : FD_OK;
+}
+
+int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt, float *grad_out,
+                    float *syn_out, double *misfit) {
+    return fwi_gradient_impl(hd, nrec, rec_xyz, d_obs, nt, 0, grad_out, syn_out, misfit);
+}
+
+int fd_fwi_gradient_checkpointed(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt,
+                                 int segment, float *grad_out, float *syn_out, double *misfit) {
+    if (segment < 1) return fail(FD_EINVAL, "segment must be >= 1");
+    return fwi_gradient_impl(hd, nrec, rec_xyz, d_obs, nt, segment, grad_out, syn_out, misfit);
 }
 
 int fd_clear_sources(fd_handle *hd) {

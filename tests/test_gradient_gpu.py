@@ -76,6 +76,31 @@ def test_fwi_gradient_matches_oracle(oracle_mod, k, offgrid, obs_kind):
     assert J == J2
 
 
+@pytest.mark.parametrize("segment", [1, 7, 13, 60])
+def test_checkpointed_gradient_is_bitwise_equal(segment):
+    """Checkpointing (states kept every `segment` steps, histories recomputed in
+    the adjoint pass) gives the full-history gradient, traces and misfit bit for
+    bit, and leaves the handle at the same final state."""
+    spec, recs, m_true = _case(8, seed=21)
+    dt = dt_for(spec, 0.8)
+    wav = inputs.ricker(25.0, dt, spec.nt)
+    rng = np.random.default_rng(5)
+    obs = (rng.standard_normal((len(recs), spec.nt)) * 1e-4).astype(np.float32)
+    out = []
+    for seg in (0, segment):
+        with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
+            shot.set_model(spec.m)
+            shot.inject_at(14.3, 17.6, 20.45, wav)
+            g, syn, J = shot.fwi_gradient(recs, obs, segment=seg)
+            out.append((g, syn, J, shot.wavefield(0), shot.wavefield(1), shot.step))
+    (g0, s0, j0, u0, p0, n0), (g1, s1, j1, u1, p1, n1) = out
+    np.testing.assert_array_equal(g1, g0)
+    np.testing.assert_array_equal(s1, s0)
+    assert j1 == j0 and n1 == n0 == spec.nt
+    np.testing.assert_array_equal(u1, u0)
+    np.testing.assert_array_equal(p1, p0)
+
+
 def test_fwi_gradient_errors():
     spec, recs, _ = _case(4, seed=3)
     dt = dt_for(spec, 0.8)
