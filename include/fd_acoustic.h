@@ -89,7 +89,8 @@ typedef struct fd_options {
     int tile_z;        /* tile width along z: STREAM 32; TMA 32, 64 or 128; 0 = autotune */
     int tile_y;        /* tile rows along y: STREAM 4, 8, 16; TMA (FP32) with tile_z 32:
                           16 or 32, 64: 8 or 16, 128: 8; TMA (16-bit) 32x16 or 64x8;
-                          0 = autotune                                              */
+                          space orders 18-24 (TMA): 32x16 or 32x32 (FP32), 32x16
+                          (16-bit); 0 = autotune                                    */
     int x_block;       /* planes per CTA along x (each CTA streams x_block
                           consecutive planes of one y-z tile); 0 = autotune         */
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
@@ -105,10 +106,10 @@ void fd_options_default(fd_options *opt);
 /* ---- single-shot solver --------------------------------------------------- */
 
 /* Create a solver for an nx*ny*nz interior with an nbl-cell absorbing layer on
- * every side, space order k (even, 2..16), grid spacing h and time step dt
+ * every side, space order k (even, 2..24), grid spacing h and time step dt
  * (both > 0, any consistent units). Allocates the device state (two wavefield
  * levels, the model fields) and zeroes the wavefields (Eq. 1: u = u_t = 0 at
- * t = 0). FD_EINVAL when k is odd or outside [2,16], n_a < 1, nbl < 0, a
+ * t = 0). FD_EINVAL when k is odd or outside [2,24], n_a < 1, nbl < 0, a
  * computational extent N_a exceeds 65535, or h, dt are not positive finite;
  * FD_ENOMEM when the device buffers do not fit. *out is NULL on failure. */
 int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
@@ -297,7 +298,8 @@ typedef struct fd_batch fd_batch;
  * buffers), for admission by memory budget. storage: FD_STORAGE_*. */
 int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long *out);
 
-/* Create an empty batch. opt: storage/form as for fd_acoustic_create_ex
+/* Create an empty batch of space order k (even, 2..16: FD_EINVAL otherwise).
+ * opt: storage/form as for fd_acoustic_create_ex
  * (16-bit storage needs the factored form), tile_z/tile_y 0 (= 32x16) or one
  * of 32x16, 64x8; x_block 0 = 96 planes (or the whole extent if shorter),
  * else used for every shot; kernel is ignored. FD_ENOTSUP for other shapes. */
@@ -361,7 +363,8 @@ int fd_batch_destroy(fd_batch *b);
  * d_u_prev when nt is odd (the other buffer holds the level before it).
  * d_m = 1/v^2 (> 0), d_eta = damping (>= 0) or NULL for none; both are read
  * as given (no validation, no stability check: the caller owns that). The
- * stencil is the expanded form of fd_forward (same arithmetic per point).
+ * stencil is the expanded form of fd_forward (same arithmetic per point),
+ * space orders 2..16.
  * Sources: ns in [0, 4] point sources at DOMAIN nodes src_xyz (host array,
  * x0,y0,z0, x1,y1,z1, ...), wavelets in the device array d_wavelet (ns rows
  * of ld samples; q = 0 beyond ld), step n uses sample n (global step, from

@@ -123,17 +123,22 @@ EncodeTiledFn encode_fn() {
 }
 
 // (tile_z, tile_y) shapes the TMA kernel has for a storage/form.
-std::vector<std::pair<int, int>> tma_tiles(int storage, int form) {
+std::vector<std::pair<int, int>> tma_tiles(int storage, int form, int radius) {
+    if (radius > 8) {  // space orders 18-24: 32-wide tiles only
+        if (storage == kF32) return {{32, 32}, {32, 16}};
+        if (form == kFactored) return {{32, 16}};
+        return {};
+    }
     if (storage == kF32) return {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
     if (form == kFactored) return {{32, 16}, {64, 8}};
     return {};
 }
 
 // Valid (tile_z, tile_y) requests of each kernel (0 = any).
-bool tile_ok(int kernel, int storage, int form, int tz, int ty) {
+bool tile_ok(int kernel, int storage, int form, int radius, int tz, int ty) {
     if (kernel == kStream) return (tz == 0 || tz == 32) && (ty == 0 || ty == 4 || ty == 8 || ty == 16);
     if (kernel == kTma) {
-        for (auto &p : tma_tiles(storage, form))
+        for (auto &p : tma_tiles(storage, form, radius))
             if ((tz == 0 || tz == p.first) && (ty == 0 || ty == p.second)) return true;
         return false;
     }
@@ -342,7 +347,7 @@ int autotune(fd_handle *hd) {
     const bool force_tile = hd->opt.tile_z > 0 || hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
     std::vector<std::pair<int, int>> tiles;
     if (kernel == kTma) {
-        for (auto &p : tma_tiles(hd->opt.storage, hd->opt.form))
+        for (auto &p : tma_tiles(hd->opt.storage, hd->opt.form, hd->r))
             if ((hd->opt.tile_z == 0 || hd->opt.tile_z == p.first) && (hd->opt.tile_y == 0 || hd->opt.tile_y == p.second))
                 tiles.push_back(p);
     } else {
@@ -714,7 +719,7 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     fd_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (space_order < 2 || space_order > 2 * kMaxRadius || space_order % 2)
-        return fail(FD_EINVAL, "space_order must be even in [2, 16], got %d", space_order);
+        return fail(FD_EINVAL, "space_order must be even in [2, 24], got %d", space_order);
     if (nx < 1 || ny < 1 || nz < 1 || nbl < 0)
         return fail(FD_EINVAL, "interior sizes must be >= 1 and nbl >= 0");
     if (!(h > 0) || !std::isfinite(h) || !(dt > 0) || !std::isfinite(dt))
@@ -731,7 +736,7 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         if (kernel != kAuto && kernel != kTma) return fail(FD_ENOTSUP, "16-bit storage runs on the TMA kernel");
     }
     if (kernel == kAuto) kernel = kTma;
-    if (!tile_ok(kernel, opt.storage, opt.form, opt.tile_z, opt.tile_y))
+    if (!tile_ok(kernel, opt.storage, opt.form, space_order / 2, opt.tile_z, opt.tile_y))
         return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
 
@@ -1584,8 +1589,8 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
 int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batch **out) {
     if (!out) return fail(FD_EINVAL, "out is NULL");
     *out = nullptr;
-    if (space_order < 2 || space_order > 2 * kMaxRadius || space_order % 2)
-        return fail(FD_EINVAL, "space_order must be even in [2, 16], got %d", space_order);
+    if (space_order < 2 || space_order > 2 * kMaxBatchRadius || space_order % 2)
+        return fail(FD_EINVAL, "batches take space orders even in [2, 16], got %d", space_order);
     if (!(h > 0) || !std::isfinite(h)) return fail(FD_EINVAL, "h must be positive and finite");
     fd_options opt;
     fd_options_default(&opt);

@@ -10,7 +10,8 @@
 
 namespace fdgb {
 
-constexpr int kMaxRadius = 8;       // space order 16
+constexpr int kMaxRadius = 12;      // space order 24
+constexpr int kMaxBatchRadius = 8;  // batches: space order 16
 constexpr int kMaxRadiusHost = 12;  // host weight generator reaches space order 24
 constexpr int kFusedSources = 4;    // sources injected inside the step kernel (more: one extra kernel)
 // Epilogue modes of the FP32 factored TMA step (the FWI gradient's two passes):
@@ -24,6 +25,9 @@ constexpr int kModeStep = 0, kModeForwardD = 1, kModeAdjointGrad = 2;
 // latency-bound: occupancy is worth more than the few spill slots this costs
 // at R = 8).
 constexpr int kTmaWarpsPerSM = 16;
+// above radius 8 the register queue needs more than 128 registers per thread:
+// 8 warps per SM
+constexpr int tma_warps_per_sm(int r) { return r > 8 ? 8 : kTmaWarpsPerSM; }
 constexpr int kTileZ = 32;          // streaming tile width along z (one warp)
 constexpr int kMaxDim = 65535;  // keeps every launch grid dimension within limits
 

@@ -1,0 +1,5 @@
+// Step kernels for stencil radius 11 (space order 22).
+#include "fd_stencil.cuh"
+#include "fd_tma.cuh"
+FDGB_INSTANTIATE_RADIUS(11)
+FDGB_INSTANTIATE_TMA_RADIUS(11)

@@ -21,6 +21,10 @@ FDGB_DECLARE_RADIUS(5)
 FDGB_DECLARE_RADIUS(6)
 FDGB_DECLARE_RADIUS(7)
 FDGB_DECLARE_RADIUS(8)
+FDGB_DECLARE_RADIUS(9)
+FDGB_DECLARE_RADIUS(10)
+FDGB_DECLARE_RADIUS(11)
+FDGB_DECLARE_RADIUS(12)
 #undef FDGB_DECLARE_RADIUS
 
 cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
@@ -34,6 +38,10 @@ cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, co
         case 6: return stream_step_radius_6(form, storage, tile_y, a, check, s);
         case 7: return stream_step_radius_7(form, storage, tile_y, a, check, s);
         case 8: return stream_step_radius_8(form, storage, tile_y, a, check, s);
+        case 9: return stream_step_radius_9(form, storage, tile_y, a, check, s);
+        case 10: return stream_step_radius_10(form, storage, tile_y, a, check, s);
+        case 11: return stream_step_radius_11(form, storage, tile_y, a, check, s);
+        case 12: return stream_step_radius_12(form, storage, tile_y, a, check, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -49,6 +57,10 @@ cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs 
         case 6: return naive_step_radius_6(form, storage, a, check, s);
         case 7: return naive_step_radius_7(form, storage, a, check, s);
         case 8: return naive_step_radius_8(form, storage, a, check, s);
+        case 9: return naive_step_radius_9(form, storage, a, check, s);
+        case 10: return naive_step_radius_10(form, storage, a, check, s);
+        case 11: return naive_step_radius_11(form, storage, a, check, s);
+        case 12: return naive_step_radius_12(form, storage, a, check, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -68,6 +80,10 @@ FDGB_DECLARE_TMA_RADIUS(5)
 FDGB_DECLARE_TMA_RADIUS(6)
 FDGB_DECLARE_TMA_RADIUS(7)
 FDGB_DECLARE_TMA_RADIUS(8)
+FDGB_DECLARE_TMA_RADIUS(9)
+FDGB_DECLARE_TMA_RADIUS(10)
+FDGB_DECLARE_TMA_RADIUS(11)
+FDGB_DECLARE_TMA_RADIUS(12)
 #undef FDGB_DECLARE_TMA_RADIUS
 
 #define FDGB_DECLARE_BATCH_RADIUS(R)                                                             \
@@ -82,6 +98,10 @@ FDGB_DECLARE_BATCH_RADIUS(5)
 FDGB_DECLARE_BATCH_RADIUS(6)
 FDGB_DECLARE_BATCH_RADIUS(7)
 FDGB_DECLARE_BATCH_RADIUS(8)
+FDGB_DECLARE_BATCH_RADIUS(9)
+FDGB_DECLARE_BATCH_RADIUS(10)
+FDGB_DECLARE_BATCH_RADIUS(11)
+FDGB_DECLARE_BATCH_RADIUS(12)
 #undef FDGB_DECLARE_BATCH_RADIUS
 
 cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z, int tile_y,
@@ -92,6 +112,7 @@ cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z,
         case R: return tma_batch_step_radius_##R(form, storage, tile_z, tile_y, shots, items, n_items, offset, s);
         FDGB_BATCH_R(1) FDGB_BATCH_R(2) FDGB_BATCH_R(3) FDGB_BATCH_R(4)
         FDGB_BATCH_R(5) FDGB_BATCH_R(6) FDGB_BATCH_R(7) FDGB_BATCH_R(8)
+        FDGB_BATCH_R(9) FDGB_BATCH_R(10) FDGB_BATCH_R(11) FDGB_BATCH_R(12)
 #undef FDGB_BATCH_R
         default: return cudaErrorInvalidValue;
     }
@@ -108,6 +129,10 @@ FDGB_DECLARE_GRAD_RADIUS(5)
 FDGB_DECLARE_GRAD_RADIUS(6)
 FDGB_DECLARE_GRAD_RADIUS(7)
 FDGB_DECLARE_GRAD_RADIUS(8)
+FDGB_DECLARE_GRAD_RADIUS(9)
+FDGB_DECLARE_GRAD_RADIUS(10)
+FDGB_DECLARE_GRAD_RADIUS(11)
+FDGB_DECLARE_GRAD_RADIUS(12)
 #undef FDGB_DECLARE_GRAD_RADIUS
 
 cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
@@ -117,6 +142,7 @@ cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const
         case R: return tma_grad_step_radius_##R(mode, map, a, check, s);
         FDGB_GRAD_R(1) FDGB_GRAD_R(2) FDGB_GRAD_R(3) FDGB_GRAD_R(4)
         FDGB_GRAD_R(5) FDGB_GRAD_R(6) FDGB_GRAD_R(7) FDGB_GRAD_R(8)
+        FDGB_GRAD_R(9) FDGB_GRAD_R(10) FDGB_GRAD_R(11) FDGB_GRAD_R(12)
 #undef FDGB_GRAD_R
         default: return cudaErrorInvalidValue;
     }
@@ -129,6 +155,7 @@ cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int t
         case R: return tma_step_radius_##R(form, storage, tile_z, tile_y, map, a, check, s);
         FDGB_TMA_R(1) FDGB_TMA_R(2) FDGB_TMA_R(3) FDGB_TMA_R(4)
         FDGB_TMA_R(5) FDGB_TMA_R(6) FDGB_TMA_R(7) FDGB_TMA_R(8)
+        FDGB_TMA_R(9) FDGB_TMA_R(10) FDGB_TMA_R(11) FDGB_TMA_R(12)
 #undef FDGB_TMA_R
         default: return cudaErrorInvalidValue;
     }
@@ -140,6 +167,7 @@ bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *w, 
         case R: return tma_box_radius_##R(form, storage, tile_z, tile_y, w, h, rz);
         FDGB_TMA_B(1) FDGB_TMA_B(2) FDGB_TMA_B(3) FDGB_TMA_B(4)
         FDGB_TMA_B(5) FDGB_TMA_B(6) FDGB_TMA_B(7) FDGB_TMA_B(8)
+        FDGB_TMA_B(9) FDGB_TMA_B(10) FDGB_TMA_B(11) FDGB_TMA_B(12)
 #undef FDGB_TMA_B
         default: return false;
     }

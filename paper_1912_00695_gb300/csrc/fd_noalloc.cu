@@ -14,6 +14,8 @@
 
 // sources this entry point accepts (its documented limit)
 constexpr int kNoallocSources = 4;
+// space orders this entry point accepts (its documented limit)
+constexpr int kNoallocMaxRadius = 8;
 
 namespace fdgb {
 void set_last_error(const char *msg);  // fd_api.cu: the fd_last_error() text
@@ -216,7 +218,7 @@ cudaError_t launch_noalloc_r(int r, const StepArgs &a, dim3 grid, unsigned *scra
 // Centred second-derivative weights by Fornberg's recursion on fixed-size
 // stack arrays (no heap use on this path).
 bool weights_on_stack(int space_order, double *c) {
-    if (space_order < 2 || space_order > 2 * kMaxRadius || space_order % 2) return false;
+    if (space_order < 2 || space_order > 2 * kNoallocMaxRadius || space_order % 2) return false;
     const int r = space_order / 2, n_nodes = 2 * r + 1;
     double w[3][2 * kMaxRadius + 1] = {};
     w[0][0] = 1.0;

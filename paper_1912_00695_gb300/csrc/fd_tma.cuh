@@ -560,7 +560,7 @@ __device__ __forceinline__ void tma_sample_receivers(const StepArgs &a, float sc
 // CTAs resident at any moment cover neighbouring tiles at the same planes and
 // share their halo rows in L2.
 template <int R, int FORM, int LZ, int W, typename T>
-__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1)) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
                                                         const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_kernel(cons
 
 // The FWI gradient's passes (FP32 factored; sources and receivers as the step).
 template <int R, int LZ, int W, int MODE>
-__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_grad_kernel(const __grid_constant__ TmaMaps maps,
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1)) fd_tma_grad_kernel(const __grid_constant__ TmaMaps maps,
                                                              const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char *ring = tma_ring_init<R, LZ, W, float>(smem_dyn);
@@ -639,7 +639,7 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
 // one segment (planes [bx x_block, (bx+1) x_block) of tile (bz, by)) of the
 // single-shot kernel's schedule.
 template <int R, int FORM, int LZ, int W, typename T>
-__global__ void __launch_bounds__(32 * W, kTmaWarpsPerSM / W) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1)) fd_tma_batch_kernel(const BatchShot *__restrict__ shots,
                                                               const int4 *__restrict__ items, int offset) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     __shared__ StepArgs sa;
@@ -689,6 +689,9 @@ cudaError_t tma_batch_launch(const BatchShot *shots, const int4 *items, int n_it
 template <int R>
 cudaError_t tma_batch_step_r(int form, int storage, int tile_z, int tile_y, const BatchShot *shots,
                              const int4 *items, int n_items, int offset, cudaStream_t s) {
+    if constexpr (R > kMaxBatchRadius) {
+        return cudaErrorInvalidValue;  // batches stop at space order 16
+    } else {
 #define FDGB_BATCH_CASE(LZ, W)                                                                          \
     if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                                            \
         if (storage == kF32)                                                                            \
@@ -703,13 +706,17 @@ cudaError_t tma_batch_step_r(int form, int storage, int tile_z, int tile_y, cons
     FDGB_BATCH_CASE(16, 4)
 #undef FDGB_BATCH_CASE
     return cudaErrorInvalidValue;
+    }
 }
 
 // Tile configurations (tile_z, tile_y) of the TMA kernel: (LZ, W) pairs. FP32
 // storage has every shape and both forms; 16-bit storage the factored form in
-// the shapes of the second list.
+// the shapes of the second list. Above radius 8 (space orders 18-24) the tiles
+// are 32 points wide (the widest z window) and the lists shorter.
 #define FDGB_TMA_CONFIGS(X) X(8, 8) X(16, 8) X(32, 8) X(8, 4) X(16, 4)
 #define FDGB_TMA_CONFIGS_16(X) X(8, 4) X(16, 4)
+#define FDGB_TMA_CONFIGS_HIGH(X) X(8, 8) X(8, 4)
+#define FDGB_TMA_CONFIGS_16_HIGH(X) X(8, 4)
 
 template <int R>
 cudaError_t tma_step_r(int form, int storage, int tile_z, int tile_y, const TmaMaps &map, const StepArgs &a,
@@ -718,14 +725,22 @@ cudaError_t tma_step_r(int form, int storage, int tile_z, int tile_y, const TmaM
     if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                   \
         return form == kFactored ? tma_launch<R, kFactored, LZ, W, float>(map, a, check, s)     \
                                  : tma_launch<R, kExpanded, LZ, W, float>(map, a, check, s);
-    FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
+    } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_CASE)
+    }
 #undef FDGB_TMA_CASE
 #define FDGB_TMA_CASE16(LZ, W)                                                                  \
     if (form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {               \
         if (storage == kBF16) return tma_launch<R, kFactored, LZ, W, __nv_bfloat16>(map, a, check, s); \
         if (storage == kF16) return tma_launch<R, kFactored, LZ, W, __half>(map, a, check, s);  \
     }
-    FDGB_TMA_CONFIGS_16(FDGB_TMA_CASE16)
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS_16(FDGB_TMA_CASE16)
+    } else {
+        FDGB_TMA_CONFIGS_16_HIGH(FDGB_TMA_CASE16)
+    }
 #undef FDGB_TMA_CASE16
     return cudaErrorInvalidValue;
 }
@@ -741,7 +756,11 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
         *rz = TmaShape<R, LZ, W, float>::RZ;                                                    \
         return true;                                                                            \
     }
-    FDGB_TMA_CONFIGS(FDGB_TMA_BOX)
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS(FDGB_TMA_BOX)
+    } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_BOX)
+    }
 #undef FDGB_TMA_BOX
 #define FDGB_TMA_BOX16(LZ, W)                                                                   \
     if (storage != kF32 && form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) { \
@@ -750,7 +769,11 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
         *rz = TmaShape<R, LZ, W, __half>::RZ;                                                   \
         return true;                                                                            \
     }
-    FDGB_TMA_CONFIGS_16(FDGB_TMA_BOX16)
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS_16(FDGB_TMA_BOX16)
+    } else {
+        FDGB_TMA_CONFIGS_16_HIGH(FDGB_TMA_BOX16)
+    }
 #undef FDGB_TMA_BOX16
     return false;
 }

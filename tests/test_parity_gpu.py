@@ -54,14 +54,15 @@ TMA_TILES = [(32, 32), (64, 16), (128, 8), (32, 16), (64, 8)]
 
 @pytest.mark.parametrize("kernel", ["stream", "tma"])
 @pytest.mark.parametrize("form", ["factored", "expanded"])
-@pytest.mark.parametrize("k", [2, 4, 6, 8, 10, 12, 14, 16])
+@pytest.mark.parametrize("k", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 24])
 def test_every_space_order_ragged(oracle_mod, k, form, kernel):
     spec = _ragged_spec(k)
     dt = dt_for(spec)
     eta = eta_for(spec)
     want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta)
+    tile = TMA_TILES[k % 5] if k <= 16 else [(32, 32), (32, 16)][k // 2 % 2]  # 32-wide above 16
     shape = dict(tile_y=8, x_block=16) if kernel == "stream" else \
-        dict(zip(("tile_z", "tile_y"), TMA_TILES[k % 5]), x_block=21)
+        dict(zip(("tile_z", "tile_y"), tile), x_block=21)
     got, got_prev, shot = run_gpu(spec, spec.nt, dt, None, form=form, kernel=kernel, **shape)
     report(f"ragged_so{k}_{form}_{kernel}{shot.config}", rel_l2(got, want),
            rel_l2(got_prev, want_prev))
@@ -70,7 +71,7 @@ def test_every_space_order_ragged(oracle_mod, k, form, kernel):
     shot.close()
 
 
-@pytest.mark.parametrize("k", [2, 8, 16])
+@pytest.mark.parametrize("k", [2, 8, 16, 24])
 def test_naive_kernel_ragged(oracle_mod, k):
     spec = _ragged_spec(k, seed=3)
     dt = dt_for(spec)
@@ -161,7 +162,7 @@ def test_load_state_resume_matches_oracle(oracle_mod):
         shot.close()
 
 
-@pytest.mark.parametrize("k", [2, 8, 16])
+@pytest.mark.parametrize("k", [2, 8, 16, 24])
 def test_full_size_sweep_parity(oracle_mod, k):
     """The benchmark workload (256^3 + 10-cell layer, 4-layer model) with the
     autotuned launch shape, 6 steps from a smooth random full-field state."""
@@ -184,8 +185,12 @@ def test_full_size_sweep_parity(oracle_mod, k):
 def test_error_codes():
     spec = inputs.plain_shot()
     dt = dt_for(spec)
-    with pytest.raises(fd.FdError) as e:
-        fd.Shot((8, 8, 8), 5, 10.0, 1e-3, 2)
+    for bad_k in (5, 26):
+        with pytest.raises(fd.FdError) as e:
+            fd.Shot((8, 8, 8), bad_k, 10.0, 1e-3, 2)
+        assert e.value.code == fd.FD_EINVAL
+    with pytest.raises(fd.FdError) as e:  # batches stop at space order 16
+        fd.Batch(18, 10.0)
     assert e.value.code == fd.FD_EINVAL
     shot = fd.Shot(spec.interior, 4, inputs.H, dt, spec.nbl)
     with pytest.raises(fd.FdError) as e:
@@ -244,7 +249,7 @@ STORAGE_TOL = {"bf16": 4 * 2.0 ** -9 * 60 ** 0.5, "f16": 4 * 2.0 ** -12 * 60 ** 
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-@pytest.mark.parametrize("k", [2, 4, 8, 12, 16])
+@pytest.mark.parametrize("k", [2, 4, 8, 12, 16, 20, 24])
 def test_16bit_storage_ragged(oracle_mod, k, storage):
     spec = _ragged_spec(k, seed=11)
     dt = dt_for(spec)
