@@ -215,6 +215,20 @@ int fd_fwi_gradient(fd_handle *hd, int nrec, const double *rec_xyz, const float 
 int fd_fwi_gradient_checkpointed(fd_handle *hd, int nrec, const double *rec_xyz, const float *d_obs, int nt,
                                  int segment, float *grad_out, float *syn_out, double *misfit);
 
+/* As fd_forward, two time steps per launch (temporal blocking along the
+ * streaming direction: the next step of the paper's data-locality argument,
+ * Sec. 5): each launch reads u^n, u^{n-1}, w (and eta's coefficient in the
+ * layer) once and writes u^{n+1} and u^{n+2}, computing the intermediate level
+ * on overlapping extended tiles; an odd last step runs the single-step
+ * kernel. Same results bit for bit as fd_forward (same per-point arithmetic).
+ * FP32 storage, factored form, space order 2 or 4, at most 4 sources, no
+ * receivers (FD_ENOTSUP otherwise). Allocates two more wavefield buffers on
+ * first use; the handle's state then rotates through the four buffers.
+ * Asynchronous like fd_forward. fd_forward itself takes this path for space
+ * order 2 when the kernel is left to the library (FD_KERNEL_AUTO) and the
+ * conditions hold. */
+int fd_forward_two_step(fd_handle *hd, int nt);
+
 /* Copy the traces into HOST memory out[n * nt_max] (r-major; samples not yet
  * recorded are zero) and the number of recorded samples per receiver into
  * *recorded. Synchronises the handle's stream; returns the device status like

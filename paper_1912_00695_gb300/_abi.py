@@ -76,6 +76,7 @@ _SIGNATURES = {
     "fd_fwi_gradient": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "fd_fwi_gradient_checkpointed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "fd_forward": (_i, [_vp, _i]),
+    "fd_forward_two_step": (_i, [_vp, _i]),
     "fd_read_wavefield": (_i, [_vp, _vp, _i]),
     "fd_read_wavefield_device": (_i, [_vp, _vp, _i]),
     "fd_set_stream": (_i, [_vp, _vp]),
@@ -240,6 +241,10 @@ def fd_read_traces(hd, out: np.ndarray) -> int:
 
 def fd_forward(hd, nt):
     _check(lib().fd_forward(hd, nt), "fd_forward")
+
+
+def fd_forward_two_step(hd, nt):
+    _check(lib().fd_forward_two_step(hd, nt), "fd_forward_two_step")
 
 
 def fd_read_wavefield(hd, out: np.ndarray, level: int = 0):

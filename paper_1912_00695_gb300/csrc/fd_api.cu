@@ -57,6 +57,8 @@ struct GraphEntry {
 // (Nx, Ny, Nz, radius, storage, form, check, kernel) -> (tile_z, tile_y, x_block)
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
+// two-step kernel: (Nx, Ny, Nz, radius) -> x_block
+std::map<std::tuple<int, int, int, int>, int> g_tb_cache;
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync) from the
 // device's default pool, whose release threshold is raised once per device so
@@ -183,6 +185,14 @@ struct fd_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
     bool extra_distinct = true;  // sources beyond the fused ones sit at pairwise distinct nodes
+    // two-step kernel: the pair of output buffers, its x_block and tensor maps by input pair
+    void *tb_buf[2] = {nullptr, nullptr};
+    int tb_xb = 0;
+    struct TbMaps {
+        const void *u, *up;
+        TmaMaps maps;
+    };
+    std::vector<TbMaps> tb_maps;
     // receivers: 8 (pitched offset, weight) pairs each; traces [n_rec][rec_nt_max]
     int n_rec = 0, rec_nt_max = 0;
     long long rec_step0 = 0;
@@ -647,7 +657,7 @@ void release_handle(fd_handle *hd) {
     cudaStream_t st = hd->stream ? hd->stream : hd->own_stream;
     void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
                     hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack, hd->d_rec_off, hd->d_rec_w,
-                    hd->d_traces};
+                    hd->d_traces, hd->tb_buf[0], hd->tb_buf[1]};
     for (void *p : bufs) dev_free(p, st);
     if (hd->ev0) cudaEventDestroy(hd->ev0);
     if (hd->ev1) cudaEventDestroy(hd->ev1);
@@ -667,6 +677,8 @@ int read_status(fd_handle *hd) {
 }  // namespace
 
 extern "C" {
+
+int fd_forward_two_step(fd_handle *hd, int nt);
 
 void fd_options_default(fd_options *opt) {
     if (!opt) return;
@@ -1172,6 +1184,134 @@ int fd_fwi_gradient_checkpointed(fd_handle *hd, int nrec, const double *rec_xyz,
     return fwi_gradient_impl(hd, nrec, rec_xyz, d_obs, nt, segment, grad_out, syn_out, misfit);
 }
 
+// Tensor maps of the two-step kernel for input pair (u^n in u, u^{n-1} in up).
+static int tb_maps_for(fd_handle *hd, const void *u, const void *up, const TmaMaps **out) {
+    for (auto &m : hd->tb_maps)
+        if (m.u == u && m.up == up) {
+            *out = &m.maps;
+            return FD_OK;
+        }
+    int tz, ty, bw, bh, ez, ey;
+    if (!tma2_geometry(hd->r, &tz, &ty, &bw, &bh, &ez, &ey)) return fail(FD_ENOTSUP, "no two-step kernel");
+    fd_handle::TbMaps m{u, up, {}};
+    int rc = encode_box(hd, u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bw, bh, &m.maps.u_halo);
+    if (rc == FD_OK) rc = encode_box(hd, u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ez, ey, &m.maps.u_pt);
+    if (rc == FD_OK) rc = encode_box(hd, up, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ez, ey, &m.maps.up_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ez, ey, &m.maps.f1_pt);
+    if (rc == FD_OK) rc = encode_box(hd, hd->f2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ez, ey, &m.maps.f2_pt);
+    if (rc != FD_OK) return rc;
+    if (hd->tb_maps.size() >= 4) hd->tb_maps.erase(hd->tb_maps.begin());
+    hd->tb_maps.push_back(m);
+    *out = &hd->tb_maps.back().maps;
+    return FD_OK;
+}
+
+int fd_forward_two_step(fd_handle *hd, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_two_step before fd_set_model");
+    if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->r > 2 || hd->n_rec > 0 ||
+        int(hd->sources.size()) > kFusedSources)
+        return fail(FD_ENOTSUP, "two steps per launch: FP32 factored, space order <= 4, <= %d sources, no receivers",
+                    kFusedSources);
+    if (nt == 0) return FD_OK;
+    cudaStream_t st = hd->stream;
+    const size_t ub = hd->n_pitched * sizeof(float);
+    if (!hd->tb_buf[0]) {
+        for (int b = 0; b < 2; ++b) {
+            if (dev_alloc(&hd->tb_buf[b], ub, st) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FD_ENOMEM, "cannot allocate the two-step output buffers");
+            }
+            FD_CUDA(cudaMemsetAsync(hd->tb_buf[b], 0, ub, st));  // the pitch padding stays zero
+        }
+    }
+    const bool check = check_enabled(hd);
+    int tz, ty, bw, bh, ez, ey;
+    tma2_geometry(hd->r, &tz, &ty, &bw, &bh, &ez, &ey);
+    if (hd->tb_xb == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tb_cache.find(std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r));
+        if (it != g_tb_cache.end()) hd->tb_xb = it->second;
+    }
+    if (hd->tb_xb == 0) {
+        // x_block by timing candidates; the launches only write the output pair, so the state stays
+        const TmaMaps *m = nullptr;
+        int rc = tb_maps_for(hd, hd->ubuf[hd->cur], hd->ubuf[hd->cur ^ 1], &m);
+        if (rc != FD_OK) return rc;
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long tiles = (long long)((hd->Nz + tz - 1) / tz) * ((hd->Ny + ty - 1) / ty);
+        std::vector<int> cand = {16, 24, 32, 48, 64, 96};
+        for (int waves = 1; waves <= 3; ++waves) {
+            const long long chunks = 2LL * sms * waves / std::max(1LL, tiles);
+            if (chunks >= 1) cand.push_back(int((hd->Nx + chunks - 1) / chunks));
+        }
+        cand.push_back(hd->Nx);
+        float best = 1e30f;
+        int best_xb = hd->Nx;
+        for (int xb : cand) {
+            if (xb < 4 || xb > hd->Nx) continue;
+            StepArgs a = make_args(hd, hd->step, hd->cur);
+            a.x_block = xb;
+            a.n_rec = 0;
+            a.rec_sample = -1;
+            a.status = nullptr;
+            cudaError_t e = cudaSuccess;
+            for (int w = 0; w < 1 && e == cudaSuccess; ++w)
+                e = launch_tma2_step(hd->r, *m, a, static_cast<float *>(hd->tb_buf[0]),
+                                     static_cast<float *>(hd->tb_buf[1]), false, st);
+            if (e == cudaSuccess) e = cudaEventRecord(hd->ev0, st);
+            for (int w = 0; w < 3 && e == cudaSuccess; ++w)
+                e = launch_tma2_step(hd->r, *m, a, static_cast<float *>(hd->tb_buf[0]),
+                                     static_cast<float *>(hd->tb_buf[1]), false, st);
+            if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(hd->ev1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, hd->ev0, hd->ev1);
+            if (e != cudaSuccess) return fail(FD_ECUDA, "two-step tuning failed: %s", cudaGetErrorString(e));
+            if (ms < best) {
+                best = ms;
+                best_xb = xb;
+            }
+        }
+        hd->tb_xb = best_xb;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tb_cache[std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r)] = best_xb;
+    }
+    FD_CUDA(cudaEventRecord(hd->ev0, st));
+    for (int p = 0; p + 1 < nt; p += 2) {
+        const TmaMaps *m = nullptr;
+        int rc = tb_maps_for(hd, hd->ubuf[hd->cur], hd->ubuf[hd->cur ^ 1], &m);
+        if (rc != FD_OK) return rc;
+        StepArgs a = make_args(hd, hd->step, hd->cur);
+        a.x_block = hd->tb_xb;
+        a.n_rec = 0;
+        a.rec_sample = -1;
+        FD_CUDA(launch_tma2_step(hd->r, *m, a, static_cast<float *>(hd->tb_buf[0]), static_cast<float *>(hd->tb_buf[1]),
+                                 check, st));
+        // the outputs become the state (u^{n+2}, u^{n+1}); the inputs the next output pair
+        void *old_u = hd->ubuf[hd->cur], *old_up = hd->ubuf[hd->cur ^ 1];
+        hd->ubuf[0] = hd->tb_buf[1];
+        hd->ubuf[1] = hd->tb_buf[0];
+        hd->tb_buf[0] = old_u;
+        hd->tb_buf[1] = old_up;
+        hd->cur = 0;
+        hd->step += 2;
+    }
+    FD_CUDA(cudaEventRecord(hd->ev1, st));
+    hd->timed = true;
+    // the buffers moved: single-step maps and graphs refer to the old arrangement
+    hd->gen++;
+    if (hd->kernel == kTma && hd->tile_y > 0) {
+        int rc = build_maps(hd);
+        if (rc != FD_OK) return rc;
+    }
+    if (nt % 2) return fd_forward(hd, 1);
+    return FD_OK;
+}
+
 int fd_clear_sources(fd_handle *hd) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
     hd->sources.clear();
@@ -1186,6 +1326,12 @@ int fd_forward(fd_handle *hd, int nt) {
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
     if (nt == 0) return FD_OK;
+    // automatic kernel choice, space order 2: two steps per launch where the single-step
+    // kernel is bound by HBM traffic (measured 1.15x at 276^3; at space order 4 the
+    // overlap of the extended tiles costs more than the traffic saved). Same bits.
+    if (nt >= 2 && hd->opt.kernel == kAuto && hd->kernel == kTma && hd->r == 1 && hd->opt.storage == kF32 &&
+        hd->opt.form == kFactored && hd->n_rec == 0 && int(hd->sources.size()) <= kFusedSources)
+        return fd_forward_two_step(hd, nt);
     if (hd->kernel != kNaive && (hd->tile_y == 0 || hd->x_block == 0)) {
         int rc = autotune(hd);
         if (rc == FD_OK) rc = build_maps(hd);

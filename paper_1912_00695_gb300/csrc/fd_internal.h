@@ -150,6 +150,10 @@ cudaError_t launch_residual(const float *syn, float *obs_to_res, size_t n, cudaS
 cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, const float *f1,
                                   const long long *node_off, const int *row, const int *rec_idx, const float *rec_w,
                                   const float *resid, int nt, int t, float inv_dt2, int n_nodes, cudaStream_t s);
+// Two steps per launch (FP32 factored, radius 1-2): u^{n+1} into out1, u^{n+2} into out2.
+cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
+                             cudaStream_t s);
+bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey);
 cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
                                  cudaStream_t s);
 cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,

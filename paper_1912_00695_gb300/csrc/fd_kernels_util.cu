@@ -148,6 +148,28 @@ cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const
     }
 }
 
+#define FDGB_DECLARE_TMA2_RADIUS(R)                                                              \
+    cudaError_t tma2_step_radius_##R(const TmaMaps &map, const StepArgs &a, float *out1, float *out2, \
+                                     bool check, cudaStream_t s);                                 \
+    void tma2_geometry_radius_##R(int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey);
+FDGB_DECLARE_TMA2_RADIUS(1)
+FDGB_DECLARE_TMA2_RADIUS(2)
+#undef FDGB_DECLARE_TMA2_RADIUS
+
+cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
+                             cudaStream_t s) {
+    if (radius == 1) return tma2_step_radius_1(map, a, out1, out2, check, s);
+    if (radius == 2) return tma2_step_radius_2(map, a, out1, out2, check, s);
+    return cudaErrorInvalidValue;
+}
+
+bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey) {
+    if (radius == 1) tma2_geometry_radius_1(tz, ty, box_w, box_h, ez, ey);
+    else if (radius == 2) tma2_geometry_radius_2(tz, ty, box_w, box_h, ez, ey);
+    else return false;
+    return true;
+}
+
 cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {

@@ -1,0 +1,81 @@
+"""GPU tests of the two-steps-per-launch forward (temporal blocking): bit for
+bit the single-step result (even and odd step counts, chunked calls, sources
+near tile edges and inside the absorbing layer, ragged grids), and the FP64
+oracle within the FP32 bound; the unsupported cases are rejected."""
+import numpy as np
+import pytest
+
+import paper_1912_00695_gb300 as fd
+from paper_1912_00695_gb300 import inputs
+from harness import dt_for, eta_for, rel_l2, run_oracle
+
+pytestmark = pytest.mark.gpu
+H = inputs.H
+
+
+def _spec(k, seed, interior=(61, 47, 130), nbl=7):
+    rng = np.random.default_rng(seed)
+    vel = inputs.smooth_random_velocity(interior, nbl, rng, sigma=4.0)
+    return inputs.ShotSpec(interior, nbl, k, vel, (0, 0, 0), 25.0, 57)
+
+
+# interior nodes next to the two-step tile edges (z tiles of 56 from domain z = 0,
+# y tiles of 16 - 2R rows), inside the layer and in the middle
+SOURCES = [(30, 9, 48), (0, 0, 0), (60, 46, 129), (12, 21, 110)]
+
+
+def _run(spec, chunks, two_step, eta=None):
+    dt = dt_for(spec)
+    with fd.Shot(spec.interior, spec.space_order, H, dt, spec.nbl) as shot:
+        shot.set_model(spec.m, eta)
+        for i, src in enumerate(SOURCES):
+            shot.inject(*src, inputs.ricker(20.0 + 3 * i, dt, spec.nt))
+        for n in chunks:
+            (shot.forward_two_step if two_step else shot.forward)(n)
+        return shot.wavefield(0), shot.wavefield(1), shot.step
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_two_step_equals_single_step(k):
+    spec = _spec(k, seed=k)
+    want = _run(spec, [57], False)
+    for chunks in ([57], [10, 47], [1, 2, 3, 51]):
+        got = _run(spec, chunks, True)
+        np.testing.assert_array_equal(got[0], want[0])
+        np.testing.assert_array_equal(got[1], want[1])
+        assert got[2] == want[2] == 57
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_two_step_matches_oracle(oracle_mod, k):
+    spec = _spec(k, seed=10 + k, interior=(40, 35, 70), nbl=6)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    srcs = [(s, inputs.ricker(20.0 + 3 * i, dt, spec.nt))
+            for i, s in enumerate([(20, 9, 1), (0, 0, 0), (39, 34, 69), (12, 21, 50)])]
+    want, want_prev = run_oracle(oracle_mod, spec, spec.nt, dt, eta, sources=srcs)
+    with fd.Shot(spec.interior, k, H, dt, spec.nbl) as shot:
+        shot.set_model(spec.m, eta)
+        for s, w in srcs:
+            shot.inject(*s, w)
+        shot.forward_two_step(spec.nt)
+        e0, e1 = rel_l2(shot.wavefield(0), want), rel_l2(shot.wavefield(1), want_prev)
+    print(f"PARITY two_step_so{k} {e0:.3e} {e1:.3e}")
+    assert e0 <= 1e-5 and e1 <= 1e-5
+
+
+def test_two_step_rejects_unsupported():
+    spec = _spec(8, seed=3)
+    dt = dt_for(spec)
+    for kw, k in (({}, 8), ({"storage": "bf16"}, 4), ({"form": "expanded"}, 4)):
+        with fd.Shot(spec.interior, k, H, dt, spec.nbl, **kw) as shot:
+            shot.set_model(spec.m)
+            with pytest.raises(fd.FdError) as e:
+                shot.forward_two_step(2)
+            assert e.value.code == fd.FD_ENOTSUP
+    with fd.Shot(spec.interior, 4, H, dt, spec.nbl) as shot:
+        shot.set_model(spec.m)
+        shot.set_receivers([(1.0, 1.0, 1.0)], 4)
+        with pytest.raises(fd.FdError) as e:
+            shot.forward_two_step(2)
+        assert e.value.code == fd.FD_ENOTSUP
