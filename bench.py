@@ -47,7 +47,7 @@ def _kernel_hash() -> str:
     """Hash of the step kernels' sources: a committed ncu traffic figure is used
     only while it was measured on these sources."""
     h = hashlib.sha256()
-    for name in ("fd_stencil.cuh", "fd_tma.cuh", "fd_internal.h"):
+    for name in ("fd_stencil.cuh", "fd_tma.cuh", "fd_tma2.cuh", "fd_internal.h"):
         with open(os.path.join(ROOT, "paper_1912_00695_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
