@@ -1046,8 +1046,22 @@ static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, con
     int rc = fd_reset(hd);
     if (rc == FD_OK) rc = fd_set_receivers(hd, nrec, rec_xyz, nt);
     TmaMaps fm[2], am[2];
+    GradMaps gm{};
     for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], tz, ty, &fm[b]);
     for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, w[b], w[b ^ 1], tz, ty, &am[b]);
+    if (rc == FD_OK) rc = encode_box(hd, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tz, ty, &gm.grad);
+    if (rc == FD_OK) {
+        // the history as one 4-D tensor: level k - 1 of step k is the fourth coordinate
+        EncodeTiledFn fn = encode_fn();
+        cuuint64_t dims[4] = {cuuint64_t(hd->Nz), cuuint64_t(hd->Ny), cuuint64_t(hd->Nx), cuuint64_t(segment)};
+        cuuint64_t strides[3] = {cuuint64_t(hd->pz) * 4, cuuint64_t(hd->plane) * 4, cuuint64_t(np) * 4};
+        cuuint32_t box[4] = {cuuint32_t(tz), cuuint32_t(ty), 1, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (!fn || fn(&gm.hist, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, hist, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            rc = fail(FD_ECUDA, "cuTensorMapEncodeTiled failed for the history");
+    }
     if (rc != FD_OK) {
         release();
         return rc;
@@ -1066,7 +1080,7 @@ static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, con
                 a.n_rec = 0;
                 a.rec_sample = -1;
             }
-            err = launch_tma_grad_step(hd->r, kModeForwardD, fm[cur], a, check, st);
+            err = launch_tma_grad_step(hd->r, kModeForwardD, fm[cur], gm, a, check, st);
             if (err == cudaSuccess && ns > kFusedSources)
                 err = launch_inject_extra(a, hd->d_src, hd->d_src + ns, hd->d_src + 2 * ns, kFusedSources,
                                           ns - kFusedSources, kF32, 0, hd->extra_distinct, st, a.hist);
@@ -1122,8 +1136,9 @@ static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, con
             a.rec_sample = -1;
             a.x_block = xb;
             a.hist = hist + size_t(k - 1 - n0) * np;
+            a.hist_slot = k - 1 - n0;
             a.grad = grad;
-            e = launch_tma_grad_step(hd->r, kModeAdjointGrad, am[c], a, check, st);
+            e = launch_tma_grad_step(hd->r, kModeAdjointGrad, am[c], gm, a, check, st);
             if (e == cudaSuccess)
                 e = launch_adjoint_inject(w[c ^ 1], grad, a.hist, hd->f1, node_off, row, rec_idx, rec_w, resid, nt,
                                           k - 1, inv_dt2, n_nodes, st);

@@ -89,6 +89,7 @@ struct StepArgs {
     // history (forward: written; adjoint: read) and the gradient (adjoint)
     float *hist;
     float *grad;
+    int hist_slot;  // adjoint pass: the history level D^{k-1} sits at
 };
 
 // Host numerics (fd_numerics.cpp)
@@ -112,6 +113,12 @@ struct TmaMaps {
     CUtensorMap up_pt;
     CUtensorMap f1_pt;
     CUtensorMap f2_pt;
+};
+
+// The FWI gradient's adjoint pass reads these through the ring too.
+struct GradMaps {
+    CUtensorMap hist;  // 4-D: the second-time-difference history [levels][Nx][Ny][pz]
+    CUtensorMap grad;  // 3-D: the gradient
 };
 
 // One shot of a batch as the batched kernel sees it (device memory): the step
@@ -154,8 +161,8 @@ cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, con
 cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
                              cudaStream_t s);
 bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey);
-cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
-                                 cudaStream_t s);
+cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a,
+                                 bool check, cudaStream_t s);
 cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
                                     const long long *off, const float *w, int n, float *out, int stride,
                                     cudaStream_t s);

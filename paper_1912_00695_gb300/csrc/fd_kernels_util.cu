@@ -119,8 +119,8 @@ cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z,
 }
 
 #define FDGB_DECLARE_GRAD_RADIUS(R)                                                              \
-    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const StepArgs &a, bool check, \
-                                         cudaStream_t s);
+    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const GradMaps &gm,          \
+                                         const StepArgs &a, bool check, cudaStream_t s);
 FDGB_DECLARE_GRAD_RADIUS(1)
 FDGB_DECLARE_GRAD_RADIUS(2)
 FDGB_DECLARE_GRAD_RADIUS(3)
@@ -135,11 +135,11 @@ FDGB_DECLARE_GRAD_RADIUS(11)
 FDGB_DECLARE_GRAD_RADIUS(12)
 #undef FDGB_DECLARE_GRAD_RADIUS
 
-cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const StepArgs &a, bool check,
-                                 cudaStream_t s) {
+cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a,
+                                 bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_GRAD_R(R) \
-        case R: return tma_grad_step_radius_##R(mode, map, a, check, s);
+        case R: return tma_grad_step_radius_##R(mode, map, gm, a, check, s);
         FDGB_GRAD_R(1) FDGB_GRAD_R(2) FDGB_GRAD_R(3) FDGB_GRAD_R(4)
         FDGB_GRAD_R(5) FDGB_GRAD_R(6) FDGB_GRAD_R(7) FDGB_GRAD_R(8)
         FDGB_GRAD_R(9) FDGB_GRAD_R(10) FDGB_GRAD_R(11) FDGB_GRAD_R(12)

@@ -93,6 +93,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, int c1, int c2) {
     asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
@@ -145,7 +154,7 @@ template <> __device__ __forceinline__ __half2 Vec4Half<__half, __half2>::from2(
 template <> struct Vec4<__nv_bfloat16> : Vec4Half<__nv_bfloat16, __nv_bfloat162> {};
 template <> struct Vec4<__half> : Vec4Half<__half, __half2> {};
 
-template <int R, int LZ, int W, typename T>
+template <int R, int LZ, int W, typename T, int EXTRA_F = 0>
 struct TmaShape {
     static constexpr int VE = 16 / int(sizeof(T));         // elements per 16 bytes
     static constexpr int RZ = (R + VE - 1) / VE * VE;       // z halo: boxes start 16-byte aligned
@@ -164,10 +173,12 @@ struct TmaShape {
     static constexpr int PT_F = (PT_F_RAW + 127) / 128 * 128;
     static constexpr int OFF_FRONT = HALO, OFF_UP = HALO + PT_T, OFF_F1 = HALO + 2 * PT_T,
                          OFF_F2 = HALO + 2 * PT_T + PT_F;
-    static constexpr int STAGE_BYTES = HALO + 2 * PT_T + 2 * PT_F;
-    // stages + their mbarriers, plus slack to align the ring to 128 bytes (bulk tensor copies
-    // need a 128-byte aligned shared destination)
-    static constexpr int SMEM_BYTES = TmaPipe<R>::STAGES * STAGE_BYTES + 64 + 128;
+    // EXTRA_F more FP32 point tiles (the gradient pass: D^{k-1}, then the gradient)
+    static constexpr int OFF_X0 = HALO + 2 * PT_T + 2 * PT_F, OFF_X1 = OFF_X0 + PT_F;
+    static constexpr int STAGE_BYTES = HALO + 2 * PT_T + (2 + EXTRA_F) * PT_F;
+    // the mbarriers (first 128 bytes), then the stages, plus slack to align to 128 bytes
+    // (bulk tensor copies need a 128-byte aligned shared destination)
+    static constexpr int SMEM_BYTES = 128 + TmaPipe<R>::STAGES * STAGE_BYTES + 128;
 };
 
 // x-loop unroll (planes per queue shift): deeper unrolling saves queue moves but
@@ -197,14 +208,16 @@ struct TmaAcc {
 
 // The ring of stages in dynamic shared memory (128-byte aligned) and its S
 // mbarriers; thread 0 initialises the barriers once per CTA.
-template <int R, int LZ, int W, typename T>
+template <int R>
 __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw) {
-    using G = TmaShape<R, LZ, W, T>;
     constexpr int S = TmaPipe<R>::STAGES;
-    unsigned char *ring = reinterpret_cast<unsigned char *>(
+    // the S mbarriers sit in the first 128 bytes, the ring right after them, so their
+    // place does not depend on the stage layout
+    unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *ring = base + 128;
     if (threadIdx.x == 0) {
-        uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
+        uint64_t *bars = reinterpret_cast<uint64_t *>(base);
         for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -220,15 +233,16 @@ __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw)
 // Returns false if a wait gave up (status set, copies in flight drained).
 template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep>
 __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs &a, const ScaleState &sc, int bz,
-                                            int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc) {
-    using G = TmaShape<R, LZ, W, T>;
+                                            int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc,
+                                            const GradMaps *gm = nullptr) {
+    using G = TmaShape<R, LZ, W, T, MODE == kModeAdjointGrad ? 2 : 0>;
     using V = Vec4<T>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
     constexpr int U = TmaUnroll<R, FORM>::U;
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window values
     constexpr int S = TmaPipe<R>::STAGES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ring + S * G::STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ring - 128);  // placed by tma_ring_init
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -258,7 +272,12 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
         const uint32_t bar = smem_addr(&bars[stage]);
         unsigned char *st = ring + stage * G::STAGE_BYTES;
         const bool need_g = !g_free(x);
-        mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW + (need_g ? 2 : 1) * G::PT_F_RAW));
+        mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW +
+                                     ((need_g ? 2 : 1) + (MODE == kModeAdjointGrad ? 2 : 0)) * G::PT_F_RAW));
+        if constexpr (MODE == kModeAdjointGrad) {
+            tma_load_4d(smem_addr(st + G::OFF_X0), &gm->hist, bar, z0, y0, x, a.hist_slot);
+            tma_load_3d(smem_addr(st + G::OFF_X1), &gm->grad, bar, z0, y0, x);
+        }
         tma_load_3d(smem_addr(st), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
         tma_load_3d(smem_addr(st + G::OFF_FRONT), &maps->u_pt, bar, z0, y0, x + R);  // zero past Nx
         tma_load_3d(smem_addr(st + G::OFF_UP), &maps->up_pt, bar, z0, y0, x);
@@ -344,11 +363,11 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
             }
             const unsigned char *st = ring + stage * G::STAGE_BYTES;
             q[2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + pt_off);
-            float4 dv, gv;  // adjoint pass: D^{k-1} and the gradient at this plane, loaded early
+            float4 dv, gv;  // adjoint pass: D^{k-1} and the gradient at this plane (from the ring)
             if constexpr (MODE == kModeAdjointGrad) {
                 if (own) {
-                    dv = __ldcs(reinterpret_cast<const float4 *>(hist + x * P));
-                    gv = *reinterpret_cast<const float4 *>(grad + x * P);
+                    dv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X0) + pt_off);
+                    gv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X1) + pt_off);
                 }
             }
             if (own) {
@@ -564,7 +583,7 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
                                                         const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
-    unsigned char *ring = tma_ring_init<R, LZ, W, T>(smem_dyn);
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);
     const ScaleState sc = read_scales<T>(a);
     if (a.rec_sample >= 0 && a.n_rec > 0) tma_sample_receivers<T>(a, sc.s_u);
     const int xb = blockIdx.z * a.x_block;
@@ -581,23 +600,24 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
 // The FWI gradient's passes (FP32 factored; sources and receivers as the step).
 template <int R, int LZ, int W, int MODE>
 __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1)) fd_tma_grad_kernel(const __grid_constant__ TmaMaps maps,
+                                                             const __grid_constant__ GradMaps gmaps,
                                                              const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char *ring = tma_ring_init<R, LZ, W, float>(smem_dyn);
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);
     const ScaleState sc = read_scales<float>(a);
     if (a.rec_sample >= 0 && a.n_rec > 0) tma_sample_receivers<float>(a, 1.0f);
     const int xb = blockIdx.z * a.x_block;
     int g = 0;
     TmaAcc acc;
     if (tma_segment<R, kFactored, LZ, W, float, MODE>(&maps, a, sc, blockIdx.x, blockIdx.y, xb,
-                                                      min(xb + a.x_block, a.Nx), ring, g, acc) &&
+                                                      min(xb + a.x_block, a.Nx), ring, g, acc, &gmaps) &&
         check)
         reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
 }
 
 template <int R, int LZ, int W, int MODE>
-cudaError_t tma_grad_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s) {
-    using G = TmaShape<R, LZ, W, float>;
+cudaError_t tma_grad_launch(const TmaMaps &maps, const GradMaps &gm, const StepArgs &a, bool check, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W, float, MODE == kModeAdjointGrad ? 2 : 0>;
     auto kernel = fd_tma_grad_kernel<R, LZ, W, MODE>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -606,15 +626,16 @@ cudaError_t tma_grad_launch(const TmaMaps &maps, const StepArgs &a, bool check, 
         attr_set = true;
     }
     const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY, (a.Nx + a.x_block - 1) / a.x_block);
-    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(maps, a, check ? 1 : 0);
+    kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(maps, gm, a, check ? 1 : 0);
     return cudaGetLastError();
 }
 
 // Gradient passes exist for the 32x16 tile (LZ 8, W 4) only.
 template <int R>
-cudaError_t tma_grad_step_r(int mode, const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
-    if (mode == kModeForwardD) return tma_grad_launch<R, 8, 4, kModeForwardD>(map, a, check, s);
-    if (mode == kModeAdjointGrad) return tma_grad_launch<R, 8, 4, kModeAdjointGrad>(map, a, check, s);
+cudaError_t tma_grad_step_r(int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a, bool check,
+                            cudaStream_t s) {
+    if (mode == kModeForwardD) return tma_grad_launch<R, 8, 4, kModeForwardD>(map, gm, a, check, s);
+    if (mode == kModeAdjointGrad) return tma_grad_launch<R, 8, 4, kModeAdjointGrad>(map, gm, a, check, s);
     return cudaErrorInvalidValue;
 }
 
@@ -660,7 +681,7 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
     }
     __syncthreads();
     publish_scales<T>(sa, it.y == 0 && it.z == 0 && it.w == 0 && threadIdx.x == 0);
-    unsigned char *ring = tma_ring_init<R, LZ, W, T>(smem_dyn);
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);
     const ScaleState sc = read_scales<T>(sa);
     const int xb = it.w * sa.x_block;
     int g = 0;
@@ -796,8 +817,8 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
                                           int offset, cudaStream_t s) {                           \
         return tma_batch_step_r<R>(form, storage, tile_z, tile_y, shots, items, n_items, offset, s); \
     }                                                                                             \
-    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const StepArgs &a, bool check, \
-                                         cudaStream_t s) {                                        \
-        return tma_grad_step_r<R>(mode, map, a, check, s);                                        \
+    cudaError_t tma_grad_step_radius_##R(int mode, const TmaMaps &map, const GradMaps &gm,          \
+                                         const StepArgs &a, bool check, cudaStream_t s) {         \
+        return tma_grad_step_r<R>(mode, map, gm, a, check, s);                                    \
     }                                                                                             \
     }
