@@ -172,6 +172,12 @@ def algorithmic_bytes_per_step(spec, storage="f32") -> int:
     return int(spec.points * (3 * e + 4) + layer_points(spec) * 4)
 
 
+def algorithmic_bytes_two_steps(spec) -> int:
+    """One launch of the two-step kernel (FP32): read u^n, u^{n-1} and the
+    coefficient, write u^{n+1} and u^{n+2}; the damping field in the layer."""
+    return int(spec.points * 20 + layer_points(spec) * 4)
+
+
 def run_ours(args, rank: int, world: int):
     import torch
 
@@ -196,9 +202,10 @@ def run_ours(args, rank: int, world: int):
     def bench_step(record=None):
         for spec, form, shot, _, _ in shots:
             shot.reset()
+            n0 = fd.fd_kernel_launches()
             shot.forward(spec.nt)
             if record is not None:
-                record.append(shot.last_forward_ms())
+                record.append((shot.last_forward_ms(), fd.fd_kernel_launches() - n0))
 
     for _ in range(args.warmup):
         bench_step()
@@ -214,6 +221,7 @@ def run_ours(args, rank: int, world: int):
     ev1 = torch.cuda.Event(enable_timing=True)
     kernel_ms = []
     torch.cuda.synchronize()
+    launches0 = fd.fd_kernel_launches()
     ev0.record(stream)
     for _ in range(args.steps):
         for spec, form, shot, _, _ in shots:
@@ -221,6 +229,7 @@ def run_ours(args, rank: int, world: int):
             shot.forward(spec.nt)
     ev1.record(stream)
     torch.cuda.synchronize()
+    gpu_launches = fd.fd_kernel_launches() - launches0
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
     # per-shot kernel time (events around each graph replay on the launching stream)
@@ -230,22 +239,37 @@ def run_ours(args, rank: int, world: int):
 
     pts_per_step = sum(spec.points * spec.nt for spec, *_ in shots)
     value = pts_per_step * args.steps * world / (total_ms * 1e-3) / 1e9
-    # roofline of the step kernel: algorithmic bytes / kernel time over all shots
-    alg_bytes = sum(algorithmic_bytes_per_step(spec) * spec.nt for spec, *_ in shots)
-    kern_s = sum(kernel_ms) * 1e-3
-    launches = sum(spec.nt for spec, *_ in shots)
-    achieved = alg_bytes / kern_s / 1e9
+    # roofline of the single-step kernel (fd_tma_kernel, most of the device time):
+    # algorithmic bytes / kernel time over the shots it ran (one launch per step);
+    # space order 2 (factored) runs two steps per launch (fd_tma2_kernel), with
+    # its own algorithmic bytes in the breakdown
     peak, peak_kind = _peaks()
+    one = [(spec, ms) for (spec, *_), (ms, nl) in zip(shots, kernel_ms) if nl == spec.nt]
+    alg_bytes = sum(algorithmic_bytes_per_step(spec) * spec.nt for spec, _ in one)
+    kern_s = sum(ms for _, ms in one) * 1e-3
+    launches = sum(spec.nt for spec, _ in one)
+    achieved = alg_bytes / kern_s / 1e9 if one else 0.0
     khash = _kernel_hash()
     traffic = _ncu_traffic(khash, f"{args.workload}_n{args.n}")
     breakdown = {}
-    for (spec, form, shot, _, _), ms in zip(shots, kernel_ms):
+    for (spec, form, shot, _, _), (ms, nl) in zip(shots, kernel_ms):
         key = f"so{spec.space_order}_{form}"
-        gbs = algorithmic_bytes_per_step(spec) * spec.nt / (ms * 1e-3) / 1e9
-        breakdown[key] = {"gpts": round(spec.points * spec.nt / (ms * 1e-3) / 1e9, 2),
-                          "us_per_step": round(ms * 1e3 / spec.nt, 2),
-                          "hbm_frac": round(gbs / peak, 4),
-                          "kernel_tz_ty_xb": list(shot.config)}
+        entry = {"gpts": round(spec.points * spec.nt / (ms * 1e-3) / 1e9, 2),
+                 "us_per_step": round(ms * 1e3 / spec.nt, 2), "launches": nl}
+        if nl == spec.nt:
+            gbs = algorithmic_bytes_per_step(spec) * spec.nt / (ms * 1e-3) / 1e9
+            entry.update(kernel="fd_tma_kernel", hbm_frac=round(gbs / peak, 4),
+                         kernel_tz_ty_xb=list(shot.config))
+        else:
+            pairs = spec.nt // 2
+            gbs = (algorithmic_bytes_two_steps(spec) * pairs
+                   + algorithmic_bytes_per_step(spec) * (spec.nt - 2 * pairs)) / (ms * 1e-3) / 1e9
+            eff = algorithmic_bytes_per_step(spec) * spec.nt / (ms * 1e-3) / 1e9
+            entry.update(kernel="fd_tma2_kernel (two steps per launch)", hbm_frac=round(gbs / peak, 4),
+                         hbm_frac_of_single_step_bytes=round(eff / peak, 4),
+                         algorithmic_bytes_per_launch=algorithmic_bytes_two_steps(spec),
+                         traffic=_ncu_traffic(khash, f"{args.workload}_n{args.n}_two_step"))
+        breakdown[key] = entry
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, shots, stream, world)
@@ -268,10 +292,10 @@ def run_ours(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": "fd_tma_kernel", "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch_avg": int(alg_bytes / launches)},
+                     "algorithmic_bytes_per_launch_avg": int(alg_bytes / launches) if launches else 0},
         "breakdown": breakdown,
         "e2e": e2e,
-        "gpu_launches": launches * args.steps,
+        "gpu_launches": gpu_launches,
         "clocks": clk,
         "cpu_baseline": cpu,
         "kernel_hash": khash,
@@ -323,18 +347,20 @@ def run_receivers(args, rank: int, world: int):
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        n0 = fd.fd_kernel_launches()
         ev0.record(stream)
         for _ in range(args.steps):
             shot.reset()
             shot.forward(spec.nt)
         ev1.record(stream)
         torch.cuda.synchronize()
-        return ev0.elapsed_time(ev1)
+        return ev0.elapsed_time(ev1), fd.fd_kernel_launches() - n0
 
-    ms_plain = max_over_ranks(timed(plain))
+    ms_plain = max_over_ranks(timed(plain)[0])
     clocks = ClockSampler(dev)
     clocks.start()
-    ms_rec = max_over_ranks(timed(rshot))
+    ms_rec, rec_launches = timed(rshot)
+    ms_rec = max_over_ranks(ms_rec)
     clk = clocks.stop()
     pts = spec.points * spec.nt * args.steps * world
     gpts, gpts_plain = pts / (ms_rec * 1e-3) / 1e9, pts / (ms_plain * 1e-3) / 1e9
@@ -374,7 +400,7 @@ def run_receivers(args, rank: int, world: int):
                      "kernel": "fd_tma_kernel + sample_receivers_kernel", "peak_source": peak_kind},
         "e2e": {"value": round(spec.points * spec.nt * args.steps * world / e2e_s / 1e9, 3), "unit": "Gpts/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 3 * spec.nt * args.steps,
+        "gpu_launches": rec_launches,
         "clocks": clk,
     }
     if rank == 0:
@@ -414,12 +440,14 @@ def run_gradient(args, rank: int, world: int):
     clocks = ClockSampler(dev)
     clocks.start()
     dev_ms, wall = [], []
+    launches0 = fd.fd_kernel_launches()
     for _ in range(args.steps):
         t0 = time.perf_counter()
         shot.fwi_gradient(recs, obs)
         wall.append(time.perf_counter() - t0)
         dev_ms.append(shot.last_forward_ms())
     clk = clocks.stop()
+    grad_launches = fd.fd_kernel_launches() - launches0
     ms = max_over_ranks(sum(dev_ms))
     wall_s = max_over_ranks(sum(wall) * 1e3) * 1e-3
     updates = 2 * spec.points * spec.nt * args.steps * world
@@ -443,7 +471,7 @@ def run_gradient(args, rank: int, world: int):
                      "kernel": "fd_tma_grad_kernel (forward D / adjoint gradient)", "peak_source": peak_kind},
         "e2e": {"value": round(updates / wall_s / 1e9, 3), "unit": "Gpts/s",
                 "h2d_bytes_per_step": int(obs.nbytes), "d2h_bytes_per_step": int(m.nbytes + obs.nbytes)},
-        "gpu_launches": (3 * spec.nt + 2) * args.steps,
+        "gpu_launches": grad_launches,
         "clocks": clk,
     }
     if rank == 0:
@@ -514,7 +542,10 @@ def run_batched(args, rank: int, world: int):
         tdist.barrier()
     clocks = ClockSampler(dev)
     clocks.start()
-    batch_ms = max_over_ranks(timed(batch_step, args.steps))
+    launches0 = fd.fd_kernel_launches()
+    batch_ms = timed(batch_step, args.steps)
+    batch_launches = fd.fd_kernel_launches() - launches0
+    batch_ms = max_over_ranks(batch_ms)
     clk = clocks.stop()
     value = pts * args.steps * world / (batch_ms * 1e-3) / 1e9
     plain = pts * args.steps / (plain_ms * 1e-3) / 1e9
@@ -542,7 +573,7 @@ def run_batched(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "fd_tma_batch_kernel", "peak_source": peak_kind},
-        "gpu_launches": nt * args.steps + 2 * len(specs) * args.steps,
+        "gpu_launches": batch_launches,
         "clocks": clk,
     }
     if rank == 0:
@@ -588,19 +619,22 @@ def run_precision(args, rank: int, world: int):
                 clocks.start()
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
+            n0 = fd.fd_kernel_launches()
             ev0.record(stream)
             for _ in range(args.steps):
                 shot.reset()
                 shot.forward(spec.nt)
             ev1.record(stream)
             torch.cuda.synchronize()
+            n_launch = fd.fd_kernel_launches() - n0
             if sample_clocks and st == "bf16":
                 clk = clocks.stop()
             ms = ev0.elapsed_time(ev1)
             gpts = spec.points * spec.nt * args.steps / (ms * 1e-3) / 1e9
             alg = algorithmic_bytes_per_step(spec, st) * spec.nt * args.steps
             res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / args.steps, 3),
-                       "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config)}
+                       "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config),
+                       "launches": n_launch}
             shot.close()
         return res
 
@@ -631,7 +665,7 @@ def run_precision(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "achieved": round(res["bf16"]["hbm_frac"] * peak, 1), "peak": peak,
                      "unit": "GB/s", "frac": res["bf16"]["hbm_frac"], "traffic": None,
                      "kernel": "fd_tma_kernel (bf16)", "peak_source": peak_kind},
-        "gpu_launches": 3 * spec.nt * args.steps,
+        "gpu_launches": res["bf16"]["launches"],
         "clocks": clk,
     }
     if rank == 0:
@@ -684,7 +718,9 @@ def run_serving(args, rank: int, world: int):
     offered = args.rate * mean_work / 1e9
     clocks = ClockSampler(dev)
     clocks.start()
+    launches0 = fd.fd_kernel_launches()
     at_rate = serve(make_requests(), realtime=True)
+    serve_launches = fd.fd_kernel_launches() - launches0
     clk = clocks.stop()
     scale70 = offered / (0.7 * capacity) if capacity > 0 else 1.0
     at70 = serve(make_requests(scale70), realtime=True)
@@ -703,7 +739,7 @@ def run_serving(args, rank: int, world: int):
         "at_trace_rate": {k: round(v, 4) if isinstance(v, float) else v for k, v in at_rate.items()},
         "at_70pct_capacity": dict({k: round(v, 4) if isinstance(v, float) else v for k, v in at70.items()},
                                   rate_per_s=round(args.rate / scale70, 3)),
-        "gpu_launches": at_rate["gpu_launches"],
+        "gpu_launches": serve_launches,
         "clocks": clk,
     }
     if rank == 0:

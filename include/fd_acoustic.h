@@ -290,10 +290,18 @@ int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz);
  * (zeros before the first fd_forward when the autotuner still has to run). */
 int fd_get_config(fd_handle *hd, int *kernel, int *tile_z, int *tile_y, int *x_block);
 
-/* Device time of the step kernels queued by the last fd_forward, in ms,
- * measured by CUDA events on the handle's stream around the graph replay
- * (synchronises). FD_ESTATE if no fd_forward was timed yet. */
+/* Device time of the step kernels queued by the last fd_forward (or
+ * fd_forward_two_step), in ms, measured by CUDA events on the handle's stream
+ * around the graph replay or the two-step launches (synchronises). FD_ESTATE
+ * if no fd_forward was timed yet. */
 int fd_last_forward_ms(fd_handle *hd, float *ms);
+
+/* Number of this library's kernel launches executed or queued since it was
+ * loaded, over all handles, batches and fd_forward_noalloc calls: a replayed
+ * CUDA graph adds the kernels it holds (launches recorded into a graph are not
+ * counted when recorded). The difference of two readings counts the launches
+ * of the span between them. No device work; FD_EINVAL if count is NULL. */
+int fd_kernel_launches(long long *count);
 
 /* Release every device buffer and the handle. NULL is accepted (no-op). */
 int fd_destroy(fd_handle *hd);

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "fd_get_dims": (_i, [_vp, _ip, _ip, _ip]),
     "fd_get_config": (_i, [_vp, _ip, _ip, _ip, _ip]),
     "fd_last_forward_ms": (_i, [_vp, _fp]),
+    "fd_kernel_launches": (_i, [ctypes.POINTER(ctypes.c_longlong)]),
     "fd_destroy": (_i, [_vp]),
     "fd_dt_max": (_i, [_i, _d, _d, _dp]),
     "fd_fd_weights": (_i, [_i, _dp]),
@@ -302,6 +303,13 @@ def fd_get_config(hd):
 def fd_last_forward_ms(hd) -> float:
     v = ctypes.c_float()
     _check(lib().fd_last_forward_ms(hd, ctypes.byref(v)), "fd_last_forward_ms")
+    return v.value
+
+
+def fd_kernel_launches() -> int:
+    """Kernel launches of this library executed or queued since it was loaded."""
+    v = ctypes.c_longlong()
+    _check(lib().fd_kernel_launches(ctypes.byref(v)), "fd_kernel_launches")
     return v.value
 
 

@@ -4,9 +4,33 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "fd_internal.h"
+#include "fd_launch_count.h"
 
 namespace fdgb {
+
+namespace {
+std::atomic<long long> g_launches{0};
+thread_local long long t_captured = 0;
+}  // namespace
+
+cudaError_t counted(cudaError_t e, cudaStream_t s, int n) {
+    if (e != cudaSuccess) return e;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        t_captured += n;
+    else
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+    return e;
+}
+
+long long captured_launches() { return t_captured; }
+
+void count_replay(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
 
 #define FDGB_DECLARE_RADIUS(R)                                                                   \
     cudaError_t stream_step_radius_##R(int form, int storage, int tile_y, const StepArgs &a,    \
@@ -27,7 +51,7 @@ FDGB_DECLARE_RADIUS(11)
 FDGB_DECLARE_RADIUS(12)
 #undef FDGB_DECLARE_RADIUS
 
-cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
+static cudaError_t launch_stream_step_dispatch(int radius, int form, int storage, int tile_y, const StepArgs &a,
                                bool check, cudaStream_t s) {
     switch (radius) {
         case 1: return stream_step_radius_1(form, storage, tile_y, a, check, s);
@@ -46,7 +70,12 @@ cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, co
     }
 }
 
-cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
+cudaError_t launch_stream_step(int radius, int form, int storage, int tile_y, const StepArgs &a,
+                               bool check, cudaStream_t s) {
+    return counted(launch_stream_step_dispatch(radius, form, storage, tile_y, a, check, s), s);
+}
+
+static cudaError_t launch_naive_step_dispatch(int radius, int form, int storage, const StepArgs &a, bool check,
                               cudaStream_t s) {
     switch (radius) {
         case 1: return naive_step_radius_1(form, storage, a, check, s);
@@ -63,6 +92,11 @@ cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs 
         case 12: return naive_step_radius_12(form, storage, a, check, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs &a, bool check,
+                              cudaStream_t s) {
+    return counted(launch_naive_step_dispatch(radius, form, storage, a, check, s), s);
 }
 
 int stream_grid_x_chunks(int Nx, int x_block) { return (Nx + x_block - 1) / x_block; }
@@ -104,7 +138,7 @@ FDGB_DECLARE_BATCH_RADIUS(11)
 FDGB_DECLARE_BATCH_RADIUS(12)
 #undef FDGB_DECLARE_BATCH_RADIUS
 
-cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z, int tile_y,
+static cudaError_t launch_tma_batch_step_dispatch(int radius, int form, int storage, int tile_z, int tile_y,
                                   const BatchShot *shots, const int4 *items, int n_items, int offset,
                                   cudaStream_t s) {
     switch (radius) {
@@ -116,6 +150,12 @@ cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z,
 #undef FDGB_BATCH_R
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z, int tile_y,
+                                  const BatchShot *shots, const int4 *items, int n_items, int offset,
+                                  cudaStream_t s) {
+    return counted(launch_tma_batch_step_dispatch(radius, form, storage, tile_z, tile_y, shots, items, n_items, offset, s), s);
 }
 
 #define FDGB_DECLARE_GRAD_RADIUS(R)                                                              \
@@ -135,7 +175,7 @@ FDGB_DECLARE_GRAD_RADIUS(11)
 FDGB_DECLARE_GRAD_RADIUS(12)
 #undef FDGB_DECLARE_GRAD_RADIUS
 
-cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a,
+static cudaError_t launch_tma_grad_step_dispatch(int radius, int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a,
                                  bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_GRAD_R(R) \
@@ -148,6 +188,11 @@ cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const
     }
 }
 
+cudaError_t launch_tma_grad_step(int radius, int mode, const TmaMaps &map, const GradMaps &gm, const StepArgs &a,
+                                 bool check, cudaStream_t s) {
+    return counted(launch_tma_grad_step_dispatch(radius, mode, map, gm, a, check, s), s);
+}
+
 #define FDGB_DECLARE_TMA2_RADIUS(R)                                                              \
     cudaError_t tma2_step_radius_##R(const TmaMaps &map, const StepArgs &a, float *out1, float *out2, \
                                      bool check, cudaStream_t s);                                 \
@@ -156,11 +201,16 @@ FDGB_DECLARE_TMA2_RADIUS(1)
 FDGB_DECLARE_TMA2_RADIUS(2)
 #undef FDGB_DECLARE_TMA2_RADIUS
 
-cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
+static cudaError_t launch_tma2_step_dispatch(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
                              cudaStream_t s) {
     if (radius == 1) return tma2_step_radius_1(map, a, out1, out2, check, s);
     if (radius == 2) return tma2_step_radius_2(map, a, out1, out2, check, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
+                             cudaStream_t s) {
+    return counted(launch_tma2_step_dispatch(radius, map, a, out1, out2, check, s), s);
 }
 
 bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey) {
@@ -170,7 +220,7 @@ bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez
     return true;
 }
 
-cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+static cudaError_t launch_tma_step_dispatch(int radius, int form, int storage, int tile_z, int tile_y,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_TMA_R(R) \
@@ -181,6 +231,11 @@ cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int t
 #undef FDGB_TMA_R
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+                            const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
+    return counted(launch_tma_step_dispatch(radius, form, storage, tile_z, tile_y, map, a, check, s), s);
 }
 
 bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *w, int *h, int *rz) {
@@ -413,19 +468,19 @@ __global__ void prepare_factored_kernel(float *f1, float *f2, long long n, float
 cudaError_t launch_model_check(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
                                ModelCheck *out, cudaStream_t s) {
     model_check_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, out);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_default_damping(const float *m, float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
                                    float dmax, cudaStream_t s) {
     default_damping_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, dmax);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, float half_dt, float dt2,
                                     cudaStream_t s) {
     prepare_factored_kernel<<<1216, 256, 0, s>>>(f1, f2, n_pitched, half_dt, dt2);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy, const int *sz,
@@ -442,7 +497,7 @@ cudaError_t launch_inject_extra(const StepArgs &a, const int *sx, const int *sy,
     else if (storage == kF16)
         inject_extra_kernel<__half><<<blocks, threads, 0, s>>>(a, sx, sy, sz, first, count, expanded, d, nullptr);
     else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, const float *f1,
@@ -452,7 +507,7 @@ cudaError_t launch_adjoint_inject(float *w, float *grad, const float *dhist, con
     const int threads = 128, blocks = (n_nodes + threads - 1) / threads;
     adjoint_inject_kernel<<<blocks, threads, 0, s>>>(w, grad, dhist, f1, node_off, row, rec_idx, rec_w, resid, nt, t,
                                                      inv_dt2, n_nodes);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 __global__ void residual_kernel(const float *syn, float *obs_to_res, long long n) {
@@ -463,7 +518,7 @@ __global__ void residual_kernel(const float *syn, float *obs_to_res, long long n
 cudaError_t launch_residual(const float *syn, float *obs_to_res, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     residual_kernel<<<608, 256, 0, s>>>(syn, obs_to_res, (long long)n);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScales *scales, int slot,
@@ -482,7 +537,7 @@ cudaError_t launch_sample_receivers(const void *u, int storage, const LevelScale
                                                                     off, w, n, out, stride);
     else
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int Nz, int pz,
@@ -498,7 +553,7 @@ cudaError_t launch_unpack_level(const void *src, float *dst, int Nx, int Ny, int
         unpack_kernel<__half><<<blocks, threads, 0, s>>>(static_cast<const __half *>(src), dst, Nx, Ny,
                                                          Nz, pz, scales, slot);
     else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int Nz, int pz,
@@ -513,13 +568,13 @@ cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int N
         pack_kernel<__half><<<blocks, threads, 0, s>>>(src, static_cast<__half *>(dst), Nx, Ny, Nz, pz,
                                                        inv_scale);
     else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_set_level_scale(LevelScales *scales, int slot, float scale, unsigned amax_bits,
                                    float dscale, unsigned damax_bits, cudaStream_t s) {
     set_level_scale_kernel<<<1, 32, 0, s>>>(scales, slot, scale, amax_bits, dscale, damax_bits);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_unpack_prev(const void *u, const void *d, float *dst, int Nx, int Ny, int Nz, int pz,
@@ -534,12 +589,12 @@ cudaError_t launch_unpack_prev(const void *u, const void *d, float *dst, int Nx,
                                                               static_cast<const __half *>(d), dst, Nx, Ny, Nz,
                                                               pz, scales, slot);
     else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_init_scales(LevelScales *scales, cudaStream_t s) {
     init_scales_kernel<<<1, 32, 0, s>>>(scales);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 }  // namespace fdgb

@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "../../include/fd_acoustic.h"
+#include "fd_launch_count.h"
 #include "fd_stencil.cuh"
 
 // sources this entry point accepts (its documented limit)
@@ -198,7 +199,7 @@ __global__ void noalloc_clear_kernel(unsigned *scratch) {
 template <int R>
 cudaError_t launch_noalloc(const StepArgs &a, dim3 grid, unsigned *scratch, cudaStream_t s) {
     noalloc_step_kernel<R><<<grid, dim3(kTileZ, kNoAllocTY), 0, s>>>(a, scratch + 64);
-    return cudaGetLastError();
+    return counted(cudaGetLastError(), s);
 }
 
 cudaError_t launch_noalloc_r(int r, const StepArgs &a, dim3 grid, unsigned *scratch, cudaStream_t s) {
@@ -329,7 +330,7 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     noalloc_clear_kernel<<<1, 32, 0, s>>>(scratch);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = counted(cudaGetLastError(), s);
     float *cur = d_u, *prev = d_u_prev;
     for (int i = 0; i < nt && e == cudaSuccess; ++i) {
         a.u = cur;
@@ -338,7 +339,7 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
         e = launch_noalloc_r(r, a, grid, scratch, s);
         if (e == cudaSuccess) {
             noalloc_reduce_kernel<<<1, 256, 0, s>>>(scratch, n_ctas);
-            e = cudaGetLastError();
+            e = counted(cudaGetLastError(), s);
         }
         std::swap(cur, prev);
     }

@@ -15,8 +15,8 @@
 //    u^{n+1} ring (x, y and z taps), u^n(x - R) (the oldest queue entry), and
 //    w, g of plane x - R (a register queue of R+1 planes), and stores it.
 // Per pair of steps HBM sees u^n, u^{n-1}, w (g in the layer) read and
-// u^{n+1}, u^{n+2} written: 24 B per point instead of 32 for two single steps
-// (halo and overlap re-reads come from L2). The extended tile costs
+// u^{n+1}, u^{n+2} written: 20 B per point (plus g in the layer) instead of 32
+// for two single steps (halo and overlap re-reads come from L2). The extended tile costs
 // 64x16 / (56 x (16-2R)) more first-step work. Outputs go to two other
 // buffers: u^{n+1} cannot overwrite u^{n-1}, which overlapping CTAs still read.
 // Sources of both steps are fused; receivers and the other storages are not

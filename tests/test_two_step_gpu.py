@@ -79,3 +79,45 @@ def test_two_step_rejects_unsupported():
         with pytest.raises(fd.FdError) as e:
             shot.forward_two_step(2)
         assert e.value.code == fd.FD_ENOTSUP
+
+
+def test_two_step_launch_count_and_timing():
+    """A forward of nt steps at space order 2 (automatic kernel choice) runs
+    nt // 2 two-step launches plus one single step for odd nt; the library's
+    launch counter sees exactly those (no other kernels), and the device time
+    of the call covers all of them, the odd step included."""
+    spec = _spec(2, seed=7, interior=(120, 120, 120), nbl=8)
+    dt = dt_for(spec)
+    with fd.Shot(spec.interior, 2, H, dt, spec.nbl) as shot:
+        shot.set_model(spec.m)
+        shot.inject(60, 60, 60, inputs.ricker(20.0, dt, 200))
+        for nt in (10, 41, 1):  # first calls tune and capture; the counts below are of repeats
+            shot.forward(nt)
+        counts, ms = {}, {}
+        for nt in (10, 41, 1):
+            n0 = fd.fd_kernel_launches()
+            shot.forward(nt)
+            counts[nt] = fd.fd_kernel_launches() - n0
+            ms[nt] = shot.last_forward_ms()
+    assert counts == {10: 5, 41: 21, 1: 1}
+    assert ms[41] > 4 * ms[1] and ms[41] > 2 * ms[10]
+
+
+def test_single_step_launch_count():
+    """One launch per step through the replayed graph, one more per step with
+    more sources than the step kernel fuses (the extra-source kernel)."""
+    spec = _spec(8, seed=8)
+    dt = dt_for(spec)
+    with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
+        shot.set_model(spec.m)
+        shot.inject(10, 10, 10, inputs.ricker(20.0, dt, 40))
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 6
+        for i in range(4):
+            shot.inject(12 + i, 10, 10, inputs.ricker(20.0, dt, 40))
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 12
