@@ -82,6 +82,14 @@ extern "C" {
                                halo fetched by tensor-map bulk copies; FP32 storage (both
                                forms) and 16-bit storage (factored form) */
 
+/* Outer boundary of the computational domain (the paper gives none; Sec. 2
+ * names absorbing layers only). */
+#define FD_BOUNDARY_ZERO 0      /* zero (Dirichlet) halo of k/2 cells: the solver's mode  */
+#define FD_BOUNDARY_PERIODIC 1  /* every axis wraps around (a 3-torus): a test mode in
+                                   which the scheme's discrete plane waves and, with
+                                   eta = 0, its discrete energy are known exactly; FP32,
+                                   naive kernel, single shots only                        */
+
 typedef struct fd_options {
     int storage;       /* FD_STORAGE_*                                             */
     int form;          /* FD_FORM_*                                                */
@@ -95,12 +103,13 @@ typedef struct fd_options {
                           consecutive planes of one y-z tile); 0 = autotune         */
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
                           fd_read_wavefield/fd_status report FD_ENONFINITE          */
+    int boundary;      /* FD_BOUNDARY_*                                            */
 } fd_options;
 
 typedef struct fd_handle fd_handle;
 
 /* Fill *opt with the defaults: FP32, factored, auto kernel, autotuned tile
- * and x_block, finite check on. */
+ * and x_block, finite check on, zero boundary. */
 void fd_options_default(fd_options *opt);
 
 /* ---- single-shot solver --------------------------------------------------- */
@@ -116,9 +125,11 @@ int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double
                        fd_handle **out);
 
 /* As fd_acoustic_create with explicit options (opt == NULL: defaults).
- * FD_ENOTSUP for an unknown storage/form/kernel value, 16-bit storage with
- * the expanded form or a kernel other than TMA/AUTO, or a (tile_z, tile_y)
- * pair the chosen kernel does not have. */
+ * FD_ENOTSUP for an unknown storage/form/kernel/boundary value, 16-bit
+ * storage with the expanded form or a kernel other than TMA/AUTO, a
+ * (tile_z, tile_y) pair the chosen kernel does not have, or the periodic
+ * boundary with 16-bit storage or a kernel other than NAIVE/AUTO (AUTO then
+ * selects NAIVE). */
 int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                           const fd_options *opt, fd_handle **out);
 

@@ -16,7 +16,7 @@ from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_for
                    fd_batch_inject, fd_batch_read, fd_batch_read_device, fd_batch_remove, fd_batch_reset,
                    fd_batch_set_stream, fd_batch_shot_status, fd_batch_shot_step, fd_batch_size,
                    fd_batch_synchronize, fd_shot_device_bytes)
-from ._abi import (FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD_EUNSTABLE,  # noqa: F401
+from ._abi import (FD_BOUNDARY_PERIODIC, FD_BOUNDARY_ZERO, FD_EFULL, FD_EINVAL, FD_ENOMEM, FD_ENONFINITE, FD_ENOTSUP, FD_EUNSTABLE,  # noqa: F401
                    FD_ERANGE, FD_ESTATE, FD_ETIMEOUT, FD_FORM_EXPANDED, FD_FORM_FACTORED,
                    FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
@@ -31,10 +31,11 @@ STORAGE = {"f32": FD_STORAGE_F32, "bf16": FD_STORAGE_BF16, "f16": FD_STORAGE_F16
 FORMS = {"factored": FD_FORM_FACTORED, "expanded": FD_FORM_EXPANDED}
 KERNELS = {"auto": FD_KERNEL_AUTO, "stream": FD_KERNEL_STREAM, "naive": FD_KERNEL_NAIVE,
            "tma": FD_KERNEL_TMA}
+BOUNDARIES = {"zero": FD_BOUNDARY_ZERO, "periodic": FD_BOUNDARY_PERIODIC}
 
 
 def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x_block=0,
-            check_finite=True) -> fd_options:
+            check_finite=True, boundary="zero") -> fd_options:
     o = fd_options_default()
     o.storage = STORAGE[storage]
     o.form = FORMS[form]
@@ -43,6 +44,7 @@ def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x
     o.tile_y = int(tile_y)
     o.x_block = int(x_block)
     o.check_finite = int(bool(check_finite))
+    o.boundary = BOUNDARIES[boundary]
     return o
 
 

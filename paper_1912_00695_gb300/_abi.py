@@ -32,6 +32,7 @@ FD_EFULL = -10
 FD_STORAGE_F32, FD_STORAGE_BF16, FD_STORAGE_F16 = 0, 1, 2
 FD_FORM_FACTORED, FD_FORM_EXPANDED = 0, 1
 FD_KERNEL_AUTO, FD_KERNEL_STREAM, FD_KERNEL_NAIVE, FD_KERNEL_TMA = 0, 1, 2, 3
+FD_BOUNDARY_ZERO, FD_BOUNDARY_PERIODIC = 0, 1
 
 ERROR_NAMES = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ERANGE", -3: "FD_EUNSTABLE", -4: "FD_ENOMEM",
                -5: "FD_ECUDA", -6: "FD_ENONFINITE", -7: "FD_ETIMEOUT", -8: "FD_ESTATE",
@@ -47,7 +48,7 @@ class FdError(RuntimeError):
 class fd_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("form", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("tile_y", ctypes.c_int), ("x_block", ctypes.c_int),
-                ("check_finite", ctypes.c_int)]
+                ("check_finite", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 _lock = threading.Lock()

@@ -16,6 +16,7 @@
 #include "../../include/fd_acoustic.h"
 #include "fd_internal.h"
 #include "fd_launch_count.h"
+#include "fd_periodic.h"
 
 using namespace fdgb;
 
@@ -274,6 +275,7 @@ cudaError_t sample_level(const fd_handle *hd, const void *u, long long level, cu
 // (TMA kernel only).
 cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y,
                           const TmaMaps *map, bool check, cudaStream_t s) {
+    if (hd->opt.boundary == FD_BOUNDARY_PERIODIC) return launch_periodic_step(hd->r, hd->opt.form, a, check, s);
     if (kernel == kNaive) return launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s);
     if (kernel == kTma)
         return launch_tma_step(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, *map, a, check, s);
@@ -691,6 +693,7 @@ void fd_options_default(fd_options *opt) {
     opt->tile_y = 0;
     opt->x_block = 0;
     opt->check_finite = 1;
+    opt->boundary = FD_BOUNDARY_ZERO;
 }
 
 const char *fd_last_error(void) { return g_last_error.c_str(); }
@@ -741,9 +744,15 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     const long long Nx = nx + 2LL * nbl, Ny = ny + 2LL * nbl, Nz = nz + 2LL * nbl;
     if (Nx > kMaxDim || Ny > kMaxDim || Nz > kMaxDim) return fail(FD_EINVAL, "extent above 65535");
     if (opt.storage < 0 || opt.storage > 2 || opt.form < 0 || opt.form > 1 || opt.kernel < 0 ||
-        opt.kernel > 3)
-        return fail(FD_ENOTSUP, "unknown storage/form/kernel option");
+        opt.kernel > 3 || (opt.boundary != FD_BOUNDARY_ZERO && opt.boundary != FD_BOUNDARY_PERIODIC))
+        return fail(FD_ENOTSUP, "unknown storage/form/kernel/boundary option");
     int kernel = opt.kernel;
+    if (opt.boundary == FD_BOUNDARY_PERIODIC) {
+        // test mode: the naive kernel with wrapped tap indices, FP32
+        if (opt.storage != kF32) return fail(FD_ENOTSUP, "the periodic boundary runs on FP32 storage");
+        if (kernel != kAuto && kernel != kNaive) return fail(FD_ENOTSUP, "the periodic boundary runs on the naive kernel");
+        kernel = kNaive;
+    }
     if (opt.storage != kF32) {
         // 16-bit storage is the increment form, computed by the TMA kernel, factored form
         if (opt.form != kFactored) return fail(FD_ENOTSUP, "16-bit storage needs the factored form");
@@ -1228,8 +1237,9 @@ int fd_forward_two_step(fd_handle *hd, int nt) {
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_two_step before fd_set_model");
     if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->r > 2 || hd->n_rec > 0 ||
-        int(hd->sources.size()) > kFusedSources)
-        return fail(FD_ENOTSUP, "two steps per launch: FP32 factored, space order <= 4, <= %d sources, no receivers",
+        int(hd->sources.size()) > kFusedSources || hd->opt.boundary != FD_BOUNDARY_ZERO)
+        return fail(FD_ENOTSUP,
+                    "two steps per launch: FP32 factored, space order <= 4, <= %d sources, no receivers, zero boundary",
                     kFusedSources);
     if (nt == 0) return FD_OK;
     cudaStream_t st = hd->stream;
@@ -1777,6 +1787,7 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
         return fail(FD_ENOTSUP, "unknown storage/form option");
     if (opt.storage != kF32 && opt.form != kFactored)
         return fail(FD_ENOTSUP, "batches with 16-bit storage use the factored form");
+    if (opt.boundary != FD_BOUNDARY_ZERO) return fail(FD_ENOTSUP, "batches use the zero boundary");
     int tz = opt.tile_z, ty = opt.tile_y;
     if (tz == 0 && ty == 0) {
         tz = kBatchTiles[0][0];

@@ -89,6 +89,15 @@ def test_version_and_error_text(built_lib):
 
 def test_options_default(built_lib):
     o = _abi.fd_options_default()
-    assert (o.storage, o.form, o.kernel, o.tile_z, o.tile_y, o.x_block, o.check_finite) == \
-        (0, 0, 0, 0, 0, 0, 1)
-    assert ctypes.sizeof(o) == 7 * 4
+    assert (o.storage, o.form, o.kernel, o.tile_z, o.tile_y, o.x_block, o.check_finite, o.boundary) == \
+        (0, 0, 0, 0, 0, 0, 1, 0)
+    assert ctypes.sizeof(o) == 8 * 4
+
+
+def test_options_struct_matches_header():
+    """The binding's fd_options has the header's fields, in the header's order."""
+    import re
+    text = open(os.path.join(ROOT, "include", "fd_acoustic.h")).read()
+    body = text[text.index("typedef struct fd_options {"):text.index("} fd_options;")]
+    fields = re.findall(r"^\s*int (\w+);", body, flags=re.M)
+    assert fields == [f for f, _ in _abi.fd_options._fields_]
