@@ -162,10 +162,12 @@ def test_load_state_resume_matches_oracle(oracle_mod):
         shot.close()
 
 
-@pytest.mark.parametrize("k", [2, 8, 16, 24])
-def test_full_size_sweep_parity(oracle_mod, k):
+@pytest.mark.parametrize("form", ["factored", "expanded"])
+@pytest.mark.parametrize("k", [2, 4, 8, 12, 16, 24])
+def test_full_size_sweep_parity(oracle_mod, k, form):
     """The benchmark workload (256^3 + 10-cell layer, 4-layer model) with the
-    autotuned launch shape, 6 steps from a smooth random full-field state."""
+    autotuned launch shape (space order 2, factored: two steps per launch), 6
+    steps from a smooth random full-field state."""
     spec = inputs.sweep_shot(k)
     dt = dt_for(spec)
     eta = eta_for(spec)
@@ -174,9 +176,24 @@ def test_full_size_sweep_parity(oracle_mod, k):
     u1 = (0.98 * u0).astype(np.float32)
     state = (u0, u1, 0)
     want, want_prev = run_oracle(oracle_mod, spec, 6, dt, eta, state=state)
-    got, got_prev, shot = run_gpu(spec, 6, dt, None, state=state)
-    report(f"full276_so{k}_factored_autotuned{shot.config}", rel_l2(got, want),
+    got, got_prev, shot = run_gpu(spec, 6, dt, None, state=state, form=form)
+    report(f"full276_so{k}_{form}_autotuned{shot.config}", rel_l2(got, want),
            rel_l2(got_prev, want_prev))
+    assert rel_l2(got, want) <= TOL
+    assert rel_l2(got_prev, want_prev) <= TOL
+    shot.close()
+
+
+@pytest.mark.parametrize("form", ["factored", "expanded"])
+def test_full_size_sweep_100_steps(oracle_mod, form):
+    """The benchmark shot itself (space order 8: 15 Hz Ricker at (128, 128, 20),
+    zero initial state) for 100 steps, the step count of the FP32 parity bound."""
+    spec = inputs.sweep_shot(8)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    want, want_prev = run_oracle(oracle_mod, spec, 100, dt, eta)
+    got, got_prev, shot = run_gpu(spec, 100, dt, None, form=form)
+    report(f"full276_so8_{form}_100steps{shot.config}", rel_l2(got, want), rel_l2(got_prev, want_prev))
     assert rel_l2(got, want) <= TOL
     assert rel_l2(got_prev, want_prev) <= TOL
     shot.close()
