@@ -240,6 +240,24 @@ int fd_fwi_gradient_checkpointed(fd_handle *hd, int nrec, const double *rec_xyz,
  * conditions hold. */
 int fd_forward_two_step(fd_handle *hd, int nt);
 
+/* As fd_forward with one persistent launch for the nt steps instead of one
+ * launch per step (the flow schedule): work items (step, y-z tile, x-chunk)
+ * are taken in step order by resident CTAs, and an item starts as soon as the
+ * 27 items of the previous step around it are done, so the SMs do not idle in
+ * the tail of each step and between launches. Same per-point arithmetic as
+ * fd_forward with the TMA kernel: the same results bit for bit. FP32 storage,
+ * the TMA kernel (either form), at most 4 sources, no receivers, zero
+ * boundary, x_block >= k/2 (FD_ENOTSUP otherwise). A device-side wait that
+ * gives up (about 2 s) ends the launch and sets FD_ETIMEOUT in the status.
+ * The x-chunk length is the options' x_block if set, else timed on the
+ * first steps of the first call for the grid and launch shape (candidates
+ * 24-64 planes, 8 steps each, as part of the requested steps) and cached
+ * for the process. fd_forward takes this path when the kernel is left to
+ * the library (FD_KERNEL_AUTO), the conditions hold and the two-step path
+ * (space order 2, factored) does not apply.
+ * Asynchronous like fd_forward; fd_last_forward_ms times the launch. */
+int fd_forward_flow(fd_handle *hd, int nt);
+
 /* Copy the traces into HOST memory out[n * nt_max] (r-major; samples not yet
  * recorded are zero) and the number of recorded samples per receiver into
  * *recorded. Synchronises the handle's stream; returns the device status like

@@ -21,7 +21,7 @@ from ._abi import (FD_BOUNDARY_PERIODIC, FD_BOUNDARY_ZERO, FD_EFULL, FD_EINVAL, 
                    FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
-                   fd_forward, fd_forward_two_step, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
+                   fd_forward, fd_forward_flow, fd_forward_two_step, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
                    fd_load_state, fd_read_traces, fd_set_receivers, fd_fwi_gradient,
                    fd_kernel_launches, fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
                    fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
@@ -208,6 +208,10 @@ class Shot:
     def forward_two_step(self, nt):
         """nt steps, two per launch (FP32 factored, space order 2 or 4)."""
         fd_forward_two_step(self.handle, nt)
+
+    def forward_flow(self, nt):
+        """nt steps in one persistent launch (FP32, TMA kernel): same bits as forward."""
+        fd_forward_flow(self.handle, nt)
 
     def inject_at(self, x, y, z, wavelet):
         """Off-grid source at continuous interior coordinates (trilinear spreading)."""

@@ -78,6 +78,7 @@ _SIGNATURES = {
     "fd_fwi_gradient_checkpointed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "fd_forward": (_i, [_vp, _i]),
     "fd_forward_two_step": (_i, [_vp, _i]),
+    "fd_forward_flow": (_i, [_vp, _i]),
     "fd_read_wavefield": (_i, [_vp, _vp, _i]),
     "fd_read_wavefield_device": (_i, [_vp, _vp, _i]),
     "fd_set_stream": (_i, [_vp, _vp]),
@@ -247,6 +248,10 @@ def fd_forward(hd, nt):
 
 def fd_forward_two_step(hd, nt):
     _check(lib().fd_forward_two_step(hd, nt), "fd_forward_two_step")
+
+
+def fd_forward_flow(hd, nt):
+    _check(lib().fd_forward_flow(hd, nt), "fd_forward_flow")
 
 
 def fd_read_wavefield(hd, out: np.ndarray, level: int = 0):

@@ -15,6 +15,7 @@
 
 #include "../../include/fd_acoustic.h"
 #include "fd_internal.h"
+#include "fd_flow.h"
 #include "fd_launch_count.h"
 #include "fd_periodic.h"
 
@@ -52,6 +53,7 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int nt = 0, cur = 0;
     long long launches = 0;  // kernel launches one replay executes
+    bool flow = false;       // the flow schedule (one persistent launch for the nt steps)
     long long step0 = 0;
     unsigned long long gen = 0;
 };
@@ -62,6 +64,8 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 // two-step kernel: (Nx, Ny, Nz, radius) -> x_block
 std::map<std::tuple<int, int, int, int>, int> g_tb_cache;
+// flow schedule: (Nx, Ny, Nz, radius, form, tile_z, tile_y) -> x_block
+std::map<std::tuple<int, int, int, int, int, int, int>, int> g_flow_cache;
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync) from the
 // device's default pool, whose release threshold is raised once per device so
@@ -191,6 +195,11 @@ struct fd_handle {
     // two-step kernel: the pair of output buffers, its x_block and tensor maps by input pair
     void *tb_buf[2] = {nullptr, nullptr};
     int tb_xb = 0;
+    // flow schedule: work counter, abort word and per-item flags; resident CTAs of its kernel
+    void *flow_buf = nullptr;
+    size_t flow_bytes = 0;
+    int flow_ctas = 0;
+    int flow_xb = 0;  // the flow schedule's x_block (0: not chosen yet)
     struct TbMaps {
         const void *u, *up;
         TmaMaps maps;
@@ -661,7 +670,7 @@ void release_handle(fd_handle *hd) {
     cudaStream_t st = hd->stream ? hd->stream : hd->own_stream;
     void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
                     hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack, hd->d_rec_off, hd->d_rec_w,
-                    hd->d_traces, hd->tb_buf[0], hd->tb_buf[1]};
+                    hd->d_traces, hd->tb_buf[0], hd->tb_buf[1], hd->flow_buf};
     for (void *p : bufs) dev_free(p, st);
     if (hd->ev0) cudaEventDestroy(hd->ev0);
     if (hd->ev1) cudaEventDestroy(hd->ev1);
@@ -1354,44 +1363,21 @@ int fd_clear_sources(fd_handle *hd) {
     return rc;
 }
 
-int fd_forward(fd_handle *hd, int nt) {
-    if (!hd) return fail(FD_EINVAL, "handle is NULL");
-    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
-    if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
-    if (nt == 0) return FD_OK;
-    // automatic kernel choice, space order 2: two steps per launch where the single-step
-    // kernel is bound by HBM traffic (measured 1.15x at 276^3; at space order 4 the
-    // overlap of the extended tiles costs more than the traffic saved). Same bits.
-    if (nt >= 2 && hd->opt.kernel == kAuto && hd->kernel == kTma && hd->r == 1 && hd->opt.storage == kF32 &&
-        hd->opt.form == kFactored && hd->n_rec == 0 && int(hd->sources.size()) <= kFusedSources)
-        return fd_forward_two_step(hd, nt);
-    if (hd->kernel != kNaive && (hd->tile_y == 0 || hd->x_block == 0)) {
-        int rc = autotune(hd);
-        if (rc == FD_OK) rc = build_maps(hd);
-        if (rc != FD_OK) {
-            hd->tile_y = hd->x_block = 0;
-            return rc;
-        }
-        hd->gen++;
-    }
+// Replays the handle's CUDA graph of nt steps from its current state
+// (recording it first, or updating it when only the step changed); `record`
+// enqueues the steps on the capturing stream. Timed by the handle's events;
+// advances the step counter and the buffer parity.
+extern "C++" {
+template <typename F>
+int replay_graph(fd_handle *hd, int nt, bool flow, F &&record) {
     GraphEntry *entry = nullptr;
     for (auto &g : hd->graphs)
-        if (g.nt == nt && g.cur == hd->cur && g.gen == hd->gen) entry = &g;
+        if (g.nt == nt && g.cur == hd->cur && g.gen == hd->gen && g.flow == flow) entry = &g;
     if (!entry || entry->step0 != hd->step) {
         cudaGraph_t graph = nullptr;
         FD_CUDA(cudaStreamBeginCapture(hd->stream, cudaStreamCaptureModeThreadLocal));
         const long long captured0 = captured_launches();
-        int cur = hd->cur;
-        cudaError_t err = cudaSuccess;
-        for (int i = 0; i < nt && err == cudaSuccess; ++i) {
-            const StepArgs a = make_args(hd, hd->step + i, cur);
-            err = enqueue_step(hd, a, hd->stream);
-            cur ^= 1;
-        }
-        // the TMA kernel samples its input level: the last level of this forward is
-        // sampled here (the next forward's first step samples it again, same values)
-        if (err == cudaSuccess && hd->n_rec > 0 && hd->kernel == kTma)
-            err = sample_level(hd, hd->ubuf[cur], hd->step + nt, hd->stream);
+        cudaError_t err = record(hd->stream);
         cudaError_t cap = cudaStreamEndCapture(hd->stream, &graph);
         if (err != cudaSuccess || cap != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -1430,6 +1416,7 @@ int fd_forward(fd_handle *hd, int nt) {
         cudaGraphDestroy(graph);
         entry->launches = captured_launches() - captured0;
         entry->nt = nt;
+        entry->flow = flow;
         entry->cur = hd->cur;
         entry->gen = hd->gen;
         entry->step0 = hd->step;
@@ -1442,6 +1429,192 @@ int fd_forward(fd_handle *hd, int nt) {
     hd->step += nt;
     hd->cur ^= (nt & 1);
     return FD_OK;
+}
+}  // extern "C++"
+
+int fd_forward(fd_handle *hd, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
+    if (nt == 0) return FD_OK;
+    // automatic kernel choice, space order 2: two steps per launch where the single-step
+    // kernel is bound by HBM traffic (measured 1.15x at 276^3; at space order 4 the
+    // overlap of the extended tiles costs more than the traffic saved). Same bits.
+    if (nt >= 2 && hd->opt.kernel == kAuto && hd->kernel == kTma && hd->r == 1 && hd->opt.storage == kF32 &&
+        hd->opt.form == kFactored && hd->n_rec == 0 && int(hd->sources.size()) <= kFusedSources)
+        return fd_forward_two_step(hd, nt);
+    // automatic kernel choice, FP32 otherwise: the flow schedule (one persistent launch,
+    // no per-step tail or launch gap; measured 1.02-1.10x over per-step launches at
+    // 276^3 for every space order and form). Same bits.
+    if (hd->opt.kernel == kAuto && hd->kernel == kTma && hd->opt.storage == kF32 && hd->n_rec == 0 &&
+        int(hd->sources.size()) <= kFusedSources && hd->opt.boundary == FD_BOUNDARY_ZERO &&
+        (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r))
+        return fd_forward_flow(hd, nt);
+    if (hd->kernel != kNaive && (hd->tile_y == 0 || hd->x_block == 0)) {
+        int rc = autotune(hd);
+        if (rc == FD_OK) rc = build_maps(hd);
+        if (rc != FD_OK) {
+            hd->tile_y = hd->x_block = 0;
+            return rc;
+        }
+        hd->gen++;
+    }
+    return replay_graph(hd, nt, false, [&](cudaStream_t st) {
+        int cur = hd->cur;
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < nt && err == cudaSuccess; ++i) {
+            const StepArgs a = make_args(hd, hd->step + i, cur);
+            err = enqueue_step(hd, a, st);
+            cur ^= 1;
+        }
+        // the TMA kernel samples its input level: the last level of this forward is
+        // sampled here (the next forward's first step samples it again, same values)
+        if (err == cudaSuccess && hd->n_rec > 0 && hd->kernel == kTma)
+            err = sample_level(hd, hd->ubuf[cur], hd->step + nt, st);
+        return err;
+    });
+}
+
+// Flow launch arguments for nt steps from the handle's state with x-chunks of
+// xb planes; *bytes: the zeroed prefix of the flow buffer (counter, abort, flags).
+int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *bytes, int *ctas) {
+    const int nbz = (hd->Nz + hd->tile_z - 1) / hd->tile_z, nby = (hd->Ny + hd->tile_y - 1) / hd->tile_y;
+    const int nbx = (hd->Nx + xb - 1) / xb;
+    const long long per_step = (long long)nbz * nby * nbx;
+    // the work counter (an int) also counts one extra claim per CTA
+    if (per_step * nt > INT32_MAX / 2) return fail(FD_EINVAL, "nt too large for one flow launch");
+    *bytes = 16 + size_t(per_step) * sizeof(unsigned);
+    if (hd->flow_bytes < *bytes) {
+        dev_free(hd->flow_buf, hd->stream);
+        hd->flow_buf = nullptr;
+        hd->flow_bytes = 0;
+        if (dev_alloc(&hd->flow_buf, *bytes, hd->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FD_ENOMEM, "cannot allocate the flow schedule's flags");
+        }
+        hd->flow_bytes = *bytes;
+        hd->gen++;  // graphs recorded with the old buffer
+    }
+    if (hd->flow_ctas == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
+        if (per_sm <= 0 || sms <= 0) return fail(FD_ENOTSUP, "no flow kernel for this launch shape");
+        hd->flow_ctas = per_sm * sms;
+    }
+    f->maps[0] = hd->tmaps[0];
+    f->maps[1] = hd->tmaps[1];
+    f->a[0] = make_args(hd, hd->step, 0);
+    f->a[1] = make_args(hd, hd->step, 1);
+    f->a[0].x_block = f->a[1].x_block = xb;
+    f->step0 = hd->step;
+    f->nt = nt;
+    f->cur0 = hd->cur;
+    f->nbz = nbz;
+    f->nby = nby;
+    f->nbx = nbx;
+    unsigned char *fb = static_cast<unsigned char *>(hd->flow_buf);
+    f->counter = reinterpret_cast<int *>(fb);
+    f->abort = reinterpret_cast<unsigned *>(fb + 4);
+    f->flags = reinterpret_cast<unsigned *>(fb + 16);
+    *ctas = int(std::min<long long>(hd->flow_ctas, per_step * nt));
+    return FD_OK;
+}
+
+// One flow launch outside a graph (x_block tuning), timed by the handle's events.
+int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
+    FlowArgs f;
+    size_t bytes = 0;
+    int ctas = 0;
+    int rc = make_flow_args(hd, nt, xb, &f, &bytes, &ctas);
+    if (rc != FD_OK) return rc;
+    FD_CUDA(cudaEventRecord(hd->ev0, hd->stream));
+    FD_CUDA(cudaMemsetAsync(hd->flow_buf, 0, bytes, hd->stream));
+    FD_CUDA(launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check_enabled(hd), hd->stream));
+    FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
+    FD_CUDA(cudaEventSynchronize(hd->ev1));
+    FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
+    hd->step += nt;
+    hd->cur ^= (nt & 1);
+    return FD_OK;
+}
+
+int fd_forward_flow(fd_handle *hd, int nt) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_flow before fd_set_model");
+    if (hd->opt.storage != kF32 || hd->kernel != kTma || hd->n_rec > 0 ||
+        int(hd->sources.size()) > kFusedSources || hd->opt.boundary != FD_BOUNDARY_ZERO)
+        return fail(FD_ENOTSUP, "the flow schedule: FP32 storage, TMA kernel, <= %d sources, no receivers, zero boundary",
+                    kFusedSources);
+    if (nt == 0) return FD_OK;
+    if (hd->tile_y == 0 || hd->x_block == 0) {
+        int rc = autotune(hd);
+        if (rc == FD_OK) rc = build_maps(hd);
+        if (rc != FD_OK) {
+            hd->tile_y = hd->x_block = 0;
+            return rc;
+        }
+        hd->gen++;
+        hd->flow_ctas = 0;
+        hd->flow_xb = 0;
+    }
+    // an item reads the queue planes and fronts of its x-neighbours only
+    int xb = hd->flow_xb;
+    if (xb == 0 && hd->opt.x_block > 0) xb = hd->opt.x_block;  // forced by the options
+    const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
+    if (xb == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_flow_cache.find(key);
+        if (it != g_flow_cache.end()) xb = it->second;
+    }
+    if (xb == 0) {
+        // x_block by timing candidates on the first steps of this call (any x_block gives
+        // the same bits): shorter chunks balance better, longer ones claim fewer items
+        constexpr int kTuneSteps = 8;
+        const int cand[] = {24, 32, 40, 48, 56, 64};
+        int n_cand = 0;
+        for (int c : cand) n_cand += (c >= hd->r && c <= hd->Nx);
+        if (nt >= kTuneSteps * (n_cand + 1) && n_cand > 0) {
+            float best = 1e30f, ms = 0.0f;
+            int best_xb = 0;
+            int rc = flow_direct(hd, kTuneSteps, std::max(40, hd->r), &ms);  // warm-up
+            for (int c : cand) {
+                if (rc != FD_OK) break;
+                if (c < hd->r || c > hd->Nx) continue;
+                rc = flow_direct(hd, kTuneSteps, c, &ms);
+                if (rc == FD_OK && ms < best) {
+                    best = ms;
+                    best_xb = c;
+                }
+            }
+            if (rc != FD_OK) return rc;
+            nt -= kTuneSteps * (n_cand + 1);
+            xb = best_xb;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_flow_cache[key] = xb;
+        } else {
+            xb = std::min(hd->Nx, std::max(40, hd->r));  // too few steps to time: the usual best
+        }
+    }
+    if (xb < hd->r) return fail(FD_ENOTSUP, "the flow schedule needs x_block >= k/2");
+    if (xb != hd->flow_xb) {
+        hd->flow_xb = xb;
+        hd->gen++;
+    }
+    if (nt == 0) return FD_OK;
+    FlowArgs f;
+    size_t bytes = 0;
+    int ctas = 0;
+    int rc = make_flow_args(hd, nt, xb, &f, &bytes, &ctas);
+    if (rc != FD_OK) return rc;
+    const bool check = check_enabled(hd);
+    return replay_graph(hd, nt, true, [&](cudaStream_t st) {
+        cudaError_t e = cudaMemsetAsync(hd->flow_buf, 0, bytes, st);
+        if (e == cudaSuccess) e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check, st);
+        return e;
+    });
 }
 
 int fd_read_wavefield(fd_handle *hd, float *out, int level) {

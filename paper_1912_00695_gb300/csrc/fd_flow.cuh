@@ -1,0 +1,187 @@
+// Flow schedule: one persistent launch advances nt time steps of a shot with
+// the single-step kernel's per-point arithmetic and ring (tma_segment), with
+// no grid-wide barrier between steps. Work items (step s, x-chunk bx, tile
+// by, tile bz), numbered step-major with z fastest, are claimed from a global
+// counter. An item of step s > 0 first waits until the 27 items of step s - 1
+// around it (x-chunks bx-1..bx+1, tiles by-1..by+1 and bz-1..bz+1) are done:
+// they wrote the u^s it reads (halo rows, queue planes, front planes) and they
+// were the last readers of the u^{s-1} it overwrites. Every dependency has a
+// lower item number, so it was claimed earlier by a running CTA: the waits
+// always end (and are bounded all the same). A launch of the per-step
+// schedule ends with a tail in which SMs idle while the last CTAs finish, and
+// the next launch starts after a gap; here the next step's items fill them.
+//
+// Memory ordering: the producer's threads store u^{s+1}, the CTA barrier
+// orders those stores before thread 0's release store of the item's flag;
+// a consumer's thread 0 acquires the flags, orders the copy engine's reads
+// after them (proxy fence) and the CTA barrier orders the other threads'
+// loads; the queue prologue reads u^s with L1-bypassing loads, since the
+// same buffer held older levels earlier in the launch.
+#pragma once
+
+#include "fd_flow.h"
+#include "fd_tma.cuh"
+
+namespace fdgb {
+
+constexpr long long kFlowWaitLimit = 1LL << 24;  // polls of one flag (about 2 s with the back-off)
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until *flag >= need; false if the wait gave up or the launch aborted.
+__device__ __forceinline__ bool flow_wait(const unsigned *flag, unsigned need, const unsigned *abort) {
+    for (long long i = 0; i < kFlowWaitLimit; ++i) {
+        if (ld_acquire_u32(flag) >= need) return true;
+        if (*reinterpret_cast<const volatile unsigned *>(abort)) return false;
+        if (i >= 4) __nanosleep(100);
+    }
+    return false;
+}
+
+template <int R, int FORM, int LZ, int W>
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1))
+    fd_tma_flow_kernel(const __grid_constant__ FlowArgs f, int check) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // item slots: the item of iteration i sits in s_item[i & 1]; thread 0 claims the
+    // next one while the current one runs (claims stay in increasing order per CTA,
+    // so the lowest unfinished item is always being worked on)
+    __shared__ int s_item[2];
+    __shared__ int s_fail;
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);
+    const ScaleState sc = read_scales<float>(f.a[0]);
+    const int per_plane = f.nbz * f.nby;
+    const int per_step = per_plane * f.nbx;
+    const int total = per_step * f.nt;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(f.counter, 1);
+    int g = 0;
+    TmaAcc acc;
+    bool ok_all = true;
+    for (int iter = 0;; ++iter) {
+        __syncthreads();  // s_item[iter & 1] is set; every thread is done with the previous item
+        const int item = s_item[iter & 1];
+        if (item >= total) break;
+        if (threadIdx.x == 0) s_item[(iter + 1) & 1] = atomicAdd(f.counter, 1);
+        const int s = item / per_step, rem = item - s * per_step;
+        const int bx = rem / per_plane, r2 = rem - bx * per_plane;
+        const int by = r2 / f.nbz, bz = r2 - by * f.nbz;
+        const int p = (f.cur0 + s) & 1;
+        const StepArgs &a = f.a[p];  // parameter space
+        if (threadIdx.x < 32) {
+            // lane l < 27 checks neighbour (l / 9 - 1, (l / 3) % 3 - 1, l % 3 - 1) of step s - 1
+            bool ok = true;
+            const int l = threadIdx.x;
+            if (s > 0 && l < 27) {
+                const int nx = bx + l / 9 - 1, ny = by + (l / 3) % 3 - 1, nz = bz + l % 3 - 1;
+                if (nx >= 0 && nx < f.nbx && ny >= 0 && ny < f.nby && nz >= 0 && nz < f.nbz)
+                    ok = flow_wait(&f.flags[nx * per_plane + ny * f.nbz + nz], unsigned(s), f.abort);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (l == 0) {
+                // the copy engine reads what the acquired flags published
+                if (s > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+                s_fail = ok ? 0 : 1;
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            ok_all = false;
+            break;
+        }
+        const int xb = bx * a.x_block;
+        if (!tma_segment<R, FORM, LZ, W, float, kModeStep, true>(&f.maps[p], a, sc, bz, by, xb,
+                                                                 min(xb + a.x_block, a.Nx), ring, g, acc, nullptr,
+                                                                 f.step0 + s)) {
+            ok_all = false;  // a ring wait gave up (status set); the ring's phases are no longer known
+            break;
+        }
+        __syncthreads();  // the item's stores precede the flag
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_u32(&f.flags[rem], unsigned(s + 1));
+        }
+    }
+    if (!ok_all) {
+        if (threadIdx.x == 0) {
+            if (f.a[0].status) atomicOr(f.a[0].status, kStatusTimeout);
+            atomicExch(f.abort, 1u);  // the other CTAs stop waiting and leave
+        }
+        return;
+    }
+    if (check) reduce_amax(f.a[0], acc.amax_bits, acc.over, acc.damax_bits);
+}
+
+template <int R, int FORM, int LZ, int W>
+cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W, float>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kernel<<<ctas, 32 * W, G::SMEM_BYTES, s>>>(f, check ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int R, int FORM, int LZ, int W>
+int tma_flow_occupancy() {
+    using G = TmaShape<R, LZ, W, float>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 32 * W, G::SMEM_BYTES) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int R>
+cudaError_t tma_flow_r(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
+#define FDGB_FLOW_CASE(LZ, W)                                                                   \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
+        return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W>(f, ctas, check, s)      \
+                                 : tma_flow_launch<R, kExpanded, LZ, W>(f, ctas, check, s);
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS(FDGB_FLOW_CASE)
+    } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_CASE)
+    }
+#undef FDGB_FLOW_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int R>
+int tma_flow_occ_r(int form, int tile_z, int tile_y) {
+#define FDGB_FLOW_OCC(LZ, W)                                                                    \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
+        return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W>()                    \
+                                 : tma_flow_occupancy<R, kExpanded, LZ, W>();
+    if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS(FDGB_FLOW_OCC)
+    } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_OCC)
+    }
+#undef FDGB_FLOW_OCC
+    return 0;
+}
+
+}  // namespace fdgb
+
+#define FDGB_INSTANTIATE_FLOW_RADIUS(R)                                                           \
+    namespace fdgb {                                                                              \
+    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, \
+                                    bool check, cudaStream_t s) {                                 \
+        return tma_flow_r<R>(form, tile_z, tile_y, f, ctas, check, s);                            \
+    }                                                                                             \
+    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y) {                               \
+        return tma_flow_occ_r<R>(form, tile_z, tile_y);                                           \
+    }                                                                                             \
+    }

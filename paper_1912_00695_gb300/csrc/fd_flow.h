@@ -1,0 +1,32 @@
+// Flow schedule of the single-step TMA kernel (see fd_flow.cuh): the
+// arguments of one persistent launch that advances nt time steps.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fd_internal.h"
+
+namespace fdgb {
+
+struct FlowArgs {
+    TmaMaps maps[2];    // maps of a step whose u^n is buffer 0 / buffer 1
+    StepArgs a[2];      // step arguments with u^n in buffer 0 / buffer 1 (step field unused)
+    long long step0;    // global index of the first step
+    int nt;             // steps of this launch
+    int cur0;           // buffer holding u^{step0}
+    int nbz, nby, nbx;  // tiles along z, y and x-chunks: work items per step = nbz nby nbx
+    // zeroed before the launch: the work counter, the abort word, then one flag
+    // per (tile, x-chunk) = the number of this launch's steps it has completed
+    int *counter;
+    unsigned *abort;
+    unsigned *flags;
+};
+
+// One persistent launch of the flow kernel for radius/form/tile; `ctas` is the
+// number of CTAs (at most the resident count). cudaErrorInvalidValue for a
+// configuration without a flow kernel.
+cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check,
+                            cudaStream_t s);
+// Resident CTAs per SM of that kernel (0 if the configuration does not exist).
+int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y);
+
+}  // namespace fdgb

@@ -1,7 +1,9 @@
 // Step kernels for stencil radius 1 (space order 2).
 #include "fd_stencil.cuh"
 #include "fd_tma.cuh"
+#include "fd_flow.cuh"
 #include "fd_tma2.cuh"
 FDGB_INSTANTIATE_RADIUS(1)
 FDGB_INSTANTIATE_TMA_RADIUS(1)
 FDGB_INSTANTIATE_TMA2_RADIUS(1)
+FDGB_INSTANTIATE_FLOW_RADIUS(1)

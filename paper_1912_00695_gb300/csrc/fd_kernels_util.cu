@@ -7,6 +7,7 @@
 #include <atomic>
 
 #include "fd_internal.h"
+#include "fd_flow.h"
 #include "fd_launch_count.h"
 
 namespace fdgb {
@@ -211,6 +212,54 @@ static cudaError_t launch_tma2_step_dispatch(int radius, const TmaMaps &map, con
 cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, float *out1, float *out2, bool check,
                              cudaStream_t s) {
     return counted(launch_tma2_step_dispatch(radius, map, a, out1, out2, check, s), s);
+}
+
+#define FDGB_DECLARE_FLOW_RADIUS(R)                                                              \
+    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, \
+                                    bool check, cudaStream_t s);                                  \
+    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y);
+FDGB_DECLARE_FLOW_RADIUS(1)
+FDGB_DECLARE_FLOW_RADIUS(2)
+FDGB_DECLARE_FLOW_RADIUS(3)
+FDGB_DECLARE_FLOW_RADIUS(4)
+FDGB_DECLARE_FLOW_RADIUS(5)
+FDGB_DECLARE_FLOW_RADIUS(6)
+FDGB_DECLARE_FLOW_RADIUS(7)
+FDGB_DECLARE_FLOW_RADIUS(8)
+FDGB_DECLARE_FLOW_RADIUS(9)
+FDGB_DECLARE_FLOW_RADIUS(10)
+FDGB_DECLARE_FLOW_RADIUS(11)
+FDGB_DECLARE_FLOW_RADIUS(12)
+#undef FDGB_DECLARE_FLOW_RADIUS
+
+static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas,
+                                            bool check, cudaStream_t s) {
+    switch (radius) {
+#define FDGB_FLOW_R(R) \
+        case R: return tma_flow_radius_##R(form, tile_z, tile_y, f, ctas, check, s);
+        FDGB_FLOW_R(1) FDGB_FLOW_R(2) FDGB_FLOW_R(3) FDGB_FLOW_R(4)
+        FDGB_FLOW_R(5) FDGB_FLOW_R(6) FDGB_FLOW_R(7) FDGB_FLOW_R(8)
+        FDGB_FLOW_R(9) FDGB_FLOW_R(10) FDGB_FLOW_R(11) FDGB_FLOW_R(12)
+#undef FDGB_FLOW_R
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check,
+                            cudaStream_t s) {
+    return counted(launch_tma_flow_dispatch(radius, form, tile_z, tile_y, f, ctas, check, s), s);
+}
+
+int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y) {
+    switch (radius) {
+#define FDGB_FLOW_O(R) \
+        case R: return tma_flow_occ_radius_##R(form, tile_z, tile_y);
+        FDGB_FLOW_O(1) FDGB_FLOW_O(2) FDGB_FLOW_O(3) FDGB_FLOW_O(4)
+        FDGB_FLOW_O(5) FDGB_FLOW_O(6) FDGB_FLOW_O(7) FDGB_FLOW_O(8)
+        FDGB_FLOW_O(9) FDGB_FLOW_O(10) FDGB_FLOW_O(11) FDGB_FLOW_O(12)
+#undef FDGB_FLOW_O
+        default: return 0;
+    }
 }
 
 bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez, int *ey) {

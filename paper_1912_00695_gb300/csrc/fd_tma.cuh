@@ -122,6 +122,8 @@ template <typename T> struct Vec4;
 template <> struct Vec4<float> {
     static constexpr CUtensorMapDataType kMapType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     static __device__ __forceinline__ float4 ldg(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    // cached in L2 only: data other CTAs of the same launch may have written
+    static __device__ __forceinline__ float4 ldcg(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
     static __device__ __forceinline__ float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
     static __device__ __forceinline__ void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 };
@@ -231,10 +233,14 @@ __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw)
 // already streamed through its ring (it selects the stage and the mbarrier
 // phase, so consecutive segments share one ring without re-initialising it).
 // Returns false if a wait gave up (status set, copies in flight drained).
-template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep>
+// COHERENT: u^n may have been written earlier in the same launch (the flow
+// schedule), so the queue prologue reads it through L2 instead of the
+// read-only path. step >= 0 replaces a.step (the flow schedule's steps share
+// one argument block).
+template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep, bool COHERENT = false>
 __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs &a, const ScaleState &sc, int bz,
                                             int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc,
-                                            const GradMaps *gm = nullptr) {
+                                            const GradMaps *gm = nullptr, long long step = -1) {
     using G = TmaShape<R, LZ, W, T, MODE == kModeAdjointGrad ? 2 : 0>;
     using V = Vec4<T>;
     constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
@@ -312,7 +318,14 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     }
 
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto load_u = [&](int x) -> float4 { return (own && x >= 0 && x < a.Nx) ? V::ldg(u + x * P) : zero4; };
+    auto load_u = [&](int x) -> float4 {
+        if (!(own && x >= 0 && x < a.Nx)) return zero4;
+        if constexpr (COHERENT) {
+            return V::ldcg(u + x * P);
+        } else {
+            return V::ldg(u + x * P);
+        }
+    };
     float4 q[Q];
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
@@ -476,7 +489,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
 #pragma unroll
                     for (int s = 0; s < kFusedSources; ++s) {
                         if (((src_mask >> s) & 1u) && a.sx[s] == x) {
-                            const float qv = source_value(a, s);
+                            const float qv = step < 0 ? source_value(a, s)
+                                                      : step < a.ld ? __ldg(a.wavelet + (long long)s * a.ld + step)
+                                                                    : 0.0f;
                             const int p = src_p[s];
                             if (p == 0) out.x = fmaf(sw[0], qv, out.x);
                             if (p == 1) out.y = fmaf(sw[1], qv, out.y);

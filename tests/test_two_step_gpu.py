@@ -104,8 +104,30 @@ def test_two_step_launch_count_and_timing():
 
 
 def test_single_step_launch_count():
-    """One launch per step through the replayed graph, one more per step with
-    more sources than the step kernel fuses (the extra-source kernel)."""
+    """Per-step schedule: one launch per step through the replayed graph, one
+    more per step with more sources than the step kernel fuses (the
+    extra-source kernel)."""
+    spec = _spec(8, seed=8)
+    dt = dt_for(spec)
+    with fd.Shot(spec.interior, 8, H, dt, spec.nbl, kernel="tma") as shot:
+        shot.set_model(spec.m)
+        shot.inject(10, 10, 10, inputs.ricker(20.0, dt, 40))
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 6
+        for i in range(4):
+            shot.inject(12 + i, 10, 10, inputs.ricker(20.0, dt, 40))
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 12
+
+
+def test_flow_launch_count():
+    """Automatic kernel choice at space order 8: one flow launch per call; with
+    more sources than the kernel fuses, back to one launch per step plus the
+    extra-source kernel."""
     spec = _spec(8, seed=8)
     dt = dt_for(spec)
     with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
@@ -114,7 +136,7 @@ def test_single_step_launch_count():
         shot.forward(6)
         n0 = fd.fd_kernel_launches()
         shot.forward(6)
-        assert fd.fd_kernel_launches() - n0 == 6
+        assert fd.fd_kernel_launches() - n0 == 1
         for i in range(4):
             shot.inject(12 + i, 10, 10, inputs.ricker(20.0, dt, 40))
         shot.forward(6)
