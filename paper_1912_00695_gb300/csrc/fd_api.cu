@@ -64,8 +64,8 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 // two-step kernel: (Nx, Ny, Nz, radius) -> x_block
 std::map<std::tuple<int, int, int, int>, int> g_tb_cache;
-// flow schedule: (Nx, Ny, Nz, radius, form, tile_z, tile_y) -> x_block
-std::map<std::tuple<int, int, int, int, int, int, int>, int> g_flow_cache;
+// flow schedule: (Nx, Ny, Nz, radius, form, tile_z, tile_y) -> (x_block, faster than per-step launches)
+std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, bool>> g_flow_cache;
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync) from the
 // device's default pool, whose release threshold is raised once per device so
@@ -199,7 +199,8 @@ struct fd_handle {
     void *flow_buf = nullptr;
     size_t flow_bytes = 0;
     int flow_ctas = 0;
-    int flow_xb = 0;  // the flow schedule's x_block (0: not chosen yet)
+    int flow_xb = 0;         // the flow schedule's x_block (0: not chosen yet)
+    bool flow_wins = true;   // the flow beat per-step launches when the two were timed
     struct TbMaps {
         const void *u, *up;
         TmaMaps maps;
@@ -1432,6 +1433,12 @@ int replay_graph(fd_handle *hd, int nt, bool flow, F &&record) {
 }
 }  // extern "C++"
 
+static int ensure_step_tuned(fd_handle *hd);
+static int run_steps(fd_handle *hd, int nt);
+static int run_flow(fd_handle *hd, int nt);
+static bool flow_eligible(const fd_handle *hd);
+static int flow_prepare(fd_handle *hd, int *nt);
+
 int fd_forward(fd_handle *hd, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
@@ -1445,39 +1452,21 @@ int fd_forward(fd_handle *hd, int nt) {
         return fd_forward_two_step(hd, nt);
     // automatic kernel choice, FP32 otherwise: the flow schedule (one persistent launch,
     // no per-step tail or launch gap; measured 1.02-1.10x over per-step launches at
-    // 276^3 for every space order and form). Same bits.
-    if (hd->opt.kernel == kAuto && hd->kernel == kTma && hd->opt.storage == kF32 && hd->n_rec == 0 &&
-        int(hd->sources.size()) <= kFusedSources && hd->opt.boundary == FD_BOUNDARY_ZERO &&
-        (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r))
-        return fd_forward_flow(hd, nt);
-    if (hd->kernel != kNaive && (hd->tile_y == 0 || hd->x_block == 0)) {
-        int rc = autotune(hd);
-        if (rc == FD_OK) rc = build_maps(hd);
-        if (rc != FD_OK) {
-            hd->tile_y = hd->x_block = 0;
-            return rc;
-        }
-        hd->gen++;
+    // 276^3 for every space order and form) where it was timed faster than the per-step
+    // launches for this grid. Same bits either way.
+    if (hd->opt.kernel == kAuto && flow_eligible(hd)) {
+        int rc = flow_prepare(hd, &nt);
+        if (rc != FD_OK || nt == 0) return rc;
+        return hd->flow_wins ? run_flow(hd, nt) : run_steps(hd, nt);
     }
-    return replay_graph(hd, nt, false, [&](cudaStream_t st) {
-        int cur = hd->cur;
-        cudaError_t err = cudaSuccess;
-        for (int i = 0; i < nt && err == cudaSuccess; ++i) {
-            const StepArgs a = make_args(hd, hd->step + i, cur);
-            err = enqueue_step(hd, a, st);
-            cur ^= 1;
-        }
-        // the TMA kernel samples its input level: the last level of this forward is
-        // sampled here (the next forward's first step samples it again, same values)
-        if (err == cudaSuccess && hd->n_rec > 0 && hd->kernel == kTma)
-            err = sample_level(hd, hd->ubuf[cur], hd->step + nt, st);
-        return err;
-    });
+    int rc = ensure_step_tuned(hd);
+    if (rc != FD_OK) return rc;
+    return run_steps(hd, nt);
 }
 
 // Flow launch arguments for nt steps from the handle's state with x-chunks of
 // xb planes; *bytes: the zeroed prefix of the flow buffer (counter, abort, flags).
-int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *bytes, int *ctas) {
+static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *bytes, int *ctas) {
     const int nbz = (hd->Nz + hd->tile_z - 1) / hd->tile_z, nby = (hd->Ny + hd->tile_y - 1) / hd->tile_y;
     const int nbx = (hd->Nx + xb - 1) / xb;
     const long long per_step = (long long)nbz * nby * nbx;
@@ -1523,7 +1512,7 @@ int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *bytes, in
 }
 
 // One flow launch outside a graph (x_block tuning), timed by the handle's events.
-int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
+static int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
     FlowArgs f;
     size_t bytes = 0;
     int ctas = 0;
@@ -1540,6 +1529,138 @@ int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
     return FD_OK;
 }
 
+// Launch shape and x_block of the single-step kernel, tuned on first use.
+static int ensure_step_tuned(fd_handle *hd) {
+    if (hd->kernel == kNaive || (hd->tile_y != 0 && hd->x_block != 0)) return FD_OK;
+    int rc = autotune(hd);
+    if (rc == FD_OK) rc = build_maps(hd);
+    if (rc != FD_OK) {
+        hd->tile_y = hd->x_block = 0;
+        return rc;
+    }
+    hd->gen++;
+    hd->flow_ctas = 0;
+    hd->flow_xb = 0;
+    return FD_OK;
+}
+
+// nt steps of the single-step kernel, one launch per step, from the handle's graph.
+static int run_steps(fd_handle *hd, int nt) {
+    return replay_graph(hd, nt, false, [&](cudaStream_t st) {
+        int cur = hd->cur;
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < nt && err == cudaSuccess; ++i) {
+            const StepArgs a = make_args(hd, hd->step + i, cur);
+            err = enqueue_step(hd, a, st);
+            cur ^= 1;
+        }
+        // the TMA kernel samples its input level: the last level of this forward is
+        // sampled here (the next forward's first step samples it again, same values)
+        if (err == cudaSuccess && hd->n_rec > 0 && hd->kernel == kTma)
+            err = sample_level(hd, hd->ubuf[cur], hd->step + nt, st);
+        return err;
+    });
+}
+
+// nt steps in one flow launch with the handle's flow x_block, from its graph.
+static int run_flow(fd_handle *hd, int nt) {
+    FlowArgs f;
+    size_t bytes = 0;
+    int ctas = 0;
+    int rc = make_flow_args(hd, nt, hd->flow_xb, &f, &bytes, &ctas);
+    if (rc != FD_OK) return rc;
+    const bool check = check_enabled(hd);
+    return replay_graph(hd, nt, true, [&](cudaStream_t st) {
+        cudaError_t e = cudaMemsetAsync(hd->flow_buf, 0, bytes, st);
+        if (e == cudaSuccess) e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check, st);
+        return e;
+    });
+}
+
+// nt per-step launches outside a graph (schedule tuning), timed by the handle's events.
+static int steps_direct(fd_handle *hd, int nt, float *ms) {
+    FD_CUDA(cudaEventRecord(hd->ev0, hd->stream));
+    int cur = hd->cur;
+    for (int i = 0; i < nt; ++i) {
+        FD_CUDA(enqueue_step(hd, make_args(hd, hd->step + i, cur), hd->stream));
+        cur ^= 1;
+    }
+    FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
+    FD_CUDA(cudaEventSynchronize(hd->ev1));
+    FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
+    hd->step += nt;
+    hd->cur ^= (nt & 1);
+    return FD_OK;
+}
+
+static bool flow_eligible(const fd_handle *hd) {
+    return hd->opt.storage == kF32 && hd->kernel == kTma && hd->n_rec == 0 &&
+           int(hd->sources.size()) <= kFusedSources && hd->opt.boundary == FD_BOUNDARY_ZERO &&
+           (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r);
+}
+
+// Chooses the flow schedule's x_block and whether it beats per-step launches,
+// timing the candidates on the first steps of this call (*nt is reduced by the
+// steps they ran; every candidate computes the same bits). Cached per grid and
+// launch shape for the process.
+static int flow_prepare(fd_handle *hd, int *nt) {
+    int rc = ensure_step_tuned(hd);
+    if (rc != FD_OK) return rc;
+    if (hd->flow_xb != 0) return FD_OK;
+    if (hd->opt.x_block > 0) {  // forced by the options
+        hd->flow_xb = hd->opt.x_block;
+        hd->flow_wins = true;
+        hd->gen++;
+        return FD_OK;
+    }
+    const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_flow_cache.find(key);
+        if (it != g_flow_cache.end()) {
+            hd->flow_xb = it->second.first;
+            hd->flow_wins = it->second.second;
+            hd->gen++;
+            return FD_OK;
+        }
+    }
+    // shorter x-chunks balance better and keep more items in flight on small grids,
+    // longer ones claim fewer items and re-read fewer queue planes
+    constexpr int kTuneSteps = 8;
+    std::vector<int> cand;
+    for (int c : {8, 12, 16, 24, 32, 40, 48, 56, 64})
+        if (c >= hd->r && c <= hd->Nx) cand.push_back(c);
+    if (cand.empty()) cand.push_back(std::max(hd->r, 1));
+    const int needed = kTuneSteps * (int(cand.size()) + 2);
+    if (*nt < needed) {
+        // too few steps to time: the usual best, not cached
+        hd->flow_xb = std::min(hd->Nx, std::max(40, hd->r));
+        hd->flow_wins = true;
+        hd->gen++;
+        return FD_OK;
+    }
+    float ms = 0.0f, best = 1e30f, step_ms = 0.0f;
+    int best_xb = cand[0];
+    rc = flow_direct(hd, kTuneSteps, cand[cand.size() / 2], &ms);  // warm-up
+    for (int c : cand) {
+        if (rc != FD_OK) break;
+        rc = flow_direct(hd, kTuneSteps, c, &ms);
+        if (rc == FD_OK && ms < best) {
+            best = ms;
+            best_xb = c;
+        }
+    }
+    if (rc == FD_OK) rc = steps_direct(hd, kTuneSteps, &step_ms);
+    if (rc != FD_OK) return rc;
+    *nt -= needed;
+    hd->flow_xb = best_xb;
+    hd->flow_wins = best <= step_ms;
+    hd->gen++;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_flow_cache[key] = std::make_pair(hd->flow_xb, hd->flow_wins);
+    return FD_OK;
+}
+
 int fd_forward_flow(fd_handle *hd, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
@@ -1548,73 +1669,13 @@ int fd_forward_flow(fd_handle *hd, int nt) {
         int(hd->sources.size()) > kFusedSources || hd->opt.boundary != FD_BOUNDARY_ZERO)
         return fail(FD_ENOTSUP, "the flow schedule: FP32 storage, TMA kernel, <= %d sources, no receivers, zero boundary",
                     kFusedSources);
-    if (nt == 0) return FD_OK;
-    if (hd->tile_y == 0 || hd->x_block == 0) {
-        int rc = autotune(hd);
-        if (rc == FD_OK) rc = build_maps(hd);
-        if (rc != FD_OK) {
-            hd->tile_y = hd->x_block = 0;
-            return rc;
-        }
-        hd->gen++;
-        hd->flow_ctas = 0;
-        hd->flow_xb = 0;
-    }
     // an item reads the queue planes and fronts of its x-neighbours only
-    int xb = hd->flow_xb;
-    if (xb == 0 && hd->opt.x_block > 0) xb = hd->opt.x_block;  // forced by the options
-    const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
-    if (xb == 0) {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_flow_cache.find(key);
-        if (it != g_flow_cache.end()) xb = it->second;
-    }
-    if (xb == 0) {
-        // x_block by timing candidates on the first steps of this call (any x_block gives
-        // the same bits): shorter chunks balance better, longer ones claim fewer items
-        constexpr int kTuneSteps = 8;
-        const int cand[] = {24, 32, 40, 48, 56, 64};
-        int n_cand = 0;
-        for (int c : cand) n_cand += (c >= hd->r && c <= hd->Nx);
-        if (nt >= kTuneSteps * (n_cand + 1) && n_cand > 0) {
-            float best = 1e30f, ms = 0.0f;
-            int best_xb = 0;
-            int rc = flow_direct(hd, kTuneSteps, std::max(40, hd->r), &ms);  // warm-up
-            for (int c : cand) {
-                if (rc != FD_OK) break;
-                if (c < hd->r || c > hd->Nx) continue;
-                rc = flow_direct(hd, kTuneSteps, c, &ms);
-                if (rc == FD_OK && ms < best) {
-                    best = ms;
-                    best_xb = c;
-                }
-            }
-            if (rc != FD_OK) return rc;
-            nt -= kTuneSteps * (n_cand + 1);
-            xb = best_xb;
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_flow_cache[key] = xb;
-        } else {
-            xb = std::min(hd->Nx, std::max(40, hd->r));  // too few steps to time: the usual best
-        }
-    }
-    if (xb < hd->r) return fail(FD_ENOTSUP, "the flow schedule needs x_block >= k/2");
-    if (xb != hd->flow_xb) {
-        hd->flow_xb = xb;
-        hd->gen++;
-    }
+    if (hd->opt.x_block > 0 && hd->opt.x_block < hd->r)
+        return fail(FD_ENOTSUP, "the flow schedule needs x_block >= k/2");
     if (nt == 0) return FD_OK;
-    FlowArgs f;
-    size_t bytes = 0;
-    int ctas = 0;
-    int rc = make_flow_args(hd, nt, xb, &f, &bytes, &ctas);
-    if (rc != FD_OK) return rc;
-    const bool check = check_enabled(hd);
-    return replay_graph(hd, nt, true, [&](cudaStream_t st) {
-        cudaError_t e = cudaMemsetAsync(hd->flow_buf, 0, bytes, st);
-        if (e == cudaSuccess) e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check, st);
-        return e;
-    });
+    int rc = flow_prepare(hd, &nt);
+    if (rc != FD_OK || nt == 0) return rc;
+    return run_flow(hd, nt);
 }
 
 int fd_read_wavefield(fd_handle *hd, float *out, int level) {

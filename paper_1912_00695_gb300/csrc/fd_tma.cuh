@@ -476,11 +476,17 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     const float ums[4] = {cum.x, cum.y, cum.z, cum.w};
                     const float ucs[4] = {uc.x, uc.y, uc.z, uc.w};
                     const float taps[4] = {lapA.x, lapA.y, lapB.x, lapB.y};
+                    // a = m / r0 by a correctly rounded division; where the damping vanishes
+                    // (the tile's plane inside the undamped box) r0 = m exactly and a = 1
+                    float am[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+                    if (!g_free(x)) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) am[p] = __fdiv_rn(ms[p], r0[p]);
+                    }
                     float v[4];
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
-                        const float am = __fdiv_rn(ms[p], r0[p]);
-                        v[p] = fmaf(1.0f - 2.0f * am, ums[p], fmaf(2.0f * am, ucs[p], taps[p]));
+                        v[p] = fmaf(1.0f - 2.0f * am[p], ums[p], fmaf(2.0f * am[p], ucs[p], taps[p]));
                         sw[p] = a.dt2 * inv[p];
                     }
                     out = make_float4(v[0], v[1], v[2], v[3]);
