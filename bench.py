@@ -761,6 +761,25 @@ def run_serving(args, rank: int, world: int):
     clk = clocks.stop()
     scale70 = offered / (0.7 * capacity) if capacity > 0 else 1.0
     at70 = serve(make_requests(scale70), realtime=True)
+
+    # the plain form on the same work: each request alone through a single-shot handle
+    # (set-up, run, read-back of the final field), one after another; wall clock
+    def plain():
+        pts = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in make_requests():
+            with fd.Shot(r.interior, r.space_order, inputs.H, r.dt, r.nbl, storage=r.storage) as shot:
+                shot.set_model(r.m)
+                shot.inject(*r.source, r.wavelet)
+                shot.forward(r.nt)
+                shot.wavefield(0)
+            pts += r.points * r.nt
+        torch.cuda.synchronize()
+        return pts / (time.perf_counter() - t0) / 1e9
+
+    plain()  # warm-up: launch shapes and schedules of every grid
+    plain_gpts = plain()
     line = {
         "metric": "served Gpts/s and p50/p99 request latency, continuous batching of shot requests",
         "value": round(at_rate["gpts"] * world, 3), "unit": "Gpts/s", "n_gpus": world, "steps": 1,
@@ -773,6 +792,10 @@ def run_serving(args, rank: int, world: int):
                    "chunk": args.chunk, "budget_bytes": budget, "parallelism": f"replicas x{world}"},
         "offered_gpts": round(offered, 2),
         "capacity_offline_gpts": round(capacity, 2),
+        "plain_one_by_one": {"value": round(plain_gpts, 3), "unit": "Gpts/s",
+                             "what": "the same requests one after another through single-shot handles "
+                                     "(set-up, run, read-back each)"},
+        "capacity_vs_plain": round(capacity / plain_gpts, 3) if plain_gpts > 0 else None,
         "at_trace_rate": {k: round(v, 4) if isinstance(v, float) else v for k, v in at_rate.items()},
         "at_70pct_capacity": dict({k: round(v, 4) if isinstance(v, float) else v for k, v in at70.items()},
                                   rate_per_s=round(args.rate / scale70, 3)),
