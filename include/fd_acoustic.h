@@ -459,6 +459,18 @@ int fd_default_damping(int Nx, int Ny, int Nz, int nbl, double h, const float *m
 const char *fd_last_error(void);
 
 /* Library version string. */
+/* Self-test of failure detection on the device (no fault involved): one
+ * 32-thread block waits, with the step kernels' own bounded wait functions,
+ * on a ring mbarrier whose phase never completes and then on a dependency
+ * flag that nothing sets; each wait gives up after its time limit (1 s and
+ * 2 s) and the kernel returns, so the context stays usable. *status: bit 0
+ * set if the mbarrier wait gave up, bit 1 if the flag wait gave up (3 when
+ * both limits work); the seconds each wait lasted go to *mbar_seconds and
+ * *flag_seconds (either may be NULL). Synchronises the device (about 3 s).
+ * FD_EINVAL if status is NULL, FD_ENOMEM/FD_ECUDA on allocation or launch
+ * failure. */
+int fd_selftest_waits(unsigned *status, double *mbar_seconds, double *flag_seconds);
+
 const char *fd_version(void);
 
 #ifdef __cplusplus

@@ -23,7 +23,7 @@ from ._abi import (FD_BOUNDARY_PERIODIC, FD_BOUNDARY_ZERO, FD_EFULL, FD_EINVAL, 
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
                    fd_forward, fd_forward_flow, fd_forward_two_step, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
                    fd_load_state, fd_read_traces, fd_set_receivers, fd_fwi_gradient,
-                   fd_kernel_launches, fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
+                   fd_kernel_launches, fd_selftest_waits, fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
                    fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
                    fd_set_model_device, fd_set_stream, fd_status, fd_synchronize, fd_version)
 

@@ -91,6 +91,7 @@ _SIGNATURES = {
     "fd_get_config": (_i, [_vp, _ip, _ip, _ip, _ip]),
     "fd_last_forward_ms": (_i, [_vp, _fp]),
     "fd_kernel_launches": (_i, [ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_selftest_waits": (_i, [ctypes.POINTER(ctypes.c_uint), _dp, _dp]),
     "fd_destroy": (_i, [_vp]),
     "fd_dt_max": (_i, [_i, _d, _d, _dp]),
     "fd_fd_weights": (_i, [_i, _dp]),
@@ -310,6 +311,15 @@ def fd_last_forward_ms(hd) -> float:
     v = ctypes.c_float()
     _check(lib().fd_last_forward_ms(hd, ctypes.byref(v)), "fd_last_forward_ms")
     return v.value
+
+
+def fd_selftest_waits():
+    """(status bits, seconds of the mbarrier wait, seconds of the flag wait): both
+    device-side waits must give up (status 3) after their limits."""
+    st = ctypes.c_uint()
+    t1, t2 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fd_selftest_waits(ctypes.byref(st), ctypes.byref(t1), ctypes.byref(t2)), "fd_selftest_waits")
+    return st.value, t1.value, t2.value
 
 
 def fd_kernel_launches() -> int:

@@ -24,7 +24,8 @@
 
 namespace fdgb {
 
-constexpr long long kFlowWaitLimit = 1LL << 24;  // polls of one flag (about 2 s with the back-off)
+constexpr unsigned long long kFlowWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
+constexpr long long kFlowWaitLimit = 1LL << 26;            // and after this many polls in any case
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
@@ -36,12 +37,18 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Waits until *flag >= need; false if the wait gave up or the launch aborted.
+// Waits until *flag >= need; false if the wait gave up (kFlowWaitNs of the global
+// timer) or the launch aborted.
 __device__ __forceinline__ bool flow_wait(const unsigned *flag, unsigned need, const unsigned *abort) {
+    unsigned long long t0 = 0;
     for (long long i = 0; i < kFlowWaitLimit; ++i) {
         if (ld_acquire_u32(flag) >= need) return true;
         if (*reinterpret_cast<const volatile unsigned *>(abort)) return false;
-        if (i >= 4) __nanosleep(100);
+        if (i >= 4) {
+            if (i == 4) t0 = global_ns();
+            else if (global_ns() - t0 > kFlowWaitNs) return false;
+            __nanosleep(100);
+        }
     }
     return false;
 }

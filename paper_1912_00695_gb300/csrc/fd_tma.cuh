@@ -74,12 +74,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after kMbarWaitLimit polls (well over a second with the
-// back-off), so that a copy that never lands cannot hang the GPU.
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kMbarWaitNs = 1000000000ull;  // a ring wait gives up after 1 s
+
+// Bounded wait: gives up after kMbarWaitNs of the global timer (or kMbarWaitLimit
+// polls, whichever comes first), so that a copy that never lands cannot hang the GPU.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    unsigned long long t0 = 0;
     for (long long i = 0; i < kMbarWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (i >= 8) __nanosleep(64);
+        if (i >= 8) {
+            if (i == 8) t0 = global_ns();
+            else if (global_ns() - t0 > kMbarWaitNs) return false;
+            __nanosleep(64);
+        }
     }
     return false;
 }
