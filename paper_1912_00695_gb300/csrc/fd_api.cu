@@ -199,7 +199,8 @@ struct fd_handle {
     void *flow_buf = nullptr;
     size_t flow_bytes = 0;
     int flow_ctas = 0;
-    int flow_xb = 0;         // the flow schedule's x_block (0: not chosen yet)
+    int flow_xb = 0;         // the flow schedule's x_block, timed, cached or forced (0: not yet)
+    int flow_run_xb = 0;     // the x_block the flow graphs are recorded with
     bool flow_wins = true;   // the flow beat per-step launches when the two were timed
     struct TbMaps {
         const void *u, *up;
@@ -1541,6 +1542,7 @@ static int ensure_step_tuned(fd_handle *hd) {
     hd->gen++;
     hd->flow_ctas = 0;
     hd->flow_xb = 0;
+    hd->flow_run_xb = 0;
     return FD_OK;
 }
 
@@ -1567,7 +1569,7 @@ static int run_flow(fd_handle *hd, int nt) {
     FlowArgs f;
     size_t bytes = 0;
     int ctas = 0;
-    int rc = make_flow_args(hd, nt, hd->flow_xb, &f, &bytes, &ctas);
+    int rc = make_flow_args(hd, nt, hd->flow_run_xb, &f, &bytes, &ctas);
     if (rc != FD_OK) return rc;
     const bool check = check_enabled(hd);
     return replay_graph(hd, nt, true, [&](cudaStream_t st) {
@@ -1606,12 +1608,19 @@ static bool flow_eligible(const fd_handle *hd) {
 static int flow_prepare(fd_handle *hd, int *nt) {
     int rc = ensure_step_tuned(hd);
     if (rc != FD_OK) return rc;
-    if (hd->flow_xb != 0) return FD_OK;
+    // the x_block the graphs use follows the chosen one
+    auto use = [&](int xb) {
+        if (xb != hd->flow_run_xb) {
+            hd->flow_run_xb = xb;
+            hd->gen++;
+        }
+        return FD_OK;
+    };
+    if (hd->flow_xb != 0) return use(hd->flow_xb);
     if (hd->opt.x_block > 0) {  // forced by the options
         hd->flow_xb = hd->opt.x_block;
         hd->flow_wins = true;
-        hd->gen++;
-        return FD_OK;
+        return use(hd->flow_xb);
     }
     const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
     {
@@ -1620,8 +1629,7 @@ static int flow_prepare(fd_handle *hd, int *nt) {
         if (it != g_flow_cache.end()) {
             hd->flow_xb = it->second.first;
             hd->flow_wins = it->second.second;
-            hd->gen++;
-            return FD_OK;
+            return use(hd->flow_xb);
         }
     }
     // shorter x-chunks balance better and keep more items in flight on small grids,
@@ -1633,11 +1641,10 @@ static int flow_prepare(fd_handle *hd, int *nt) {
     if (cand.empty()) cand.push_back(std::max(hd->r, 1));
     const int needed = kTuneSteps * (int(cand.size()) + 2);
     if (*nt < needed) {
-        // too few steps to time: the usual best, not cached
-        hd->flow_xb = std::min(hd->Nx, std::max(40, hd->r));
+        // too few steps to time: the usual best for this call, the timing left to a
+        // later, longer call
         hd->flow_wins = true;
-        hd->gen++;
-        return FD_OK;
+        return use(std::min(hd->Nx, std::max(40, hd->r)));
     }
     float ms = 0.0f, best = 1e30f, step_ms = 0.0f;
     int best_xb = cand[0];
@@ -1655,10 +1662,11 @@ static int flow_prepare(fd_handle *hd, int *nt) {
     *nt -= needed;
     hd->flow_xb = best_xb;
     hd->flow_wins = best <= step_ms;
-    hd->gen++;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_flow_cache[key] = std::make_pair(hd->flow_xb, hd->flow_wins);
-    return FD_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_flow_cache[key] = std::make_pair(hd->flow_xb, hd->flow_wins);
+    }
+    return use(hd->flow_xb);
 }
 
 int fd_forward_flow(fd_handle *hd, int nt) {
