@@ -1,0 +1,40 @@
+"""The benchmark script's host logic: the algorithmic byte counts behind every
+roofline figure, and the reference arm (the FP64 oracle on the host cores),
+which runs without a GPU and must print the contract's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1912_00695_gb300 import inputs  # noqa: E402
+
+
+def test_algorithmic_bytes_of_the_sweep_shot():
+    spec = inputs.sweep_shot(8, n=256, nt=10)
+    pts = 276 ** 3
+    layer = 276 ** 3 - 256 ** 3
+    assert spec.points == pts and bench.layer_points(spec) == layer
+    # FP32: read u^n, u^{n-1}, w, write u^{n+1}; g only in the layer
+    assert bench.algorithmic_bytes_per_step(spec) == pts * 16 + layer * 4 == 353382656
+    # 16-bit levels: the method's three 2-byte levels and the 4-byte coefficient
+    assert bench.algorithmic_bytes_per_step(spec, "bf16") == pts * 10 + layer * 4
+    # two steps per launch: read u^n, u^{n-1}, w, write u^{n+1}, u^{n+2}
+    assert bench.algorithmic_bytes_two_steps(spec) == pts * 20 + layer * 4 == 437480960
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "Gpts/s" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] >= 3
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["metric"].startswith("Gpts/s")
