@@ -250,11 +250,14 @@ int fd_forward_two_step(fd_handle *hd, int nt);
  * boundary, x_block >= k/2 (FD_ENOTSUP otherwise). A device-side wait that
  * gives up (about 2 s) ends the launch and sets FD_ETIMEOUT in the status.
  * The x-chunk length is the options' x_block if set, else timed on the
- * first steps of the first call for the grid and launch shape (candidates
- * 24-64 planes, 8 steps each, as part of the requested steps) and cached
- * for the process. fd_forward takes this path when the kernel is left to
- * the library (FD_KERNEL_AUTO), the conditions hold and the two-step path
- * (space order 2, factored) does not apply.
+ * first steps of the first call of at least 88 steps for the grid and launch
+ * shape (candidates 8-64 planes, 8 steps each, then 8 per-step launches for
+ * comparison; all of them part of the requested steps, same bits) and cached
+ * for the process; a shorter first call uses 40 planes for that call only.
+ * fd_forward takes this path when the kernel is left to the library
+ * (FD_KERNEL_AUTO), the conditions hold, the two-step path (space order 2,
+ * factored) does not apply and the timing did not find the per-step launches
+ * faster for the grid.
  * Asynchronous like fd_forward; fd_last_forward_ms times the launch. */
 int fd_forward_flow(fd_handle *hd, int nt);
 
@@ -267,8 +270,11 @@ int fd_read_traces(fd_handle *hd, float *out, int *recorded);
 /* Queue nt time steps on the handle's stream (asynchronous; returns before
  * the GPU finishes). The global step counter persists across calls, so
  * fd_forward(a) followed by fd_forward(b) equals fd_forward(a + b) bit for
- * bit. Steps are replayed from a cached CUDA graph. FD_ESTATE without a model;
- * FD_EINVAL for nt < 0. */
+ * bit. Steps are replayed from a cached CUDA graph. With the kernel left to
+ * the library, FP32 shots run the flow schedule (fd_forward_flow) or, at
+ * space order 2 factored without receivers, two steps per launch
+ * (fd_forward_two_step); every schedule gives the same bits. FD_ESTATE
+ * without a model; FD_EINVAL for nt < 0. */
 int fd_forward(fd_handle *hd, int nt);
 
 /* Copy a wavefield level to a HOST array of N_x*N_y*N_z floats (dense C-order;
