@@ -101,3 +101,38 @@ def test_options_struct_matches_header():
     body = text[text.index("typedef struct fd_options {"):text.index("} fd_options;")]
     fields = re.findall(r"^\s*int (\w+);", body, flags=re.M)
     assert fields == [f for f, _ in _abi.fd_options._fields_]
+
+
+def test_null_arguments_fail_before_any_device_work(built_lib):
+    """Argument errors are reported on the host, with no CUDA call made (these
+    run on a machine without a GPU)."""
+    lib = built_lib
+    assert lib.fd_kernel_launches(None) == _abi.FD_EINVAL
+    assert lib.fd_selftest_waits(None, None, None) == _abi.FD_EINVAL
+    assert lib.fd_forward(None, 1) == _abi.FD_EINVAL
+    assert lib.fd_forward_flow(None, 1) == _abi.FD_EINVAL
+    assert lib.fd_forward_two_step(None, 2) == _abi.FD_EINVAL
+    assert lib.fd_read_wavefield(None, None, 0) == _abi.FD_EINVAL
+    assert lib.fd_destroy(None) == _abi.FD_OK
+    assert "NULL" in _abi.fd_last_error() or _abi.fd_last_error() != ""
+
+
+def test_kernel_launch_counter_reads_on_the_host(built_lib):
+    n = _abi.fd_kernel_launches()
+    import torch
+    if not torch.cuda.is_available():
+        assert n == 0  # nothing can have been launched in this process
+    else:
+        assert n >= 0
+
+
+def test_shot_device_bytes_counts_the_pitched_fields(built_lib):
+    out = ctypes.c_longlong()
+    for (nx, ny, nz, nbl, st) in ((64, 64, 64, 10, 0), (100, 37, 250, 20, 1), (1, 1, 1, 0, 2)):
+        assert built_lib.fd_shot_device_bytes(nx, ny, nz, nbl, st, ctypes.byref(out)) == _abi.FD_OK
+        Nx, Ny, Nz = nx + 2 * nbl, ny + 2 * nbl, nz + 2 * nbl
+        n = Nx * Ny * (-(-Nz // 64) * 64)  # rows padded to 64 elements
+        levels = 2 * n * 4 if st == 0 else 3 * n * 2  # FP32: two levels; 16-bit: u twice and the increment
+        assert out.value == levels + 2 * n * 4 + (1 << 16)  # plus the two coefficient fields and slack
+    assert built_lib.fd_shot_device_bytes(0, 1, 1, 0, 0, ctypes.byref(out)) == _abi.FD_EINVAL
+    assert built_lib.fd_shot_device_bytes(1, 1, 1, 0, 3, ctypes.byref(out)) == _abi.FD_EINVAL
