@@ -38,3 +38,15 @@ def test_reference_arm_prints_the_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["metric"].startswith("Gpts/s")
+
+
+def test_clock_record_rules():
+    """The timed region is measured again when it saw a hardware or thermal
+    slowdown or clocks well below maximum with no reason; a power cap is kept."""
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert bench.clocks_ok(ok)
+    assert bench.clocks_ok(dict(ok, sm_mhz=1800.0, reasons=["sw_power_cap"]))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert not bench.clocks_ok(dict(ok, reasons=[r]))
+    assert not bench.clocks_ok(dict(ok, sm_mhz=1200.0))  # locked low, no reason given
+    assert bench.clocks_ok({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
