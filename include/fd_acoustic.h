@@ -257,7 +257,7 @@ int fd_forward_two_step(fd_handle *hd, int nt);
  * fd_forward takes this path when the kernel is left to the library
  * (FD_KERNEL_AUTO), the conditions hold, the two-step path (space order 2,
  * factored) does not apply and the timing did not find the per-step launches
- * faster for the grid.
+ * clearly (8 %) faster for the grid.
  * Asynchronous like fd_forward; fd_last_forward_ms times the launch. */
 int fd_forward_flow(fd_handle *hd, int nt);
 

@@ -1661,7 +1661,10 @@ static int flow_prepare(fd_handle *hd, int *nt) {
     if (rc != FD_OK) return rc;
     *nt -= needed;
     hd->flow_xb = best_xb;
-    hd->flow_wins = best <= step_ms;
+    // an 8-step flow launch still carries its start-up and its last step's tail (about
+    // an item's time, several % of 8 steps), which a long run spreads out: the per-step
+    // launches keep the run only when they are clearly faster
+    hd->flow_wins = !(step_ms < 0.92f * best);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_flow_cache[key] = std::make_pair(hd->flow_xb, hd->flow_wins);
