@@ -359,10 +359,26 @@ def run_ours(args, rank: int, world: int):
         "cpu_baseline": cpu,
         "kernel_hash": khash,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for *_, shot, _, _ in shots:
         shot.close()
+    # the metric's other half: batched, reduced-precision and served forms on the same GPU
+    legs = [x for x in args.legs.split(",") if x and x != "none"] if args.workload == "sweep" else []
+    for leg in legs:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        if leg == "batched":
+            rec = leg_batched(args, world)
+        elif leg == "precision":
+            rec = leg_precision(args, world)
+        elif leg == "serving":
+            rec = leg_serving(args, world, args.leg_requests)
+        else:
+            raise SystemExit(f"unknown leg {leg!r}")
+        rec["leg_wall_s"] = round(time.perf_counter() - t0, 1)
+        line[leg] = rec
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_receivers(args, rank: int, world: int):
@@ -538,17 +554,17 @@ def run_gradient(args, rank: int, world: int):
     shot.close()
 
 
-def run_batched(args, rank: int, world: int):
+def leg_batched(args, world: int) -> dict:
     """64 uneven shots (each axis U{96..256} + 10, smooth random velocity, k=8,
     300 steps): the batch (one launch per step over all shots) against the same
-    shots run one after another through the single-shot path."""
+    shots run one after another through the single-shot path. Returns the
+    leg's record (its own clocks, roofline and launch count)."""
     import torch
 
     import paper_1912_00695_gb300 as fd
     from paper_1912_00695_gb300 import inputs
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
+    dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     specs = inputs.batched_shots(count=args.shots, nt=args.nt_batched, lo=args.shot_range[0],
                                  hi=args.shot_range[1])
@@ -556,7 +572,7 @@ def run_batched(args, rank: int, world: int):
     batch = fd.Batch(k, inputs.H, tile_z=args.batch_tile[0], tile_y=args.batch_tile[1],
                      x_block=args.batch_xb)
     batch.set_stream(stream.cuda_stream)
-    singles, ms = [], []
+    singles = []
     for spec in specs:
         spec.dt = 0.9 * fd.fd_dt_max(k, inputs.H, spec.vmax)
         m = spec.m
@@ -591,72 +607,81 @@ def run_batched(args, rank: int, world: int):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1)
 
+    steps = max(1, args.leg_steps)
     for _ in range(args.warmup):
         plain_step()
         batch_step()
     torch.cuda.synchronize()
-    plain_ms = timed(plain_step, args.steps)
+    plain_ms = max_over_ranks(timed(plain_step, steps))
     if world > 1:
         import torch.distributed as tdist
         tdist.barrier()
     clocks = ClockSampler(dev)
     clocks.start()
     launches0 = fd.fd_kernel_launches()
-    batch_ms = timed(batch_step, args.steps)
+    batch_ms = timed(batch_step, steps)
     batch_launches = fd.fd_kernel_launches() - launches0
     batch_ms = max_over_ranks(batch_ms)
     clk = clocks.stop()
-    value = pts * args.steps * world / (batch_ms * 1e-3) / 1e9
-    plain = pts * args.steps / (plain_ms * 1e-3) / 1e9
+    value = pts * steps * world / (batch_ms * 1e-3) / 1e9
+    plain = pts * steps * world / (plain_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    alg = sum(algorithmic_bytes_per_step(spec) for spec in specs) * nt * args.steps
+    alg = sum(algorithmic_bytes_per_step(spec) for spec in specs) * nt * steps
     achieved = alg / (batch_ms * 1e-3) / 1e9
     active, items = batch.size()
-    line = {
-        "metric": "Gpts/s, 64 uneven shots advanced as one batch (one launch per step over "
-                  "all shots) vs the same shots one by one",
-        "value": round(value, 3), "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(batch_ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded smooth random velocity models, Ricker sources)",
+    cfg = batch.config() if hasattr(batch, "config") else (args.batch_tile[0], args.batch_tile[1], args.batch_xb)
+    rec = {
+        "metric": "Gpts/s, 64 uneven shots advanced as one batch vs the same shots one by one",
+        "value": round(value, 3), "unit": "Gpts/s", "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(batch_ms / steps, 3),
         "config": {"workload": f"batched: {len(specs)} shots, interiors U{{{args.shot_range[0]}.."
                                f"{args.shot_range[1]}}} per axis + 10, space order {k}, {nt} steps, "
-                               "factored, FP32",
-                   "batch_tile": list(args.batch_tile), "batch_x_block": args.batch_xb,
-                   "points": sum(spec.points for spec in specs), "work_items_per_step": items,
-                   "l2": "inputs larger than L2 (7.8 GB of fields)",
-                   "parallelism": f"replicas x{world}"},
+                               "factored, FP32, smooth random velocity (sigma 8 cells)",
+                   "batch_tile_z_y_x_block": list(cfg), "points": sum(spec.points for spec in specs),
+                   "work_items_per_step": items, "l2": "inputs larger than L2 (5.6 GB of fields per copy)"},
         "plain_one_by_one": {"value": round(plain, 3), "unit": "Gpts/s",
-                             "ms_per_step": round(plain_ms / args.steps, 3)},
-        "speedup_vs_plain": round(value / world / plain, 3),
+                             "ms_per_step": round(plain_ms / steps, 3),
+                             "what": "the same shots one after another through fd_forward (device-timed)"},
+        "speedup_vs_plain": round(value / plain, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "fd_tma_batch_kernel", "peak_source": peak_kind},
+                     "kernel": "fd_tma_batch_kernel", "peak_source": peak_kind,
+                     "algorithmic_bytes_per_step": int(alg / steps)},
         "gpu_launches": batch_launches,
         "clocks": clk,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     batch.close()
     for shot in singles:
         shot.close()
+    return rec
 
 
-def run_precision(args, rank: int, world: int):
-    """384^3 + 20 (424^3 points), space order 12, 4-layer model: the same shot
-    with FP32, BF16 and FP16 wavefield storage (per-level power-of-two scales,
-    FP32 arithmetic). The errors against the FP64 oracle are measured by the
-    precision test at a size the oracle finishes (96^3 + 20, 1000 steps)."""
+def run_batched(args, rank: int, world: int):
+    rec = leg_batched(args, world)
+    line = dict(rec, n_gpus=world, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic (seeded smooth random velocity models, Ricker sources)")
+    line["config"] = dict(rec["config"], parallelism=f"replicas x{world}")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def leg_precision(args, world: int) -> dict:
+    """384^3 + 20 (424^3 points), space order 12, 4-layer model, 1000 steps: the
+    same shot with FP32, BF16 and FP16 wavefield storage (per-level
+    power-of-two scales, FP32 arithmetic), and the three storages on the
+    256^3 + 10 sweep shot at the requested space orders. The error of each
+    storage against the FP64 oracle at this configuration is measured by the
+    precision_error workload."""
     import torch
 
     import paper_1912_00695_gb300 as fd
     from paper_1912_00695_gb300 import inputs
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
+    dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     peak, peak_kind = _peaks()
     clk = None
+    steps = max(1, args.leg_steps)
 
     def measure(spec, sample_clocks):
         nonlocal clk
@@ -680,7 +705,7 @@ def run_precision(args, rank: int, world: int):
             ev1 = torch.cuda.Event(enable_timing=True)
             n0 = fd.fd_kernel_launches()
             ev0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 shot.reset()
                 shot.forward(spec.nt)
             ev1.record(stream)
@@ -688,10 +713,10 @@ def run_precision(args, rank: int, world: int):
             n_launch = fd.fd_kernel_launches() - n0
             if sample_clocks and st == "bf16":
                 clk = clocks.stop()
-            ms = ev0.elapsed_time(ev1)
-            gpts = spec.points * spec.nt * args.steps / (ms * 1e-3) / 1e9
-            alg = algorithmic_bytes_per_step(spec, st) * spec.nt * args.steps
-            res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / args.steps, 3),
+            ms = max_over_ranks(ev0.elapsed_time(ev1))
+            gpts = spec.points * spec.nt * steps * world / (ms * 1e-3) / 1e9
+            alg = algorithmic_bytes_per_step(spec, st) * spec.nt * steps
+            res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / steps, 3),
                        "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config),
                        "launches": n_launch}
             shot.close()
@@ -699,7 +724,6 @@ def run_precision(args, rank: int, world: int):
 
     spec = inputs.precision_shot(n=args.n_precision, nt=args.nt_precision)
     res = measure(spec, True)
-    # the same storages on the 256^3 + 10 sweep shot at every requested space order
     by_order = {}
     for k in args.precision_orders:
         sp = inputs.sweep_shot(k, n=args.n, nt=min(args.nt, args.nt_precision))
@@ -707,60 +731,117 @@ def run_precision(args, rank: int, world: int):
         by_order[f"so{k}"] = {st: {"gpts": v["gpts"], "hbm_frac": v["hbm_frac"]} for st, v in r.items()}
         by_order[f"so{k}"]["bf16_vs_f32"] = round(r["bf16"]["gpts"] / r["f32"]["gpts"], 3)
         by_order[f"so{k}"]["f16_vs_f32"] = round(r["f16"]["gpts"] / r["f32"]["gpts"], 3)
-    line = {
-        "metric": "Gpts/s with BF16 wavefield storage (per-level scale, FP32 arithmetic) vs FP32 "
+    return {
+        "metric": "Gpts/s with BF16 / FP16 wavefield storage (per-level scale, FP32 arithmetic) vs FP32 "
                   "storage, 384^3+20, space order 12",
-        "value": round(res["bf16"]["gpts"] * world, 3), "unit": "Gpts/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["bf16"]["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 storage, f32 math",
-        "data": "synthetic (seeded layered velocity model, Ricker source)",
+        "value": round(res["bf16"]["gpts"], 3), "unit": "Gpts/s", "steps": steps, "warmup": args.warmup,
+        "ms_per_step": res["bf16"]["ms_per_step"],
         "config": {"workload": f"precision: {args.n_precision}^3+20, space order 12, 4-layer model, "
-                               f"{spec.nt} steps", "points": spec.points,
-                   "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+                               f"{spec.nt} steps", "points": spec.points, "l2": "inputs larger than L2"},
         "by_storage": res,
         "speedup_bf16_vs_f32": round(res["bf16"]["gpts"] / res["f32"]["gpts"], 3),
         "speedup_f16_vs_f32": round(res["f16"]["gpts"] / res["f32"]["gpts"], 3),
         "sweep_shot_by_order": by_order,
+        "sweep_shot_steps": min(args.nt, args.nt_precision),
         "roofline": {"bound": "hbm", "achieved": round(res["bf16"]["hbm_frac"] * peak, 1), "peak": peak,
                      "unit": "GB/s", "frac": res["bf16"]["hbm_frac"], "traffic": None,
-                     "kernel": "fd_tma_kernel (bf16)", "peak_source": peak_kind},
+                     "kernel": "fd_tma_kernel (bf16)", "peak_source": peak_kind,
+                     "algorithmic_bytes_per_point": "10 + 4 in the layer (three 2-byte levels, FP32 coefficient)"},
         "gpu_launches": res["bf16"]["launches"],
         "clocks": clk,
     }
+
+
+def run_precision(args, rank: int, world: int):
+    rec = leg_precision(args, world)
+    line = dict(rec, n_gpus=world, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="bf16 storage, f32 math",
+                data="synthetic (seeded layered velocity model, Ricker source)")
+    line["config"] = dict(rec["config"], parallelism=f"replicas x{world}")
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serving(args, rank: int, world: int):
-    """Continuous-batching server (paper_1912_00695_gb300.serve) on a Poisson
-    trace of shot requests: cubic interiors U{lo..hi} + 10, space order 8 or 16,
-    FP32 or BF16 storage (50/50), steps U{steps}, smooth random velocity.
-    Two runs of the same requests: at the trace's Poisson rate, and at 70 % of
-    the capacity measured by an offline pass (all requests present at t=0), so
-    that the latency percentiles are also reported below saturation."""
+class ModelSource:
+    """Velocity models (as squared slowness) of a serving trace, made on demand:
+    a thread pool generates the models of the next `ahead` requests in
+    arrival order while the current ones are served, and keeps them in host
+    memory up to `keep_bytes` (the rest is regenerated when asked for again),
+    so that a trace of hundreds of large requests neither waits for all its
+    models up front nor holds them all."""
+
+    def __init__(self, trace, ahead: int = 12, workers: int = 8, keep_bytes: int = 0):
+        import concurrent.futures as cf
+        self.trace = trace
+        self.ahead = ahead
+        self.keep_bytes = keep_bytes
+        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
+        self.futs = {}
+        self.kept = {}
+        self.kept_bytes = 0
+
+    def _make(self, i):
+        from paper_1912_00695_gb300 import inputs
+        return inputs.slowness2(inputs.velocity_for(self.trace[i]))
+
+    def _submit(self, i):
+        if 0 <= i < len(self.trace) and i not in self.kept and i not in self.futs:
+            self.futs[i] = self.pool.submit(self._make, i)
+
+    def get(self, i):
+        for j in range(i, i + self.ahead):
+            self._submit(j)
+        if i in self.kept:
+            return self.kept[i]
+        m = self.futs.pop(i).result()
+        if self.kept_bytes + m.nbytes <= self.keep_bytes:
+            self.kept[i] = m
+            self.kept_bytes += m.nbytes
+        return m
+
+    def close(self):
+        self.pool.shutdown(wait=True, cancel_futures=True)
+        self.futs.clear()
+        self.kept.clear()
+
+
+def leg_serving(args, world: int, requests: int) -> dict:
+    """Continuous-batching server (paper_1912_00695_gb300.serve) on the Poisson
+    trace of shot requests: cubic interiors U{lo..hi} + 10, space order 8 or
+    16, FP32 or BF16 storage (50/50), steps U{steps}, smooth random velocity,
+    the first `requests` requests of the seeded trace. Passes over the same
+    requests: offline (all present at t=0: the capacity), at the trace's
+    Poisson rate, at 70 % of the measured capacity (arrival times rescaled, so
+    that latency percentiles are also reported below saturation), and the
+    plain form (each request alone through a single-shot handle: set-up, run,
+    read-back), all on the wall clock."""
     import torch
 
     import paper_1912_00695_gb300 as fd
     from paper_1912_00695_gb300 import inputs
     from paper_1912_00695_gb300.serve import Request, Server
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    trace = inputs.serving_trace(count=args.requests, rate=args.rate, lo=args.serve_range[0],
+    dev = torch.cuda.current_device()
+    trace = inputs.serving_trace(count=requests, rate=args.rate, lo=args.serve_range[0],
                                  hi=args.serve_range[1], steps=args.serve_steps)
+    try:
+        import psutil
+        avail = int(psutil.virtual_memory().available)
+    except Exception:
+        avail = 16 << 30
+    models = ModelSource(trace, keep_bytes=max(0, int(0.4 * avail) - (8 << 30)))
+    vmax = 4500.0  # the smooth models are min-max rescaled to [1.5, 4.5] km/s
 
     def make_requests(rate_scale=1.0):
         reqs = []
         for i, spec in enumerate(trace):
-            vel = models[i]
-            dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, float(vel.max()))
+            dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, vmax)
             reqs.append(Request(i, spec.arrival * rate_scale, spec.interior, spec.nbl, spec.space_order,
-                                spec.storage, dt, ms[i], spec.source,
-                                inputs.ricker(spec.f0, dt, spec.nt), spec.nt))
+                                spec.storage, dt, None, spec.source,
+                                inputs.ricker(spec.f0, dt, spec.nt), spec.nt,
+                                m_fn=(lambda i=i: models.get(i))))
         return reqs
 
-    models = [inputs.velocity_for(spec) for spec in trace]
-    ms = [inputs.slowness2(v) for v in models]
     free, _ = torch.cuda.mem_get_info()
     budget = int(args.serve_budget * free)
 
@@ -770,7 +851,7 @@ def run_serving(args, rank: int, world: int):
         srv.close()
         return stats
 
-    serve(make_requests()[: min(4, len(trace))], realtime=False)  # warm-up: tuner, graphs
+    serve(make_requests()[: min(4, len(trace))], realtime=False)  # warm-up: graphs, classes
     offline = serve(make_requests(), realtime=False)
     capacity = offline["gpts"]
     mean_work = np.mean([spec.points * spec.nt for spec in trace])
@@ -784,15 +865,13 @@ def run_serving(args, rank: int, world: int):
     scale70 = offered / (0.7 * capacity) if capacity > 0 else 1.0
     at70 = serve(make_requests(scale70), realtime=True)
 
-    # the plain form on the same work: each request alone through a single-shot handle
-    # (set-up, run, read-back of the final field), one after another; wall clock
     def plain():
         pts = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for r in make_requests():
             with fd.Shot(r.interior, r.space_order, inputs.H, r.dt, r.nbl, storage=r.storage) as shot:
-                shot.set_model(r.m)
+                shot.set_model(r.model())
                 shot.inject(*r.source, r.wavelet)
                 shot.forward(r.nt)
                 shot.wavefield(0)
@@ -800,30 +879,40 @@ def run_serving(args, rank: int, world: int):
         torch.cuda.synchronize()
         return pts / (time.perf_counter() - t0) / 1e9
 
-    plain()  # warm-up: launch shapes and schedules of every grid
     plain_gpts = plain()
-    line = {
+    models.close()
+    rnd = (lambda d: {k: round(v, 4) if isinstance(v, float) else v for k, v in d.items()})
+    return {
         "metric": "served Gpts/s and p50/p99 request latency, continuous batching of shot requests",
-        "value": round(at_rate["gpts"] * world, 3), "unit": "Gpts/s", "n_gpus": world, "steps": 1,
-        "warmup": 1, "ms_per_step": round(at_rate["makespan_s"] * 1e3, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 / bf16 storage per request",
-        "data": "synthetic (seeded smooth random velocity models, Ricker sources, Poisson arrivals)",
-        "config": {"workload": f"serving: {len(trace)} requests, Poisson {args.rate}/s, cubic interiors "
-                               f"U{{{args.serve_range[0]}..{args.serve_range[1]}}} + 10, space order 8/16, "
-                               f"FP32/BF16, steps U{{{args.serve_steps[0]}..{args.serve_steps[1]}}}",
-                   "chunk": args.chunk, "budget_bytes": budget, "parallelism": f"replicas x{world}"},
+        "value": round(at_rate["gpts"] * world, 3), "unit": "Gpts/s",
+        "config": {"workload": f"serving: first {len(trace)} requests of the seeded Poisson trace "
+                               f"({args.rate}/s), cubic interiors U{{{args.serve_range[0]}..{args.serve_range[1]}}}"
+                               f" + 10, space order 8/16, FP32/BF16, steps U{{{args.serve_steps[0]}.."
+                               f"{args.serve_steps[1]}}}, smooth random velocity per request",
+                   "requests": len(trace), "chunk": args.chunk, "budget_bytes": budget,
+                   "models": "generated per request from its seed by a host thread pool ahead of admission"},
         "offered_gpts": round(offered, 2),
+        "offered_vs_capacity": round(offered / capacity, 3) if capacity > 0 else None,
         "capacity_offline_gpts": round(capacity, 2),
         "plain_one_by_one": {"value": round(plain_gpts, 3), "unit": "Gpts/s",
                              "what": "the same requests one after another through single-shot handles "
-                                     "(set-up, run, read-back each)"},
+                                     "(set-up, run, read-back each), wall clock"},
         "capacity_vs_plain": round(capacity / plain_gpts, 3) if plain_gpts > 0 else None,
-        "at_trace_rate": {k: round(v, 4) if isinstance(v, float) else v for k, v in at_rate.items()},
-        "at_70pct_capacity": dict({k: round(v, 4) if isinstance(v, float) else v for k, v in at70.items()},
-                                  rate_per_s=round(args.rate / scale70, 3)),
+        "served_at_rate_vs_plain": round(at_rate["gpts"] / plain_gpts, 3) if plain_gpts > 0 else None,
+        "at_trace_rate": rnd(at_rate),
+        "at_70pct_capacity": dict(rnd(at70), rate_per_s=round(args.rate / scale70, 3)),
+        "offline": rnd(offline),
         "gpu_launches": serve_launches,
         "clocks": clk,
     }
+
+
+def run_serving(args, rank: int, world: int):
+    rec = leg_serving(args, world, args.requests)
+    line = dict(rec, n_gpus=world, steps=1, warmup=1, ms_per_step=round(rec["at_trace_rate"]["makespan_s"] * 1e3, 1),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32 / bf16 storage per request",
+                data="synthetic (seeded smooth random velocity models, Ricker sources, Poisson arrivals)")
+    line["config"] = dict(rec["config"], parallelism=f"replicas x{world}")
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -952,17 +1041,23 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "plain", "batched", "precision", "serving", "receivers", "gradient"])
-    ap.add_argument("--requests", type=int, default=40, help="serving: requests in the trace")
+    ap.add_argument("--legs", default="batched,precision,serving",
+                    help="sweep workload: legs added to the line (batched, precision, serving; 'none')")
+    ap.add_argument("--leg-steps", type=int, default=2, help="timed repetitions of the batched/precision legs")
+    ap.add_argument("--leg-requests", type=int, default=60,
+                    help="serving leg of the default line: the first N requests of the trace")
+    ap.add_argument("--requests", type=int, default=200, help="serving workload: requests in the trace")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrivals per second")
-    ap.add_argument("--serve-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(128, 256),
+    ap.add_argument("--serve-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(128, 512),
                     help="serving: cubic interior size range lo,hi")
-    ap.add_argument("--serve-steps", type=lambda v: tuple(int(x) for x in v.split(",")), default=(200, 1000),
+    ap.add_argument("--serve-steps", type=lambda v: tuple(int(x) for x in v.split(",")), default=(200, 2000),
                     help="serving: steps range lo,hi")
     ap.add_argument("--serve-budget", type=float, default=0.8, help="serving: fraction of free HBM to admit into")
     ap.add_argument("--chunk", type=int, default=50, help="serving: steps per scheduling chunk")
     ap.add_argument("--n-precision", type=int, default=384, help="precision workload: interior size")
     ap.add_argument("--nt-precision", type=int, default=1000, help="precision workload: steps")
-    ap.add_argument("--precision-orders", type=lambda v: tuple(int(x) for x in v.split(",") if x), default=(),
+    ap.add_argument("--precision-orders", type=lambda v: tuple(int(x) for x in v.split(",") if x),
+                    default=(2, 4, 8, 12, 16),
                     help="precision workload: also compare the storages on the sweep shot at these orders")
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")

@@ -250,14 +250,17 @@ int fd_forward_two_step(fd_handle *hd, int nt);
  * boundary, x_block >= k/2 (FD_ENOTSUP otherwise). A device-side wait that
  * gives up (about 2 s) ends the launch and sets FD_ETIMEOUT in the status.
  * The x-chunk length is the options' x_block if set, else timed on the
- * first steps of the first call of at least 88 steps for the grid and launch
- * shape (candidates 8-64 planes, 8 steps each, then 8 per-step launches for
- * comparison; all of them part of the requested steps, same bits) and cached
- * for the process; a shorter first call uses 40 planes for that call only.
+ * first steps of the first call of at least 136 steps for the grid and launch
+ * shape (candidates 8-64 planes, 8 steps each; all of them part of the
+ * requested steps, same bits) and cached for the process; a shorter first
+ * call uses 40 planes for that call only. The same first call compares the
+ * two schedules by the cost of one more step: the best length and the
+ * per-step launches each run 8 and 24 steps, and (t24 - t8) / 16 is compared,
+ * which cancels a launch's start-up and last tail.
  * fd_forward takes this path when the kernel is left to the library
  * (FD_KERNEL_AUTO), the conditions hold, the two-step path (space order 2,
- * factored) does not apply and the timing did not find the per-step launches
- * clearly (8 %) faster for the grid.
+ * factored) does not apply and that comparison did not find the per-step
+ * launches cheaper per step for the grid.
  * Asynchronous like fd_forward; fd_last_forward_ms times the launch. */
 int fd_forward_flow(fd_handle *hd, int nt);
 
@@ -268,7 +271,11 @@ int fd_forward_flow(fd_handle *hd, int nt);
 int fd_read_traces(fd_handle *hd, float *out, int *recorded);
 
 /* Queue nt time steps on the handle's stream (asynchronous; returns before
- * the GPU finishes). The global step counter persists across calls, so
+ * the GPU finishes). Each step is the explicit leapfrog update of Eq. 1 with
+ * the damping term of Listing 2 (its r0 = dt m + dt^2/2 damp denominator) and
+ * the point sources' q_s, over the three time levels that Listing 2 names
+ * t0, t1, t2 (Sec. 2.1); the paper's measured runs repeat it 30,000 times
+ * (Sec. 4). The global step counter persists across calls, so
  * fd_forward(a) followed by fd_forward(b) equals fd_forward(a + b) bit for
  * bit. Steps are replayed from a cached CUDA graph. With the kernel left to
  * the library, FP32 shots run the flow schedule (fd_forward_flow) or, at
@@ -278,7 +285,8 @@ int fd_read_traces(fd_handle *hd, float *out, int *recorded);
 int fd_forward(fd_handle *hd, int nt);
 
 /* Copy a wavefield level to a HOST array of N_x*N_y*N_z floats (dense C-order;
- * 16-bit storage is converted and scaled to FP32). level 0 = u^n (the newest),
+ * Sec. 5 names returning the result to the host workflow as future work, so
+ * the paper defines no read-back format; 16-bit storage is converted and scaled to FP32). level 0 = u^n (the newest),
  * 1 = u^{n-1}. Synchronises the stream. Returns FD_ENONFINITE when the finite
  * check saw NaN/Inf (or 16-bit overflow) in any step since the last reset. */
 int fd_read_wavefield(fd_handle *hd, float *out, int level);
@@ -287,14 +295,16 @@ int fd_read_wavefield(fd_handle *hd, float *out, int level);
  * handle's stream, returns without synchronising (status not checked). */
 int fd_read_wavefield_device(fd_handle *hd, float *d_out, int level);
 
-/* Bind the handle to a CUDA stream (a cudaStream_t, e.g. torch's
+/* (The paper has no counterpart: stream binding is this library's host
+ * runtime.) Bind the handle to a CUDA stream (a cudaStream_t, e.g. torch's
  * torch.cuda.current_stream().cuda_stream); NULL = the handle's own stream
  * (created blocking, so it orders with the legacy default stream). Waits for
  * the work already queued on the previous stream. */
 int fd_set_stream(fd_handle *hd, void *cuda_stream);
 
 /* Wait for the handle's queued work; returns the device status (FD_OK,
- * FD_ENONFINITE) or FD_ECUDA. */
+ * FD_ENONFINITE) or FD_ECUDA. (The paper has no counterpart: status and
+ * synchronisation are this library's host runtime.) */
 int fd_synchronize(fd_handle *hd);
 
 /* Device status without waiting beyond what is queued: same as fd_synchronize. */
@@ -310,8 +320,9 @@ int fd_status(fd_handle *hd);
  * FD_EINVAL for NULL arrays, non-finite values or step < 0. */
 int fd_load_state(fd_handle *hd, const float *u, const float *u_prev, long long step);
 
-/* Zero both wavefield levels, the step counter and the device status. Keeps
- * the model and the sources. Queued on the handle's stream (asynchronous). */
+/* Zero both wavefield levels, the step counter and the device status: the
+ * zero initial conditions u = u_t = 0 of Eq. 1 (Sec. 2.1). Keeps the model
+ * and the sources. Queued on the handle's stream (asynchronous). */
 int fd_reset(fd_handle *hd);
 
 /* Global step counter n (the wavefield level u^n held as level 0). */
@@ -338,7 +349,8 @@ int fd_last_forward_ms(fd_handle *hd, float *ms);
  * of the span between them. No device work; FD_EINVAL if count is NULL. */
 int fd_kernel_launches(long long *count);
 
-/* Release every device buffer and the handle. NULL is accepted (no-op). */
+/* Release every device buffer and the handle. NULL is accepted (no-op).
+ * (The paper has no counterpart: buffer ownership is this library's.) */
 int fd_destroy(fd_handle *hd);
 
 /* ---- batches of uneven shots ---------------------------------------------- */
@@ -432,8 +444,9 @@ int fd_batch_destroy(fd_batch *b);
  * loading the library holds until exit. FD_EINVAL when one step would need
  * more than 16,384 CTAs (Ny*Nz above about 4.2 million points) or for bad
  * arguments; FD_ERANGE for a source outside the domain. The first call on a
- * device looks up that device's copy of the array (cudaGetSymbolAddress) once;
- * make that first call before any stream capture. Every call on a device
+ * device looks up that device's copy of the array (cudaGetSymbolAddress) and
+ * its multiprocessor count (which sizes the x-chunks: four CTAs per
+ * multiprocessor) once; make that first call before any stream capture. Every call on a device
  * shares the same array and clears the running maximum at its start, so calls
  * that overlap on the GPU (other streams, other threads) race on it.
  *
@@ -448,7 +461,10 @@ int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m, const floa
 /* ---- host numerics -------------------------------------------------------- */
 
 /* Stability limit dt_max = 2 h / (v_max sqrt(3 sum_{j=-r..r} |c_j|)) of the
- * 3D leapfrog scheme (von Neumann analysis at the Nyquist mode). */
+ * 3D leapfrog scheme (von Neumann analysis at the Nyquist mode). The paper
+ * states no limit; this is the classic analysis of the scheme it discretises
+ * (Eq. 1, Listing 2), applied to every space order. FD_EINVAL for an odd or
+ * out-of-range space order, non-positive h or vmax, or a NULL out. */
 int fd_dt_max(int space_order, double h, double vmax, double *out);
 
 /* Centred second-derivative weights c_0..c_r of accuracy order k for unit

@@ -148,16 +148,25 @@ def step(u, u_prev, m, eta, space_order: int, h: float, dt: float,
 
 
 def forward(m, eta, space_order: int, h: float, dt: float, nt: int, sources=(), wavelets=None,
-            u0=None, u_prev0=None, step0: int = 0, periodic: bool = False):
+            u0=None, u_prev0=None, step0: int = 0, periodic: bool = False, inplace: bool = False):
     """Advance nt steps; returns (u^{step0+nt}, u^{step0+nt-1}) as float64 arrays.
 
     sources: sequence of (x, y, z) domain nodes; wavelets: array (ns, ld) of
-    source samples indexed by global step (zero beyond ld).
+    source samples indexed by global step (zero beyond ld). inplace: advance
+    the given u0 and u_prev0 (contiguous float64 arrays) in place instead of
+    copies (marshalling only: the same arithmetic, no per-call copy of large
+    fields).
     """
     m = _f64(m)
     shape = m.shape
-    u = np.zeros(shape) if u0 is None else _f64(u0).copy()
-    up = np.zeros(shape) if u_prev0 is None else _f64(u_prev0).copy()
+    if inplace and u0 is not None and u_prev0 is not None:
+        u, up = u0, u_prev0
+        for a in (u, up):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != shape:
+                raise ValueError("inplace forward needs contiguous float64 levels of the model's shape")
+    else:
+        u = np.zeros(shape) if u0 is None else _f64(u0).copy()
+        up = np.zeros(shape) if u_prev0 is None else _f64(u_prev0).copy()
     eta_a = None if eta is None else _f64(eta)
     ns = len(sources)
     src = np.asarray(sources, dtype=np.int32).reshape(ns, 3)

@@ -24,8 +24,9 @@
  *
  * Pins (tests/test_oracle_*.py): weights against an exact rational Vandermonde
  * solve and polynomial exactness; the Laplacian against the closed-form plane
- * wave symbol and symmetry; the step against the literal Listing 2 algebra
- * (k=2, h=1), a dense-matrix brute force, the exact discrete plane-wave
+ * wave symbol and symmetry; the step against u^{n+1} solved from the damped
+ * Eq. 1 at k=2, h=1 (damping sign and r0 denominator as in Listing 2), a
+ * dense-matrix brute force, the exact discrete plane-wave
  * solution and discrete energy conservation; dt_max against power iteration;
  * off-grid sampling against a library interpolator and affine exactness,
  * off-grid spreading against integer-node sources combined by linearity and a

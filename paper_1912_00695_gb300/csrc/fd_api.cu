@@ -1634,19 +1634,21 @@ static int flow_prepare(fd_handle *hd, int *nt) {
     }
     // shorter x-chunks balance better and keep more items in flight on small grids,
     // longer ones claim fewer items and re-read fewer queue planes
-    constexpr int kTuneSteps = 8;
+    constexpr int kTuneSteps = 8, kLongSteps = 24;
     std::vector<int> cand;
     for (int c : {8, 12, 16, 24, 32, 40, 48, 56, 64})
         if (c >= hd->r && c <= hd->Nx) cand.push_back(c);
     if (cand.empty()) cand.push_back(std::max(hd->r, 1));
-    const int needed = kTuneSteps * (int(cand.size()) + 2);
+    // warm-up + candidates, then the best length and the per-step launches each
+    // timed over kTuneSteps and kLongSteps
+    const int needed = kTuneSteps * (int(cand.size()) + 1) + kLongSteps + kTuneSteps + kLongSteps;
     if (*nt < needed) {
         // too few steps to time: the usual best for this call, the timing left to a
         // later, longer call
         hd->flow_wins = true;
         return use(std::min(hd->Nx, std::max(40, hd->r)));
     }
-    float ms = 0.0f, best = 1e30f, step_ms = 0.0f;
+    float ms = 0.0f, best = 1e30f, flow_long = 0.0f, step_short = 0.0f, step_long = 0.0f;
     int best_xb = cand[0];
     rc = flow_direct(hd, kTuneSteps, cand[cand.size() / 2], &ms);  // warm-up
     for (int c : cand) {
@@ -1657,14 +1659,19 @@ static int flow_prepare(fd_handle *hd, int *nt) {
             best_xb = c;
         }
     }
-    if (rc == FD_OK) rc = steps_direct(hd, kTuneSteps, &step_ms);
+    // schedule choice by differential timing: the cost of one more step, (t_long -
+    // t_short) / (kLongSteps - kTuneSteps), for both schedules. A flow launch carries a
+    // start-up and a last tail that a long run spreads out; the difference cancels them
+    // (and the per-step launches' first-launch overhead) instead of a hand-set margin.
+    if (rc == FD_OK) rc = flow_direct(hd, kLongSteps, best_xb, &flow_long);
+    if (rc == FD_OK) rc = steps_direct(hd, kTuneSteps, &step_short);
+    if (rc == FD_OK) rc = steps_direct(hd, kLongSteps, &step_long);
     if (rc != FD_OK) return rc;
     *nt -= needed;
     hd->flow_xb = best_xb;
-    // an 8-step flow launch still carries its start-up and its last step's tail (about
-    // an item's time, several % of 8 steps), which a long run spreads out: the per-step
-    // launches keep the run only when they are clearly faster
-    hd->flow_wins = !(step_ms < 0.92f * best);
+    const float flow_per_step = (flow_long - best) / float(kLongSteps - kTuneSteps);
+    const float steps_per_step = (step_long - step_short) / float(kLongSteps - kTuneSteps);
+    hd->flow_wins = flow_per_step <= steps_per_step;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_flow_cache[key] = std::make_pair(hd->flow_xb, hd->flow_wins);
@@ -1925,10 +1932,11 @@ int batch_stage_upload(fd_batch *b, void *dst, const void *src, size_t bytes) {
 // the launches already queued that read it).
 int batch_reserve(fd_batch *b, void **ptr, size_t *cap, size_t need, size_t elem) {
     if (need <= *cap) return FD_OK;
+    const size_t old = *cap;  // grow geometrically: churn of added shots reallocates rarely
     dev_free(*ptr, b->stream);
     *ptr = nullptr;
     *cap = 0;
-    const size_t n = std::max<size_t>(need, 2 * *cap);
+    const size_t n = std::max<size_t>(need, 2 * old);
     if (dev_alloc(ptr, n * elem, b->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(FD_ENOMEM, "cannot allocate a batch table");

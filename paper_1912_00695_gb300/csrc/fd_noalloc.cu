@@ -34,6 +34,7 @@ static __device__ __align__(256) unsigned g_noalloc_scratch[64 + kNoAllocMaxCtas
 
 std::mutex g_noalloc_mu;
 unsigned *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};  // multiprocessors of each device, read with its address
 
 // Streaming step (expanded form, FP32 storage, dense [Nx][Ny][Nz] layout): the
 // same per-point arithmetic as fd_stream_kernel<R, kExpanded, TY, float>, with
@@ -216,34 +217,6 @@ cudaError_t launch_noalloc_r(int r, const StepArgs &a, dim3 grid, unsigned *scra
     }
 }
 
-// Centred second-derivative weights by Fornberg's recursion on fixed-size
-// stack arrays (no heap use on this path).
-bool weights_on_stack(int space_order, double *c) {
-    if (space_order < 2 || space_order > 2 * kNoallocMaxRadius || space_order % 2) return false;
-    const int r = space_order / 2, n_nodes = 2 * r + 1;
-    double w[3][2 * kMaxRadius + 1] = {};
-    w[0][0] = 1.0;
-    double prod_prev = 1.0, dist_last = double(-r);
-    for (int n = 1; n < n_nodes; ++n) {
-        double prod = 1.0;
-        const double dist_prev = dist_last;
-        dist_last = double(n - r);
-        const int mmax = n < 2 ? n : 2;
-        for (int nu = 0; nu < n; ++nu) {
-            const double gap = double(n - nu);
-            prod *= gap;
-            if (nu == n - 1)
-                for (int m = mmax; m >= 0; --m)
-                    w[m][n] = prod_prev * (double(m) * (m > 0 ? w[m - 1][n - 1] : 0.0) - dist_prev * w[m][n - 1]) / prod;
-            for (int m = mmax; m >= 0; --m)
-                w[m][nu] = (dist_last * w[m][nu] - double(m) * (m > 0 ? w[m - 1][nu] : 0.0)) / gap;
-        }
-        prod_prev = prod;
-    }
-    for (int j = 0; j <= r; ++j) c[j] = w[2][r + j];
-    return true;
-}
-
 }  // namespace
 }  // namespace fdgb
 
@@ -262,8 +235,10 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
     if (!d_u || !d_u_prev || !d_m) return fail(FD_EINVAL, "u, u_prev and m must be device pointers");
     if (Nx < 1 || Ny < 1 || Nz < 1 || Nx > kMaxDim || Ny > kMaxDim || Nz > kMaxDim)
         return fail(FD_EINVAL, "extents must be in [1, 65535]");
-    double c[kMaxRadius + 1];
-    if (!weights_on_stack(space_order, c)) return fail(FD_EINVAL, "space_order must be even in [2, 16]");
+    // the library's weight generator (Fornberg's recursion on fixed-size arrays: no heap use)
+    double c[kMaxRadiusHost + 1];
+    if (space_order > 2 * kNoallocMaxRadius || !fornberg_second_derivative(space_order, c))
+        return fail(FD_EINVAL, "space_order must be even in [2, 16]");
     if (!(h > 0) || !std::isfinite(h) || !(dt > 0) || !std::isfinite(dt))
         return fail(FD_EINVAL, "h and dt must be positive and finite");
     if (ns < 0 || ns > kNoallocSources) return fail(FD_EINVAL, "ns must be in [0, 4]");
@@ -274,8 +249,29 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
     const long long tiles = (long long)tiles_z * tiles_y;
     if (tiles > kNoAllocMaxCtas)
         return fail(FD_EINVAL, "Ny*Nz too large: one step would need more than 16384 CTAs of scratch");
-    // x-chunks: enough CTAs to fill the GPU, within the scratch capacity
-    long long chunks = (4 * 152 + tiles - 1) / tiles;
+    // per-device set-up: the address of this device's copy of the scratch array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(FD_ECUDA, "no usable current device");
+    unsigned *scratch = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return fail(FD_ECUDA, cudaGetErrorString(e));
+            int n_sm = 0;
+            e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return fail(FD_ECUDA, cudaGetErrorString(e));
+            g_noalloc_sms[dev] = n_sm > 0 ? n_sm : 1;
+            g_noalloc_ptr[dev] = static_cast<unsigned *>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+    // x-chunks: enough CTAs for four per multiprocessor, within the scratch capacity
+    long long chunks = (4LL * sms + tiles - 1) / tiles;
     const long long max_chunks = std::max<long long>(1, std::min<long long>(kNoAllocMaxCtas / tiles, Nx / 16));
     chunks = std::max<long long>(1, std::min(chunks, max_chunks));
     const int x_block = int((Nx + chunks - 1) / chunks);
@@ -313,21 +309,6 @@ extern "C" int fd_forward_noalloc(float *d_u, float *d_u_prev, const float *d_m,
     a.wavelet = d_wavelet;
     a.ld = ld;
 
-    // per-device set-up: the address of this device's copy of the scratch array
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
-        return fail(FD_ECUDA, "no usable current device");
-    unsigned *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) return fail(FD_ECUDA, cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = static_cast<unsigned *>(p);
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     noalloc_clear_kernel<<<1, 32, 0, s>>>(scratch);
     cudaError_t e = counted(cudaGetLastError(), s);

@@ -19,12 +19,13 @@ bool fornberg_second_derivative(int space_order, double *c) {
     if (space_order < 2 || space_order % 2 != 0 || space_order > 2 * kMaxRadiusHost) return false;
     const int r = space_order / 2;
     const int n_nodes = 2 * r + 1;
-    const int M = 2;  // highest derivative order carried
-    std::vector<double> node(n_nodes);
+    constexpr int M = 2;  // highest derivative order carried
+    // fixed-size arrays: no heap use, so the allocation-free entry point can call it too
+    double node[2 * kMaxRadiusHost + 1];
     for (int i = 0; i < n_nodes; ++i) node[i] = double(i - r);
     const double x0 = 0.0;
     // w[m][nu]: weight of node nu for derivative m, using the nodes seen so far
-    std::vector<std::vector<double>> w(M + 1, std::vector<double>(n_nodes, 0.0));
+    double w[M + 1][2 * kMaxRadiusHost + 1] = {};
     w[0][0] = 1.0;
     double prod_prev = 1.0;
     double dist_last = node[0] - x0;

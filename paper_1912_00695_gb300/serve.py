@@ -42,7 +42,7 @@ class Request:
     space_order: int
     storage: str
     dt: float
-    m: np.ndarray             # squared slowness over the computational domain (float32)
+    m: np.ndarray | None      # squared slowness over the computational domain (float32)
     source: tuple             # interior node
     wavelet: np.ndarray       # float32 samples
     nt: int
@@ -50,6 +50,12 @@ class Request:
     admitted: float = -1.0
     completed: float = -1.0
     visible: float = 0.0      # when the server could first see it (latency is measured from here)
+    # the model may instead come from a callable, asked for it at admission (a
+    # client that streams its model in, or a generator bounded in host memory)
+    m_fn: object = field(default=None, repr=False)
+
+    def model(self) -> np.ndarray:
+        return self.m if self.m is not None or self.m_fn is None else self.m_fn()
 
     @property
     def points(self) -> int:
@@ -112,7 +118,7 @@ class Server:
             return False
         key = (req.space_order, req.storage)
         b = self._batch(key)
-        slot = b.add(req.interior, req.nbl, req.dt, req.m)
+        slot = b.add(req.interior, req.nbl, req.dt, req.model())
         b.inject(slot, *req.source, req.wavelet)
         self.used += need
         self.launches += 4

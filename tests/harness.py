@@ -1,8 +1,11 @@
 """Test-side helpers: run the same seeded shot through the C-ABI and the oracle.
 
 Both sides receive identical inputs from paper_1912_00695_gb300.inputs (the
-model m as float32, the wavelet as float32 samples, the damping eta as float32
-from the library's host helper or a test array) and the same dt.
+model m as float32, the wavelet as float32 samples) and the same dt and damping
+eta. dt and the default eta come from the oracle (its stability limit and its
+damping profile, eta rounded to float32), so no value the oracle consumes
+originates in the library; the library's own helpers are checked against these
+in tests/test_abi_cpu.py.
 """
 from __future__ import annotations
 
@@ -13,12 +16,16 @@ from paper_1912_00695_gb300 import inputs
 
 
 def dt_for(spec, frac=0.9) -> float:
-    return frac * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
+    """frac times the oracle's stability limit for the shot's largest velocity."""
+    import oracle
+    return frac * oracle.dt_max(spec.space_order, inputs.H, spec.vmax)
 
 
 def eta_for(spec) -> np.ndarray:
-    """Default damping as float32 (the exact array both sides then consume)."""
-    return fd.fd_default_damping(spec.m, spec.nbl, inputs.H)
+    """The oracle's default damping rounded to float32 (the exact array both
+    sides then consume)."""
+    import oracle
+    return oracle.default_damping(spec.m, spec.nbl, inputs.H).astype(np.float32)
 
 
 def run_gpu(spec, nt, dt, eta=None, sources=None, chunks=None, state=None, **opts):

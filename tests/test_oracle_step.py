@@ -1,6 +1,7 @@
 """Pins of the oracle's damped leapfrog step, sources and initial conditions.
 
-Fixed against: the literal Listing 2 algebra (space order 2, h = 1, with damp),
+Fixed against: the damped Eq. 1 discretised at space order 2 on a unit grid
+(sign of the damping and the r0 denominator as in Listing 2),
 a dense-matrix brute force with sources, the exact discrete plane-wave
 solution, discrete energy conservation (and decay with damping), reciprocity,
 linearity and the zero initial conditions of Eq. 1.
@@ -13,39 +14,46 @@ import pytest
 from pinlib import dense_forward, symbol, vandermonde_weights
 
 
-def _listing2_rows():
-    path = os.path.join(os.path.dirname(__file__), "golden", "listing2_k2.txt")
+def _eq1_rows():
+    path = os.path.join(os.path.dirname(__file__), "golden", "eq1_k2_damped.txt")
     rows = []
     with open(path) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
             if line:
-                field, dx, dy, dz, sign, p, factor, scale = line.split()
-                rows.append((field, (int(dx), int(dy), int(dz)), int(sign), int(p), factor,
-                             float(scale)))
+                term, level, dx, dy, dz, sign, scale, factor, p = line.split()
+                rows.append((term, int(level), (int(dx), int(dy), int(dz)), int(sign) * float(scale),
+                             factor, int(p)))
     return rows
 
 
-def _listing2_update(u, u_prev, m, damp, dt):
-    """Evaluate the Listing 2 expression term by term from the golden rows, at
-    the points whose neighbours all lie inside the arrays."""
+def _eq1_update(u, u_prev, m, damp, dt):
+    """Solve the fixture's discrete residual of Eq. 1 (damped, k = 2, h = 1)
+    for u^{n+1} at the points whose neighbours all lie inside the arrays:
+    residual = A u^{n+1} + B = 0 with A the u^{n+1} coefficient and B every
+    other term applied to u^n and u^{n-1}. Also returns A dt^3, which must be
+    Listing 2's r0 = dt m + dt^2 damp / 2."""
     nx, ny, nz = u.shape
     core = (slice(1, nx - 1), slice(1, ny - 1), slice(1, nz - 1))
-    fields = {"u": u, "u_prev": u_prev}
-    factors = {"1": np.ones_like(m[core]), "m": m[core], "damp": damp[core]}
-    num = np.zeros_like(m[core])
-    r0 = np.zeros_like(m[core])
-    for field, (dx, dy, dz), sign, p, factor, scale in _listing2_rows():
-        coef = sign * scale * dt ** p * factors[factor]
-        if field == "r0":
-            r0 += coef
+    fields = {0: u, -1: u_prev}
+    factors = {"1": np.ones_like(m[core]), "m": m[core], "eta": damp[core]}
+    a = np.zeros_like(m[core])
+    b = np.zeros_like(m[core])
+    for term, level, (dx, dy, dz), coef, factor, p in _eq1_rows():
+        c = coef * factors[factor] * dt ** p
+        if level == 1:
+            assert (dx, dy, dz) == (0, 0, 0)
+            a += c
             continue
         sh = (slice(1 + dx, nx - 1 + dx), slice(1 + dy, ny - 1 + dy), slice(1 + dz, nz - 1 + dz))
-        num += coef * fields[field][sh]
-    return num / r0, core
+        b += c * fields[level][sh]
+    return -b / a, a * dt ** 3, core
 
 
-def test_step_reproduces_listing2(oracle_mod):
+def test_step_solves_damped_eq1_k2(oracle_mod):
+    """The oracle's step equals u^{n+1} solved from the damped Eq. 1 residual
+    (space order 2, unit grid) written out in the golden fixture, and the
+    u^{n+1} coefficient times dt^3 is Listing 2's denominator r0."""
     rng = np.random.default_rng(0)
     shape = (7, 8, 9)
     u = rng.standard_normal(shape)
@@ -53,9 +61,10 @@ def test_step_reproduces_listing2(oracle_mod):
     m = rng.uniform(0.2, 1.5, shape)
     damp = rng.uniform(0.0, 0.8, shape)
     dt = 0.37
-    want, core = _listing2_update(u, u_prev, m, damp, dt)
+    want, r0, core = _eq1_update(u, u_prev, m, damp, dt)
+    np.testing.assert_allclose(r0, dt * m[core] + 0.5 * dt ** 2 * damp[core], rtol=1e-15)
     got = oracle_mod.step(u, u_prev, m, damp, 2, 1.0, dt)
-    np.testing.assert_allclose(got[core], want, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(got[core], want, rtol=1e-12, atol=1e-12)
 
 
 @pytest.mark.parametrize("k,shape", [(2, (5, 6, 7)), (4, (6, 7, 5)), (8, (7, 5, 6)),

@@ -51,30 +51,30 @@ def test_weights_exact_on_polynomials(oracle_mod, k):
             assert err >= abs(lead) / 2, (k, float(err), float(lead))
 
 
-def _read_listing2():
-    path = os.path.join(os.path.dirname(__file__), "golden", "listing2_k2.txt")
+def _read_eq1_lap_rows():
+    path = os.path.join(os.path.dirname(__file__), "golden", "eq1_k2_damped.txt")
     rows = []
     with open(path) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
-            if line:
-                field, dx, dy, dz, sign, p, factor, scale = line.split()
-                rows.append((field, int(dx), int(dy), int(dz), int(sign), int(p), factor,
-                             float(scale)))
+            if line and line.split()[0] == "lap":
+                _, _, dx, dy, dz, sign, scale, _, _ = line.split()
+                rows.append(((int(dx), int(dy), int(dz)), int(sign) * float(scale)))
     return rows
 
 
-def test_weights_k2_match_listing2(oracle_mod):
-    """Listing 2 (k=2, h=1): each of the six neighbours enters with dt^3 and the
-    centre with -6 dt^3 in front of u, i.e. c_1 = 1 and 3*c_0 = -6."""
-    rows = _read_listing2()
-    nb = [r for r in rows if r[0] == "u" and (r[1], r[2], r[3]) != (0, 0, 0)]
-    centre = [r for r in rows if r[0] == "u" and (r[1], r[2], r[3]) == (0, 0, 0) and r[5] == 3]
+def test_weights_k2_match_three_point_laplacian(oracle_mod):
+    """Space order 2 (h = 1): the residual's -lap(u) rows give each of the six
+    neighbours -1 and the centre +6, i.e. c_1 = 1 and 3*c_0 = -6 (the same 1 and
+    -6 that Listing 2, Sec. 2.1, multiplies by dt^3)."""
+    rows = _read_eq1_lap_rows()
+    nb = [c for off, c in rows if off != (0, 0, 0)]
+    centre = [c for off, c in rows if off == (0, 0, 0)]
     assert len(nb) == 6 and len(centre) == 1
     c = oracle_mod.fd_weights(2)
-    for r_ in nb:
-        assert r_[4] * r_[7] == c[1]
-    assert centre[0][4] * centre[0][7] == 3 * c[0]
+    for v in nb:
+        assert -v == c[1]
+    assert -centre[0] == 3 * c[0]
 
 
 @pytest.mark.parametrize("k", [2, 4, 8, 12, 16])
