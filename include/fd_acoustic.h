@@ -415,6 +415,74 @@ int fd_batch_synchronize(fd_batch *b);
 /* Free every shot and the batch. NULL is accepted. */
 int fd_batch_destroy(fd_batch *b);
 
+/* ---- slabs: one shot split along x ---------------------------------------- */
+/* The paper's OPS backend partitions a block across a distributed-memory set
+ * of processes (Sec. 3, Devito-OPS integration, item (vii): ops_partition),
+ * and Devito exchanges halos between such subdomains, overlapping the
+ * exchange with computation (Sec. 5). A slab is that subdomain for this step:
+ * the planes [x0, x1) (computational-domain indices along x, the slowest axis)
+ * of one shot, with r = k/2 ghost planes below x0 (if x0 > 0) and above x1 (if
+ * x1 < N_x) that hold the neighbouring slabs' values. A step updates only the
+ * slab's own planes; its stencil reads the ghost planes, which the caller
+ * fills between steps by copying r planes from each neighbour
+ * (fd_slab_exchange, or the pointers of fd_slab_exchange_ptrs with any
+ * transport). With the ghosts exchanged every step, every point gets the
+ * same arithmetic on the same inputs as in the undivided shot: the slabs'
+ * planes equal fd_forward's bit for bit.
+ *
+ * A slab is an fd_handle: fd_set_model (arrays over the slab's buffer: its
+ * planes plus ghosts, C-order [x][y][z], N_x = x1 - x0 + ghosts; eta is
+ * REQUIRED, since the default profile depends on the whole model),
+ * fd_inject (INTERIOR coordinates of the whole shot; a source outside the
+ * slab's own planes is ignored, so every slab may be given every source; at
+ * most 4 per slab), fd_read_wavefield (the buffer, ghosts included),
+ * fd_get_dims, fd_reset, fd_get_step, fd_load_state, fd_set_stream and
+ * fd_destroy work as for a shot. fd_forward and the other forward paths,
+ * receivers and off-grid sources return FD_ENOTSUP: a slab advances through
+ * fd_slab_step. FP32 storage, the TMA kernel, zero boundary (FD_ENOTSUP
+ * otherwise); every slab needs at least k/2 own planes (FD_EINVAL). The
+ * buffers live on the device current at creation. */
+
+#define FD_SLAB_BOUNDARY 1 /* the own planes within r of a neighbour (they read ghost planes) */
+#define FD_SLAB_INTERIOR 2 /* the other own planes; then the step counter advances          */
+#define FD_SLAB_ALL 3      /* both                                                          */
+
+/* Create the slab of planes [x0, x1) of an nx*ny*nz (+ nbl layer) shot; the
+ * other arguments as fd_acoustic_create_ex. FD_EINVAL for x0 < 0, x1 <= x0,
+ * x1 > N_x or fewer than k/2 planes. */
+int fd_slab_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl, int x0, int x1,
+                   const fd_options *opt, fd_handle **out);
+
+/* The slab's own planes [*x0, *x1) in domain indices and its ghost plane
+ * counts (0 or k/2 each; any pointer may be NULL). A whole shot reports
+ * [0, N_x) and no ghosts. */
+int fd_slab_info(fd_handle *hd, int *x0, int *x1, int *ghost_lo, int *ghost_hi);
+
+/* Queue part of one time step on the slab's stream. A step is
+ * FD_SLAB_BOUNDARY then FD_SLAB_INTERIOR (or FD_SLAB_ALL). Between two steps
+ * the ghost planes of the level the step wrote must be filled; the
+ * boundary part writes every plane a neighbour needs, so the exchange can run
+ * while the interior part computes (overlap of communication with
+ * computation). The boundary part of step n+1 reads the ghosts: order the
+ * exchange before it (stream order or events). FD_ESTATE without a model. */
+int fd_slab_step(fd_handle *hd, int part);
+
+/* Device pointers for the exchange, in the buffer of `level` (0: u^n, the
+ * newest level; 1: the other buffer, which the running step writes: between
+ * FD_SLAB_BOUNDARY and FD_SLAB_INTERIOR the new values are at level 1, after
+ * the step at level 0): send_lo / send_hi = the first / last r own planes
+ * (to the lower / upper neighbour's ghosts), recv_lo / recv_hi = the ghost
+ * planes below / above; NULL where the slab has no neighbour. *bytes = r
+ * planes (r * N_y * pz * 4; pz the padded row pitch). Any output may be NULL. */
+int fd_slab_exchange_ptrs(fd_handle *hd, int level, void **send_lo, void **send_hi, void **recv_lo,
+                          void **recv_hi, size_t *bytes);
+
+/* Copy the planes of `from` that its x-neighbour `to` needs into `to`'s ghost
+ * planes, both at `level`, queued on `stream` (a cudaStream_t; the slabs may
+ * live on different devices: a peer copy). FD_EINVAL when the slabs are not
+ * neighbours of one shot. */
+int fd_slab_exchange(fd_handle *from, fd_handle *to, int level, void *stream);
+
 /* ---- allocation-free stepping -------------------------------------------- */
 
 /* nt time steps on CALLER-OWNED device buffers, allocating no device memory.

@@ -33,6 +33,7 @@ FD_STORAGE_F32, FD_STORAGE_BF16, FD_STORAGE_F16 = 0, 1, 2
 FD_FORM_FACTORED, FD_FORM_EXPANDED = 0, 1
 FD_KERNEL_AUTO, FD_KERNEL_STREAM, FD_KERNEL_NAIVE, FD_KERNEL_TMA = 0, 1, 2, 3
 FD_BOUNDARY_ZERO, FD_BOUNDARY_PERIODIC = 0, 1
+FD_SLAB_BOUNDARY, FD_SLAB_INTERIOR, FD_SLAB_ALL = 1, 2, 3
 
 ERROR_NAMES = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ERANGE", -3: "FD_EUNSTABLE", -4: "FD_ENOMEM",
                -5: "FD_ECUDA", -6: "FD_ENONFINITE", -7: "FD_ETIMEOUT", -8: "FD_ESTATE",
@@ -99,6 +100,13 @@ _SIGNATURES = {
     "fd_forward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _i, _vp, _vp, _i,
                                ctypes.c_longlong, _i, _vp, _fp]),
     "fd_shot_device_bytes": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "fd_slab_create": (_i, [_i, _i, _i, _i, _d, _d, _i, _i, _i, ctypes.POINTER(fd_options),
+                            ctypes.POINTER(_vp)]),
+    "fd_slab_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
+    "fd_slab_step": (_i, [_vp, _i]),
+    "fd_slab_exchange_ptrs": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)]),
+    "fd_slab_exchange": (_i, [_vp, _vp, _i, _vp]),
     "fd_batch_create": (_i, [_i, _d, ctypes.POINTER(fd_options), ctypes.POINTER(_vp)]),
     "fd_batch_add": (_i, [_vp, _i, _i, _i, _i, _d, _vp, _vp, _ip]),
     "fd_batch_inject": (_i, [_vp, _i, _i, _i, _i, _vp, _i]),
@@ -374,6 +382,39 @@ def fd_shot_device_bytes(nx, ny, nz, nbl, storage) -> int:
     _check(lib().fd_shot_device_bytes(nx, ny, nz, nbl, storage, ctypes.byref(v)),
            "fd_shot_device_bytes")
     return v.value
+
+
+def fd_slab_create(nx, ny, nz, space_order, h, dt, nbl, x0, x1, opt: fd_options | None = None) -> int:
+    out = _vp()
+    _check(lib().fd_slab_create(nx, ny, nz, space_order, h, dt, nbl, x0, x1,
+                                ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)),
+           "fd_slab_create")
+    return out.value
+
+
+def fd_slab_info(hd):
+    """(x0, x1, ghost_lo, ghost_hi): own planes [x0, x1) in domain indices, ghost counts."""
+    v = [_i() for _ in range(4)]
+    _check(lib().fd_slab_info(hd, *[ctypes.byref(x) for x in v]), "fd_slab_info")
+    return tuple(x.value for x in v)
+
+
+def fd_slab_step(hd, part: int = FD_SLAB_ALL):
+    _check(lib().fd_slab_step(hd, part), "fd_slab_step")
+
+
+def fd_slab_exchange_ptrs(hd, level: int):
+    """(send_lo, send_hi, recv_lo, recv_hi, bytes): device addresses (None where
+    the slab has no neighbour) in the buffer of `level`."""
+    v = [_vp() for _ in range(4)]
+    n = ctypes.c_size_t()
+    _check(lib().fd_slab_exchange_ptrs(hd, level, *[ctypes.byref(x) for x in v], ctypes.byref(n)),
+           "fd_slab_exchange_ptrs")
+    return tuple(x.value for x in v) + (n.value,)
+
+
+def fd_slab_exchange(src, dst, level: int, stream_ptr: int | None):
+    _check(lib().fd_slab_exchange(src, dst, level, stream_ptr), "fd_slab_exchange")
 
 
 def fd_batch_create(space_order, h, opt: fd_options | None = None) -> int:

@@ -207,6 +207,13 @@ struct fd_handle {
         TmaMaps maps;
     };
     std::vector<TbMaps> tb_maps;
+    // slab of a shot split along x (fd_slab_create): the buffers hold planes
+    // [x_off, x_off + Nx) of a domain of Nx_glob planes; the step updates local planes
+    // [x_lo, x_hi) and reads ghost_lo / ghost_hi planes of the neighbours' data below
+    // and above them. An ordinary handle is its own single slab.
+    bool slab = false;
+    int device = 0;  // the CUDA device the buffers live on (current at creation)
+    int x_off = 0, Nx_glob = 0, x_lo = 0, x_hi = 0, ghost_lo = 0, ghost_hi = 0;
     // receivers: 8 (pitched offset, weight) pairs each; traces [n_rec][rec_nt_max]
     int n_rec = 0, rec_nt_max = 0;
     long long rec_step0 = 0;
@@ -237,6 +244,8 @@ StepArgs make_args(const fd_handle *hd, long long step, int cur) {
     a.pz = hd->pz;
     a.plane = hd->plane;
     a.x_block = hd->x_block > 0 ? hd->x_block : hd->Nx;
+    a.x_lo = hd->x_lo;
+    a.x_hi = hd->x_hi;
     a.bx0 = hd->box[0];
     a.bx1 = hd->box[1];
     a.by0 = hd->box[2];
@@ -572,6 +581,8 @@ int update_src_bound(fd_handle *hd) {
 // form's per-point coefficients. On failure the handle has no model until a
 // valid one is set.
 int set_model_common(fd_handle *hd, const float *m, const float *eta, cudaMemcpyKind kind) {
+    if (hd->slab && !eta)
+        return fail(FD_EINVAL, "a slab needs an explicit eta (the default profile depends on the whole model)");
     hd->has_model = false;
     const size_t row_bytes = size_t(hd->Nz) * sizeof(float);
     const size_t pitch = size_t(hd->pz) * sizeof(float);
@@ -581,7 +592,7 @@ int set_model_common(fd_handle *hd, const float *m, const float *eta, cudaMemcpy
     const ModelCheck init{0u, 0u, 0x7f800000u, 0u};
     FD_CUDA(cudaMemcpyAsync(hd->d_check, &init, sizeof init, cudaMemcpyHostToDevice, hd->stream));
     FD_CUDA(launch_model_check(hd->f1, eta ? hd->f2 : nullptr, hd->Nx, hd->Ny, hd->Nz, hd->pz, hd->nbl,
-                               hd->d_check, hd->stream));
+                               hd->x_off, hd->Nx_glob, hd->d_check, hd->stream));
     ModelCheck chk;
     FD_CUDA(cudaMemcpyAsync(&chk, hd->d_check, sizeof chk, cudaMemcpyDeviceToHost, hd->stream));
     FD_CUDA(cudaStreamSynchronize(hd->stream));
@@ -603,7 +614,9 @@ int set_model_common(fd_handle *hd, const float *m, const float *eta, cudaMemcpy
     }
     const int lo = hd->nbl;
     if (interior_zero) {
-        const int b[6] = {lo, hd->Nx - lo, lo, hd->Ny - lo, lo, hd->Nz - lo};
+        // the interior box in local planes (a slab sees a window of the domain's planes)
+        const int bx0 = std::max(0, lo - hd->x_off), bx1 = std::min(hd->Nx, hd->Nx_glob - lo - hd->x_off);
+        const int b[6] = {bx0, std::max(bx0, bx1), lo, hd->Ny - lo, lo, hd->Nz - lo};
         std::memcpy(hd->box, b, sizeof b);
     } else {
         std::memset(hd->box, 0, sizeof hd->box);
@@ -739,8 +752,17 @@ int fd_dt_max(int space_order, double h, double vmax, double *out) {
     return FD_OK;
 }
 
+static int create_handle(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                         const fd_options *opt_in, int slab_x0, int slab_x1, fd_handle **out);
+
 int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                           const fd_options *opt_in, fd_handle **out) {
+    return create_handle(nx, ny, nz, space_order, h, dt, nbl, opt_in, -1, -1, out);
+}
+
+// A whole shot (slab_x0 < 0) or the slab of planes [slab_x0, slab_x1) of it.
+static int create_handle(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
+                         const fd_options *opt_in, int slab_x0, int slab_x1, fd_handle **out) {
     if (!out) return fail(FD_EINVAL, "out is NULL");
     *out = nullptr;
     fd_options opt;
@@ -773,6 +795,18 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     if (!tile_ok(kernel, opt.storage, opt.form, space_order / 2, opt.tile_z, opt.tile_y))
         return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
+    const bool slab = slab_x0 >= 0;
+    int ghost_lo = 0, ghost_hi = 0;
+    if (slab) {
+        if (opt.storage != kF32) return fail(FD_ENOTSUP, "slabs use FP32 storage (16-bit scales are per shot)");
+        if (kernel != kTma || opt.boundary != FD_BOUNDARY_ZERO)
+            return fail(FD_ENOTSUP, "slabs run on the TMA kernel with the zero boundary");
+        if (slab_x1 > Nx || slab_x1 - slab_x0 < space_order / 2)
+            return fail(FD_EINVAL, "slab planes [%d, %d) must lie in [0, %lld) and number at least k/2 = %d",
+                        slab_x0, slab_x1, Nx, space_order / 2);
+        ghost_lo = slab_x0 > 0 ? space_order / 2 : 0;
+        ghost_hi = slab_x1 < Nx ? space_order / 2 : 0;
+    }
 
     fd_handle *hd = new fd_handle();
     hd->nx = nx;
@@ -786,6 +820,17 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
     hd->Nx = int(Nx);
     hd->Ny = int(Ny);
     hd->Nz = int(Nz);
+    hd->Nx_glob = int(Nx);
+    hd->x_hi = int(Nx);
+    if (slab) {
+        hd->slab = true;
+        hd->ghost_lo = ghost_lo;
+        hd->ghost_hi = ghost_hi;
+        hd->x_off = slab_x0 - ghost_lo;
+        hd->Nx = (slab_x1 - slab_x0) + ghost_lo + ghost_hi;
+        hd->x_lo = ghost_lo;
+        hd->x_hi = ghost_lo + (slab_x1 - slab_x0);
+    }
     hd->opt = opt;
     hd->kernel = kernel;
     hd->pz = int((Nz + 63) / 64 * 64);  // 128-byte rows for 16-bit and 256-byte rows for FP32
@@ -797,6 +842,7 @@ int fd_acoustic_create_ex(int nx, int ny, int nz, int space_order, double h, dou
         fd_destroy(hd);
         return fail(code, "%s", msg);
     };
+    if (cudaGetDevice(&hd->device) != cudaSuccess) return bail(FD_ECUDA, "no current CUDA device");
     if (cudaStreamCreateWithFlags(&hd->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(FD_ECUDA, "cudaStreamCreate failed");
     hd->stream = hd->own_stream;
@@ -850,7 +896,11 @@ int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int n
                     hd->ny, hd->nz);
     for (int i = 0; i < nt; ++i)
         if (!std::isfinite(wavelet[i])) return fail(FD_EINVAL, "wavelet[%d] is not finite", i);
-    Source s{ix + hd->nbl, iy + hd->nbl, iz + hd->nbl, std::vector<float>(wavelet, wavelet + nt)};
+    const int lx = ix + hd->nbl - hd->x_off;  // local plane (a slab keeps only its own planes' sources)
+    if (hd->slab && (lx < hd->x_lo || lx >= hd->x_hi)) return FD_OK;
+    if (hd->slab && int(hd->sources.size()) >= kFusedSources)
+        return fail(FD_ENOTSUP, "a slab takes at most %d sources in its planes", kFusedSources);
+    Source s{lx, iy + hd->nbl, iz + hd->nbl, std::vector<float>(wavelet, wavelet + nt)};
     hd->sources.push_back(std::move(s));
     int rc = upload_sources(hd);
     if (rc != FD_OK) {
@@ -863,6 +913,7 @@ int fd_inject(fd_handle *hd, int ix, int iy, int iz, const float *wavelet, int n
 
 int fd_inject_at(fd_handle *hd, double x, double y, double z, const float *wavelet, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (hd->slab) return fail(FD_ENOTSUP, "slabs take integer-node sources and no receivers");
     if (!wavelet || nt < 1) return fail(FD_EINVAL, "wavelet is NULL or nt < 1");
     if (!interior_point_ok(hd, x, y, z))
         return fail(FD_ERANGE, "source (%g,%g,%g) outside the [0,%d]x[0,%d]x[0,%d] interior", x, y, z, hd->nx - 1,
@@ -890,6 +941,7 @@ int fd_inject_at(fd_handle *hd, double x, double y, double z, const float *wavel
 
 int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (hd->slab) return fail(FD_ENOTSUP, "slabs take integer-node sources and no receivers");
     if (n < 0 || (n > 0 && (!xyz || nt_max < 1))) return fail(FD_EINVAL, "bad receiver count, positions or nt_max");
     if (n > 0 && (long long)n * nt_max > (1LL << 31))
         return fail(FD_EINVAL, "n * nt_max above 2^31 samples");
@@ -965,6 +1017,7 @@ static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, con
                              int segment, float *grad_out, float *syn_out, double *misfit) {
     if (!hd || nrec < 1 || !rec_xyz || !d_obs || nt < 1 || !grad_out || !misfit || segment < 0)
         return fail(FD_EINVAL, "bad receivers, data, nt, segment or output pointers");
+    if (hd->slab) return fail(FD_ENOTSUP, "the FWI gradient runs on whole shots, not slabs");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_fwi_gradient before fd_set_model");
     if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->kernel != kTma)
         return fail(FD_ENOTSUP, "the FWI gradient runs on FP32 storage, factored form, TMA kernel");
@@ -1245,6 +1298,7 @@ static int tb_maps_for(fd_handle *hd, const void *u, const void *up, const TmaMa
 
 int fd_forward_two_step(fd_handle *hd, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (hd->slab) return fail(FD_ENOTSUP, "a slab advances through fd_slab_step, with its halo exchange");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_two_step before fd_set_model");
     if (hd->opt.storage != kF32 || hd->opt.form != kFactored || hd->r > 2 || hd->n_rec > 0 ||
@@ -1442,6 +1496,7 @@ static int flow_prepare(fd_handle *hd, int *nt);
 
 int fd_forward(fd_handle *hd, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (hd->slab) return fail(FD_ENOTSUP, "a slab advances through fd_slab_step, with its halo exchange");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward before fd_set_model");
     if (nt == 0) return FD_OK;
@@ -1681,6 +1736,7 @@ static int flow_prepare(fd_handle *hd, int *nt) {
 
 int fd_forward_flow(fd_handle *hd, int nt) {
     if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (hd->slab) return fail(FD_ENOTSUP, "a slab advances through fd_slab_step, with its halo exchange");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_flow before fd_set_model");
     if (hd->opt.storage != kF32 || hd->kernel != kTma || hd->n_rec > 0 ||
@@ -1840,6 +1896,100 @@ int fd_last_forward_ms(fd_handle *hd, float *ms) {
     if (!hd->timed) return fail(FD_ESTATE, "no fd_forward timed yet");
     FD_CUDA(cudaEventSynchronize(hd->ev1));
     FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
+    return FD_OK;
+}
+
+// ---- slabs: one shot split along x ------------------------------------------
+
+int fd_slab_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl, int x0, int x1,
+                   const fd_options *opt, fd_handle **out) {
+    if (x0 < 0 || x1 <= x0) {
+        if (out) *out = nullptr;
+        return fail(FD_EINVAL, "slab planes [%d, %d): need 0 <= x0 < x1", x0, x1);
+    }
+    return create_handle(nx, ny, nz, space_order, h, dt, nbl, opt, x0, x1, out);
+}
+
+int fd_slab_info(fd_handle *hd, int *x0, int *x1, int *ghost_lo, int *ghost_hi) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (x0) *x0 = hd->x_off + hd->x_lo;
+    if (x1) *x1 = hd->x_off + hd->x_hi;
+    if (ghost_lo) *ghost_lo = hd->ghost_lo;
+    if (ghost_hi) *ghost_hi = hd->ghost_hi;
+    return FD_OK;
+}
+
+int fd_slab_step(fd_handle *hd, int part) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (!hd->slab) return fail(FD_ENOTSUP, "fd_slab_step takes a slab (fd_slab_create)");
+    if (part < FD_SLAB_BOUNDARY || part > FD_SLAB_ALL) return fail(FD_EINVAL, "part must be 1, 2 or 3");
+    if (!hd->has_model) return fail(FD_ESTATE, "fd_slab_step before fd_set_model");
+    int rc = ensure_step_tuned(hd);
+    if (rc != FD_OK) return rc;
+    const int r = hd->r, lo = hd->x_lo, hi = hd->x_hi;
+    // [lo, b0) reads the low ghost planes, [b1, hi) the high ones, [b0, b1) neither
+    const int b0 = hd->ghost_lo > 0 ? std::min(lo + r, hi) : lo;
+    const int b1 = std::max(b0, hd->ghost_hi > 0 ? std::max(hi - r, lo) : hi);
+    const StepArgs a = make_args(hd, hd->step, hd->cur);
+    const TmaMaps &map = hd->tmaps[hd->cur];  // u^n in ubuf[cur]
+    const bool check = check_enabled(hd);
+    auto run = [&](int xa, int xb) -> cudaError_t {
+        if (xb <= xa) return cudaSuccess;
+        StepArgs b = a;
+        b.x_lo = xa;
+        b.x_hi = xb;
+        return launch_tma_step(hd->r, hd->opt.form, kF32, hd->tile_z, hd->tile_y, map, b, check, hd->stream);
+    };
+    if (part & FD_SLAB_BOUNDARY) {
+        FD_CUDA(run(lo, b0));
+        FD_CUDA(run(b1, hi));
+    }
+    if (part & FD_SLAB_INTERIOR) {
+        FD_CUDA(run(b0, b1));
+        hd->step += 1;
+        hd->cur ^= 1;
+    }
+    return FD_OK;
+}
+
+int fd_slab_exchange_ptrs(fd_handle *hd, int level, void **send_lo, void **send_hi, void **recv_lo,
+                          void **recv_hi, size_t *bytes) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    if (level != 0 && level != 1) return fail(FD_EINVAL, "level must be 0 or 1");
+    char *buf = static_cast<char *>(hd->ubuf[level == 0 ? hd->cur : hd->cur ^ 1]);
+    const size_t pb = size_t(hd->plane) * sizeof(float);
+    if (send_lo) *send_lo = hd->ghost_lo > 0 ? buf + size_t(hd->x_lo) * pb : nullptr;
+    if (send_hi) *send_hi = hd->ghost_hi > 0 ? buf + size_t(hd->x_hi - hd->r) * pb : nullptr;
+    if (recv_lo) *recv_lo = hd->ghost_lo > 0 ? buf : nullptr;
+    if (recv_hi) *recv_hi = hd->ghost_hi > 0 ? buf + size_t(hd->x_hi) * pb : nullptr;
+    if (bytes) *bytes = size_t(hd->r) * pb;
+    return FD_OK;
+}
+
+int fd_slab_exchange(fd_handle *from, fd_handle *to, int level, void *stream) {
+    if (!from || !to) return fail(FD_EINVAL, "handle is NULL");
+    if (!from->slab || !to->slab) return fail(FD_ENOTSUP, "fd_slab_exchange takes two slabs");
+    if (level != 0 && level != 1) return fail(FD_EINVAL, "level must be 0 or 1");
+    if (from->Ny != to->Ny || from->Nz != to->Nz || from->pz != to->pz || from->r != to->r ||
+        from->Nx_glob != to->Nx_glob)
+        return fail(FD_EINVAL, "the slabs belong to different shots");
+    void *s_lo, *s_hi, *r_lo, *r_hi;
+    size_t bytes = 0;
+    fd_slab_exchange_ptrs(from, level, &s_lo, &s_hi, nullptr, nullptr, &bytes);
+    fd_slab_exchange_ptrs(to, level, nullptr, nullptr, &r_lo, &r_hi, nullptr);
+    const int from_end = from->x_off + from->x_hi, to_end = to->x_off + to->x_hi;
+    const void *src = nullptr;
+    void *dst = nullptr;
+    if (from_end == to->x_off + to->x_lo && s_hi && r_lo) {
+        src = s_hi;  // `to` is the right neighbour: its low ghosts
+        dst = r_lo;
+    } else if (to_end == from->x_off + from->x_lo && s_lo && r_hi) {
+        src = s_lo;  // `to` is the left neighbour: its high ghosts
+        dst = r_hi;
+    } else {
+        return fail(FD_EINVAL, "the slabs are not x-neighbours");
+    }
+    FD_CUDA(cudaMemcpyPeerAsync(dst, to->device, src, from->device, bytes, static_cast<cudaStream_t>(stream)));
     return FD_OK;
 }
 

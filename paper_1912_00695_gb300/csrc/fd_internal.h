@@ -63,6 +63,8 @@ struct StepArgs {
     int pz;             // row pitch in elements (multiple of 32)
     long long plane;    // elements per x-plane = Ny * pz
     int x_block;        // planes per CTA (streaming kernel)
+    int x_lo, x_hi;     // planes the TMA step kernel updates: [x_lo, x_hi) (a slab's own
+                        // planes; [0, Nx) otherwise). Planes outside are read, not written.
     // box where f2 == 0 (damping absent): [bx0,bx1) x [by0,by1) x [bz0,bz1)
     int bx0, bx1, by0, by1, bz0, bz1;
     float coef[kMaxRadius + 1];  // factored: c_j/h^2; expanded: c_j dt^2/h^2 (j >= 1;
@@ -179,8 +181,10 @@ struct ModelCheck {
     unsigned min_m_bits;            // min m as float bits (positive floats order as uints)
     unsigned eta_interior_nonzero;  // eta != 0 somewhere inside the interior box
 };
+// x_off: global plane of local plane 0 and Nx_glob the global extent (a slab's
+// window onto the domain; 0 and Nx otherwise), for the interior box test.
 cudaError_t launch_model_check(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
-                               ModelCheck *out, cudaStream_t s);
+                               int x_off, int Nx_glob, ModelCheck *out, cudaStream_t s);
 cudaError_t launch_default_damping(const float *m, float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
                                    float dmax, cudaStream_t s);
 cudaError_t launch_prepare_factored(float *f1, float *f2, long long n_pitched, float half_dt, float dt2,

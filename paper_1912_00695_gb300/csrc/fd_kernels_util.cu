@@ -443,7 +443,7 @@ __global__ void init_scales_kernel(LevelScales *ls) {
 // One pass over the model: validation flags, min(m), and whether eta vanishes
 // inside the interior box [nbl, N - nbl)^3 (the kernels then skip its loads there).
 __global__ void model_check_kernel(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
-                                   ModelCheck *out) {
+                                   int x_off, int Nx_glob, ModelCheck *out) {
     const long long n = (long long)Nx * Ny * Nz;
     unsigned bad_m = 0, bad_eta = 0, inner = 0, mn = 0x7f800000u;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -458,7 +458,9 @@ __global__ void model_check_kernel(const float *m, const float *eta, int Nx, int
         if (eta) {
             const float e = eta[p];
             if (!(e >= 0.0f) || !isfinite(e)) bad_eta = 1;
-            if (e != 0.0f && x >= nbl && x < Nx - nbl && y >= nbl && y < Ny - nbl && z >= nbl && z < Nz - nbl)
+            const int xg = x + x_off;  // global plane
+            if (e != 0.0f && xg >= nbl && xg < Nx_glob - nbl && y >= nbl && y < Ny - nbl && z >= nbl &&
+                z < Nz - nbl)
                 inner = 1;
         }
     }
@@ -515,8 +517,8 @@ __global__ void prepare_factored_kernel(float *f1, float *f2, long long n, float
 }  // namespace
 
 cudaError_t launch_model_check(const float *m, const float *eta, int Nx, int Ny, int Nz, int pz, int nbl,
-                               ModelCheck *out, cudaStream_t s) {
-    model_check_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, out);
+                               int x_off, int Nx_glob, ModelCheck *out, cudaStream_t s) {
+    model_check_kernel<<<1216, 256, 0, s>>>(m, eta, Nx, Ny, Nz, pz, nbl, x_off, Nx_glob, out);
     return counted(cudaGetLastError(), s);
 }
 

@@ -621,10 +621,10 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
     unsigned char *ring = tma_ring_init<R>(smem_dyn);
     const ScaleState sc = read_scales<T>(a);
     if (a.rec_sample >= 0 && a.n_rec > 0) tma_sample_receivers<T>(a, sc.s_u);
-    const int xb = blockIdx.z * a.x_block;
+    const int xb = a.x_lo + blockIdx.z * a.x_block;
     int g = 0;
     TmaAcc acc;
-    if (tma_segment<R, FORM, LZ, W, T>(&maps, a, sc, blockIdx.x, blockIdx.y, xb, min(xb + a.x_block, a.Nx), ring,
+    if (tma_segment<R, FORM, LZ, W, T>(&maps, a, sc, blockIdx.x, blockIdx.y, xb, min(xb + a.x_block, a.x_hi), ring,
                                        g, acc) &&
         check) {
         tma_finish<T>(acc, sc);
@@ -684,7 +684,9 @@ cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaS
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY, (a.Nx + a.x_block - 1) / a.x_block);
+    if (a.x_hi <= a.x_lo) return cudaSuccess;  // no planes to update
+    const dim3 grid((a.Nz + G::TZ - 1) / G::TZ, (a.Ny + G::TY - 1) / G::TY,
+                    (a.x_hi - a.x_lo + a.x_block - 1) / a.x_block);
     kernel<<<grid, 32 * W, G::SMEM_BYTES, s>>>(maps, a, check ? 1 : 0);
     return cudaGetLastError();
 }
