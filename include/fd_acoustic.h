@@ -104,6 +104,9 @@ typedef struct fd_options {
     int check_finite;  /* 1 = fold a max|u| reduction into each step so that
                           fd_read_wavefield/fd_status report FD_ENONFINITE          */
     int boundary;      /* FD_BOUNDARY_*                                            */
+    int rows;          /* TMA kernel: y rows per thread, 1 or 2 (space orders <= 16;
+                          two rows share the y-tap loads: tiles 32x32 and 64x16,
+                          tile_y counting every row); 0 = autotune                  */
 } fd_options;
 
 typedef struct fd_handle fd_handle;
@@ -335,6 +338,14 @@ int fd_get_dims(fd_handle *hd, int *Nx, int *Ny, int *Nz);
  * tile_z, tile_y, x_block): what the autotuner picked or the options forced
  * (zeros before the first fd_forward when the autotuner still has to run). */
 int fd_get_config(fd_handle *hd, int *kernel, int *tile_z, int *tile_y, int *x_block);
+
+/* The schedule fd_forward runs for this handle: *rows = y rows per thread of
+ * the TMA kernel; *schedule = 0 one launch per step, 1 the flow schedule (one
+ * persistent launch per call), 2 two steps per launch; *flow_x_block = the
+ * flow schedule's x-chunk (0 until chosen). Zeros before the first fd_forward
+ * when the autotuner still has to run. Any pointer may be NULL. (The paper has
+ * no counterpart: launch shapes are this library's.) */
+int fd_get_schedule(fd_handle *hd, int *rows, int *schedule, int *flow_x_block);
 
 /* Device time of the step kernels queued by the last fd_forward (or
  * fd_forward_two_step), in ms, measured by CUDA events on the handle's stream

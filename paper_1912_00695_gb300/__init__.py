@@ -21,7 +21,7 @@ from ._abi import (FD_BOUNDARY_PERIODIC, FD_BOUNDARY_ZERO, FD_EFULL, FD_EINVAL, 
                    FD_KERNEL_AUTO, FD_KERNEL_NAIVE, FD_KERNEL_STREAM, FD_KERNEL_TMA, FD_OK, FD_STORAGE_BF16,
                    FD_STORAGE_F16, FD_STORAGE_F32, FdError, fd_acoustic_create,
                    fd_acoustic_create_ex, fd_clear_sources, fd_default_damping, fd_destroy, fd_dt_max, fd_fd_weights,
-                   fd_forward, fd_forward_flow, fd_forward_two_step, fd_get_config, fd_get_dims, fd_get_step, fd_inject, fd_inject_at,
+                   fd_forward, fd_forward_flow, fd_forward_two_step, fd_get_config, fd_get_dims, fd_get_schedule, fd_get_step, fd_inject, fd_inject_at,
                    fd_load_state, fd_read_traces, fd_set_receivers, fd_fwi_gradient,
                    fd_kernel_launches, fd_selftest_waits, fd_last_error, fd_last_forward_ms, fd_options, fd_options_default,
                    fd_read_wavefield, fd_read_wavefield_device, fd_reset, fd_set_model,
@@ -35,7 +35,7 @@ BOUNDARIES = {"zero": FD_BOUNDARY_ZERO, "periodic": FD_BOUNDARY_PERIODIC}
 
 
 def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x_block=0,
-            check_finite=True, boundary="zero") -> fd_options:
+            check_finite=True, boundary="zero", rows=0) -> fd_options:
     o = fd_options_default()
     o.storage = STORAGE[storage]
     o.form = FORMS[form]
@@ -45,6 +45,7 @@ def options(storage="f32", form="factored", kernel="auto", tile_z=0, tile_y=0, x
     o.x_block = int(x_block)
     o.check_finite = int(bool(check_finite))
     o.boundary = BOUNDARIES[boundary]
+    o.rows = int(rows)
     return o
 
 
@@ -268,6 +269,11 @@ class Shot:
     @property
     def config(self):
         return fd_get_config(self.handle)
+
+    @property
+    def schedule(self):
+        """(rows per thread, schedule 0 per-step / 1 flow / 2 two-step, flow x-chunk)."""
+        return fd_get_schedule(self.handle)
 
     def last_forward_ms(self) -> float:
         return fd_last_forward_ms(self.handle)

@@ -49,7 +49,7 @@ class FdError(RuntimeError):
 class fd_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("form", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("tile_y", ctypes.c_int), ("x_block", ctypes.c_int),
-                ("check_finite", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("check_finite", ctypes.c_int), ("boundary", ctypes.c_int), ("rows", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -90,6 +90,7 @@ _SIGNATURES = {
     "fd_get_step": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "fd_get_dims": (_i, [_vp, _ip, _ip, _ip]),
     "fd_get_config": (_i, [_vp, _ip, _ip, _ip, _ip]),
+    "fd_get_schedule": (_i, [_vp, _ip, _ip, _ip]),
     "fd_last_forward_ms": (_i, [_vp, _fp]),
     "fd_kernel_launches": (_i, [ctypes.POINTER(ctypes.c_longlong)]),
     "fd_selftest_waits": (_i, [ctypes.POINTER(ctypes.c_uint), _dp, _dp]),
@@ -312,6 +313,14 @@ def fd_get_config(hd):
     """(kernel, tile_z, tile_y, x_block) of the handle's step kernel."""
     v = [_i() for _ in range(4)]
     _check(lib().fd_get_config(hd, *[ctypes.byref(x) for x in v]), "fd_get_config")
+    return tuple(x.value for x in v)
+
+
+def fd_get_schedule(hd):
+    """(rows per thread, schedule: 0 per-step launches / 1 flow / 2 two steps per
+    launch, flow x-chunk) that fd_forward runs for the handle."""
+    v = [_i() for _ in range(3)]
+    _check(lib().fd_get_schedule(hd, *[ctypes.byref(x) for x in v]), "fd_get_schedule")
     return tuple(x.value for x in v)
 
 

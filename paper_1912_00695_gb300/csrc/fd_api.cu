@@ -61,7 +61,7 @@ struct GraphEntry {
 // Process-wide launch-shape cache:
 // (Nx, Ny, Nz, radius, storage, form, check, kernel) -> (tile_z, tile_y, x_block)
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int, int>> g_tune_cache;
 // two-step kernel: (Nx, Ny, Nz, radius) -> x_block
 std::map<std::tuple<int, int, int, int>, int> g_tb_cache;
 // flow schedule: (Nx, Ny, Nz, radius, form, tile_z, tile_y) -> (x_block, faster than per-step launches)
@@ -131,27 +131,38 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// (tile_z, tile_y) shapes the TMA kernel has for a storage/form.
-std::vector<std::pair<int, int>> tma_tiles(int storage, int form, int radius) {
-    if (radius > 8) {  // space orders 18-24: 32-wide tiles only
-        if (storage == kF32) return {{32, 32}, {32, 16}};
-        if (form == kFactored) return {{32, 16}};
+// Launch shapes of the TMA kernel: tile (z, y) and y rows per thread.
+struct TileShape {
+    int tz, ty, rows;
+};
+
+// The TMA kernel's shapes for a storage/form.
+std::vector<TileShape> tma_tiles(int storage, int form, int radius) {
+    if (radius > 8) {  // space orders 18-24: 32-wide tiles only, one row per thread
+        if (storage == kF32) return {{32, 32, 1}, {32, 16, 1}};
+        if (form == kFactored) return {{32, 16, 1}};
         return {};
     }
-    if (storage == kF32) return {{32, 32}, {64, 16}, {128, 8}, {32, 16}, {64, 8}};
-    if (form == kFactored) return {{32, 16}, {64, 8}};
+    if (storage == kF32)
+        return {{32, 32, 1}, {64, 16, 1}, {128, 8, 1}, {32, 16, 1}, {64, 8, 1}, {32, 32, 2}, {64, 16, 2}};
+    if (form == kFactored) return {{32, 16, 1}, {64, 8, 1}, {32, 32, 2}, {64, 16, 2}};
     return {};
 }
 
-// Valid (tile_z, tile_y) requests of each kernel (0 = any).
-bool tile_ok(int kernel, int storage, int form, int radius, int tz, int ty) {
-    if (kernel == kStream) return (tz == 0 || tz == 32) && (ty == 0 || ty == 4 || ty == 8 || ty == 16);
+bool shape_matches(const TileShape &p, int tz, int ty, int rows) {
+    return (tz == 0 || tz == p.tz) && (ty == 0 || ty == p.ty) && (rows == 0 || rows == p.rows);
+}
+
+// Valid (tile_z, tile_y, rows) requests of each kernel (0 = any).
+bool tile_ok(int kernel, int storage, int form, int radius, int tz, int ty, int rows) {
+    if (kernel == kStream)
+        return (tz == 0 || tz == 32) && (ty == 0 || ty == 4 || ty == 8 || ty == 16) && rows <= 1;
     if (kernel == kTma) {
         for (auto &p : tma_tiles(storage, form, radius))
-            if ((tz == 0 || tz == p.first) && (ty == 0 || ty == p.second)) return true;
+            if (shape_matches(p, tz, ty, rows)) return true;
         return false;
     }
-    return true;
+    return rows <= 1;
 }
 
 }  // namespace
@@ -168,6 +179,7 @@ struct fd_handle {
     size_t n_pitched = 0;
     fd_options opt{};
     int tile_z = 0, tile_y = 0, x_block = 0, kernel = kStream;
+    int rows = 1;  // y rows per thread of the TMA kernel
     TmaMaps tmaps[2];  // TMA kernel: maps of the step whose u^n is ubuf[0] / ubuf[1]
     void *ubuf[2] = {nullptr, nullptr};
     void *dbuf = nullptr;  // 16-bit storage: the increment d^n = u^n - u^{n-1}
@@ -293,19 +305,19 @@ cudaError_t sample_level(const fd_handle *hd, const void *u, long long level, cu
 
 // One step with the given launch shape; `map` holds the tensor maps of this step
 // (TMA kernel only).
-cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y,
+cudaError_t launch_kernel(const fd_handle *hd, const StepArgs &a, int kernel, int tile_z, int tile_y, int rows,
                           const TmaMaps *map, bool check, cudaStream_t s) {
     if (hd->opt.boundary == FD_BOUNDARY_PERIODIC) return launch_periodic_step(hd->r, hd->opt.form, a, check, s);
     if (kernel == kNaive) return launch_naive_step(hd->r, hd->opt.form, hd->opt.storage, a, check, s);
     if (kernel == kTma)
-        return launch_tma_step(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, *map, a, check, s);
+        return launch_tma_step(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, rows, *map, a, check, s);
     return launch_stream_step(hd->r, hd->opt.form, hd->opt.storage, tile_y, a, check, s);
 }
 
 cudaError_t enqueue_step(const fd_handle *hd, const StepArgs &a, cudaStream_t s) {
     const bool check = check_enabled(hd);
     const TmaMaps *map = a.u == hd->ubuf[0] ? &hd->tmaps[0] : &hd->tmaps[1];
-    cudaError_t e = launch_kernel(hd, a, hd->kernel, hd->tile_z, hd->tile_y, map, check, s);
+    cudaError_t e = launch_kernel(hd, a, hd->kernel, hd->tile_z, hd->tile_y, hd->rows, map, check, s);
     if (e != cudaSuccess) return e;
     const int ns = int(hd->sources.size());
     if (ns > kFusedSources)
@@ -339,9 +351,9 @@ int encode_box(const fd_handle *hd, const void *base, CUtensorMapDataType dtype,
 }
 
 // Maps of one step of the TMA kernel with u^n in `u` and u^{n-1} in `up`.
-int make_maps(const fd_handle *hd, const void *u, const void *up, int tile_z, int tile_y, TmaMaps *out) {
+int make_maps(const fd_handle *hd, const void *u, const void *up, int tile_z, int tile_y, int rows, TmaMaps *out) {
     int bw = 0, bh = 0, rz = 0;
-    if (!tma_box(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, &bw, &bh, &rz))
+    if (!tma_box(hd->r, hd->opt.form, hd->opt.storage, tile_z, tile_y, rows, &bw, &bh, &rz))
         return fail(FD_ENOTSUP, "no TMA tile %dx%d for this storage/form", tile_z, tile_y);
     const int es = int(elem_size(hd->opt.storage));
     const CUtensorMapDataType ut = hd->opt.storage == kF32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -359,7 +371,7 @@ int build_maps(fd_handle *hd) {
     if (hd->kernel != kTma) return FD_OK;
     for (int b = 0; b < 2; ++b) {
         const void *up = hd->opt.storage == kF32 ? hd->ubuf[b ^ 1] : hd->dbuf;
-        int rc = make_maps(hd, hd->ubuf[b], up, hd->tile_z, hd->tile_y, &hd->tmaps[b]);
+        int rc = make_maps(hd, hd->ubuf[b], up, hd->tile_z, hd->tile_y, hd->rows, &hd->tmaps[b]);
         if (rc != FD_OK) return rc;
     }
     return FD_OK;
@@ -373,20 +385,20 @@ int heuristic_x_block(const fd_handle *hd, int tile_z, int tile_y) {
     return (hd->Nx + chunks - 1) / chunks;
 }
 
-// Pick (tile_z, tile_y, x_block) for the handle's kernel by timing candidate
+// Pick (tile_z, tile_y, rows, x_block) for the handle's kernel by timing candidate
 // launch shapes. The candidates run on scratch wavefields, scale slots and
 // status word (zeroed, no sources), so the handle's own state is never touched.
 int autotune(fd_handle *hd) {
     const int kernel = hd->kernel;
-    const bool force_tile = hd->opt.tile_z > 0 || hd->opt.tile_y > 0, force_xb = hd->opt.x_block > 0;
-    std::vector<std::pair<int, int>> tiles;
+    const bool force_tile = hd->opt.tile_z > 0 || hd->opt.tile_y > 0 || hd->opt.rows > 0,
+               force_xb = hd->opt.x_block > 0;
+    std::vector<TileShape> tiles;
     if (kernel == kTma) {
         for (auto &p : tma_tiles(hd->opt.storage, hd->opt.form, hd->r))
-            if ((hd->opt.tile_z == 0 || hd->opt.tile_z == p.first) && (hd->opt.tile_y == 0 || hd->opt.tile_y == p.second))
-                tiles.push_back(p);
+            if (shape_matches(p, hd->opt.tile_z, hd->opt.tile_y, hd->opt.rows)) tiles.push_back(p);
     } else {
         for (int ty : {4, 8, 16})
-            if (hd->opt.tile_y == 0 || hd->opt.tile_y == ty) tiles.push_back({32, ty});
+            if (hd->opt.tile_y == 0 || hd->opt.tile_y == ty) tiles.push_back({32, ty, 1});
     }
     if (tiles.empty()) return fail(FD_ENOTSUP, "no tile shape matches the options");
     std::vector<int> xbs;
@@ -401,7 +413,7 @@ int autotune(fd_handle *hd) {
     }
     // TMA kernel: add the x_block whose CTA count (tiles x chunks) just fits the GPU's
     // resident CTA slots once, twice or three times
-    auto tile_xbs = [&](int tz, int ty) {
+    auto tile_xbs = [&](int tz, int ty, int rows) {
         std::vector<int> v = xbs;
         if (kernel != kTma || force_xb) return v;
         int dev = 0, sms = 0;
@@ -410,8 +422,8 @@ int autotune(fd_handle *hd) {
             cudaGetLastError();
             return v;
         }
-        const long long warps = (long long)tz * ty / 128;  // 4 points per thread
-        const long long slots = (long long)sms * std::max(1LL, kTmaWarpsPerSM / warps);
+        const long long warps = (long long)tz * ty / (128 * rows);  // 4 points per thread and row
+        const long long slots = (long long)sms * std::max(1LL, tma_warps_per_sm(hd->r, rows) / warps);
         const long long tiles = (long long)((hd->Nz + tz - 1) / tz) * ((hd->Ny + ty - 1) / ty);
         for (int waves = 1; waves <= 3; ++waves) {
             const long long chunks = slots * waves / tiles;  // chunks per tile that still fit
@@ -422,10 +434,14 @@ int autotune(fd_handle *hd) {
         }
         return v;
     };
-    if (tiles.size() == 1 && tile_xbs(tiles[0].first, tiles[0].second).size() == 1) {
-        hd->tile_z = tiles[0].first;
-        hd->tile_y = tiles[0].second;
-        hd->x_block = xbs[0];
+    auto take = [&](const TileShape &t, int xb) {
+        hd->tile_z = t.tz;
+        hd->tile_y = t.ty;
+        hd->rows = t.rows;
+        hd->x_block = xb;
+    };
+    if (tiles.size() == 1 && tile_xbs(tiles[0].tz, tiles[0].ty, tiles[0].rows).size() == 1) {
+        take(tiles[0], xbs[0]);
         return FD_OK;
     }
     auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.storage, hd->opt.form,
@@ -434,15 +450,13 @@ int autotune(fd_handle *hd) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            std::tie(hd->tile_z, hd->tile_y, hd->x_block) = it->second;
+            std::tie(hd->tile_z, hd->tile_y, hd->rows, hd->x_block) = it->second;
             return FD_OK;
         }
     }
     const char *env = std::getenv("FDGB_NO_TUNE");
     if (env && env[0] == '1') {
-        hd->tile_z = tiles[0].first;
-        hd->tile_y = tiles[0].second;
-        hd->x_block = force_xb ? xbs[0] : heuristic_x_block(hd, hd->tile_z, hd->tile_y);
+        take(tiles[0], force_xb ? xbs[0] : heuristic_x_block(hd, tiles[0].tz, tiles[0].ty));
         return FD_OK;
     }
     const size_t ub = hd->n_pitched * elem_size(hd->opt.storage);
@@ -456,9 +470,7 @@ int autotune(fd_handle *hd) {
         dev_free(s2, hd->stream);
         dev_free(aux, hd->stream);
         // not enough memory for scratch fields: take the first shape, heuristic x_block
-        hd->tile_z = tiles[0].first;
-        hd->tile_y = tiles[0].second;
-        hd->x_block = force_xb ? xbs[0] : heuristic_x_block(hd, hd->tile_z, hd->tile_y);
+        take(tiles[0], force_xb ? xbs[0] : heuristic_x_block(hd, tiles[0].tz, tiles[0].ty));
         return FD_OK;
     }
     LevelScales *ls = static_cast<LevelScales *>(aux);
@@ -483,15 +495,16 @@ int autotune(fd_handle *hd) {
     const bool check = check_enabled(hd);
     for (size_t ti = 0; ti < tiles.size() && e == cudaSuccess && rc == FD_OK; ++ti) {
         TmaMaps map;
-        if (kernel == kTma) rc = make_maps(hd, s0, s1, tiles[ti].first, tiles[ti].second, &map);
-        const std::vector<int> xbs = tile_xbs(tiles[ti].first, tiles[ti].second);
+        const TileShape &t = tiles[ti];
+        if (kernel == kTma) rc = make_maps(hd, s0, s1, t.tz, t.ty, t.rows, &map);
+        const std::vector<int> xbs = tile_xbs(t.tz, t.ty, t.rows);
         for (size_t xi = 0; xi < xbs.size() && e == cudaSuccess && rc == FD_OK; ++xi) {
             a.x_block = xbs[xi];
             for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-                e = launch_kernel(hd, a, kernel, tiles[ti].first, tiles[ti].second, &map, check, hd->stream);
+                e = launch_kernel(hd, a, kernel, t.tz, t.ty, t.rows, &map, check, hd->stream);
             if (e == cudaSuccess) e = cudaEventRecord(hd->ev0, hd->stream);
             for (int w = 0; w < 4 && e == cudaSuccess; ++w)
-                e = launch_kernel(hd, a, kernel, tiles[ti].first, tiles[ti].second, &map, check, hd->stream);
+                e = launch_kernel(hd, a, kernel, t.tz, t.ty, t.rows, &map, check, hd->stream);
             if (e == cudaSuccess) e = cudaEventRecord(hd->ev1, hd->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(hd->ev1);
             float ms = 0;
@@ -510,12 +523,10 @@ int autotune(fd_handle *hd) {
     dev_free(aux, hd->stream);
     cudaStreamSynchronize(hd->stream);
     if (rc != FD_OK) return rc;
-    hd->tile_z = tiles[best_t].first;
-    hd->tile_y = tiles[best_t].second;
-    hd->x_block = best_xb;
+    take(tiles[best_t], best_xb);
     if (!force_tile && !force_xb) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = std::make_tuple(hd->tile_z, hd->tile_y, hd->x_block);
+        g_tune_cache[key] = std::make_tuple(hd->tile_z, hd->tile_y, hd->rows, hd->x_block);
     }
     return FD_OK;
 }
@@ -718,6 +729,7 @@ void fd_options_default(fd_options *opt) {
     opt->x_block = 0;
     opt->check_finite = 1;
     opt->boundary = FD_BOUNDARY_ZERO;
+    opt->rows = 0;
 }
 
 const char *fd_last_error(void) { return g_last_error.c_str(); }
@@ -792,8 +804,10 @@ static int create_handle(int nx, int ny, int nz, int space_order, double h, doub
         if (kernel != kAuto && kernel != kTma) return fail(FD_ENOTSUP, "16-bit storage runs on the TMA kernel");
     }
     if (kernel == kAuto) kernel = kTma;
-    if (!tile_ok(kernel, opt.storage, opt.form, space_order / 2, opt.tile_z, opt.tile_y))
-        return fail(FD_ENOTSUP, "tile %dx%d is not a shape of the chosen kernel", opt.tile_z, opt.tile_y);
+    if (opt.rows < 0 || opt.rows > 2) return fail(FD_EINVAL, "rows must be 0, 1 or 2");
+    if (!tile_ok(kernel, opt.storage, opt.form, space_order / 2, opt.tile_z, opt.tile_y, opt.rows))
+        return fail(FD_ENOTSUP, "tile %dx%d with %d rows per thread is not a shape of the chosen kernel", opt.tile_z,
+                    opt.tile_y, opt.rows);
     if (opt.x_block < 0) return fail(FD_EINVAL, "x_block must be >= 0");
     const bool slab = slab_x0 >= 0;
     int ghost_lo = 0, ghost_hi = 0;
@@ -1122,8 +1136,8 @@ static int fwi_gradient_impl(fd_handle *hd, int nrec, const double *rec_xyz, con
     if (rc == FD_OK) rc = fd_set_receivers(hd, nrec, rec_xyz, nt);
     TmaMaps fm[2], am[2];
     GradMaps gm{};
-    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], tz, ty, &fm[b]);
-    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, w[b], w[b ^ 1], tz, ty, &am[b]);
+    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, hd->ubuf[b], hd->ubuf[b ^ 1], tz, ty, 1, &fm[b]);
+    for (int b = 0; b < 2 && rc == FD_OK; ++b) rc = make_maps(hd, w[b], w[b ^ 1], tz, ty, 1, &am[b]);
     if (rc == FD_OK) rc = encode_box(hd, grad, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tz, ty, &gm.grad);
     if (rc == FD_OK) {
         // the history as one 4-D tensor: level k - 1 of step k is the fourth coordinate
@@ -1544,7 +1558,7 @@ static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *by
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
+        const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows);
         if (per_sm <= 0 || sms <= 0) return fail(FD_ENOTSUP, "no flow kernel for this launch shape");
         hd->flow_ctas = per_sm * sms;
     }
@@ -1576,7 +1590,8 @@ static int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
     if (rc != FD_OK) return rc;
     FD_CUDA(cudaEventRecord(hd->ev0, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->flow_buf, 0, bytes, hd->stream));
-    FD_CUDA(launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check_enabled(hd), hd->stream));
+    FD_CUDA(launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows, f, ctas, check_enabled(hd),
+                            hd->stream));
     FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
     FD_CUDA(cudaEventSynchronize(hd->ev1));
     FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
@@ -1629,7 +1644,8 @@ static int run_flow(fd_handle *hd, int nt) {
     const bool check = check_enabled(hd);
     return replay_graph(hd, nt, true, [&](cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(hd->flow_buf, 0, bytes, st);
-        if (e == cudaSuccess) e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, f, ctas, check, st);
+        if (e == cudaSuccess)
+            e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows, f, ctas, check, st);
         return e;
     });
 }
@@ -1891,6 +1907,18 @@ int fd_get_config(fd_handle *hd, int *kernel, int *tile_z, int *tile_y, int *x_b
     return FD_OK;
 }
 
+int fd_get_schedule(fd_handle *hd, int *rows, int *schedule, int *flow_x_block) {
+    if (!hd) return fail(FD_EINVAL, "handle is NULL");
+    const bool tuned = hd->kernel == kNaive || (hd->tile_y != 0 && hd->x_block != 0);
+    const bool two_step = hd->opt.kernel == kAuto && hd->kernel == kTma && hd->r == 1 &&
+                          hd->opt.storage == kF32 && hd->opt.form == kFactored && hd->n_rec == 0 &&
+                          int(hd->sources.size()) <= kFusedSources && !hd->slab;
+    if (rows) *rows = tuned ? hd->rows : 0;
+    if (schedule) *schedule = !tuned ? 0 : two_step ? 2 : (hd->opt.kernel == kAuto && flow_eligible(hd) && hd->flow_wins && hd->flow_xb) ? 1 : 0;
+    if (flow_x_block) *flow_x_block = hd->flow_xb;
+    return FD_OK;
+}
+
 int fd_last_forward_ms(fd_handle *hd, float *ms) {
     if (!hd || !ms) return fail(FD_EINVAL, "NULL argument");
     if (!hd->timed) return fail(FD_ESTATE, "no fd_forward timed yet");
@@ -1938,7 +1966,8 @@ int fd_slab_step(fd_handle *hd, int part) {
         StepArgs b = a;
         b.x_lo = xa;
         b.x_hi = xb;
-        return launch_tma_step(hd->r, hd->opt.form, kF32, hd->tile_z, hd->tile_y, map, b, check, hd->stream);
+        return launch_tma_step(hd->r, hd->opt.form, kF32, hd->tile_z, hd->tile_y, hd->rows, map, b, check,
+                               hd->stream);
     };
     if (part & FD_SLAB_BOUNDARY) {
         FD_CUDA(run(lo, b0));

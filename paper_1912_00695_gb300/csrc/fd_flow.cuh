@@ -53,8 +53,8 @@ __device__ __forceinline__ bool flow_wait(const unsigned *flag, unsigned need, c
     return false;
 }
 
-template <int R, int FORM, int LZ, int W>
-__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1))
+template <int R, int FORM, int LZ, int W, int YB = 1>
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma_warps_per_sm(R, YB) / W : 1))
     fd_tma_flow_kernel(const __grid_constant__ FlowArgs f, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // item slots: the item of iteration i sits in s_item[i & 1]; thread 0 claims the
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
             break;
         }
         const int xb = bx * a.x_block;
-        if (!tma_segment<R, FORM, LZ, W, float, kModeStep, true>(&f.maps[p], a, sc, bz, by, xb,
+        if (!tma_segment<R, FORM, LZ, W, float, kModeStep, true, YB>(&f.maps[p], a, sc, bz, by, xb,
                                                                  min(xb + a.x_block, a.Nx), ring, g, acc, nullptr,
                                                                  f.step0 + s)) {
             ok_all = false;  // a ring wait gave up (status set); the ring's phases are no longer known
@@ -125,10 +125,10 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
     if (check) reduce_amax(f.a[0], acc.amax_bits, acc.over, acc.damax_bits);
 }
 
-template <int R, int FORM, int LZ, int W>
+template <int R, int FORM, int LZ, int W, int YB = 1>
 cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
-    using G = TmaShape<R, LZ, W, float>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W>;
+    using G = TmaShape<R, LZ, W, float, 0, YB>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -139,10 +139,10 @@ cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_
     return cudaGetLastError();
 }
 
-template <int R, int FORM, int LZ, int W>
+template <int R, int FORM, int LZ, int W, int YB = 1>
 int tma_flow_occupancy() {
-    using G = TmaShape<R, LZ, W, float>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W>;
+    using G = TmaShape<R, LZ, W, float, 0, YB>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) != cudaSuccess)
         return 0;
     int n = 0;
@@ -151,11 +151,24 @@ int tma_flow_occupancy() {
 }
 
 template <int R>
-cudaError_t tma_flow_r(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
+cudaError_t tma_flow_r(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas, bool check,
+                       cudaStream_t s) {
 #define FDGB_FLOW_CASE(LZ, W)                                                                   \
     if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
         return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W>(f, ctas, check, s)      \
                                  : tma_flow_launch<R, kExpanded, LZ, W>(f, ctas, check, s);
+#define FDGB_FLOW_CASE2(LZ, W)                                                                  \
+    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W))                                  \
+        return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, 2>(f, ctas, check, s)   \
+                                 : tma_flow_launch<R, kExpanded, LZ, W, 2>(f, ctas, check, s);
+    if (rows == 2) {
+        if constexpr (R <= 8) {
+            FDGB_TMA_CONFIGS2(FDGB_FLOW_CASE2)
+        }
+        return cudaErrorInvalidValue;
+    }
+#undef FDGB_FLOW_CASE2
+    if (rows != 1) return cudaErrorInvalidValue;
     if constexpr (R <= 8) {
         FDGB_TMA_CONFIGS(FDGB_FLOW_CASE)
     } else {
@@ -166,11 +179,23 @@ cudaError_t tma_flow_r(int form, int tile_z, int tile_y, const FlowArgs &f, int 
 }
 
 template <int R>
-int tma_flow_occ_r(int form, int tile_z, int tile_y) {
+int tma_flow_occ_r(int form, int tile_z, int tile_y, int rows) {
 #define FDGB_FLOW_OCC(LZ, W)                                                                    \
     if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
         return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W>()                    \
                                  : tma_flow_occupancy<R, kExpanded, LZ, W>();
+#define FDGB_FLOW_OCC2(LZ, W)                                                                   \
+    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W))                                  \
+        return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, 2>()                 \
+                                 : tma_flow_occupancy<R, kExpanded, LZ, W, 2>();
+    if (rows == 2) {
+        if constexpr (R <= 8) {
+            FDGB_TMA_CONFIGS2(FDGB_FLOW_OCC2)
+        }
+        return 0;
+    }
+#undef FDGB_FLOW_OCC2
+    if (rows != 1) return 0;
     if constexpr (R <= 8) {
         FDGB_TMA_CONFIGS(FDGB_FLOW_OCC)
     } else {
@@ -184,11 +209,11 @@ int tma_flow_occ_r(int form, int tile_z, int tile_y) {
 
 #define FDGB_INSTANTIATE_FLOW_RADIUS(R)                                                           \
     namespace fdgb {                                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, \
-                                    bool check, cudaStream_t s) {                                 \
-        return tma_flow_r<R>(form, tile_z, tile_y, f, ctas, check, s);                            \
+    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, \
+                                    int ctas, bool check, cudaStream_t s) {                       \
+        return tma_flow_r<R>(form, tile_z, tile_y, rows, f, ctas, check, s);                      \
     }                                                                                             \
-    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y) {                               \
-        return tma_flow_occ_r<R>(form, tile_z, tile_y);                                           \
+    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y, int rows) {                     \
+        return tma_flow_occ_r<R>(form, tile_z, tile_y, rows);                                     \
     }                                                                                             \
     }

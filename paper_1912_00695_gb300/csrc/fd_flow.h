@@ -24,9 +24,9 @@ struct FlowArgs {
 // One persistent launch of the flow kernel for radius/form/tile; `ctas` is the
 // number of CTAs (at most the resident count). cudaErrorInvalidValue for a
 // configuration without a flow kernel.
-cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check,
-                            cudaStream_t s);
+cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
+                            bool check, cudaStream_t s);
 // Resident CTAs per SM of that kernel (0 if the configuration does not exist).
-int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y);
+int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y, int rows);
 
 }  // namespace fdgb

@@ -27,7 +27,8 @@ constexpr int kModeStep = 0, kModeForwardD = 1, kModeAdjointGrad = 2;
 constexpr int kTmaWarpsPerSM = 16;
 // above radius 8 the register queue needs more than 128 registers per thread:
 // 8 warps per SM
-constexpr int tma_warps_per_sm(int r) { return r > 8 ? 8 : kTmaWarpsPerSM; }
+// Two y rows per thread double the x queues: 8 warps per SM as well.
+constexpr int tma_warps_per_sm(int r, int rows = 1) { return (r > 8 || rows > 1) ? 8 : kTmaWarpsPerSM; }
 constexpr int kTileZ = 32;          // streaming tile width along z (one warp)
 constexpr int kMaxDim = 65535;  // keeps every launch grid dimension within limits
 
@@ -146,9 +147,11 @@ cudaError_t launch_tma_batch_step(int radius, int form, int storage, int tile_z,
 // (128,8), (32,16), (64,8)} and both forms; 16-bit storage in (32,16) and (64,8), factored
 // form. The halo box of `maps.u_halo` is (box_w, box_h, 1) from tma_box (false: no such
 // configuration).
-cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+// `rows`: y rows per thread (1, or 2 in the shapes of FDGB_TMA_CONFIGS2; the
+// tile's tile_y counts the rows of all threads).
+cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y, int rows,
                             const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s);
-bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *box_w, int *box_h,
+bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int rows, int *box_w, int *box_h,
              int *rz);
 
 // Utility kernels (fd_kernels_util.cu)

@@ -103,10 +103,10 @@ cudaError_t launch_naive_step(int radius, int form, int storage, const StepArgs 
 int stream_grid_x_chunks(int Nx, int x_block) { return (Nx + x_block - 1) / x_block; }
 
 #define FDGB_DECLARE_TMA_RADIUS(R)                                                               \
-    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y,               \
+    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y, int rows,     \
                                     const TmaMaps &map, const StepArgs &a, bool check,           \
                                     cudaStream_t s);                                             \
-    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int *w, int *h, int *rz);
+    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, int *w, int *h, int *rz);
 FDGB_DECLARE_TMA_RADIUS(1)
 FDGB_DECLARE_TMA_RADIUS(2)
 FDGB_DECLARE_TMA_RADIUS(3)
@@ -215,9 +215,9 @@ cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, 
 }
 
 #define FDGB_DECLARE_FLOW_RADIUS(R)                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, \
+    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas, \
                                     bool check, cudaStream_t s);                                  \
-    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y);
+    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y, int rows);
 FDGB_DECLARE_FLOW_RADIUS(1)
 FDGB_DECLARE_FLOW_RADIUS(2)
 FDGB_DECLARE_FLOW_RADIUS(3)
@@ -232,11 +232,11 @@ FDGB_DECLARE_FLOW_RADIUS(11)
 FDGB_DECLARE_FLOW_RADIUS(12)
 #undef FDGB_DECLARE_FLOW_RADIUS
 
-static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas,
-                                            bool check, cudaStream_t s) {
+static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f,
+                                            int ctas, bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_FLOW_R(R) \
-        case R: return tma_flow_radius_##R(form, tile_z, tile_y, f, ctas, check, s);
+        case R: return tma_flow_radius_##R(form, tile_z, tile_y, rows, f, ctas, check, s);
         FDGB_FLOW_R(1) FDGB_FLOW_R(2) FDGB_FLOW_R(3) FDGB_FLOW_R(4)
         FDGB_FLOW_R(5) FDGB_FLOW_R(6) FDGB_FLOW_R(7) FDGB_FLOW_R(8)
         FDGB_FLOW_R(9) FDGB_FLOW_R(10) FDGB_FLOW_R(11) FDGB_FLOW_R(12)
@@ -245,15 +245,15 @@ static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, in
     }
 }
 
-cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, const FlowArgs &f, int ctas, bool check,
-                            cudaStream_t s) {
-    return counted(launch_tma_flow_dispatch(radius, form, tile_z, tile_y, f, ctas, check, s), s);
+cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
+                            bool check, cudaStream_t s) {
+    return counted(launch_tma_flow_dispatch(radius, form, tile_z, tile_y, rows, f, ctas, check, s), s);
 }
 
-int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y) {
+int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y, int rows) {
     switch (radius) {
 #define FDGB_FLOW_O(R) \
-        case R: return tma_flow_occ_radius_##R(form, tile_z, tile_y);
+        case R: return tma_flow_occ_radius_##R(form, tile_z, tile_y, rows);
         FDGB_FLOW_O(1) FDGB_FLOW_O(2) FDGB_FLOW_O(3) FDGB_FLOW_O(4)
         FDGB_FLOW_O(5) FDGB_FLOW_O(6) FDGB_FLOW_O(7) FDGB_FLOW_O(8)
         FDGB_FLOW_O(9) FDGB_FLOW_O(10) FDGB_FLOW_O(11) FDGB_FLOW_O(12)
@@ -269,11 +269,11 @@ bool tma2_geometry(int radius, int *tz, int *ty, int *box_w, int *box_h, int *ez
     return true;
 }
 
-static cudaError_t launch_tma_step_dispatch(int radius, int form, int storage, int tile_z, int tile_y,
+static cudaError_t launch_tma_step_dispatch(int radius, int form, int storage, int tile_z, int tile_y, int rows,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_TMA_R(R) \
-        case R: return tma_step_radius_##R(form, storage, tile_z, tile_y, map, a, check, s);
+        case R: return tma_step_radius_##R(form, storage, tile_z, tile_y, rows, map, a, check, s);
         FDGB_TMA_R(1) FDGB_TMA_R(2) FDGB_TMA_R(3) FDGB_TMA_R(4)
         FDGB_TMA_R(5) FDGB_TMA_R(6) FDGB_TMA_R(7) FDGB_TMA_R(8)
         FDGB_TMA_R(9) FDGB_TMA_R(10) FDGB_TMA_R(11) FDGB_TMA_R(12)
@@ -282,15 +282,15 @@ static cudaError_t launch_tma_step_dispatch(int radius, int form, int storage, i
     }
 }
 
-cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y,
+cudaError_t launch_tma_step(int radius, int form, int storage, int tile_z, int tile_y, int rows,
                             const TmaMaps &map, const StepArgs &a, bool check, cudaStream_t s) {
-    return counted(launch_tma_step_dispatch(radius, form, storage, tile_z, tile_y, map, a, check, s), s);
+    return counted(launch_tma_step_dispatch(radius, form, storage, tile_z, tile_y, rows, map, a, check, s), s);
 }
 
-bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int *w, int *h, int *rz) {
+bool tma_box(int radius, int form, int storage, int tile_z, int tile_y, int rows, int *w, int *h, int *rz) {
     switch (radius) {
 #define FDGB_TMA_B(R) \
-        case R: return tma_box_radius_##R(form, storage, tile_z, tile_y, w, h, rz);
+        case R: return tma_box_radius_##R(form, storage, tile_z, tile_y, rows, w, h, rz);
         FDGB_TMA_B(1) FDGB_TMA_B(2) FDGB_TMA_B(3) FDGB_TMA_B(4)
         FDGB_TMA_B(5) FDGB_TMA_B(6) FDGB_TMA_B(7) FDGB_TMA_B(8)
         FDGB_TMA_B(9) FDGB_TMA_B(10) FDGB_TMA_B(11) FDGB_TMA_B(12)

@@ -170,13 +170,13 @@ template <> __device__ __forceinline__ __half2 Vec4Half<__half, __half2>::from2(
 template <> struct Vec4<__nv_bfloat16> : Vec4Half<__nv_bfloat16, __nv_bfloat162> {};
 template <> struct Vec4<__half> : Vec4Half<__half, __half2> {};
 
-template <int R, int LZ, int W, typename T, int EXTRA_F = 0>
+template <int R, int LZ, int W, typename T, int EXTRA_F = 0, int YB = 1>
 struct TmaShape {
     static constexpr int VE = 16 / int(sizeof(T));         // elements per 16 bytes
     static constexpr int RZ = (R + VE - 1) / VE * VE;       // z halo: boxes start 16-byte aligned
     static constexpr int LY = 32 / LZ;
     static constexpr int TZ = 4 * LZ;
-    static constexpr int TY = LY * W;
+    static constexpr int TY = LY * W * YB;  // YB rows per thread
     static constexpr int SW = TZ + 2 * RZ;  // box width (elements)
     static constexpr int SH = TY + 2 * R;   // box height (rows)
     // one ring stage: the halo tile of u^n(x), then the point tiles (TZ x TY, no halo)
@@ -251,35 +251,51 @@ __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw)
 // schedule), so the queue prologue reads it through L2 instead of the
 // read-only path. step >= 0 replaces a.step (the flow schedule's steps share
 // one argument block).
-template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep, bool COHERENT = false>
+// YB: y rows per thread (1 or 2). With two adjacent rows a thread loads each
+// y-tap row of the halo tile once for both (2R + 2 row loads for 8 points
+// instead of 2 (2R + 1)), carries twice the independent accumulation chains
+// and meets one CTA barrier per 8 points instead of 4; its x queues take
+// twice the registers, so such CTAs run at half the warps per SM. The
+// per-point arithmetic and its order are those of one row per thread.
+template <int R, int FORM, int LZ, int W, typename T, int MODE = kModeStep, bool COHERENT = false, int YB = 1>
 __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs &a, const ScaleState &sc, int bz,
                                             int by, int xb, int xe, unsigned char *ring, int &g, TmaAcc &acc,
                                             const GradMaps *gm = nullptr, long long step = -1) {
-    using G = TmaShape<R, LZ, W, T, MODE == kModeAdjointGrad ? 2 : 0>;
+    using G = TmaShape<R, LZ, W, T, MODE == kModeAdjointGrad ? 2 : 0, YB>;
     using V = Vec4<T>;
-    constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW, SH = G::SH;
+    constexpr int RZ = G::RZ, LY = G::LY, TZ = G::TZ, TY = G::TY, SW = G::SW;
     constexpr int U = TmaUnroll<R, FORM>::U;
     constexpr int Q = 2 * R + U;  // queue slots: 2R planes of history/lookahead + U fronts
     constexpr int NWIN = 4 + 2 * RZ;  // z window values
     constexpr int S = TmaPipe<R>::STAGES;
+    static_assert(YB == 1 || YB == 2, "one or two rows per thread");
+    static_assert(YB == 1 || MODE == kModeStep, "two rows per thread: the plain step");
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring - 128);  // placed by tma_ring_init
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int lz = lane % LZ, ly = lane / LZ;
     const int z0 = bz * TZ, y0 = by * TY;
-    const int ty = warp * LY + ly;
-    const int y = y0 + ty;
+    const int ty = (warp * LY + ly) * YB;  // the thread's first row in the tile
     const int z4 = z0 + 4 * lz;
-    const bool own = (y < a.Ny) && (z4 < a.Nz);
     const long long P = a.plane;
-    const long long col = (long long)y * a.pz + z4;
-    const T *__restrict__ u = static_cast<const T *>(a.u) + col;
-    T *up = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
-    T *un = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
+    bool own[YB];
+    const T *u[YB];
+    T *up[YB];
+    T *un[YB];
+#pragma unroll
+    for (int r = 0; r < YB; ++r) {
+        const int y = y0 + ty + r;
+        own[r] = (y < a.Ny) && (z4 < a.Nz);
+        const long long col = (long long)y * a.pz + z4;
+        u[r] = static_cast<const T *>(a.u) + col;
+        up[r] = static_cast<T *>(a.up) + col;  // FP32: u^{n-1} -> u^{n+1}; 16-bit: d^n -> d^{n+1}
+        un[r] = Io<T>::kScaled ? static_cast<T *>(a.un) + col : nullptr;  // 16-bit: u^{n+1}
+    }
     static_assert(MODE == kModeStep || (FORM == kFactored && !Io<T>::kScaled), "gradient modes: FP32 factored");
-    float *hist = MODE != kModeStep ? a.hist + col : nullptr;
-    float *grad = MODE == kModeAdjointGrad ? a.grad + col : nullptr;
+    const long long col0 = (long long)(y0 + ty) * a.pz + z4;
+    float *hist = MODE != kModeStep ? a.hist + col0 : nullptr;
+    float *grad = MODE == kModeAdjointGrad ? a.grad + col0 : nullptr;
     const int g0 = g;
     g += xe - xb;
 
@@ -318,32 +334,37 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
         for (int d = 1; d <= kPrefetchAhead; ++d) prefetch(xb + d);
     }
 
-    // sources among this thread's 4 points: bit s set, sub-index in src_p
-    unsigned src_mask = 0;
-    int src_p[kFusedSources];
+    // sources among each row's 4 points: bit s set, sub-index in src_p
+    unsigned src_mask[YB];
+    int src_p[YB][kFusedSources];
 #pragma unroll
-    for (int s = 0; s < kFusedSources; ++s) {
-        src_p[s] = 0;
-        if (own && s < a.ns && a.sy[s] == y && a.sz[s] >= z4 && a.sz[s] < z4 + 4 && a.sx[s] >= xb &&
-            a.sx[s] < xe) {
-            src_mask |= 1u << s;
-            src_p[s] = a.sz[s] - z4;
+    for (int r = 0; r < YB; ++r) {
+        src_mask[r] = 0;
+#pragma unroll
+        for (int s = 0; s < kFusedSources; ++s) {
+            src_p[r][s] = 0;
+            if (own[r] && s < a.ns && a.sy[s] == y0 + ty + r && a.sz[s] >= z4 && a.sz[s] < z4 + 4 &&
+                a.sx[s] >= xb && a.sx[s] < xe) {
+                src_mask[r] |= 1u << s;
+                src_p[r][s] = a.sz[s] - z4;
+            }
         }
     }
 
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto load_u = [&](int x) -> float4 {
-        if (!(own && x >= 0 && x < a.Nx)) return zero4;
+    auto load_u = [&](int r, int x) -> float4 {
+        if (!(own[r] && x >= 0 && x < a.Nx)) return zero4;
         if constexpr (COHERENT) {
-            return V::ldcg(u + x * P);
+            return V::ldcg(u[r] + x * P);
         } else {
-            return V::ldg(u + x * P);
+            return V::ldg(u[r] + x * P);
         }
     };
-    float4 q[Q];
+    float4 q[YB][Q];
 #pragma unroll
-    for (int k = 0; k < 2 * R; ++k) q[k] = load_u(xb - R + k);
-    const int pt_off = ty * TZ + 4 * lz;  // the thread's 4 points in a point tile
+    for (int r = 0; r < YB; ++r)
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) q[r][k] = load_u(r, xb - R + k);
 
     float2 cz2[R + 1];
 #pragma unroll
@@ -356,7 +377,6 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     const float2 su2 = f2(sc.s_u * kd, sc.s_u * kd), sd2 = f2(sc.s_d * kd, sc.s_d * kd);
     const float2 uu2 = f2(sc.s_u * sc.inv_s_out, sc.s_u * sc.inv_s_out);
     const float2 rr2 = f2(sc.s_d_out * sc.inv_s_out, sc.s_d_out * sc.inv_s_out);
-    const int rowc = ty + R;
     const int colw = 4 * lz;  // first element of the thread's z window in a tile row
     unsigned amax_bits = acc.amax_bits, damax_bits = acc.damax_bits;
     bool over = acc.over;
@@ -365,6 +385,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     int it_failed = 0;                  // first plane whose wait gave up
     int stage = g0 % S;                 // ring stage and mbarrier phase of the current plane
     uint32_t phase = uint32_t(g0 / S) & 1u;
+    bool any_own = false;
+#pragma unroll
+    for (int r = 0; r < YB; ++r) any_own |= own[r];
 
     for (int xo = xb; xo < xe; xo += U) {
 #pragma unroll
@@ -389,170 +412,234 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                 prefetch(x + 1 + kPrefetchAhead);
             }
             const unsigned char *st = ring + stage * G::STAGE_BYTES;
-            q[2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + pt_off);
+#pragma unroll
+            for (int r = 0; r < YB; ++r)
+                q[r][2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + (ty + r) * TZ + 4 * lz);
             float4 dv, gv;  // adjoint pass: D^{k-1} and the gradient at this plane (from the ring)
             if constexpr (MODE == kModeAdjointGrad) {
-                if (own) {
-                    dv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X0) + pt_off);
-                    gv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X1) + pt_off);
+                if (own[0]) {
+                    const int po = ty * TZ + 4 * lz;
+                    dv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X0) + po);
+                    gv = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_X1) + po);
                 }
             }
-            if (own) {
-                const float4 cum = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + pt_off);
-                const float4 cf1 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + pt_off);
-                const float4 cf2 = g_free(x) ? zero4
-                                             : *reinterpret_cast<const float4 *>(
-                                                   reinterpret_cast<const float *>(st + G::OFF_F2) + pt_off);
+            if (any_own) {
                 const T *t = reinterpret_cast<const T *>(st);
-                const T *rowp = t + rowc * SW + colw;
-                float win[NWIN];
+                const T *rowp = t + (ty + R) * SW + colw;  // the first row's window in the halo tile
+                const bool gf = g_free(x);
+                float win[YB][NWIN];
 #pragma unroll
-                for (int m = 0; m < NWIN / 4; ++m) {
-                    const float4 v = V::ld(rowp + 4 * m);
-                    win[4 * m] = v.x;
-                    win[4 * m + 1] = v.y;
-                    win[4 * m + 2] = v.z;
-                    win[4 * m + 3] = v.w;
+                for (int r = 0; r < YB; ++r)
+#pragma unroll
+                    for (int m = 0; m < NWIN / 4; ++m) {
+                        const float4 v = V::ld(rowp + r * SW + 4 * m);
+                        win[r][4 * m] = v.x;
+                        win[r][4 * m + 1] = v.y;
+                        win[r][4 * m + 2] = v.z;
+                        win[r][4 * m + 3] = v.w;
+                    }
+                float4 uc[YB];
+#pragma unroll
+                for (int r = 0; r < YB; ++r) uc[r] = q[r][R + i];
+                // the y taps at distance j of row r: ym(r, j) = row r - j, yp(r, j) = row r + j.
+                // Two rows share the loads: iteration j loads rows -j and j + 1 (relative to
+                // the first row) and keeps rows j and 1 - j from the previous iteration
+                // (iteration 1 takes them from the rows' centres).
+                float4 lo_prev = uc[0], hi_prev = uc[YB - 1];
+                auto ytaps = [&](int j, float4 *ym, float4 *yp) {
+                    if constexpr (YB == 1) {
+                        ym[0] = V::ld(rowp + RZ - j * SW);
+                        yp[0] = V::ld(rowp + RZ + j * SW);
+                    } else {
+                        const float4 lo = V::ld(rowp + RZ - j * SW), hi = V::ld(rowp + RZ + (j + 1) * SW);
+                        ym[0] = lo;
+                        yp[0] = hi_prev;
+                        ym[1] = lo_prev;
+                        yp[1] = hi;
+                        lo_prev = lo;
+                        hi_prev = hi;
+                    }
+                };
+                float2 lapA[YB], lapB[YB];
+#pragma unroll
+                for (int r = 0; r < YB; ++r) lapA[r] = lapB[r] = f2(0.f, 0.f);
+                float4 cum[YB], cf1[YB], cf2[YB], out[YB];
+#pragma unroll
+                for (int r = 0; r < YB; ++r) {
+                    const int po = (ty + r) * TZ + 4 * lz;  // the row's 4 points in a point tile
+                    cum[r] = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + po);
+                    cf1[r] = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + po);
+                    cf2[r] = gf ? zero4
+                                : *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F2) + po);
                 }
-                const float4 uc = q[R + i];
-                float2 lapA = f2(0.f, 0.f), lapB = f2(0.f, 0.f);
-                float4 out;
-                float sw[4];
+                float sw[YB][4];
                 if constexpr (FORM == kFactored) {
                     // -6 u_c is added to each distance-j sum: exact zero for a constant field
-                    const float2 nsixA = mul2(f2(-6.f, -6.f), lo2(uc)), nsixB = mul2(f2(-6.f, -6.f), hi2(uc));
+                    float2 nsixA[YB], nsixB[YB];
+#pragma unroll
+                    for (int r = 0; r < YB; ++r) {
+                        nsixA[r] = mul2(f2(-6.f, -6.f), lo2(uc[r]));
+                        nsixB[r] = mul2(f2(-6.f, -6.f), hi2(uc[r]));
+                    }
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
-                        const float4 ym = V::ld(rowp + RZ - j * SW);
-                        const float4 yp = V::ld(rowp + RZ + j * SW);
-                        const float4 xm = q[R + i - j], xp = q[R + i + j];
-                        const float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym), lo2(yp))),
-                                               ztap_pair<RZ>(win, j));
-                        const float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym), hi2(yp))),
-                                               ztap_pair<RZ + 2>(win, j));
-                        lapA = fma2(cz2[j], add2(sA, nsixA), lapA);
-                        lapB = fma2(cz2[j], add2(sB, nsixB), lapB);
-                    }
-                    if constexpr (Io<T>::kScaled) {
-                        // increment form: d+ = w L u + (1 - 2g) d, u+ = u + d+ (formed below,
-                        // after the source), directly in the output scales
-                        lapA = mul2(lapA, su2);
-                        lapB = mul2(lapB, su2);
-                        const float2 omA = fma2(f2(-2.f, -2.f), lo2(cf2), f2(1.f, 1.f));
-                        const float2 omB = fma2(f2(-2.f, -2.f), hi2(cf2), f2(1.f, 1.f));
-                        const float2 dA = fma2(lo2(cf1), lapA, mul2(omA, mul2(lo2(cum), sd2)));
-                        const float2 dB = fma2(hi2(cf1), lapB, mul2(omB, mul2(hi2(cum), sd2)));
-                        out = make_float4(dA.x, dA.y, dB.x, dB.y);
-                    } else {
-                        // u+ = w L + (2u - u-) - 2 g (u - u-)
-                        const float2 ucA = lo2(uc), ucB = hi2(uc), umA = lo2(cum), umB = hi2(cum);
-                        const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2)), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2));
-                        const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
-                        float2 vA = fma2(lo2(cf1), lapA, add2(ucA, dA));
-                        float2 vB = fma2(hi2(cf1), lapB, add2(ucB, dB));
-                        vA = fma2(m2gA, dA, vA);
-                        vB = fma2(m2gB, dB, vB);
-                        out = make_float4(vA.x, vA.y, vB.x, vB.y);
-                    }
-                    sw[0] = cf1.x * kd;  // kd = 1 for FP32 storage
-                    sw[1] = cf1.y * kd;
-                    sw[2] = cf1.z * kd;
-                    sw[3] = cf1.w * kd;
-                } else {
-                    // expanded: every tap (u_tap - u_c) times (c_j dt^2/h^2)/r0
-                    const float r0[4] = {fmaf(a.half_dt, cf2.x, cf1.x), fmaf(a.half_dt, cf2.y, cf1.y),
-                                         fmaf(a.half_dt, cf2.z, cf1.z), fmaf(a.half_dt, cf2.w, cf1.w)};
-                    const float inv[4] = {__frcp_rn(r0[0]), __frcp_rn(r0[1]), __frcp_rn(r0[2]),
-                                          __frcp_rn(r0[3])};
-                    const float2 invA = f2(inv[0], inv[1]), invB = f2(inv[2], inv[3]);
-                    const float2 ucA = lo2(uc), ucB = hi2(uc);
+                        float4 ym[YB], yp[YB];
+                        ytaps(j, ym, yp);
 #pragma unroll
-                    for (int j = 1; j <= R; ++j) {
-                        const float4 ym = V::ld(rowp + RZ - j * SW);
-                        const float4 yp = V::ld(rowp + RZ + j * SW);
-                        const float4 xm = q[R + i - j], xp = q[R + i + j];
-                        const float2 cA = mul2(cz2[j], invA), cB = mul2(cz2[j], invB);
-                        lapA = fma2(cA, sub2(lo2(xm), ucA), lapA);
-                        lapA = fma2(cA, sub2(lo2(xp), ucA), lapA);
-                        lapA = fma2(cA, sub2(lo2(ym), ucA), lapA);
-                        lapA = fma2(cA, sub2(lo2(yp), ucA), lapA);
-                        lapA = fma2(cA, sub2(f2(win[RZ - j], win[RZ + 1 - j]), ucA), lapA);
-                        lapA = fma2(cA, sub2(f2(win[RZ + j], win[RZ + 1 + j]), ucA), lapA);
-                        lapB = fma2(cB, sub2(hi2(xm), ucB), lapB);
-                        lapB = fma2(cB, sub2(hi2(xp), ucB), lapB);
-                        lapB = fma2(cB, sub2(hi2(ym), ucB), lapB);
-                        lapB = fma2(cB, sub2(hi2(yp), ucB), lapB);
-                        lapB = fma2(cB, sub2(f2(win[RZ + 2 - j], win[RZ + 3 - j]), ucB), lapB);
-                        lapB = fma2(cB, sub2(f2(win[RZ + 2 + j], win[RZ + 3 + j]), ucB), lapB);
-                    }
-                    static_assert(!Io<T>::kScaled, "16-bit storage uses the factored form");
-                    const float ms[4] = {cf1.x, cf1.y, cf1.z, cf1.w};
-                    const float ums[4] = {cum.x, cum.y, cum.z, cum.w};
-                    const float ucs[4] = {uc.x, uc.y, uc.z, uc.w};
-                    const float taps[4] = {lapA.x, lapA.y, lapB.x, lapB.y};
-                    // a = m / r0 by a correctly rounded division; where the damping vanishes
-                    // (the tile's plane inside the undamped box) r0 = m exactly and a = 1
-                    float am[4] = {1.0f, 1.0f, 1.0f, 1.0f};
-                    if (!g_free(x)) {
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) am[p] = __fdiv_rn(ms[p], r0[p]);
-                    }
-                    float v[4];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        v[p] = fmaf(1.0f - 2.0f * am[p], ums[p], fmaf(2.0f * am[p], ucs[p], taps[p]));
-                        sw[p] = a.dt2 * inv[p];
-                    }
-                    out = make_float4(v[0], v[1], v[2], v[3]);
-                }
-                if (src_mask) {
-#pragma unroll
-                    for (int s = 0; s < kFusedSources; ++s) {
-                        if (((src_mask >> s) & 1u) && a.sx[s] == x) {
-                            const float qv = step < 0 ? source_value(a, s)
-                                                      : step < a.ld ? __ldg(a.wavelet + (long long)s * a.ld + step)
-                                                                    : 0.0f;
-                            const int p = src_p[s];
-                            if (p == 0) out.x = fmaf(sw[0], qv, out.x);
-                            if (p == 1) out.y = fmaf(sw[1], qv, out.y);
-                            if (p == 2) out.z = fmaf(sw[2], qv, out.z);
-                            if (p == 3) out.w = fmaf(sw[3], qv, out.w);
+                        for (int r = 0; r < YB; ++r) {
+                            const float4 xm = q[r][R + i - j], xp = q[r][R + i + j];
+                            const float2 sA = add2(add2(add2(lo2(xm), lo2(xp)), add2(lo2(ym[r]), lo2(yp[r]))),
+                                                   ztap_pair<RZ>(win[r], j));
+                            const float2 sB = add2(add2(add2(hi2(xm), hi2(xp)), add2(hi2(ym[r]), hi2(yp[r]))),
+                                                   ztap_pair<RZ + 2>(win[r], j));
+                            lapA[r] = fma2(cz2[j], add2(sA, nsixA[r]), lapA[r]);
+                            lapB[r] = fma2(cz2[j], add2(sB, nsixB[r]), lapB[r]);
                         }
                     }
-                }
-                if (z4 + 3 >= a.Nz) {  // row tail: keep the pitch padding zero
-                    if (z4 + 1 >= a.Nz) out.y = 0.f;
-                    if (z4 + 2 >= a.Nz) out.z = 0.f;
-                    if (z4 + 3 >= a.Nz) out.w = 0.f;
-                }
-                auto bits4 = [](const float4 &v) {
-                    return max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
-                               max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w))));
-                };
-                if constexpr (Io<T>::kScaled) {
-                    // out is the stored d^{n+1}; u^{n+1} = u^n + d^{n+1}, stored (padding
-                    // stays zero: both terms are). The maxima are of stored values (scaled
-                    // back once, after the loop); the 16-bit range is checked there too.
-                    const float2 nA = fma2(lo2(uc), uu2, mul2(f2(out.x, out.y), rr2));
-                    const float2 nB = fma2(hi2(uc), uu2, mul2(f2(out.z, out.w), rr2));
-                    const float4 unew = make_float4(nA.x, nA.y, nB.x, nB.y);
-                    damax_bits = max(damax_bits, bits4(out));
-                    amax_bits = max(amax_bits, bits4(unew));
-                    V::st(un + x * P, unew);
+#pragma unroll
+                    for (int r = 0; r < YB; ++r) {
+                        if constexpr (Io<T>::kScaled) {
+                            // increment form: d+ = w L u + (1 - 2g) d, u+ = u + d+ (formed below,
+                            // after the source), directly in the output scales
+                            const float2 lA = mul2(lapA[r], su2), lB = mul2(lapB[r], su2);
+                            const float2 omA = fma2(f2(-2.f, -2.f), lo2(cf2[r]), f2(1.f, 1.f));
+                            const float2 omB = fma2(f2(-2.f, -2.f), hi2(cf2[r]), f2(1.f, 1.f));
+                            const float2 dA = fma2(lo2(cf1[r]), lA, mul2(omA, mul2(lo2(cum[r]), sd2)));
+                            const float2 dB = fma2(hi2(cf1[r]), lB, mul2(omB, mul2(hi2(cum[r]), sd2)));
+                            out[r] = make_float4(dA.x, dA.y, dB.x, dB.y);
+                        } else {
+                            // u+ = w L + (2u - u-) - 2 g (u - u-)
+                            const float2 ucA = lo2(uc[r]), ucB = hi2(uc[r]), umA = lo2(cum[r]), umB = hi2(cum[r]);
+                            const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2[r])), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2[r]));
+                            const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
+                            float2 vA = fma2(lo2(cf1[r]), lapA[r], add2(ucA, dA));
+                            float2 vB = fma2(hi2(cf1[r]), lapB[r], add2(ucB, dB));
+                            vA = fma2(m2gA, dA, vA);
+                            vB = fma2(m2gB, dB, vB);
+                            out[r] = make_float4(vA.x, vA.y, vB.x, vB.y);
+                        }
+                        sw[r][0] = cf1[r].x * kd;  // kd = 1 for FP32 storage
+                        sw[r][1] = cf1[r].y * kd;
+                        sw[r][2] = cf1[r].z * kd;
+                        sw[r][3] = cf1[r].w * kd;
+                    }
                 } else {
-                    amax_bits = max(amax_bits, bits4(out));
+                    // expanded: every tap (u_tap - u_c) times (c_j dt^2/h^2)/r0
+                    static_assert(!Io<T>::kScaled, "16-bit storage uses the factored form");
+                    float inv[YB][4];
+                    float2 invA[YB], invB[YB];
+#pragma unroll
+                    for (int r = 0; r < YB; ++r) {
+                        const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
+                                             fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) inv[r][p] = __frcp_rn(r0[p]);
+                        invA[r] = f2(inv[r][0], inv[r][1]);
+                        invB[r] = f2(inv[r][2], inv[r][3]);
+                    }
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        float4 ym[YB], yp[YB];
+                        ytaps(j, ym, yp);
+#pragma unroll
+                        for (int r = 0; r < YB; ++r) {
+                            const float4 xm = q[r][R + i - j], xp = q[r][R + i + j];
+                            const float2 ucA = lo2(uc[r]), ucB = hi2(uc[r]);
+                            const float *w = win[r];
+                            const float2 cA = mul2(cz2[j], invA[r]), cB = mul2(cz2[j], invB[r]);
+                            lapA[r] = fma2(cA, sub2(lo2(xm), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, sub2(lo2(xp), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, sub2(lo2(ym[r]), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, sub2(lo2(yp[r]), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, sub2(f2(w[RZ - j], w[RZ + 1 - j]), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, sub2(f2(w[RZ + j], w[RZ + 1 + j]), ucA), lapA[r]);
+                            lapB[r] = fma2(cB, sub2(hi2(xm), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, sub2(hi2(xp), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, sub2(hi2(ym[r]), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, sub2(hi2(yp[r]), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, sub2(f2(w[RZ + 2 - j], w[RZ + 3 - j]), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, sub2(f2(w[RZ + 2 + j], w[RZ + 3 + j]), ucB), lapB[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < YB; ++r) {
+                        const float ms[4] = {cf1[r].x, cf1[r].y, cf1[r].z, cf1[r].w};
+                        const float ums[4] = {cum[r].x, cum[r].y, cum[r].z, cum[r].w};
+                        const float ucs[4] = {uc[r].x, uc[r].y, uc[r].z, uc[r].w};
+                        const float taps[4] = {lapA[r].x, lapA[r].y, lapB[r].x, lapB[r].y};
+                        const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
+                                             fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
+                        // a = m / r0 by a correctly rounded division; where the damping vanishes
+                        // (the tile's plane inside the undamped box) r0 = m exactly and a = 1
+                        float am[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+                        if (!gf) {
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) am[p] = __fdiv_rn(ms[p], r0[p]);
+                        }
+                        float v[4];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            v[p] = fmaf(1.0f - 2.0f * am[p], ums[p], fmaf(2.0f * am[p], ucs[p], taps[p]));
+                            sw[r][p] = a.dt2 * inv[r][p];
+                        }
+                        out[r] = make_float4(v[0], v[1], v[2], v[3]);
+                    }
                 }
-                V::st(up + x * P, out);
-                if constexpr (MODE == kModeForwardD) {
-                    // D = (u^{n+1} - 2u^n) + u^{n-1}; FP32 factored: cum is u^{n-1}
-                    const float4 d4 = make_float4(fmaf(-2.0f, uc.x, out.x) + cum.x, fmaf(-2.0f, uc.y, out.y) + cum.y,
-                                                  fmaf(-2.0f, uc.z, out.z) + cum.z, fmaf(-2.0f, uc.w, out.w) + cum.w);
-                    __stcs(reinterpret_cast<float4 *>(hist + x * P), d4);
-                }
-                if constexpr (MODE == kModeAdjointGrad) {
-                    gv = make_float4(fmaf(-out.x, dv.x, gv.x), fmaf(-out.y, dv.y, gv.y), fmaf(-out.z, dv.z, gv.z),
-                                     fmaf(-out.w, dv.w, gv.w));
-                    *reinterpret_cast<float4 *>(grad + x * P) = gv;
+#pragma unroll
+                for (int r = 0; r < YB; ++r) {
+                    if (!own[r]) continue;
+                    float4 o = out[r];
+                    if (src_mask[r]) {
+#pragma unroll
+                        for (int s = 0; s < kFusedSources; ++s) {
+                            if (((src_mask[r] >> s) & 1u) && a.sx[s] == x) {
+                                const float qv = step < 0 ? source_value(a, s)
+                                                          : step < a.ld ? __ldg(a.wavelet + (long long)s * a.ld + step)
+                                                                        : 0.0f;
+                                const int p = src_p[r][s];
+                                if (p == 0) o.x = fmaf(sw[r][0], qv, o.x);
+                                if (p == 1) o.y = fmaf(sw[r][1], qv, o.y);
+                                if (p == 2) o.z = fmaf(sw[r][2], qv, o.z);
+                                if (p == 3) o.w = fmaf(sw[r][3], qv, o.w);
+                            }
+                        }
+                    }
+                    if (z4 + 3 >= a.Nz) {  // row tail: keep the pitch padding zero
+                        if (z4 + 1 >= a.Nz) o.y = 0.f;
+                        if (z4 + 2 >= a.Nz) o.z = 0.f;
+                        if (z4 + 3 >= a.Nz) o.w = 0.f;
+                    }
+                    auto bits4 = [](const float4 &v) {
+                        return max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
+                                   max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w))));
+                    };
+                    if constexpr (Io<T>::kScaled) {
+                        // o is the stored d^{n+1}; u^{n+1} = u^n + d^{n+1}, stored (padding
+                        // stays zero: both terms are). The maxima are of stored values (scaled
+                        // back once, after the loop); the 16-bit range is checked there too.
+                        const float2 nA = fma2(lo2(uc[r]), uu2, mul2(f2(o.x, o.y), rr2));
+                        const float2 nB = fma2(hi2(uc[r]), uu2, mul2(f2(o.z, o.w), rr2));
+                        const float4 unew = make_float4(nA.x, nA.y, nB.x, nB.y);
+                        damax_bits = max(damax_bits, bits4(o));
+                        amax_bits = max(amax_bits, bits4(unew));
+                        V::st(un[r] + x * P, unew);
+                    } else {
+                        amax_bits = max(amax_bits, bits4(o));
+                    }
+                    V::st(up[r] + x * P, o);
+                    if constexpr (MODE == kModeForwardD) {
+                        // D = (u^{n+1} - 2u^n) + u^{n-1}; FP32 factored: cum is u^{n-1}
+                        const float4 d4 = make_float4(fmaf(-2.0f, uc[r].x, o.x) + cum[r].x,
+                                                      fmaf(-2.0f, uc[r].y, o.y) + cum[r].y,
+                                                      fmaf(-2.0f, uc[r].z, o.z) + cum[r].z,
+                                                      fmaf(-2.0f, uc[r].w, o.w) + cum[r].w);
+                        __stcs(reinterpret_cast<float4 *>(hist + x * P), d4);
+                    }
+                    if constexpr (MODE == kModeAdjointGrad) {
+                        gv = make_float4(fmaf(-o.x, dv.x, gv.x), fmaf(-o.y, dv.y, gv.y), fmaf(-o.z, dv.z, gv.z),
+                                         fmaf(-o.w, dv.w, gv.w));
+                        *reinterpret_cast<float4 *>(grad + x * P) = gv;
+                    }
                 }
             }
             if (++stage == S) {
@@ -562,7 +649,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
         }
         if (failed) break;
 #pragma unroll
-        for (int k = 0; k < 2 * R; ++k) q[k] = q[k + U];
+        for (int r = 0; r < YB; ++r)
+#pragma unroll
+            for (int k = 0; k < 2 * R; ++k) q[r][k] = q[r][k + U];
     }
     if (failed) {
         // planes it_failed .. issued-1 are the only copies not yet waited for (one per stage)
@@ -613,9 +702,9 @@ __device__ __forceinline__ void tma_sample_receivers(const StepArgs &a, float sc
 // of tile (bz, by). The grid runs z-tiles fastest and x-chunks slowest, so the
 // CTAs resident at any moment cover neighbouring tiles at the same planes and
 // share their halo rows in L2.
-template <int R, int FORM, int LZ, int W, typename T>
-__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1)) fd_tma_kernel(const __grid_constant__ TmaMaps maps,
-                                                        const StepArgs a, int check) {
+template <int R, int FORM, int LZ, int W, typename T, int YB = 1>
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma_warps_per_sm(R, YB) / W : 1))
+    fd_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a, int check) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     publish_scales<T>(a, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0);
     unsigned char *ring = tma_ring_init<R>(smem_dyn);
@@ -624,8 +713,8 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
     const int xb = a.x_lo + blockIdx.z * a.x_block;
     int g = 0;
     TmaAcc acc;
-    if (tma_segment<R, FORM, LZ, W, T>(&maps, a, sc, blockIdx.x, blockIdx.y, xb, min(xb + a.x_block, a.x_hi), ring,
-                                       g, acc) &&
+    if (tma_segment<R, FORM, LZ, W, T, kModeStep, false, YB>(&maps, a, sc, blockIdx.x, blockIdx.y, xb,
+                                                            min(xb + a.x_block, a.x_hi), ring, g, acc) &&
         check) {
         tma_finish<T>(acc, sc);
         reduce_amax(a, acc.amax_bits, acc.over, acc.damax_bits);
@@ -674,10 +763,10 @@ cudaError_t tma_grad_step_r(int mode, const TmaMaps &map, const GradMaps &gm, co
     return cudaErrorInvalidValue;
 }
 
-template <int R, int FORM, int LZ, int W, typename T>
+template <int R, int FORM, int LZ, int W, typename T, int YB = 1>
 cudaError_t tma_launch(const TmaMaps &maps, const StepArgs &a, bool check, cudaStream_t s) {
-    using G = TmaShape<R, LZ, W, T>;
-    auto kernel = fd_tma_kernel<R, FORM, LZ, W, T>;
+    using G = TmaShape<R, LZ, W, T, 0, YB>;
+    auto kernel = fd_tma_kernel<R, FORM, LZ, W, T, YB>;
     static bool attr_set = false;  // per instantiation, set once per process
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -775,64 +864,91 @@ cudaError_t tma_batch_step_r(int form, int storage, int tile_z, int tile_y, cons
 #define FDGB_TMA_CONFIGS_16(X) X(8, 4) X(16, 4)
 #define FDGB_TMA_CONFIGS_HIGH(X) X(8, 8) X(8, 4)
 #define FDGB_TMA_CONFIGS_16_HIGH(X) X(8, 4)
+// Two y rows per thread (radius <= 8, every storage; the factored form for 16-bit):
+// 32x32 and 64x16 tiles of 128 threads.
+#define FDGB_TMA_CONFIGS2(X) X(8, 4) X(16, 4)
 
 template <int R>
-cudaError_t tma_step_r(int form, int storage, int tile_z, int tile_y, const TmaMaps &map, const StepArgs &a,
-                       bool check, cudaStream_t s) {
+cudaError_t tma_step_r(int form, int storage, int tile_z, int tile_y, int rows, const TmaMaps &map,
+                       const StepArgs &a, bool check, cudaStream_t s) {
 #define FDGB_TMA_CASE(LZ, W)                                                                    \
     if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                   \
         return form == kFactored ? tma_launch<R, kFactored, LZ, W, float>(map, a, check, s)     \
                                  : tma_launch<R, kExpanded, LZ, W, float>(map, a, check, s);
-    if constexpr (R <= 8) {
-        FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
-    } else {
-        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_CASE)
-    }
-#undef FDGB_TMA_CASE
 #define FDGB_TMA_CASE16(LZ, W)                                                                  \
     if (form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {               \
         if (storage == kBF16) return tma_launch<R, kFactored, LZ, W, __nv_bfloat16>(map, a, check, s); \
         if (storage == kF16) return tma_launch<R, kFactored, LZ, W, __half>(map, a, check, s);  \
     }
+#define FDGB_TMA_CASE2(LZ, W)                                                                   \
+    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W)) {                                \
+        if (storage == kF32)                                                                    \
+            return form == kFactored ? tma_launch<R, kFactored, LZ, W, float, 2>(map, a, check, s) \
+                                     : tma_launch<R, kExpanded, LZ, W, float, 2>(map, a, check, s); \
+        if (form == kFactored && storage == kBF16)                                              \
+            return tma_launch<R, kFactored, LZ, W, __nv_bfloat16, 2>(map, a, check, s);         \
+        if (form == kFactored && storage == kF16)                                               \
+            return tma_launch<R, kFactored, LZ, W, __half, 2>(map, a, check, s);                \
+    }
+    if (rows == 2) {
+        if constexpr (R <= 8) {
+            FDGB_TMA_CONFIGS2(FDGB_TMA_CASE2)
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (rows != 1) return cudaErrorInvalidValue;
     if constexpr (R <= 8) {
+        FDGB_TMA_CONFIGS(FDGB_TMA_CASE)
         FDGB_TMA_CONFIGS_16(FDGB_TMA_CASE16)
     } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_CASE)
         FDGB_TMA_CONFIGS_16_HIGH(FDGB_TMA_CASE16)
     }
+#undef FDGB_TMA_CASE
 #undef FDGB_TMA_CASE16
+#undef FDGB_TMA_CASE2
     return cudaErrorInvalidValue;
 }
 
 // Box geometry the host needs to encode the tensor map for a configuration
 // (false when the configuration does not exist).
 template <int R>
-bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *box_h, int *rz) {
-#define FDGB_TMA_BOX(LZ, W)                                                                     \
-    if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) {                 \
-        *box_w = TmaShape<R, LZ, W, float>::SW;                                                 \
-        *box_h = TmaShape<R, LZ, W, float>::SH;                                                 \
-        *rz = TmaShape<R, LZ, W, float>::RZ;                                                    \
+bool tma_box_r(int form, int storage, int tile_z, int tile_y, int rows, int *box_w, int *box_h, int *rz) {
+#define FDGB_TMA_BOX_T(LZ, W, T, YB)                                                            \
+    {                                                                                           \
+        *box_w = TmaShape<R, LZ, W, T, 0, YB>::SW;                                              \
+        *box_h = TmaShape<R, LZ, W, T, 0, YB>::SH;                                              \
+        *rz = TmaShape<R, LZ, W, T, 0, YB>::RZ;                                                 \
         return true;                                                                            \
     }
+#define FDGB_TMA_BOX(LZ, W)                                                                     \
+    if (storage == kF32 && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) FDGB_TMA_BOX_T(LZ, W, float, 1)
+#define FDGB_TMA_BOX16(LZ, W)                                                                   \
+    if (storage != kF32 && form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) \
+        FDGB_TMA_BOX_T(LZ, W, __half, 1)
+#define FDGB_TMA_BOX2(LZ, W)                                                                    \
+    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W)) {                                \
+        if (storage == kF32) FDGB_TMA_BOX_T(LZ, W, float, 2)                                    \
+        if (form == kFactored) FDGB_TMA_BOX_T(LZ, W, __half, 2)                                 \
+    }
+    if (rows == 2) {
+        if constexpr (R <= 8) {
+            FDGB_TMA_CONFIGS2(FDGB_TMA_BOX2)
+        }
+        return false;
+    }
+    if (rows != 1) return false;
     if constexpr (R <= 8) {
         FDGB_TMA_CONFIGS(FDGB_TMA_BOX)
-    } else {
-        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_BOX)
-    }
-#undef FDGB_TMA_BOX
-#define FDGB_TMA_BOX16(LZ, W)                                                                   \
-    if (storage != kF32 && form == kFactored && tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W)) { \
-        *box_w = TmaShape<R, LZ, W, __half>::SW;                                                \
-        *box_h = TmaShape<R, LZ, W, __half>::SH;                                                \
-        *rz = TmaShape<R, LZ, W, __half>::RZ;                                                   \
-        return true;                                                                            \
-    }
-    if constexpr (R <= 8) {
         FDGB_TMA_CONFIGS_16(FDGB_TMA_BOX16)
     } else {
+        FDGB_TMA_CONFIGS_HIGH(FDGB_TMA_BOX)
         FDGB_TMA_CONFIGS_16_HIGH(FDGB_TMA_BOX16)
     }
+#undef FDGB_TMA_BOX_T
+#undef FDGB_TMA_BOX
 #undef FDGB_TMA_BOX16
+#undef FDGB_TMA_BOX2
     return false;
 }
 
@@ -840,14 +956,14 @@ bool tma_box_r(int form, int storage, int tile_z, int tile_y, int *box_w, int *b
 
 #define FDGB_INSTANTIATE_TMA_RADIUS(R)                                                            \
     namespace fdgb {                                                                              \
-    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y,                \
+    cudaError_t tma_step_radius_##R(int form, int storage, int tile_z, int tile_y, int rows,      \
                                     const TmaMaps &map, const StepArgs &a, bool check,            \
                                     cudaStream_t s) {                                             \
-        return tma_step_r<R>(form, storage, tile_z, tile_y, map, a, check, s);                    \
+        return tma_step_r<R>(form, storage, tile_z, tile_y, rows, map, a, check, s);              \
     }                                                                                             \
-    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int *w, int *h,        \
-                            int *rz) {                                                            \
-        return tma_box_r<R>(form, storage, tile_z, tile_y, w, h, rz);                             \
+    bool tma_box_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, int *w,      \
+                            int *h, int *rz) {                                                    \
+        return tma_box_r<R>(form, storage, tile_z, tile_y, rows, w, h, rz);                       \
     }                                                                                             \
     cudaError_t tma_batch_step_radius_##R(int form, int storage, int tile_z, int tile_y,          \
                                           const BatchShot *shots, const int4 *items, int n_items, \

@@ -89,9 +89,9 @@ def test_version_and_error_text(built_lib):
 
 def test_options_default(built_lib):
     o = _abi.fd_options_default()
-    assert (o.storage, o.form, o.kernel, o.tile_z, o.tile_y, o.x_block, o.check_finite, o.boundary) == \
-        (0, 0, 0, 0, 0, 0, 1, 0)
-    assert ctypes.sizeof(o) == 8 * 4
+    assert (o.storage, o.form, o.kernel, o.tile_z, o.tile_y, o.x_block, o.check_finite, o.boundary, o.rows) == \
+        (0, 0, 0, 0, 0, 0, 1, 0, 0)
+    assert ctypes.sizeof(o) == 9 * 4
 
 
 def test_options_struct_matches_header():
