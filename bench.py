@@ -315,7 +315,7 @@ def run_ours(args, rank: int, world: int):
             gbs = algorithmic_bytes_per_step(spec) * spec.nt / (ms * 1e-3) / 1e9
             entry.update(kernel="fd_tma_flow_kernel (one launch for the nt steps)" if sched == "flow"
                          else "fd_tma_kernel", hbm_frac=round(gbs / peak, 4),
-                         kernel_tz_ty_xb=list(shot.config))
+                         kernel_tz_ty_xb=list(shot.config), rows_schedule_flowxb=list(shot.schedule))
         else:
             pairs = spec.nt // 2
             gbs = (algorithmic_bytes_two_steps(spec) * pairs

@@ -229,8 +229,10 @@ __device__ __forceinline__ unsigned char *tma_ring_init(unsigned char *smem_raw)
     constexpr int S = TmaPipe<R>::STAGES;
     // the S mbarriers sit in the first 128 bytes, the ring right after them, so their
     // place does not depend on the stage layout
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // aligned by pointer arithmetic on the shared array itself (not through an
+    // integer), so that the compiler keeps its address space and every access to
+    // the ring is a shared-memory load with 32-bit addressing
+    unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     unsigned char *ring = base + 128;
     if (threadIdx.x == 0) {
         uint64_t *bars = reinterpret_cast<uint64_t *>(base);

@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(256, 2) fd_tma2_kernel(const __grid_constant__
     using G = Tb2Shape<R>;
     constexpr int S = G::STAGES, U = G::U, Q = 2 * R + U, NWIN = 4 + 2 * G::HZ, EZ = G::EZ, SW = G::SW;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char *ring = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    // aligned by pointer arithmetic on the shared array (keeps its address space)
+    unsigned char *ring = smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u);
     float *u1ring = reinterpret_cast<float *>(ring + G::U1_OFF);
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring + G::BAR_OFF);
 

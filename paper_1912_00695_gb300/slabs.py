@@ -237,13 +237,13 @@ class GpuSlab:
 
     def __init__(self, interior, space_order, h, dt, nbl, ranges, index, **opts):
         import torch
-        self.interior = tuple(int(n) for n in interior)
+        self.interior_dims = tuple(int(n) for n in interior)
         self.nbl, self.k, self.r, self.h = int(nbl), int(space_order), int(space_order) // 2, float(h)
-        self.shape = tuple(n + 2 * self.nbl for n in self.interior)
+        self.shape = tuple(n + 2 * self.nbl for n in self.interior_dims)
         self.ranges, self.index = ranges, index
         x0, x1 = ranges[index]
         self.window = slab_window(ranges, index, self.r, self.shape[0])
-        self.handle = fd_slab_create(*self.interior, self.k, self.h, dt, self.nbl, x0, x1, _options(**opts))
+        self.handle = fd_slab_create(*self.interior_dims, self.k, self.h, dt, self.nbl, x0, x1, _options(**opts))
         self.device = torch.cuda.current_device()
         fd_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
         self.dims = fd_get_dims(self.handle)
