@@ -380,9 +380,17 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
 
 /* Create an empty batch of space order k (even, 2..16: FD_EINVAL otherwise).
  * opt: storage/form as for fd_acoustic_create_ex
- * (16-bit storage needs the factored form), tile_z/tile_y 0 (= 32x16) or one
- * of 32x16, 64x8; x_block 0 = 96 planes (or the whole extent if shorter),
- * else used for every shot; kernel is ignored. FD_ENOTSUP for other shapes. */
+ * (16-bit storage needs the factored form), tile_z/tile_y 0 (autotuned) or
+ * one of 32x16, 64x8; x_block 0 (autotuned) or the planes per CTA of every
+ * shot (the whole extent if shorter); rows 0 or 1; kernel is ignored.
+ * FD_ENOTSUP for other shapes. The autotuner (the batch counterpart of the
+ * loop blocking and auto-tuning Devito applies, Sec. 5) times the launch
+ * shapes not forced — both tiles, x-chunks of 32/48/64/96/128 planes and whole
+ * extents — on 3 real steps each of the first fd_batch_forward of at least
+ * 39 steps (21 with a forced x_block) over at least 4 shots, and keeps the
+ * fastest for the batch's lifetime (shots added later take it); before that,
+ * 96-plane chunks. Results do not depend on the shape (same arithmetic per
+ * point). */
 int fd_batch_create(int space_order, double h, const fd_options *opt, fd_batch **out);
 
 /* Add a shot: interior nx*ny*nz, layer nbl, time step dt, HOST model m and
@@ -411,6 +419,11 @@ int fd_batch_read_device(fd_batch *b, int slot, float *d_out, int level);
 /* A shot's global step counter; a shot's device status (as fd_status). */
 int fd_batch_shot_step(fd_batch *b, int slot, long long *step);
 int fd_batch_shot_status(fd_batch *b, int slot);
+
+/* The batch's launch shape: tile, x-chunk policy (planes per CTA, 0 = whole
+ * extents) and whether the autotuner has run or the shape was forced (any
+ * pointer may be NULL). (The paper has no counterpart.) */
+int fd_batch_get_config(fd_batch *b, int *tile_z, int *tile_y, int *x_block, int *tuned);
 
 /* Number of shots in the batch and work items (CTAs) per step (-1 until the
  * next fd_batch_forward rebuilds the work list). */

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_forward,  # noqa: F401
+from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_forward, fd_batch_get_config,  # noqa: F401
                    fd_batch_inject, fd_batch_read, fd_batch_read_device, fd_batch_remove, fd_batch_reset,
                    fd_batch_set_stream, fd_batch_shot_status, fd_batch_shot_step, fd_batch_size,
                    fd_batch_synchronize, fd_shot_device_bytes)
@@ -142,6 +142,10 @@ class Batch:
 
     def size(self):
         return fd_batch_size(self.handle)
+
+    def config(self):
+        """(tile_z, tile_y, x-chunk policy, tuned) of the batch's launches."""
+        return fd_batch_get_config(self.handle)
 
     def reset(self):
         fd_batch_reset(self.handle)

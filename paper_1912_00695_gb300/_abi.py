@@ -118,6 +118,7 @@ _SIGNATURES = {
     "fd_batch_shot_step": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
     "fd_batch_shot_status": (_i, [_vp, _i]),
     "fd_batch_size": (_i, [_vp, _ip, _ip]),
+    "fd_batch_get_config": (_i, [_vp, _ip, _ip, _ip, _ip]),
     "fd_batch_reset": (_i, [_vp]),
     "fd_batch_set_stream": (_i, [_vp, _vp]),
     "fd_batch_synchronize": (_i, [_vp]),
@@ -479,6 +480,13 @@ def fd_batch_size(b):
     a, w = _i(), _i()
     _check(lib().fd_batch_size(b, ctypes.byref(a), ctypes.byref(w)), "fd_batch_size")
     return a.value, w.value
+
+
+def fd_batch_get_config(b):
+    """(tile_z, tile_y, x-chunk policy, tuned) of the batch."""
+    v = [_i() for _ in range(4)]
+    _check(lib().fd_batch_get_config(b, *[ctypes.byref(x) for x in v]), "fd_batch_get_config")
+    return tuple(x.value for x in v)
 
 
 def fd_batch_reset(b):

@@ -2048,6 +2048,11 @@ struct fd_batch {
     double h = 0;
     fd_options opt{};
     int tile_z = 0, tile_y = 0;
+    // x-chunk policy: every shot streams min(xb_policy, N_x) planes per CTA (0: whole
+    // extents); tile and policy are timed on the first long forward unless forced
+    int xb_policy = 0;
+    bool tile_forced = false, tuned = false;
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;
     std::vector<fd_handle *> slots;  // slot id -> shot (nullptr when free)
     BatchShot *d_shots = nullptr;
     size_t cap_shots = 0;
@@ -2186,6 +2191,99 @@ int batch_upload_table(fd_batch *b) {
     return batch_stage_upload(b, b->d_shots, b->host_table.data(), b->host_table.size() * sizeof(BatchShot));
 }
 
+// Every shot to the batch's launch shape: tile (tz, ty) and x-chunks of min(xb, N_x)
+// planes (xb = 0: whole extents). The per-point arithmetic does not depend on
+// either, so a shape change never changes a result.
+int batch_apply_shape(fd_batch *b, int tz, int ty, int xb) {
+    const bool tile_changed = tz != b->tile_z || ty != b->tile_y;
+    b->tile_z = b->opt.tile_z = tz;
+    b->tile_y = b->opt.tile_y = ty;
+    b->xb_policy = xb;
+    for (fd_handle *hd : b->slots) {
+        if (!hd) continue;
+        hd->x_block = xb > 0 ? std::min(xb, hd->Nx) : hd->Nx;
+        hd->opt.x_block = hd->x_block;
+        if (tile_changed) {
+            hd->tile_z = hd->opt.tile_z = tz;
+            hd->tile_y = hd->opt.tile_y = ty;
+            hd->rows = 1;
+            int rc = build_maps(hd);
+            if (rc != FD_OK) return rc;
+        }
+    }
+    b->dirty = true;
+    return FD_OK;
+}
+
+// nt launches of the current work list, outside a graph, timed on the batch stream
+// (the shots advance by nt steps).
+int batch_timed_steps(fd_batch *b, int nt, float *ms) {
+    int rc = batch_rebuild(b);
+    if (rc == FD_OK) rc = batch_upload_table(b);
+    if (rc != FD_OK) return rc;
+    FD_CUDA(cudaEventRecord(b->tev0, b->stream));
+    for (int i = 0; i < nt; ++i) {
+        cudaError_t err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y, b->d_shots,
+                                                b->d_items, b->n_items, i, b->stream);
+        if (err != cudaSuccess) return fail(FD_ECUDA, "batch launch failed: %s", cudaGetErrorString(err));
+    }
+    FD_CUDA(cudaEventRecord(b->tev1, b->stream));
+    FD_CUDA(cudaEventSynchronize(b->tev1));
+    FD_CUDA(cudaEventElapsedTime(ms, b->tev0, b->tev1));
+    for (int s : b->order) {
+        fd_handle *hd = b->slots[s];
+        hd->step += nt;
+        hd->cur ^= (nt & 1);
+    }
+    return FD_OK;
+}
+
+// Launch shapes timed by the batch autotuner: both tiles (unless forced) and
+// x-chunk policies from short chunks (more CTAs, shorter queue warm-ups per
+// chunk: neither) to whole extents.
+constexpr int kBatchTuneSteps = 3;
+constexpr int kBatchTuneXb[] = {32, 48, 64, 96, 128, 0};
+constexpr int kBatchTuneMinShots = 4;
+
+// Times every candidate shape on kBatchTuneSteps real steps of this forward (*nt is
+// reduced by the steps they took) and keeps the fastest for the batch's lifetime.
+// Runs once, on the first forward long enough with at least kBatchTuneMinShots shots.
+int batch_autotune(fd_batch *b, int *nt) {
+    int n_tiles = 0;
+    int tiles[2][2];
+    for (auto &t : kBatchTiles)
+        if (!b->tile_forced || (t[0] == b->tile_z && t[1] == b->tile_y)) {
+            tiles[n_tiles][0] = t[0];
+            tiles[n_tiles][1] = t[1];
+            ++n_tiles;
+        }
+    const int n_xb = b->opt.x_block > 0 ? 1 : int(sizeof(kBatchTuneXb) / sizeof(int));
+    const int needed = kBatchTuneSteps * (n_tiles * n_xb + 1);
+    if (*nt < needed || int(b->order.size()) < kBatchTuneMinShots) return FD_OK;  // later, longer call
+    float best = 1e30f, ms = 0.0f;
+    int best_t = 0, best_x = b->xb_policy;
+    bool warmed = false;
+    for (int ti = 0; ti < n_tiles; ++ti)
+        for (int xi = 0; xi < n_xb; ++xi) {
+            const int xb = b->opt.x_block > 0 ? b->opt.x_block : kBatchTuneXb[xi];
+            int rc = batch_apply_shape(b, tiles[ti][0], tiles[ti][1], xb);
+            if (rc == FD_OK && !warmed) {
+                rc = batch_timed_steps(b, kBatchTuneSteps, &ms);  // the first launches run cold
+                warmed = true;
+            }
+            if (rc == FD_OK) rc = batch_timed_steps(b, kBatchTuneSteps, &ms);
+            if (rc != FD_OK) return rc;
+            if (ms < best) {
+                best = ms;
+                best_t = ti;
+                best_x = xb;
+            }
+        }
+    *nt -= needed;
+    b->tuned = true;
+    return batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
+}
+
 fd_handle *batch_shot(fd_batch *b, int slot) {
     if (!b || slot < 0 || size_t(slot) >= b->slots.size()) return nullptr;
     return b->slots[slot];
@@ -2228,7 +2326,11 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
     bool ok = false;
     for (auto &t : kBatchTiles) ok |= (t[0] == tz && t[1] == ty);
     if (!ok) return fail(FD_ENOTSUP, "batch tile must be 32x16 or 64x8");
+    if (opt.rows > 1) return fail(FD_ENOTSUP, "batches run one row per thread");
     fd_batch *b = new fd_batch();
+    b->tile_forced = opt.tile_z != 0 || opt.tile_y != 0;
+    b->xb_policy = opt.x_block > 0 ? opt.x_block : kBatchXBlock;
+    b->tuned = opt.x_block > 0 && b->tile_forced;  // nothing left to time
     b->k = space_order;
     b->r = space_order / 2;
     b->h = h;
@@ -2240,7 +2342,8 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
     b->tile_z = tz;
     b->tile_y = ty;
     if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->tev0) != cudaSuccess || cudaEventCreate(&b->tev1) != cudaSuccess) {
         if (b->own_stream) cudaStreamDestroy(b->own_stream);
         delete b;
         return fail(FD_ECUDA, "cudaStreamCreate failed");
@@ -2256,7 +2359,7 @@ int fd_batch_add(fd_batch *b, int nx, int ny, int nz, int nbl, double dt, const 
     // tile fixed by the batch; x_block forced, else long x-runs: a batch has work items to
     // spare, so it trades CTA count for fewer queue warm-ups (measured best near 96 planes)
     fd_options opt = b->opt;
-    if (opt.x_block == 0) opt.x_block = std::min(kBatchXBlock, nx + 2 * nbl);
+    opt.x_block = b->xb_policy > 0 ? std::min(b->xb_policy, nx + 2 * nbl) : nx + 2 * nbl;
     fd_handle *hd = nullptr;
     int rc = fd_acoustic_create_ex(nx, ny, nz, b->k, b->h, dt, nbl, &opt, &hd);
     if (rc != FD_OK) return rc;
@@ -2315,6 +2418,15 @@ int fd_batch_forward(fd_batch *b, int nt) {
         if (rc != FD_OK) return rc;
     }
     if (nt == 0 || b->order.empty()) return FD_OK;
+    if (!b->tuned) {
+        int rc = batch_autotune(b, &nt);
+        if (rc != FD_OK) return rc;
+        if (b->dirty) {
+            rc = batch_rebuild(b);
+            if (rc != FD_OK) return rc;
+        }
+        if (nt == 0) return FD_OK;
+    }
     int rc = batch_upload_table(b);
     if (rc != FD_OK) return rc;
     fd_batch::Graph *g = nullptr;
@@ -2444,8 +2556,19 @@ int fd_batch_destroy(fd_batch *b) {
         if (sg.host) cudaFreeHost(sg.host);
     }
     if (b->join_ev) cudaEventDestroy(b->join_ev);
+    if (b->tev0) cudaEventDestroy(b->tev0);
+    if (b->tev1) cudaEventDestroy(b->tev1);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
+    return FD_OK;
+}
+
+int fd_batch_get_config(fd_batch *b, int *tile_z, int *tile_y, int *x_block, int *tuned) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    if (tile_z) *tile_z = b->tile_z;
+    if (tile_y) *tile_y = b->tile_y;
+    if (x_block) *x_block = b->xb_policy;
+    if (tuned) *tuned = b->tuned ? 1 : 0;
     return FD_OK;
 }
 
