@@ -205,7 +205,12 @@ def run_ours(args, rank: int, world: int):
     shots = []
     for spec, form in runs:
         dt = 0.9 * fd.fd_dt_max(spec.space_order, inputs.H, spec.vmax)
-        shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, form=form)
+        shape = {}
+        if args.rows:
+            shape["rows"] = args.rows
+        if args.tile[0]:
+            shape.update(tile_z=args.tile[0], tile_y=args.tile[1])
+        shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, form=form, **shape)
         m = spec.m
         shot.set_model(m)
         wav = inputs.ricker(spec.f0, dt, spec.nt)
@@ -1070,6 +1075,9 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=0, help="sweep: y rows per thread of the step kernel (0 = autotuned)")
+    ap.add_argument("--tile", type=lambda v: tuple(int(x) for x in v.split("x")), default=(0, 0),
+                    help="sweep: step kernel tile as ZxY (default autotuned)")
     ap.add_argument("--orders", type=lambda v: tuple(int(x) for x in v.split(",")), default=ORDERS,
                     help="comma-separated space orders of the sweep (default 2,4,8,12,16)")
     ap.add_argument("--forms", type=lambda v: tuple(v.split(",")), default=FORMS,

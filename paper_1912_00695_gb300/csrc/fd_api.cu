@@ -1558,7 +1558,8 @@ static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *by
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows);
+        const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->opt.storage, hd->tile_z, hd->tile_y,
+                                                hd->rows);
         if (per_sm <= 0 || sms <= 0) return fail(FD_ENOTSUP, "no flow kernel for this launch shape");
         hd->flow_ctas = per_sm * sms;
     }
@@ -1576,6 +1577,7 @@ static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *by
     unsigned char *fb = static_cast<unsigned char *>(hd->flow_buf);
     f->counter = reinterpret_cast<int *>(fb);
     f->abort = reinterpret_cast<unsigned *>(fb + 4);
+    f->amax = reinterpret_cast<unsigned *>(fb + 8);
     f->flags = reinterpret_cast<unsigned *>(fb + 16);
     *ctas = int(std::min<long long>(hd->flow_ctas, per_step * nt));
     return FD_OK;
@@ -1590,8 +1592,10 @@ static int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
     if (rc != FD_OK) return rc;
     FD_CUDA(cudaEventRecord(hd->ev0, hd->stream));
     FD_CUDA(cudaMemsetAsync(hd->flow_buf, 0, bytes, hd->stream));
-    FD_CUDA(launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows, f, ctas, check_enabled(hd),
-                            hd->stream));
+    FD_CUDA(launch_tma_flow(hd->r, hd->opt.form, hd->opt.storage, hd->tile_z, hd->tile_y, hd->rows, f, ctas,
+                            check_enabled(hd), hd->stream));
+    if (hd->opt.storage != kF32)
+        FD_CUDA(launch_flow_finish_scales(hd->d_scales, int(((hd->step + nt) % 3 + 3) % 3), f.amax, hd->stream));
     FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
     FD_CUDA(cudaEventSynchronize(hd->ev1));
     FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
@@ -1645,7 +1649,10 @@ static int run_flow(fd_handle *hd, int nt) {
     return replay_graph(hd, nt, true, [&](cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(hd->flow_buf, 0, bytes, st);
         if (e == cudaSuccess)
-            e = launch_tma_flow(hd->r, hd->opt.form, hd->tile_z, hd->tile_y, hd->rows, f, ctas, check, st);
+            e = launch_tma_flow(hd->r, hd->opt.form, hd->opt.storage, hd->tile_z, hd->tile_y, hd->rows, f, ctas,
+                                check, st);
+        if (e == cudaSuccess && hd->opt.storage != kF32)
+            e = launch_flow_finish_scales(hd->d_scales, int(((hd->step + nt) % 3 + 3) % 3), f.amax, st);
         return e;
     });
 }
@@ -1667,7 +1674,7 @@ static int steps_direct(fd_handle *hd, int nt, float *ms) {
 }
 
 static bool flow_eligible(const fd_handle *hd) {
-    return hd->opt.storage == kF32 && hd->kernel == kTma && hd->n_rec == 0 &&
+    return (hd->opt.storage == kF32 || hd->opt.storage == kBF16) && hd->kernel == kTma && hd->n_rec == 0 &&
            int(hd->sources.size()) <= kFusedSources && hd->opt.boundary == FD_BOUNDARY_ZERO &&
            (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r);
 }
@@ -1755,9 +1762,9 @@ int fd_forward_flow(fd_handle *hd, int nt) {
     if (hd->slab) return fail(FD_ENOTSUP, "a slab advances through fd_slab_step, with its halo exchange");
     if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_flow before fd_set_model");
-    if (hd->opt.storage != kF32 || hd->kernel != kTma || hd->n_rec > 0 ||
-        int(hd->sources.size()) > kFusedSources || hd->opt.boundary != FD_BOUNDARY_ZERO)
-        return fail(FD_ENOTSUP, "the flow schedule: FP32 storage, TMA kernel, <= %d sources, no receivers, zero boundary",
+    if (!flow_eligible(hd) && !(hd->opt.x_block > 0 && hd->opt.x_block < hd->r))
+        return fail(FD_ENOTSUP,
+                    "the flow schedule: FP32 or BF16 storage, TMA kernel, <= %d sources, no receivers, zero boundary",
                     kFusedSources);
     // an item reads the queue planes and fronts of its x-neighbours only
     if (hd->opt.x_block > 0 && hd->opt.x_block < hd->r)

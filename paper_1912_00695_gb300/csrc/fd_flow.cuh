@@ -19,6 +19,8 @@
 // same buffer held older levels earlier in the launch.
 #pragma once
 
+#include <type_traits>
+
 #include "fd_flow.h"
 #include "fd_tma.cuh"
 
@@ -53,9 +55,27 @@ __device__ __forceinline__ bool flow_wait(const unsigned *flag, unsigned need, c
     return false;
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1>
+// Scales of a flow launch's step s: FP32 none; BF16 the stored levels' own scales
+// for the first step's inputs and unit scales otherwise (every level the launch
+// writes is stored unscaled: BF16 rounding does not depend on a power-of-two scale).
+template <typename T>
+__device__ __forceinline__ ScaleState flow_scales(const FlowArgs &f, bool first) {
+    ScaleState st{1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
+    if constexpr (Io<T>::kScaled) {
+        if (first) {
+            const int n = level_slot(f.step0);
+            st.s_u = f.a[0].scales->scale[n];
+            st.s_d = f.a[0].scales->dscale[n];
+        }
+    }
+    return st;
+}
+
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
 __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma_warps_per_sm(R, YB) / W : 1))
     fd_tma_flow_kernel(const __grid_constant__ FlowArgs f, int check) {
+    static_assert(std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value,
+                  "the flow schedule stores FP32 or BF16 (FP16 needs per-level scales)");
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // item slots: the item of iteration i sits in s_item[i & 1]; thread 0 claims the
     // next one while the current one runs (claims stay in increasing order per CTA,
@@ -63,7 +83,7 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
     __shared__ int s_item[2];
     __shared__ int s_fail;
     unsigned char *ring = tma_ring_init<R>(smem_dyn);
-    const ScaleState sc = read_scales<float>(f.a[0]);
+    const ScaleState sc0 = flow_scales<T>(f, true), sc1 = flow_scales<T>(f, false);
     const int per_plane = f.nbz * f.nby;
     const int per_step = per_plane * f.nbx;
     const int total = per_step * f.nt;
@@ -103,7 +123,7 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
             break;
         }
         const int xb = bx * a.x_block;
-        if (!tma_segment<R, FORM, LZ, W, float, kModeStep, true, YB>(&f.maps[p], a, sc, bz, by, xb,
+        if (!tma_segment<R, FORM, LZ, W, T, kModeStep, true, YB>(&f.maps[p], a, s == 0 ? sc0 : sc1, bz, by, xb,
                                                                  min(xb + a.x_block, a.Nx), ring, g, acc, nullptr,
                                                                  f.step0 + s)) {
             ok_all = false;  // a ring wait gave up (status set); the ring's phases are no longer known
@@ -122,13 +142,31 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
         }
         return;
     }
-    if (check) reduce_amax(f.a[0], acc.amax_bits, acc.over, acc.damax_bits);
+    if constexpr (Io<T>::kScaled) {
+        // maxima of the stored (unscaled) values of every level written, the range check
+        tma_finish<T>(acc, sc1);
+        unsigned bits = acc.amax_bits, dbits = acc.damax_bits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+            dbits = max(dbits, __shfl_xor_sync(0xffffffffu, dbits, o));
+        }
+        const unsigned any_over = __any_sync(0xffffffffu, acc.over);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&f.amax[0], bits);
+            atomicMax(&f.amax[1], dbits);
+            if (f.a[0].status && (bits >= 0x7f800000u || dbits >= 0x7f800000u || any_over))
+                atomicOr(f.a[0].status, kStatusNonFinite);
+        }
+    } else {
+        if (check) reduce_amax(f.a[0], acc.amax_bits, acc.over, acc.damax_bits);
+    }
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1>
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
 cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
-    using G = TmaShape<R, LZ, W, float, 0, YB>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB>;
+    using G = TmaShape<R, LZ, W, T, 0, YB>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -139,10 +177,10 @@ cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_
     return cudaGetLastError();
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1>
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
 int tma_flow_occupancy() {
-    using G = TmaShape<R, LZ, W, float, 0, YB>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB>;
+    using G = TmaShape<R, LZ, W, T, 0, YB>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) != cudaSuccess)
         return 0;
     int n = 0;
@@ -151,57 +189,65 @@ int tma_flow_occupancy() {
 }
 
 template <int R>
-cudaError_t tma_flow_r(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas, bool check,
-                       cudaStream_t s) {
-#define FDGB_FLOW_CASE(LZ, W)                                                                   \
-    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
-        return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W>(f, ctas, check, s)      \
-                                 : tma_flow_launch<R, kExpanded, LZ, W>(f, ctas, check, s);
-#define FDGB_FLOW_CASE2(LZ, W)                                                                  \
-    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W))                                  \
-        return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, 2>(f, ctas, check, s)   \
-                                 : tma_flow_launch<R, kExpanded, LZ, W, 2>(f, ctas, check, s);
-    if (rows == 2) {
-        if constexpr (R <= 8) {
-            FDGB_TMA_CONFIGS2(FDGB_FLOW_CASE2)
-        }
-        return cudaErrorInvalidValue;
+cudaError_t tma_flow_r(int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
+                       bool check, cudaStream_t s) {
+#define FDGB_FLOW_CASE(LZ, W, YB)                                                               \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB) {                 \
+        if (storage == kF32)                                                                    \
+            return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, YB>(f, ctas, check, s) \
+                                     : tma_flow_launch<R, kExpanded, LZ, W, YB>(f, ctas, check, s); \
     }
-#undef FDGB_FLOW_CASE2
-    if (rows != 1) return cudaErrorInvalidValue;
+#define FDGB_FLOW_CASE16(LZ, W, YB)                                                             \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kBF16 && \
+        form == kFactored)                                                                      \
+        return tma_flow_launch<R, kFactored, LZ, W, YB, __nv_bfloat16>(f, ctas, check, s);
+#define FDGB_FLOW_1(LZ, W) FDGB_FLOW_CASE(LZ, W, 1)
+#define FDGB_FLOW_2(LZ, W) FDGB_FLOW_CASE(LZ, W, 2) FDGB_FLOW_CASE16(LZ, W, 2)
+#define FDGB_FLOW_16(LZ, W) FDGB_FLOW_CASE16(LZ, W, 1)
     if constexpr (R <= 8) {
-        FDGB_TMA_CONFIGS(FDGB_FLOW_CASE)
+        FDGB_TMA_CONFIGS(FDGB_FLOW_1)
+        FDGB_TMA_CONFIGS_16(FDGB_FLOW_16)
+        FDGB_TMA_CONFIGS2(FDGB_FLOW_2)
     } else {
-        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_CASE)
+        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_1)
+        FDGB_TMA_CONFIGS_16_HIGH(FDGB_FLOW_16)
     }
+#undef FDGB_FLOW_1
+#undef FDGB_FLOW_2
+#undef FDGB_FLOW_16
 #undef FDGB_FLOW_CASE
+#undef FDGB_FLOW_CASE16
     return cudaErrorInvalidValue;
 }
 
 template <int R>
-int tma_flow_occ_r(int form, int tile_z, int tile_y, int rows) {
-#define FDGB_FLOW_OCC(LZ, W)                                                                    \
-    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                      \
-        return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W>()                    \
-                                 : tma_flow_occupancy<R, kExpanded, LZ, W>();
-#define FDGB_FLOW_OCC2(LZ, W)                                                                   \
-    if (tile_z == 4 * (LZ) && tile_y == 2 * (32 / (LZ)) * (W))                                  \
-        return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, 2>()                 \
-                                 : tma_flow_occupancy<R, kExpanded, LZ, W, 2>();
-    if (rows == 2) {
-        if constexpr (R <= 8) {
-            FDGB_TMA_CONFIGS2(FDGB_FLOW_OCC2)
-        }
-        return 0;
+int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows) {
+#define FDGB_FLOW_OCC(LZ, W, YB)                                                                \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB) {                 \
+        if (storage == kF32)                                                                    \
+            return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, YB>()            \
+                                     : tma_flow_occupancy<R, kExpanded, LZ, W, YB>();           \
     }
-#undef FDGB_FLOW_OCC2
-    if (rows != 1) return 0;
+#define FDGB_FLOW_OCC16(LZ, W, YB)                                                              \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kBF16 && \
+        form == kFactored)                                                                      \
+        return tma_flow_occupancy<R, kFactored, LZ, W, YB, __nv_bfloat16>();
+#define FDGB_FLOW_1(LZ, W) FDGB_FLOW_OCC(LZ, W, 1)
+#define FDGB_FLOW_2(LZ, W) FDGB_FLOW_OCC(LZ, W, 2) FDGB_FLOW_OCC16(LZ, W, 2)
+#define FDGB_FLOW_16(LZ, W) FDGB_FLOW_OCC16(LZ, W, 1)
     if constexpr (R <= 8) {
-        FDGB_TMA_CONFIGS(FDGB_FLOW_OCC)
+        FDGB_TMA_CONFIGS(FDGB_FLOW_1)
+        FDGB_TMA_CONFIGS_16(FDGB_FLOW_16)
+        FDGB_TMA_CONFIGS2(FDGB_FLOW_2)
     } else {
-        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_OCC)
+        FDGB_TMA_CONFIGS_HIGH(FDGB_FLOW_1)
+        FDGB_TMA_CONFIGS_16_HIGH(FDGB_FLOW_16)
     }
+#undef FDGB_FLOW_1
+#undef FDGB_FLOW_2
+#undef FDGB_FLOW_16
 #undef FDGB_FLOW_OCC
+#undef FDGB_FLOW_OCC16
     return 0;
 }
 
@@ -209,11 +255,11 @@ int tma_flow_occ_r(int form, int tile_z, int tile_y, int rows) {
 
 #define FDGB_INSTANTIATE_FLOW_RADIUS(R)                                                           \
     namespace fdgb {                                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, \
-                                    int ctas, bool check, cudaStream_t s) {                       \
-        return tma_flow_r<R>(form, tile_z, tile_y, rows, f, ctas, check, s);                      \
+    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows,      \
+                                    const FlowArgs &f, int ctas, bool check, cudaStream_t s) {    \
+        return tma_flow_r<R>(form, storage, tile_z, tile_y, rows, f, ctas, check, s);             \
     }                                                                                             \
-    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y, int rows) {                     \
-        return tma_flow_occ_r<R>(form, tile_z, tile_y, rows);                                     \
+    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows) {        \
+        return tma_flow_occ_r<R>(form, storage, tile_z, tile_y, rows);                            \
     }                                                                                             \
     }

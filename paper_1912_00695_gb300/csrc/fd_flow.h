@@ -19,14 +19,23 @@ struct FlowArgs {
     int *counter;
     unsigned *abort;
     unsigned *flags;
+    // BF16 storage: the launch stores every level it writes with unit scales (BF16
+    // has FP32's exponent range, so a power-of-two scale changes no rounding);
+    // the first step reads the levels' own scales from the handle's slots, and
+    // the maxima of every stored value land in amax[0] (u) and amax[1] (d), zeroed
+    // with the flags, for the next launch's scale selection
+    unsigned *amax;
 };
 
 // One persistent launch of the flow kernel for radius/form/tile; `ctas` is the
 // number of CTAs (at most the resident count). cudaErrorInvalidValue for a
 // configuration without a flow kernel.
-cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
-                            bool check, cudaStream_t s);
+cudaError_t launch_tma_flow(int radius, int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f,
+                            int ctas, bool check, cudaStream_t s);
+// After a BF16 flow launch: the level it ended on gets unit scales and the
+// launch's maxima (the next per-step launch selects its scales from them).
+cudaError_t launch_flow_finish_scales(LevelScales *scales, int slot, const unsigned *amax, cudaStream_t s);
 // Resident CTAs per SM of that kernel (0 if the configuration does not exist).
-int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y, int rows);
+int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows);
 
 }  // namespace fdgb

@@ -215,9 +215,9 @@ cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, 
 }
 
 #define FDGB_DECLARE_FLOW_RADIUS(R)                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas, \
-                                    bool check, cudaStream_t s);                                  \
-    int tma_flow_occ_radius_##R(int form, int tile_z, int tile_y, int rows);
+    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f, \
+                                    int ctas, bool check, cudaStream_t s);                        \
+    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows);
 FDGB_DECLARE_FLOW_RADIUS(1)
 FDGB_DECLARE_FLOW_RADIUS(2)
 FDGB_DECLARE_FLOW_RADIUS(3)
@@ -232,11 +232,11 @@ FDGB_DECLARE_FLOW_RADIUS(11)
 FDGB_DECLARE_FLOW_RADIUS(12)
 #undef FDGB_DECLARE_FLOW_RADIUS
 
-static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f,
-                                            int ctas, bool check, cudaStream_t s) {
+static cudaError_t launch_tma_flow_dispatch(int radius, int form, int storage, int tile_z, int tile_y, int rows,
+                                            const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
     switch (radius) {
 #define FDGB_FLOW_R(R) \
-        case R: return tma_flow_radius_##R(form, tile_z, tile_y, rows, f, ctas, check, s);
+        case R: return tma_flow_radius_##R(form, storage, tile_z, tile_y, rows, f, ctas, check, s);
         FDGB_FLOW_R(1) FDGB_FLOW_R(2) FDGB_FLOW_R(3) FDGB_FLOW_R(4)
         FDGB_FLOW_R(5) FDGB_FLOW_R(6) FDGB_FLOW_R(7) FDGB_FLOW_R(8)
         FDGB_FLOW_R(9) FDGB_FLOW_R(10) FDGB_FLOW_R(11) FDGB_FLOW_R(12)
@@ -245,15 +245,15 @@ static cudaError_t launch_tma_flow_dispatch(int radius, int form, int tile_z, in
     }
 }
 
-cudaError_t launch_tma_flow(int radius, int form, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
-                            bool check, cudaStream_t s) {
-    return counted(launch_tma_flow_dispatch(radius, form, tile_z, tile_y, rows, f, ctas, check, s), s);
+cudaError_t launch_tma_flow(int radius, int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f,
+                            int ctas, bool check, cudaStream_t s) {
+    return counted(launch_tma_flow_dispatch(radius, form, storage, tile_z, tile_y, rows, f, ctas, check, s), s);
 }
 
-int tma_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y, int rows) {
+int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows) {
     switch (radius) {
 #define FDGB_FLOW_O(R) \
-        case R: return tma_flow_occ_radius_##R(form, tile_z, tile_y, rows);
+        case R: return tma_flow_occ_radius_##R(form, storage, tile_z, tile_y, rows);
         FDGB_FLOW_O(1) FDGB_FLOW_O(2) FDGB_FLOW_O(3) FDGB_FLOW_O(4)
         FDGB_FLOW_O(5) FDGB_FLOW_O(6) FDGB_FLOW_O(7) FDGB_FLOW_O(8)
         FDGB_FLOW_O(9) FDGB_FLOW_O(10) FDGB_FLOW_O(11) FDGB_FLOW_O(12)
@@ -428,6 +428,16 @@ __global__ void set_level_scale_kernel(LevelScales *ls, int slot, float scale, u
         ls->amax_bits[slot] = amax_bits;
         ls->dscale[slot] = dscale;
         ls->damax_bits[slot] = damax_bits;
+    }
+}
+
+// The level a BF16 flow launch ended on: unit scales, the launch's maxima.
+__global__ void flow_finish_scales_kernel(LevelScales *ls, int slot, const unsigned *amax) {
+    if (threadIdx.x == 0) {
+        ls->scale[slot] = 1.0f;
+        ls->dscale[slot] = 1.0f;
+        ls->amax_bits[slot] = amax[0];
+        ls->damax_bits[slot] = amax[1];
     }
 }
 
@@ -619,6 +629,11 @@ cudaError_t launch_pack_level(const float *src, void *dst, int Nx, int Ny, int N
         pack_kernel<__half><<<blocks, threads, 0, s>>>(src, static_cast<__half *>(dst), Nx, Ny, Nz, pz,
                                                        inv_scale);
     else return cudaErrorInvalidValue;
+    return counted(cudaGetLastError(), s);
+}
+
+cudaError_t launch_flow_finish_scales(LevelScales *scales, int slot, const unsigned *amax, cudaStream_t s) {
+    flow_finish_scales_kernel<<<1, 32, 0, s>>>(scales, slot, amax);
     return counted(cudaGetLastError(), s);
 }
 

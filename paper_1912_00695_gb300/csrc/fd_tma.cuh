@@ -149,6 +149,8 @@ template <typename H, typename H2> struct Vec4Half {
         return make_float4(a.x, a.y, b.x, b.y);
     }
     static __device__ __forceinline__ float4 ldg(const H *p) { return cvt(__ldg(reinterpret_cast<const uint2 *>(p))); }
+    // cached in L2 only: data other CTAs of the same launch may have written
+    static __device__ __forceinline__ float4 ldcg(const H *p) { return cvt(__ldcg(reinterpret_cast<const uint2 *>(p))); }
     static __device__ __forceinline__ float4 ld(const H *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
     static __device__ __forceinline__ void st(H *p, float4 v) {
         uint2 r;

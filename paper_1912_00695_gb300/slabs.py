@@ -27,6 +27,7 @@ drives every slab (:class:`SlabGroup`), or point-to-point messages of
 """
 from __future__ import annotations
 
+import contextlib
 from dataclasses import dataclass
 
 import numpy as np
@@ -232,8 +233,10 @@ class _DeviceView:
 
 class GpuSlab:
     """This rank's slab as a :class:`HaloDriver` stepper: a library slab on the
-    current CUDA device whose kernels run on torch's current stream, so that
-    torch.distributed's point-to-point operations order with them."""
+    current CUDA device whose kernels run on a torch stream of its own; the
+    driver makes that stream current around each step, so that
+    torch.distributed's point-to-point operations (and host staging copies)
+    order with the slab's kernels."""
 
     def __init__(self, interior, space_order, h, dt, nbl, ranges, index, **opts):
         import torch
@@ -245,8 +248,15 @@ class GpuSlab:
         self.window = slab_window(ranges, index, self.r, self.shape[0])
         self.handle = fd_slab_create(*self.interior_dims, self.k, self.h, dt, self.nbl, x0, x1, _options(**opts))
         self.device = torch.cuda.current_device()
-        fd_set_stream(self.handle, torch.cuda.current_stream().cuda_stream)
+        # a stream object of its own: the library reads a null stream handle as "the
+        # handle's own stream", which would not order with torch's default stream
+        self.stream = torch.cuda.Stream()
+        fd_set_stream(self.handle, self.stream.cuda_stream)
         self.dims = fd_get_dims(self.handle)
+
+    def stream_context(self):
+        import torch
+        return torch.cuda.stream(self.stream)
 
     def set_model(self, m, eta):
         w0, w1 = self.window
@@ -274,6 +284,7 @@ class GpuSlab:
                      for p in ptrs)
 
     def own_planes(self, level: int = 0) -> np.ndarray:
+        self.stream.synchronize()
         buf = np.empty(self.dims, dtype=np.float32)
         fd_read_wavefield(self.handle, buf, level)
         x0, x1 = self.ranges[self.index]
@@ -290,7 +301,8 @@ class HaloDriver:
     process group (rank i owns slab i): per step, the boundary part, the halo
     sends and receives posted (isend/irecv to the ranks i - 1 and i + 1), the
     interior part while they are in flight, and the receives completed before
-    the next step. `stepper` provides boundary(), interior() and views(level)
+    the next step, all with the stepper's stream current (stream_context(), if
+    it has one). `stepper` provides boundary(), interior() and views(level)
     (send_lo, send_hi, recv_lo, recv_hi: tensors the transport accepts, or
     None at the domain's ends); `stage` (optional) maps a view to the tensor
     actually sent or received and back (host staging for a CPU-only
@@ -307,6 +319,11 @@ class HaloDriver:
         self.steps = 0
 
     def step(self):
+        ctx = getattr(self.stepper, "stream_context", None)
+        with (ctx() if ctx else contextlib.nullcontext()):
+            self._step()
+
+    def _step(self):
         d, st = self.dist, self.stepper
         st.boundary()
         s_lo, s_hi, r_lo, r_hi = st.views(1)  # the level this step writes

@@ -105,7 +105,7 @@ def test_flow_full_size(k):
 def test_flow_rejections():
     spec = _spec(8, seed=2)
     dt = dt_for(spec)
-    for kw in (dict(storage="bf16"), dict(kernel="naive"), dict(kernel="stream"), dict(x_block=2)):
+    for kw in (dict(storage="f16"), dict(kernel="naive"), dict(kernel="stream"), dict(x_block=2)):
         with fd.Shot(spec.interior, 8, H, dt, spec.nbl, **kw) as shot:
             shot.set_model(spec.m)
             with pytest.raises(fd.FdError) as e:
@@ -124,3 +124,57 @@ def test_flow_rejections():
         with pytest.raises(fd.FdError) as e:
             shot.forward_flow(2)
         assert e.value.code == fd.FD_ENOTSUP
+
+
+def _bf16_run(spec, eta, schedule, chunks, **opts):
+    dt = dt_for(spec)
+    with fd.Shot(spec.interior, spec.space_order, H, dt, spec.nbl, storage="bf16", kernel="tma", **opts) as shot:
+        shot.set_model(spec.m, eta)
+        for i, src in enumerate(SOURCES):
+            shot.inject(*src, inputs.ricker(20.0 + 3 * i, dt, spec.nt))
+        for n, how in zip(chunks, schedule):
+            (shot.forward_flow if how == "flow" else shot.forward)(n)
+        return shot.wavefield(0), shot.wavefield(1)
+
+
+def _same_values(got, want):
+    """Equal bit for bit wherever the value is a normal float: the flow stores BF16
+    levels unscaled, the per-step launches with power-of-two scales, which round
+    identically except where a value is subnormal in one of the two."""
+    big = np.abs(want) >= 1e-30
+    np.testing.assert_array_equal(got[big], want[big])
+    assert np.abs(got[~big]).max(initial=0.0) <= 1e-30
+
+
+@pytest.mark.parametrize("k,tz,ty,rows", [(2, 32, 16, 1), (8, 64, 8, 1), (8, 32, 32, 2), (16, 64, 16, 2),
+                                          (24, 32, 16, 1)])
+def test_bf16_flow_equals_per_step_launches(k, tz, ty, rows):
+    """BF16 storage on the flow schedule (unit scales inside the launch) against
+    the per-step launches (per-level power-of-two scales): the same values, for
+    one launch, chunked launches, and flow and per-step calls interleaved (the
+    scale slots handed over in both directions)."""
+    spec = _spec(k, seed=300 + k)
+    eta = eta_for(spec)
+    opts = dict(tile_z=tz, tile_y=ty, rows=rows, x_block=max(k // 2, 9))
+    want = _bf16_run(spec, eta, ["step"], [40], **opts)
+    for sched, chunks in ((["flow"], [40]), (["flow", "flow", "flow"], [1, 16, 23]),
+                          (["step", "flow", "step", "flow"], [5, 11, 7, 17])):
+        got = _bf16_run(spec, eta, sched, chunks, **opts)
+        _same_values(got[0], want[0])
+        _same_values(got[1], want[1])
+
+
+def test_bf16_flow_matches_oracle(oracle_mod):
+    k = 8
+    spec = _spec(k, seed=7, interior=(40, 35, 44), nbl=6)
+    dt = dt_for(spec)
+    eta = eta_for(spec)
+    srcs = [(s, inputs.ricker(20.0 + 3 * i, dt, spec.nt)) for i, s in enumerate(SOURCES[:1])]
+    want, _ = run_oracle(oracle_mod, spec, spec.nt, dt, eta, sources=srcs)
+    with fd.Shot(spec.interior, k, H, dt, spec.nbl, storage="bf16") as shot:
+        shot.set_model(spec.m, eta)
+        shot.inject(*srcs[0][0], srcs[0][1])
+        shot.forward_flow(spec.nt)
+        e = rel_l2(shot.wavefield(0), want)
+    print(f"PARITY flow_bf16_so{k} {e:.3e}")
+    assert e <= 4 * 2.0 ** -9 * spec.nt ** 0.5
