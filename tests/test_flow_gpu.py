@@ -138,12 +138,17 @@ def _bf16_run(spec, eta, schedule, chunks, **opts):
 
 
 def _same_values(got, want):
-    """Equal bit for bit wherever the value is a normal float: the flow stores BF16
-    levels unscaled, the per-step launches with power-of-two scales, which round
-    identically except where a value is subnormal in one of the two."""
-    big = np.abs(want) >= 1e-30
-    np.testing.assert_array_equal(got[big], want[big])
-    assert np.abs(got[~big]).max(initial=0.0) <= 1e-30
+    """The flow stores BF16 levels unscaled, the per-step launches with
+    power-of-two scales: the two round identically wherever every intermediate is
+    a normal float. Far ahead of the wave front values fall into the FP32
+    subnormal range in one and not the other; the tiny difference can flip a
+    BF16 rounding there, so a vanishing fraction of elements, all negligible
+    against the field, may differ."""
+    diff = got != want
+    assert diff.mean() <= 1e-4, diff.mean()
+    scale = np.abs(want).max()
+    assert scale > 0
+    assert np.abs(got[diff] - want[diff]).max(initial=0.0) <= 1e-20 * scale
 
 
 @pytest.mark.parametrize("k,tz,ty,rows", [(2, 32, 16, 1), (8, 64, 8, 1), (8, 32, 32, 2), (16, 64, 16, 2),

@@ -13,7 +13,8 @@ constant noise floor: the peak-relative figures are the stable ones.)
 The oracle needs minutes of host time at this size, so the test runs only
 with FDGB_RUN_SLOW=1; it writes the per-step series to
 gpurun_out/precision_error_424.json when that folder exists. Bounds: about
-twice the errors measured at this configuration (see the assertions)."""
+twice the errors measured at this configuration (see CROP_BOUND and
+ENERGY_BOUND)."""
 import json
 import os
 import time
@@ -106,11 +107,14 @@ def test_precision_error_full_config(oracle_mod):
         with open(os.path.join(out_dir, "precision_error_424.json"), "w") as f:
             json.dump(record, f)
     # bounds: about twice the errors this configuration measured
-    assert summary["f32"]["crop_err_vs_peak_max"] <= BOUND["f32"]
-    assert summary["f16"]["crop_err_vs_peak_max"] <= BOUND["f16"]
-    assert summary["bf16"]["crop_err_vs_peak_max"] <= BOUND["bf16"]
+    for st in storages:
+        assert summary[st]["crop_err_vs_peak_max"] <= CROP_BOUND[st], st
+        assert summary[st]["energy_err_vs_peak_max"] <= ENERGY_BOUND[st], st
 
 
-# crop error relative to the peak crop norm; provisional (the 96^3 figures x2)
-# until the full configuration has been measured
-BOUND = {"f32": 4e-5, "f16": 5e-3, "bf16": 3.5e-2}
+# Largest crop error relative to the peak crop norm, and largest energy error
+# relative to the peak energy, over the 1000 steps: about twice the measured
+# values (GB300: crop FP32 1.77e-6, FP16 2.67e-3, BF16 1.98e-2; energy FP32
+# 4.9e-7, FP16 7.1e-4, BF16 1.14e-2).
+CROP_BOUND = {"f32": 3.5e-6, "f16": 5.5e-3, "bf16": 4e-2}
+ENERGY_BOUND = {"f32": 1e-6, "f16": 1.5e-3, "bf16": 2.3e-2}
