@@ -142,13 +142,14 @@ def _same_values(got, want):
     power-of-two scales: the two round identically wherever every intermediate is
     a normal float. Far ahead of the wave front values fall into the FP32
     subnormal range in one and not the other; the tiny difference can flip a
-    BF16 rounding there, so a vanishing fraction of elements, all negligible
-    against the field, may differ."""
-    diff = got != want
-    assert diff.mean() <= 1e-4, diff.mean()
+    BF16 rounding there; such a flip is far too small to flip anything 20 orders
+    of magnitude larger, so every element above 1e-20 of the field's maximum is
+    equal bit for bit and the rest differs by less than that."""
     scale = np.abs(want).max()
     assert scale > 0
-    assert np.abs(got[diff] - want[diff]).max(initial=0.0) <= 1e-20 * scale
+    big = np.abs(want) >= 1e-20 * scale
+    np.testing.assert_array_equal(got[big], want[big])
+    assert np.abs(got[~big] - want[~big]).max(initial=0.0) <= 1e-20 * scale
 
 
 @pytest.mark.parametrize("k,tz,ty,rows", [(2, 32, 16, 1), (8, 64, 8, 1), (8, 32, 32, 2), (16, 64, 16, 2),
