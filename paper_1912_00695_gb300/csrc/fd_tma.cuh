@@ -307,36 +307,23 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     // inside the box's x range need no g tile
     const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
     auto g_free = [&](int x) { return tile_yz_box && x >= a.bx0 && x < a.bx1; };
-    // every input of plane x arrives in its ring stage by bulk tensor copies, issued
-    // in three parts (role 0: the byte count and the halo tile; 1: the queue front and
-    // u^{n-1} (d^n); 2: the coefficients) so that the per-plane issue work can be
-    // spread over the warps instead of delaying one warp at every CTA barrier (the
-    // mbarrier's transaction count may run below zero until the byte count arrives)
-    auto issue_part = [&](int role, int x, int stage) {
+    // every input of plane x arrives in its ring stage by bulk tensor copies
+    auto issue = [&](int x, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
         unsigned char *st = ring + stage * G::STAGE_BYTES;
-        if (role == 0) {
-            const bool need_g = !g_free(x);
-            mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW +
-                                         ((need_g ? 2 : 1) + (MODE == kModeAdjointGrad ? 2 : 0)) * G::PT_F_RAW));
-            if constexpr (MODE == kModeAdjointGrad)
-                tma_load_4d(smem_addr(st + G::OFF_X0), &gm->hist, bar, z0, y0, x, a.hist_slot);
-            tma_load_3d(smem_addr(st), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
-        } else if (role == 1) {
-            if constexpr (MODE == kModeAdjointGrad) tma_load_3d(smem_addr(st + G::OFF_X1), &gm->grad, bar, z0, y0, x);
-            tma_load_3d(smem_addr(st + G::OFF_FRONT), &maps->u_pt, bar, z0, y0, x + R);  // zero past Nx
-            tma_load_3d(smem_addr(st + G::OFF_UP), &maps->up_pt, bar, z0, y0, x);
-        } else if (role == 2) {
-            tma_load_3d(smem_addr(st + G::OFF_F1), &maps->f1_pt, bar, z0, y0, x);
-            if (!g_free(x)) tma_load_3d(smem_addr(st + G::OFF_F2), &maps->f2_pt, bar, z0, y0, x);
+        const bool need_g = !g_free(x);
+        mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW +
+                                     ((need_g ? 2 : 1) + (MODE == kModeAdjointGrad ? 2 : 0)) * G::PT_F_RAW));
+        if constexpr (MODE == kModeAdjointGrad) {
+            tma_load_4d(smem_addr(st + G::OFF_X0), &gm->hist, bar, z0, y0, x, a.hist_slot);
+            tma_load_3d(smem_addr(st + G::OFF_X1), &gm->grad, bar, z0, y0, x);
         }
+        tma_load_3d(smem_addr(st), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
+        tma_load_3d(smem_addr(st + G::OFF_FRONT), &maps->u_pt, bar, z0, y0, x + R);  // zero past Nx
+        tma_load_3d(smem_addr(st + G::OFF_UP), &maps->up_pt, bar, z0, y0, x);
+        tma_load_3d(smem_addr(st + G::OFF_F1), &maps->f1_pt, bar, z0, y0, x);
+        if (need_g) tma_load_3d(smem_addr(st + G::OFF_F2), &maps->f2_pt, bar, z0, y0, x);
     };
-    auto issue = [&](int x, int stage) {
-        for (int role = 0; role < 3; ++role) issue_part(role, x, stage);
-    };
-    // the per-plane producer roles of this thread's warp: parts 0-2 of the issue and
-    // (role 3) the L2 prefetches, one role per warp (all on warp 0 with fewer warps)
-    constexpr int kRoles = 4;
     auto prefetch = [&](int x) {
         // point data of plane x and the queue front of plane x + R into L2
         if (x < xe) {
@@ -398,7 +385,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     unsigned amax_bits = acc.amax_bits, damax_bits = acc.damax_bits;
     bool over = acc.over;
     bool failed = false;
-    int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (every thread's count)
+    int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
     int it_failed = 0;                  // first plane whose wait gave up
     int stage = g0 % S;                 // ring stage and mbarrier phase of the current plane
     uint32_t phase = uint32_t(g0 / S) & 1u;
@@ -418,21 +405,16 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                 it_failed = it;
                 break;
             }
-            if (lane == 0) {
-                for (int role = warp; role < kRoles; role += W) {
-                    if (role < 3) {
-                        if (x + S - 1 < xe) {
-                            // plane x + S - 1 takes the stage of plane x - 1, which every
-                            // thread has finished reading (it passed the barrier above)
-                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            issue_part(role, x + S - 1, stage == 0 ? S - 1 : stage - 1);
-                        }
-                    } else {
-                        prefetch(x + 1 + kPrefetchAhead);
-                    }
+            if (tid == 0) {
+                if (x + S - 1 < xe) {
+                    // plane x + S - 1 takes the stage of plane x - 1, which every thread has
+                    // finished reading (it passed the barrier above)
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(x + S - 1, stage == 0 ? S - 1 : stage - 1);
+                    ++issued;
                 }
+                prefetch(x + 1 + kPrefetchAhead);
             }
-            if (x + S - 1 < xe) ++issued;
             const unsigned char *st = ring + stage * G::STAGE_BYTES;
 #pragma unroll
             for (int r = 0; r < YB; ++r)
