@@ -210,6 +210,8 @@ def run_ours(args, rank: int, world: int):
             shape["rows"] = args.rows
         if args.tile[0]:
             shape.update(tile_z=args.tile[0], tile_y=args.tile[1])
+        if args.xblock:
+            shape["x_block"] = args.xblock
         shot = fd.Shot(spec.interior, spec.space_order, inputs.H, dt, spec.nbl, form=form, **shape)
         m = spec.m
         shot.set_model(m)
@@ -1078,6 +1080,8 @@ def main():
     ap.add_argument("--rows", type=int, default=0, help="sweep: y rows per thread of the step kernel (0 = autotuned)")
     ap.add_argument("--tile", type=lambda v: tuple(int(x) for x in v.split("x")), default=(0, 0),
                     help="sweep: step kernel tile as ZxY (default autotuned)")
+    ap.add_argument("--xblock", type=int, default=0,
+                    help="sweep: planes per CTA / flow x-chunk of the step kernel (0 = tuned)")
     ap.add_argument("--orders", type=lambda v: tuple(int(x) for x in v.split(",")), default=ORDERS,
                     help="comma-separated space orders of the sweep (default 2,4,8,12,16)")
     ap.add_argument("--forms", type=lambda v: tuple(v.split(",")), default=FORMS,
