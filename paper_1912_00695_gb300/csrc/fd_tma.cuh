@@ -377,12 +377,16 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     // scales into the input scales changes no rounding (barring subnormals):
     // d_st = w (L u_raw) s_u/s_d' + (1 - 2g) d_raw s_d/s_d' and
     // u_st = u_raw s_u/s_u' + d_st s_d'/s_u' are the stored (scaled) values directly
-    const float kd = sc.inv_s_d_out;
+    // FP32 storage has no scales: the factor is a compile-time 1 there
+    const float kd = Io<T>::kScaled ? sc.inv_s_d_out : 1.0f;
     const float2 su2 = f2(sc.s_u * kd, sc.s_u * kd), sd2 = f2(sc.s_d * kd, sc.s_d * kd);
     const float2 uu2 = f2(sc.s_u * sc.inv_s_out, sc.s_u * sc.inv_s_out);
     const float2 rr2 = f2(sc.s_d_out * sc.inv_s_out, sc.s_d_out * sc.inv_s_out);
     const int colw = 4 * lz;  // first element of the thread's z window in a tile row
     unsigned amax_bits = acc.amax_bits, damax_bits = acc.damax_bits;
+    // FP32 storage needs only to know whether a non-finite value was written:
+    // v - v is 0 for finite v and NaN otherwise, and NaN persists through the sum
+    float2 nonfinite = f2(0.f, 0.f);
     bool over = acc.over;
     bool failed = false;
     int issued = min(S - 1, xe - xb);  // planes handed to the copy engine (tid 0's count)
@@ -628,7 +632,8 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         amax_bits = max(amax_bits, bits4(unew));
                         V::st(un[r] + x * P, unew);
                     } else {
-                        amax_bits = max(amax_bits, bits4(o));
+                        const float2 oA = f2(o.x, o.y), oB = f2(o.z, o.w);
+                        nonfinite = add2(nonfinite, add2(sub2(oA, oA), sub2(oB, oB)));
                     }
                     V::st(up[r] + x * P, o);
                     if constexpr (MODE == kModeForwardD) {
@@ -665,6 +670,10 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                 mbar_wait_bounded(smem_addr(&bars[(g0 + it) % S]), uint32_t((g0 + it) / S) & 1u);
         }
         return false;
+    }
+    if constexpr (!Io<T>::kScaled) {
+        // as bits: NaN sorts above every finite magnitude (the status test)
+        if (!(nonfinite.x == 0.f && nonfinite.y == 0.f)) amax_bits = 0x7fc00000u;
     }
     acc.amax_bits = amax_bits;
     acc.damax_bits = damax_bits;
