@@ -48,9 +48,6 @@ struct TmaPipe {
 };
 constexpr long long kMbarWaitLimit = 1LL << 22;
 constexpr int kPrefetchAhead = 6;  // planes between the L2 prefetch and the register load
-#ifndef FDGB_PT_LDG
-#define FDGB_PT_LDG 0
-#endif
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -277,9 +274,6 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     constexpr int S = TmaPipe<R>::STAGES;
     static_assert(YB == 1 || YB == 2, "one or two rows per thread");
     static_assert(YB == 1 || MODE == kModeStep, "two rows per thread: the plain step");
-    // point data (queue front, u^{n-1} or d^n, coefficients) by loads through L2 instead
-    // of the ring's bulk copies
-    constexpr bool kPtLdg = FDGB_PT_LDG && MODE == kModeStep;
     uint64_t *bars = reinterpret_cast<uint64_t *>(ring - 128);  // placed by tma_ring_init
 
     const int tid = threadIdx.x;
@@ -318,16 +312,13 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
         const uint32_t bar = smem_addr(&bars[stage]);
         unsigned char *st = ring + stage * G::STAGE_BYTES;
         const bool need_g = !g_free(x);
-        mbar_expect_tx(bar, kPtLdg ? uint32_t(G::HALO_RAW)
-                                   : uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW +
-                                              ((need_g ? 2 : 1) + (MODE == kModeAdjointGrad ? 2 : 0)) *
-                                                  G::PT_F_RAW));
+        mbar_expect_tx(bar, uint32_t(G::HALO_RAW + 2 * G::PT_T_RAW +
+                                     ((need_g ? 2 : 1) + (MODE == kModeAdjointGrad ? 2 : 0)) * G::PT_F_RAW));
         if constexpr (MODE == kModeAdjointGrad) {
             tma_load_4d(smem_addr(st + G::OFF_X0), &gm->hist, bar, z0, y0, x, a.hist_slot);
             tma_load_3d(smem_addr(st + G::OFF_X1), &gm->grad, bar, z0, y0, x);
         }
         tma_load_3d(smem_addr(st), &maps->u_halo, bar, z0 - RZ, y0 - R, x);
-        if constexpr (kPtLdg) return;
         tma_load_3d(smem_addr(st + G::OFF_FRONT), &maps->u_pt, bar, z0, y0, x + R);  // zero past Nx
         tma_load_3d(smem_addr(st + G::OFF_UP), &maps->up_pt, bar, z0, y0, x);
         tma_load_3d(smem_addr(st + G::OFF_F1), &maps->f1_pt, bar, z0, y0, x);
@@ -429,23 +420,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                 prefetch(x + 1 + kPrefetchAhead);
             }
             const unsigned char *st = ring + stage * G::STAGE_BYTES;
-            float4 pcum[YB], pf1[YB], pf2[YB];  // point data loaded through L2 (kPtLdg)
-            if constexpr (kPtLdg) {
-                const bool gfx = g_free(x);
 #pragma unroll
-                for (int r = 0; r < YB; ++r) {
-                    const long long col = (long long)(y0 + ty + r) * a.pz + z4;
-                    q[r][2 * R + i] = (own[r] && x + R < a.Nx) ? V::ldcg(u[r] + (long long)(x + R) * P) : zero4;
-                    pcum[r] = own[r] ? V::ldcg(up[r] + (long long)x * P) : zero4;
-                    pf1[r] = own[r] ? __ldg(reinterpret_cast<const float4 *>(a.f1 + col + (long long)x * P)) : zero4;
-                    pf2[r] = (own[r] && !gfx) ? __ldg(reinterpret_cast<const float4 *>(a.f2 + col + (long long)x * P))
-                                              : zero4;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < YB; ++r)
-                    q[r][2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + (ty + r) * TZ + 4 * lz);
-            }
+            for (int r = 0; r < YB; ++r)
+                q[r][2 * R + i] = V::ld(reinterpret_cast<const T *>(st + G::OFF_FRONT) + (ty + r) * TZ + 4 * lz);
             float4 dv, gv;  // adjoint pass: D^{k-1} and the gradient at this plane (from the ring)
             if constexpr (MODE == kModeAdjointGrad) {
                 if (own[0]) {
@@ -497,17 +474,11 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                 float4 cum[YB], cf1[YB], cf2[YB], out[YB];
 #pragma unroll
                 for (int r = 0; r < YB; ++r) {
-                    if constexpr (kPtLdg) {
-                        cum[r] = pcum[r];
-                        cf1[r] = pf1[r];
-                        cf2[r] = pf2[r];
-                    } else {
-                        const int po = (ty + r) * TZ + 4 * lz;  // the row's 4 points in a point tile
-                        cum[r] = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + po);
-                        cf1[r] = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + po);
-                        cf2[r] = gf ? zero4
-                                    : *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F2) + po);
-                    }
+                    const int po = (ty + r) * TZ + 4 * lz;  // the row's 4 points in a point tile
+                    cum[r] = V::ld(reinterpret_cast<const T *>(st + G::OFF_UP) + po);
+                    cf1[r] = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F1) + po);
+                    cf2[r] = gf ? zero4
+                                : *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(st + G::OFF_F2) + po);
                 }
                 float sw[YB][4];
                 if constexpr (FORM == kFactored) {
