@@ -725,7 +725,7 @@ def leg_precision(args, world: int) -> dict:
             alg = algorithmic_bytes_per_step(spec, st) * spec.nt * steps
             res[st] = {"gpts": round(gpts, 2), "ms_per_step": round(ms / steps, 3),
                        "hbm_frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4), "config": list(shot.config),
-                       "launches": n_launch}
+                       "rows_schedule_flowxb": list(shot.schedule), "launches": n_launch}
             shot.close()
         return res
 
@@ -735,7 +735,8 @@ def leg_precision(args, world: int) -> dict:
     for k in args.precision_orders:
         sp = inputs.sweep_shot(k, n=args.n, nt=min(args.nt, args.nt_precision))
         r = measure(sp, False)
-        by_order[f"so{k}"] = {st: {"gpts": v["gpts"], "hbm_frac": v["hbm_frac"]} for st, v in r.items()}
+        by_order[f"so{k}"] = {st: {"gpts": v["gpts"], "hbm_frac": v["hbm_frac"],
+                                   "rows_schedule_flowxb": v["rows_schedule_flowxb"]} for st, v in r.items()}
         by_order[f"so{k}"]["bf16_vs_f32"] = round(r["bf16"]["gpts"] / r["f32"]["gpts"], 3)
         by_order[f"so{k}"]["f16_vs_f32"] = round(r["f16"]["gpts"] / r["f32"]["gpts"], 3)
     return {

@@ -253,7 +253,7 @@ int fd_forward_two_step(fd_handle *hd, int nt);
  * boundary, x_block >= k/2 (FD_ENOTSUP otherwise). A device-side wait that
  * gives up (about 2 s) ends the launch and sets FD_ETIMEOUT in the status.
  * The x-chunk length is the options' x_block if set, else timed on the
- * first steps of the first call of at least 136 steps for the grid and launch
+ * first steps of the first call of at least 144 steps for the grid and launch
  * shape (candidates 8-64 planes, 8 steps each; all of them part of the
  * requested steps, same bits) and cached for the process; a shorter first
  * call uses 40 planes for that call only. The same first call compares the

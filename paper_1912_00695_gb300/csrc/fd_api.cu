@@ -1718,15 +1718,15 @@ static int flow_prepare(fd_handle *hd, int *nt) {
         if (c >= hd->r && c <= hd->Nx) cand.push_back(c);
     if (cand.empty()) cand.push_back(std::max(hd->r, 1));
     // warm-up + candidates, then the best length and the per-step launches each
-    // timed over kTuneSteps and kLongSteps
-    const int needed = kTuneSteps * (int(cand.size()) + 1) + kLongSteps + kTuneSteps + kLongSteps;
+    // timed afresh over kTuneSteps and kLongSteps
+    const int needed = kTuneSteps * (int(cand.size()) + 1) + 2 * (kTuneSteps + kLongSteps);
     if (*nt < needed) {
         // too few steps to time: the usual best for this call, the timing left to a
         // later, longer call
         hd->flow_wins = true;
         return use(std::min(hd->Nx, std::max(40, hd->r)));
     }
-    float ms = 0.0f, best = 1e30f, flow_long = 0.0f, step_short = 0.0f, step_long = 0.0f;
+    float ms = 0.0f, best = 1e30f, flow_short = 0.0f, flow_long = 0.0f, step_short = 0.0f, step_long = 0.0f;
     int best_xb = cand[0];
     rc = flow_direct(hd, kTuneSteps, cand[cand.size() / 2], &ms);  // warm-up
     for (int c : cand) {
@@ -1741,13 +1741,15 @@ static int flow_prepare(fd_handle *hd, int *nt) {
     // t_short) / (kLongSteps - kTuneSteps), for both schedules. A flow launch carries a
     // start-up and a last tail that a long run spreads out; the difference cancels them
     // (and the per-step launches' first-launch overhead) instead of a hand-set margin.
+    // Both lengths are timed afresh: the candidates' minimum is biased low.
+    if (rc == FD_OK) rc = flow_direct(hd, kTuneSteps, best_xb, &flow_short);
     if (rc == FD_OK) rc = flow_direct(hd, kLongSteps, best_xb, &flow_long);
     if (rc == FD_OK) rc = steps_direct(hd, kTuneSteps, &step_short);
     if (rc == FD_OK) rc = steps_direct(hd, kLongSteps, &step_long);
     if (rc != FD_OK) return rc;
     *nt -= needed;
     hd->flow_xb = best_xb;
-    const float flow_per_step = (flow_long - best) / float(kLongSteps - kTuneSteps);
+    const float flow_per_step = (flow_long - flow_short) / float(kLongSteps - kTuneSteps);
     const float steps_per_step = (step_long - step_short) / float(kLongSteps - kTuneSteps);
     hd->flow_wins = flow_per_step <= steps_per_step;
     {
