@@ -447,6 +447,10 @@ def run_receivers(args, rank: int, world: int):
     pts = spec.points * spec.nt * args.steps * world
     gpts, gpts_plain = pts / (ms_rec * 1e-3) / 1e9, pts / (ms_plain * 1e-3) / 1e9
     tr = rshot.traces()
+    sched = rshot.schedule[1]
+    rec_kernel = ("fd_tma_flow_kernel (receivers sampled and extra sources added per work item) "
+                  "+ sample_receivers_kernel (last level)" if sched == 1 else
+                  "fd_tma_kernel (receivers sampled) + inject_extra_kernel + sample_receivers_kernel (last level)")
     # end to end through the public API with host buffers: model upload, source,
     # receivers, the run, read-back of the traces and the final field
     h2d = m.nbytes + wav.nbytes + recs.nbytes
@@ -477,9 +481,11 @@ def run_receivers(args, rank: int, world: int):
                    "receivers": len(recs), "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
         "plain_gpts": round(gpts_plain, 3),
         "receiver_cost_frac": round(ms_rec / ms_plain - 1.0, 4),
+        "schedule": {0: "per-step", 1: "flow", 2: "two-step"}.get(sched, str(sched)),
+        "plain_schedule": {0: "per-step", 1: "flow", 2: "two-step"}.get(plain.schedule[1], "?"),
         "roofline": {"bound": "hbm", "achieved": round(alg / (ms_rec * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(alg / (ms_rec * 1e-3) / 1e9 / peak, 4), "traffic": None,
-                     "kernel": "fd_tma_kernel + sample_receivers_kernel", "peak_source": peak_kind},
+                     "kernel": rec_kernel, "peak_source": peak_kind},
         "e2e": {"value": round(spec.points * spec.nt * args.steps * world / e2e_s / 1e9, 3), "unit": "Gpts/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": rec_launches,

@@ -248,9 +248,16 @@ int fd_forward_two_step(fd_handle *hd, int nt);
  * are taken in step order by resident CTAs, and an item starts as soon as the
  * 27 items of the previous step around it are done, so the SMs do not idle in
  * the tail of each step and between launches. Same per-point arithmetic as
- * fd_forward with the TMA kernel: the same results bit for bit. FP32 storage,
- * the TMA kernel (either form), at most 4 sources, no receivers, zero
- * boundary, x_block >= k/2 (FD_ENOTSUP otherwise). A device-side wait that
+ * fd_forward with the TMA kernel: the same results bit for bit. FP32 storage
+ * (BF16 with at most 4 sources and no receivers), the TMA kernel (either
+ * form), zero boundary, x_block >= k/2 (FD_ENOTSUP otherwise). With FP32,
+ * receivers and sources beyond the 4 fused ones ride on the items: an item
+ * samples its input level at the receivers whose lower trilinear corner lies
+ * in its region, and adds the extra sources of its region (in their order)
+ * after its stores, so traces and fields equal the per-step launches' bit for
+ * bit; the per-region lists are built on the host and kept on the device
+ * (rebuilt when the x-chunk, the tile, the sources or the receivers change).
+ * A device-side wait that
  * gives up (about 2 s) ends the launch and sets FD_ETIMEOUT in the status.
  * The x-chunk length is the options' x_block if set, else timed on the
  * first steps of the first call of at least 144 steps for the grid and launch

@@ -65,7 +65,7 @@ std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int
 // two-step kernel: (Nx, Ny, Nz, radius) -> x_block
 std::map<std::tuple<int, int, int, int>, int> g_tb_cache;
 // flow schedule: (Nx, Ny, Nz, radius, form, tile_z, tile_y) -> (x_block, faster than per-step launches)
-std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, bool>> g_flow_cache;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, std::pair<int, bool>> g_flow_cache;
 
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync) from the
 // device's default pool, whose release threshold is raised once per device so
@@ -210,10 +210,11 @@ struct fd_handle {
     // flow schedule: work counter, abort word and per-item flags; resident CTAs of its kernel
     void *flow_buf = nullptr;
     size_t flow_bytes = 0;
-    int flow_ctas = 0;
+    int flow_ctas = 0, flow_ctas_ex = 0;  // resident CTAs: plain flow kernel / receivers + extra sources variant
     int flow_xb = 0;         // the flow schedule's x_block, timed, cached or forced (0: not yet)
     int flow_run_xb = 0;     // the x_block the flow graphs are recorded with
     bool flow_wins = true;   // the flow beat per-step launches when the two were timed
+    int flow_extras = -1;    // receivers (1) / extra sources (2) present when flow_xb was chosen
     struct TbMaps {
         const void *u, *up;
         TmaMaps maps;
@@ -232,6 +233,15 @@ struct fd_handle {
     long long *d_rec_off = nullptr;
     float *d_rec_w = nullptr;
     float *d_traces = nullptr;
+    std::vector<int> rec_node;  // lower corner node (x, y, z) of each receiver
+    std::vector<long long> rec_off_h;  // host copies of the receivers' corner offsets and weights
+    std::vector<float> rec_w_h;
+    // flow schedule with receivers or extra sources (FP32): the per-region entry
+    // tables, built for one x_block and the handle's state (gen)
+    unsigned char *d_flow_tab = nullptr;
+    size_t flow_tab_bytes = 0;
+    unsigned long long flow_tab_gen = 0;
+    int flow_tab_xb = 0;
 };
 
 namespace {
@@ -696,7 +706,7 @@ void release_handle(fd_handle *hd) {
     cudaStream_t st = hd->stream ? hd->stream : hd->own_stream;
     void *bufs[] = {hd->ubuf[0], hd->ubuf[1], hd->dbuf, hd->f1, hd->f2, hd->d_wavelet, hd->d_src,
                     hd->d_status, hd->d_scales, hd->d_check, hd->d_unpack, hd->d_rec_off, hd->d_rec_w,
-                    hd->d_traces, hd->tb_buf[0], hd->tb_buf[1], hd->flow_buf};
+                    hd->d_traces, hd->tb_buf[0], hd->tb_buf[1], hd->flow_buf, hd->d_flow_tab};
     for (void *p : bufs) dev_free(p, st);
     if (hd->ev0) cudaEventDestroy(hd->ev0);
     if (hd->ev1) cudaEventDestroy(hd->ev1);
@@ -972,14 +982,19 @@ int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max) {
     hd->d_traces = nullptr;
     hd->n_rec = 0;
     hd->rec_nt_max = 0;
+    hd->rec_node.clear();
+    hd->rec_off_h.clear();
+    hd->rec_w_h.clear();
     hd->gen++;
     if (n == 0) return FD_OK;
     std::vector<long long> off(size_t(n) * 8);
     std::vector<float> w(size_t(n) * 8);
+    std::vector<int> lower(size_t(n) * 3);
     for (int r = 0; r < n; ++r) {
         int nodes[8][3];
         double wd[8];
         trilinear_nodes(hd, xyz[3 * r], xyz[3 * r + 1], xyz[3 * r + 2], nodes, wd);
+        for (int a = 0; a < 3; ++a) lower[size_t(r) * 3 + a] = nodes[0][a];
         for (int c = 0; c < 8; ++c) {
             off[size_t(r) * 8 + c] = (long long)nodes[c][0] * hd->plane + (long long)nodes[c][1] * hd->pz + nodes[c][2];
             w[size_t(r) * 8 + c] = float(wd[c]);
@@ -1006,6 +1021,9 @@ int fd_set_receivers(fd_handle *hd, int n, const double *xyz, int nt_max) {
     hd->n_rec = n;
     hd->rec_nt_max = nt_max;
     hd->rec_step0 = hd->step;
+    hd->rec_node = std::move(lower);
+    hd->rec_off_h = std::move(off);
+    hd->rec_w_h = std::move(w);
     return FD_OK;
 }
 
@@ -1534,6 +1552,115 @@ int fd_forward(fd_handle *hd, int nt) {
     return run_steps(hd, nt);
 }
 
+// FP32 flow with receivers or sources beyond the fused ones: the per-region
+// entry tables (regions numbered as the flow's flags: x-chunk, y tile, z tile,
+// z fastest; a receiver belongs to the region of its lower corner node, a source
+// to that of its node; entries of a region in receiver / source order). One
+// device buffer: rec_start[P + 1], rec_row[n_rec], xs_start[P + 1],
+// xs_idx[n_x], then (64-byte aligned) rec_off[8 n_rec], xs_off[n_x] and
+// rec_w[8 n_rec]. Rebuilt when the x_block or the handle's state changes; a
+// rebuild re-records the graphs.
+struct FlowTables {
+    size_t rec_start, rec_row, xs_start, xs_idx, rec_off, xs_off, rec_w, bytes;
+};
+
+static FlowTables flow_table_layout(long long regions, int n_rec, int n_x) {
+    auto up = [](size_t b, size_t a) { return (b + a - 1) / a * a; };
+    FlowTables t{};
+    size_t b = 0;
+    t.rec_start = b;
+    b += n_rec > 0 ? size_t(regions + 1) * sizeof(int) : 0;
+    t.rec_row = b;
+    b += size_t(n_rec) * sizeof(int);
+    t.xs_start = b;
+    b += n_x > 0 ? size_t(regions + 1) * sizeof(int) : 0;
+    t.xs_idx = b;
+    b += size_t(n_x) * sizeof(int);
+    t.rec_off = b = up(b, 64);
+    b += size_t(n_rec) * 8 * sizeof(long long);
+    t.xs_off = b;
+    b += size_t(n_x) * sizeof(long long);
+    t.rec_w = b = up(b, 64);
+    b += size_t(n_rec) * 8 * sizeof(float);
+    t.bytes = up(b, 64);
+    return t;
+}
+
+static int flow_tables(fd_handle *hd, int xb, int nbz, int nby, int nbx) {
+    const int ns = int(hd->sources.size());
+    const int n_x = ns > kFusedSources ? ns - kFusedSources : 0;
+    if (hd->opt.storage != kF32 || (hd->n_rec == 0 && n_x == 0)) return FD_OK;
+    if (hd->d_flow_tab && hd->flow_tab_gen == hd->gen && hd->flow_tab_xb == xb) return FD_OK;
+    const long long regions = (long long)nbz * nby * nbx;
+    auto region = [&](int x, int y, int z) {
+        return (long long)(x / xb) * nby * nbz + (long long)(y / hd->tile_y) * nbz + z / hd->tile_z;
+    };
+    const FlowTables L = flow_table_layout(regions, hd->n_rec, n_x);
+    std::vector<unsigned char> buf(L.bytes, 0);
+    // counting sort of entries 0..count-1 by region: start[regions + 1], order[count]
+    auto by_region = [&](const std::vector<long long> &reg, int *start, std::vector<int> &order) {
+        for (long long g = 0; g <= regions; ++g) start[g] = 0;
+        for (size_t i = 0; i < reg.size(); ++i) start[reg[i] + 1]++;
+        for (long long g = 0; g < regions; ++g) start[g + 1] += start[g];
+        std::vector<int> fill(start, start + regions);
+        order.resize(reg.size());
+        for (size_t i = 0; i < reg.size(); ++i) order[size_t(fill[size_t(reg[i])]++)] = int(i);
+    };
+    std::vector<int> order;
+    if (hd->n_rec > 0) {
+        std::vector<long long> reg(size_t(hd->n_rec));
+        for (int r = 0; r < hd->n_rec; ++r) {
+            const int *n = &hd->rec_node[size_t(r) * 3];
+            reg[size_t(r)] = region(n[0], n[1], n[2]);
+        }
+        by_region(reg, reinterpret_cast<int *>(&buf[L.rec_start]), order);
+        int *row = reinterpret_cast<int *>(&buf[L.rec_row]);
+        long long *off = reinterpret_cast<long long *>(&buf[L.rec_off]);
+        float *w = reinterpret_cast<float *>(&buf[L.rec_w]);
+        for (size_t e = 0; e < order.size(); ++e) {
+            const size_t r = size_t(order[e]);
+            row[e] = int(r);
+            for (int c = 0; c < 8; ++c) {
+                off[8 * e + size_t(c)] = hd->rec_off_h[8 * r + size_t(c)];
+                w[8 * e + size_t(c)] = hd->rec_w_h[8 * r + size_t(c)];
+            }
+        }
+    }
+    if (n_x > 0) {
+        std::vector<long long> reg(static_cast<size_t>(n_x));
+        for (int i = 0; i < n_x; ++i) {
+            const Source &q = hd->sources[size_t(i + kFusedSources)];
+            reg[size_t(i)] = region(q.x, q.y, q.z);
+        }
+        by_region(reg, reinterpret_cast<int *>(&buf[L.xs_start]), order);
+        int *idx = reinterpret_cast<int *>(&buf[L.xs_idx]);
+        long long *off = reinterpret_cast<long long *>(&buf[L.xs_off]);
+        for (size_t e = 0; e < order.size(); ++e) {
+            const Source &q = hd->sources[size_t(order[e] + kFusedSources)];
+            idx[e] = order[e] + kFusedSources;
+            off[e] = (long long)q.x * hd->plane + (long long)q.y * hd->pz + q.z;
+        }
+    }
+    if (hd->flow_tab_bytes < L.bytes) {
+        dev_free(hd->d_flow_tab, hd->stream);
+        hd->d_flow_tab = nullptr;
+        hd->flow_tab_bytes = 0;
+        if (dev_alloc(reinterpret_cast<void **>(&hd->d_flow_tab), L.bytes, hd->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FD_ENOMEM, "cannot allocate the flow schedule's receiver and source tables");
+        }
+        hd->flow_tab_bytes = L.bytes;
+    }
+    if (reinterpret_cast<uintptr_t>(hd->d_flow_tab) % 64 != 0)
+        return fail(FD_ECUDA, "flow tables not 64-byte aligned");
+    FD_CUDA(cudaMemcpyAsync(hd->d_flow_tab, buf.data(), L.bytes, cudaMemcpyHostToDevice, hd->stream));
+    FD_CUDA(cudaStreamSynchronize(hd->stream));  // the host table goes out of scope
+    hd->gen++;  // graphs recorded with the old tables
+    hd->flow_tab_gen = hd->gen;
+    hd->flow_tab_xb = xb;
+    return FD_OK;
+}
+
 // Flow launch arguments for nt steps from the handle's state with x-chunks of
 // xb planes; *bytes: the zeroed prefix of the flow buffer (counter, abort, flags).
 static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *bytes, int *ctas) {
@@ -1554,14 +1681,18 @@ static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *by
         hd->flow_bytes = *bytes;
         hd->gen++;  // graphs recorded with the old buffer
     }
-    if (hd->flow_ctas == 0) {
+    // the FP32 variant that samples receivers and adds extra sources per item
+    const int ns = int(hd->sources.size()), n_x = ns > kFusedSources ? ns - kFusedSources : 0;
+    const bool ex = hd->opt.storage == kF32 && (hd->n_rec > 0 || n_x > 0);
+    int &flow_ctas = ex ? hd->flow_ctas_ex : hd->flow_ctas;
+    if (flow_ctas == 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int per_sm = tma_flow_ctas_per_sm(hd->r, hd->opt.form, hd->opt.storage, hd->tile_z, hd->tile_y,
-                                                hd->rows);
+                                                hd->rows, ex);
         if (per_sm <= 0 || sms <= 0) return fail(FD_ENOTSUP, "no flow kernel for this launch shape");
-        hd->flow_ctas = per_sm * sms;
+        flow_ctas = per_sm * sms;
     }
     f->maps[0] = hd->tmaps[0];
     f->maps[1] = hd->tmaps[1];
@@ -1579,7 +1710,34 @@ static int make_flow_args(fd_handle *hd, int nt, int xb, FlowArgs *f, size_t *by
     f->abort = reinterpret_cast<unsigned *>(fb + 4);
     f->amax = reinterpret_cast<unsigned *>(fb + 8);
     f->flags = reinterpret_cast<unsigned *>(fb + 16);
-    *ctas = int(std::min<long long>(hd->flow_ctas, per_step * nt));
+    f->a[0].n_rec = f->a[1].n_rec = 0;  // the flow kernel samples per item
+    f->rec_start = f->rec_row = f->xs_start = f->xs_idx = nullptr;
+    f->rec_off = f->xs_off = nullptr;
+    f->rec_w = f->traces = nullptr;
+    f->rec_stride = 0;
+    f->rec_s0 = 0;
+    f->xs_distinct = hd->extra_distinct ? 1 : 0;
+    const int rc = flow_tables(hd, xb, nbz, nby, nbx);
+    if (rc != FD_OK) return rc;
+    if (ex) {
+        const FlowTables L = flow_table_layout(per_step, hd->n_rec, n_x);
+        unsigned char *t = hd->d_flow_tab;
+        if (hd->n_rec > 0) {
+            f->rec_start = reinterpret_cast<const int *>(t + L.rec_start);
+            f->rec_row = reinterpret_cast<const int *>(t + L.rec_row);
+            f->rec_off = reinterpret_cast<const long long *>(t + L.rec_off);
+            f->rec_w = reinterpret_cast<const float *>(t + L.rec_w);
+            f->traces = hd->d_traces;
+            f->rec_stride = hd->rec_nt_max;
+            f->rec_s0 = hd->rec_step0;
+        }
+        if (n_x > 0) {
+            f->xs_start = reinterpret_cast<const int *>(t + L.xs_start);
+            f->xs_idx = reinterpret_cast<const int *>(t + L.xs_idx);
+            f->xs_off = reinterpret_cast<const long long *>(t + L.xs_off);
+        }
+    }
+    *ctas = int(std::min<long long>(flow_ctas, per_step * nt));
     return FD_OK;
 }
 
@@ -1596,6 +1754,7 @@ static int flow_direct(fd_handle *hd, int nt, int xb, float *ms) {
                             check_enabled(hd), hd->stream));
     if (hd->opt.storage != kF32)
         FD_CUDA(launch_flow_finish_scales(hd->d_scales, int(((hd->step + nt) % 3 + 3) % 3), f.amax, hd->stream));
+    FD_CUDA(sample_level(hd, hd->ubuf[hd->cur ^ (nt & 1)], hd->step + nt, hd->stream));
     FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
     FD_CUDA(cudaEventSynchronize(hd->ev1));
     FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
@@ -1614,7 +1773,7 @@ static int ensure_step_tuned(fd_handle *hd) {
         return rc;
     }
     hd->gen++;
-    hd->flow_ctas = 0;
+    hd->flow_ctas = hd->flow_ctas_ex = 0;
     hd->flow_xb = 0;
     hd->flow_run_xb = 0;
     return FD_OK;
@@ -1653,6 +1812,8 @@ static int run_flow(fd_handle *hd, int nt) {
                                 check, st);
         if (e == cudaSuccess && hd->opt.storage != kF32)
             e = launch_flow_finish_scales(hd->d_scales, int(((hd->step + nt) % 3 + 3) % 3), f.amax, st);
+        // the items sample their input levels: the last level is sampled here
+        if (e == cudaSuccess) e = sample_level(hd, hd->ubuf[hd->cur ^ (nt & 1)], hd->step + nt, st);
         return e;
     });
 }
@@ -1665,6 +1826,7 @@ static int steps_direct(fd_handle *hd, int nt, float *ms) {
         FD_CUDA(enqueue_step(hd, make_args(hd, hd->step + i, cur), hd->stream));
         cur ^= 1;
     }
+    if (hd->kernel == kTma) FD_CUDA(sample_level(hd, hd->ubuf[cur], hd->step + nt, hd->stream));
     FD_CUDA(cudaEventRecord(hd->ev1, hd->stream));
     FD_CUDA(cudaEventSynchronize(hd->ev1));
     FD_CUDA(cudaEventElapsedTime(ms, hd->ev0, hd->ev1));
@@ -1674,9 +1836,9 @@ static int steps_direct(fd_handle *hd, int nt, float *ms) {
 }
 
 static bool flow_eligible(const fd_handle *hd) {
-    return (hd->opt.storage == kF32 || hd->opt.storage == kBF16) && hd->kernel == kTma && hd->n_rec == 0 &&
-           int(hd->sources.size()) <= kFusedSources && hd->opt.boundary == FD_BOUNDARY_ZERO &&
-           (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r);
+    const bool plain = hd->n_rec == 0 && int(hd->sources.size()) <= kFusedSources;
+    return (hd->opt.storage == kF32 || (hd->opt.storage == kBF16 && plain)) && hd->kernel == kTma &&
+           hd->opt.boundary == FD_BOUNDARY_ZERO && (hd->opt.x_block == 0 || hd->opt.x_block >= hd->r);
 }
 
 // Chooses the flow schedule's x_block and whether it beats per-step launches,
@@ -1694,13 +1856,18 @@ static int flow_prepare(fd_handle *hd, int *nt) {
         }
         return FD_OK;
     };
-    if (hd->flow_xb != 0) return use(hd->flow_xb);
+    // receivers and extra sources change the balance of the two schedules: their
+    // presence is part of the choice (made again when it changes)
+    const int extras = (hd->n_rec > 0 ? 1 : 0) | (int(hd->sources.size()) > kFusedSources ? 2 : 0);
+    if (hd->flow_xb != 0 && hd->flow_extras == extras) return use(hd->flow_xb);
+    hd->flow_extras = extras;
     if (hd->opt.x_block > 0) {  // forced by the options
         hd->flow_xb = hd->opt.x_block;
         hd->flow_wins = true;
         return use(hd->flow_xb);
     }
-    const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y);
+    hd->flow_xb = 0;
+    const auto key = std::make_tuple(hd->Nx, hd->Ny, hd->Nz, hd->r, hd->opt.form, hd->tile_z, hd->tile_y, extras);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_flow_cache.find(key);
@@ -1766,7 +1933,8 @@ int fd_forward_flow(fd_handle *hd, int nt) {
     if (!hd->has_model) return fail(FD_ESTATE, "fd_forward_flow before fd_set_model");
     if (!flow_eligible(hd) && !(hd->opt.x_block > 0 && hd->opt.x_block < hd->r))
         return fail(FD_ENOTSUP,
-                    "the flow schedule: FP32 or BF16 storage, TMA kernel, <= %d sources, no receivers, zero boundary",
+                    "the flow schedule: FP32 storage (BF16 with <= %d sources and no receivers), TMA kernel, "
+                    "zero boundary",
                     kFusedSources);
     // an item reads the queue planes and fronts of its x-neighbours only
     if (hd->opt.x_block > 0 && hd->opt.x_block < hd->r)
@@ -1923,8 +2091,13 @@ int fd_get_schedule(fd_handle *hd, int *rows, int *schedule, int *flow_x_block) 
                           hd->opt.storage == kF32 && hd->opt.form == kFactored && hd->n_rec == 0 &&
                           int(hd->sources.size()) <= kFusedSources && !hd->slab;
     if (rows) *rows = tuned ? hd->rows : 0;
-    if (schedule) *schedule = !tuned ? 0 : two_step ? 2 : (hd->opt.kernel == kAuto && flow_eligible(hd) && hd->flow_wins && hd->flow_xb) ? 1 : 0;
-    if (flow_x_block) *flow_x_block = hd->flow_xb;
+    // flow_run_xb: the x-chunk of the last flow call (also a short first call's)
+    if (schedule)
+        *schedule = !tuned ? 0
+                    : two_step ? 2
+                    : (hd->opt.kernel == kAuto && flow_eligible(hd) && hd->flow_wins && hd->flow_run_xb) ? 1
+                                                                                                          : 0;
+    if (flow_x_block) *flow_x_block = hd->flow_run_xb;
     return FD_OK;
 }
 

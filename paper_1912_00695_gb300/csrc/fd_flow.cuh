@@ -71,17 +71,88 @@ __device__ __forceinline__ ScaleState flow_scales(const FlowArgs &f, bool first)
     return st;
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
+// Receivers of the item of step s (FP32): entries [i0, i1) of the region's
+// list, one per thread. Each receiver's other corners lie in the neighbouring
+// regions, whose u^{step0+s} the dependency wait has seen completed and which no
+// item overwrites before this item's flag. The corners are summed in the
+// single-step kernel's order (same bits); the field loads bypass L1, since the
+// buffer held older levels earlier in the launch. Kept out of line: the
+// kernel's register allocation stays that of the plain flow.
+static __device__ __noinline__ void flow_sample_receivers(const FlowArgs &f, const StepArgs &a, int s, int i0,
+                                                          int i1) {
+    const long long smp = f.step0 + s - f.rec_s0 - 1;
+    if (smp < 0 || smp >= f.rec_stride) return;
+    const float *__restrict__ u = static_cast<const float *>(a.u);
+    for (int i = i0 + int(threadIdx.x); i < i1; i += int(blockDim.x)) {
+        const longlong2 *o = reinterpret_cast<const longlong2 *>(f.rec_off) + 4 * (long long)i;
+        const float4 *wp = reinterpret_cast<const float4 *>(f.rec_w) + 2 * (long long)i;
+        const longlong2 o01 = __ldg(o), o23 = __ldg(o + 1), o45 = __ldg(o + 2), o67 = __ldg(o + 3);
+        const float4 w03 = __ldg(wp), w47 = __ldg(wp + 1);
+        const long long off[8] = {o01.x, o01.y, o23.x, o23.y, o45.x, o45.y, o67.x, o67.y};
+        const float w[8] = {w03.x, w03.y, w03.z, w03.w, w47.x, w47.y, w47.z, w47.w};
+        float c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = __ldcg(u + off[k]);
+        float v = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v = fmaf(w[k], c[k], v);
+        f.traces[(long long)__ldg(f.rec_row + i) * f.rec_stride + smp] = v;
+    }
+}
+
+// Sources beyond the fused ones, item of step s (FP32): entries [i0, i1) of the
+// region's list, added after the item's stores of u^{step0+s+1} and before its
+// flag, as the per-step extra-source kernel adds them (one thread per entry at
+// distinct nodes, else one thread in source order).
+static __device__ __noinline__ void flow_inject_extra(const FlowArgs &f, const StepArgs &a, int s, int i0, int i1,
+                                                      bool expanded) {
+    const long long step = f.step0 + s;
+    if (step < 0 || step >= a.ld) return;
+    float *up = static_cast<float *>(a.up);
+    const int t = int(threadIdx.x);
+    if (!f.xs_distinct) {
+        if (t != 0) return;
+        for (int i = i0; i < i1; ++i) {
+            const long long p = f.xs_off[i];
+            add_extra_source_f32(up, p, extra_source_weight(a, p, expanded), a.wavelet[(long long)f.xs_idx[i] * a.ld + step]);
+        }
+        return;
+    }
+    for (int i = i0 + t; i < i1; i += int(blockDim.x)) {
+        const long long p = f.xs_off[i];
+        add_extra_source_f32(up, p, extra_source_weight(a, p, expanded), a.wavelet[(long long)f.xs_idx[i] * a.ld + step]);
+    }
+}
+
+// The region's entry ranges [rec begin, rec end, source begin, source end) (FP32
+// flow with receivers or extra sources; zeros otherwise).
+static __device__ __noinline__ void flow_region_ranges(const FlowArgs &f, int rem, int *out) {
+    out[0] = out[1] = out[2] = out[3] = 0;
+    if (f.rec_start) {
+        out[0] = f.rec_start[rem];
+        out[1] = f.rec_start[rem + 1];
+    }
+    if (f.xs_start) {
+        out[2] = f.xs_start[rem];
+        out[3] = f.xs_start[rem + 1];
+    }
+}
+
+// EX: the FP32 variant with receivers and extra sources handled per item; the
+// plain variant carries none of that code.
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float, bool EX = false>
 __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma_warps_per_sm(R, YB) / W : 1))
     fd_tma_flow_kernel(const __grid_constant__ FlowArgs f, int check) {
     static_assert(std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value,
                   "the flow schedule stores FP32 or BF16 (FP16 needs per-level scales)");
+    static_assert(!EX || std::is_same<T, float>::value, "receivers and extra sources ride on the FP32 flow only");
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // item slots: the item of iteration i sits in s_item[i & 1]; thread 0 claims the
     // next one while the current one runs (claims stay in increasing order per CTA,
     // so the lowest unfinished item is always being worked on)
     __shared__ int s_item[2];
     __shared__ int s_fail;
+    __shared__ int s_ranges[4];  // the item's receiver and extra-source entries (EX)
     unsigned char *ring = tma_ring_init<R>(smem_dyn);
     const ScaleState sc0 = flow_scales<T>(f, true), sc1 = flow_scales<T>(f, false);
     const int per_plane = f.nbz * f.nby;
@@ -110,6 +181,10 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
                 if (nx >= 0 && nx < f.nbx && ny >= 0 && ny < f.nby && nz >= 0 && nz < f.nbz)
                     ok = flow_wait(&f.flags[nx * per_plane + ny * f.nbz + nz], unsigned(s), f.abort);
             }
+            if constexpr (EX) {
+                // lane 31 waits on no neighbour: it fetches the item's entry ranges meanwhile
+                if (l == 31) flow_region_ranges(f, rem, s_ranges);
+            }
             ok = __all_sync(0xffffffffu, ok);
             if (l == 0) {
                 // the copy engine reads what the acquired flags published
@@ -122,6 +197,9 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
             ok_all = false;
             break;
         }
+        if constexpr (EX) {
+            if (s_ranges[1] > s_ranges[0]) flow_sample_receivers(f, a, s, s_ranges[0], s_ranges[1]);
+        }
         const int xb = bx * a.x_block;
         if (!tma_segment<R, FORM, LZ, W, T, kModeStep, true, YB>(&f.maps[p], a, s == 0 ? sc0 : sc1, bz, by, xb,
                                                                  min(xb + a.x_block, a.Nx), ring, g, acc, nullptr,
@@ -130,6 +208,12 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
             break;
         }
         __syncthreads();  // the item's stores precede the flag
+        if constexpr (EX) {
+            if (s_ranges[3] > s_ranges[2]) {
+                flow_inject_extra(f, a, s, s_ranges[2], s_ranges[3], FORM == kExpanded);
+                __syncthreads();  // and the added sources
+            }
+        }
         if (threadIdx.x == 0) {
             __threadfence();
             st_release_u32(&f.flags[rem], unsigned(s + 1));
@@ -163,10 +247,10 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R, YB) / W > 0 ? tma
     }
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float, bool EX = false>
 cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
     using G = TmaShape<R, LZ, W, T, 0, YB>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T, EX>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -177,10 +261,10 @@ cudaError_t tma_flow_launch(const FlowArgs &f, int ctas, bool check, cudaStream_
     return cudaGetLastError();
 }
 
-template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float>
+template <int R, int FORM, int LZ, int W, int YB = 1, typename T = float, bool EX = false>
 int tma_flow_occupancy() {
     using G = TmaShape<R, LZ, W, T, 0, YB>;
-    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T>;
+    auto kernel = fd_tma_flow_kernel<R, FORM, LZ, W, YB, T, EX>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) != cudaSuccess)
         return 0;
     int n = 0;
@@ -189,17 +273,19 @@ int tma_flow_occupancy() {
 }
 
 template <int R>
-cudaError_t tma_flow_r(int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f, int ctas,
-                       bool check, cudaStream_t s) {
-#define FDGB_FLOW_CASE(LZ, W, YB)                                                               \
-    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB) {                 \
-        if (storage == kF32)                                                                    \
-            return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, YB>(f, ctas, check, s) \
-                                     : tma_flow_launch<R, kExpanded, LZ, W, YB>(f, ctas, check, s); \
+cudaError_t tma_flow_r(int form, int storage, int tile_z, int tile_y, int rows, bool ex, const FlowArgs &f,
+                       int ctas, bool check, cudaStream_t s) {
+#define FDGB_FLOW_CASE(LZ, W, YB)                                                                        \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kF32) {       \
+        if (ex)                                                                                          \
+            return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, YB, float, true>(f, ctas, check, s) \
+                                     : tma_flow_launch<R, kExpanded, LZ, W, YB, float, true>(f, ctas, check, s); \
+        return form == kFactored ? tma_flow_launch<R, kFactored, LZ, W, YB>(f, ctas, check, s)           \
+                                 : tma_flow_launch<R, kExpanded, LZ, W, YB>(f, ctas, check, s);          \
     }
 #define FDGB_FLOW_CASE16(LZ, W, YB)                                                             \
     if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kBF16 && \
-        form == kFactored)                                                                      \
+        form == kFactored && !ex)                                                               \
         return tma_flow_launch<R, kFactored, LZ, W, YB, __nv_bfloat16>(f, ctas, check, s);
 #define FDGB_FLOW_1(LZ, W) FDGB_FLOW_CASE(LZ, W, 1)
 #define FDGB_FLOW_2(LZ, W) FDGB_FLOW_CASE(LZ, W, 2) FDGB_FLOW_CASE16(LZ, W, 2)
@@ -221,16 +307,18 @@ cudaError_t tma_flow_r(int form, int storage, int tile_z, int tile_y, int rows, 
 }
 
 template <int R>
-int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows) {
+int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows, bool ex) {
 #define FDGB_FLOW_OCC(LZ, W, YB)                                                                \
-    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB) {                 \
-        if (storage == kF32)                                                                    \
-            return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, YB>()            \
-                                     : tma_flow_occupancy<R, kExpanded, LZ, W, YB>();           \
+    if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kF32) { \
+        if (ex)                                                                                 \
+            return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, YB, float, true>() \
+                                     : tma_flow_occupancy<R, kExpanded, LZ, W, YB, float, true>(); \
+        return form == kFactored ? tma_flow_occupancy<R, kFactored, LZ, W, YB>()                \
+                                 : tma_flow_occupancy<R, kExpanded, LZ, W, YB>();               \
     }
 #define FDGB_FLOW_OCC16(LZ, W, YB)                                                              \
     if (tile_z == 4 * (LZ) && tile_y == YB * (32 / (LZ)) * (W) && rows == YB && storage == kBF16 && \
-        form == kFactored)                                                                      \
+        form == kFactored && !ex)                                                               \
         return tma_flow_occupancy<R, kFactored, LZ, W, YB, __nv_bfloat16>();
 #define FDGB_FLOW_1(LZ, W) FDGB_FLOW_OCC(LZ, W, 1)
 #define FDGB_FLOW_2(LZ, W) FDGB_FLOW_OCC(LZ, W, 2) FDGB_FLOW_OCC16(LZ, W, 2)
@@ -255,11 +343,11 @@ int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows) {
 
 #define FDGB_INSTANTIATE_FLOW_RADIUS(R)                                                           \
     namespace fdgb {                                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows,      \
+    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex, \
                                     const FlowArgs &f, int ctas, bool check, cudaStream_t s) {    \
-        return tma_flow_r<R>(form, storage, tile_z, tile_y, rows, f, ctas, check, s);             \
+        return tma_flow_r<R>(form, storage, tile_z, tile_y, rows, ex, f, ctas, check, s);         \
     }                                                                                             \
-    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows) {        \
-        return tma_flow_occ_r<R>(form, storage, tile_z, tile_y, rows);                            \
+    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex) { \
+        return tma_flow_occ_r<R>(form, storage, tile_z, tile_y, rows, ex);                        \
     }                                                                                             \
     }

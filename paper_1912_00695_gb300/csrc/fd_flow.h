@@ -25,6 +25,26 @@ struct FlowArgs {
     // the maxima of every stored value land in amax[0] (u) and amax[1] (d), zeroed
     // with the flags, for the next launch's scale selection
     unsigned *amax;
+    // FP32 only, null / zero otherwise. Regions are numbered as the flags.
+    // Receivers: the item of step s samples its input level u^{step0+s} at the
+    // receivers of its region (entries rec_start[rem] .. rec_start[rem + 1] - 1:
+    // trace row rec_row, 8 pitched corner offsets rec_off and weights rec_w, in
+    // the corner order of the receivers' own tables) into
+    // traces[row * rec_stride + (step0 + s - rec_s0 - 1)] when that index lies in
+    // [0, rec_stride). Sources beyond the fused ones: the item of step s adds the
+    // sources of its region (entries xs_start[rem] ..: source index xs_idx and
+    // pitched node offset xs_off, in source order) to u^{step0+s+1} after its
+    // own stores, one thread per entry when the nodes are pairwise distinct
+    // (xs_distinct), else one thread in order.
+    const int *rec_start, *rec_row;
+    const long long *rec_off;
+    const float *rec_w;
+    float *traces;
+    int rec_stride;
+    long long rec_s0;
+    const int *xs_start, *xs_idx;
+    const long long *xs_off;
+    int xs_distinct;
 };
 
 // One persistent launch of the flow kernel for radius/form/tile; `ctas` is the
@@ -35,7 +55,9 @@ cudaError_t launch_tma_flow(int radius, int form, int storage, int tile_z, int t
 // After a BF16 flow launch: the level it ended on gets unit scales and the
 // launch's maxima (the next per-step launch selects its scales from them).
 cudaError_t launch_flow_finish_scales(LevelScales *scales, int slot, const unsigned *amax, cudaStream_t s);
-// Resident CTAs per SM of that kernel (0 if the configuration does not exist).
-int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows);
+// Resident CTAs per SM of that kernel (0 if the configuration does not exist);
+// ex: the FP32 variant with receivers and extra sources (launched when the
+// arguments carry their tables).
+int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows, bool ex);
 
 }  // namespace fdgb

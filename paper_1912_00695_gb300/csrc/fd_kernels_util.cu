@@ -5,8 +5,10 @@
 #include <cuda_fp16.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "fd_internal.h"
+#include "fd_stencil.cuh"
 #include "fd_flow.h"
 #include "fd_launch_count.h"
 
@@ -215,9 +217,9 @@ cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, 
 }
 
 #define FDGB_DECLARE_FLOW_RADIUS(R)                                                              \
-    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, const FlowArgs &f, \
-                                    int ctas, bool check, cudaStream_t s);                        \
-    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows);
+    cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex,   \
+                                    const FlowArgs &f, int ctas, bool check, cudaStream_t s);     \
+    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex);
 FDGB_DECLARE_FLOW_RADIUS(1)
 FDGB_DECLARE_FLOW_RADIUS(2)
 FDGB_DECLARE_FLOW_RADIUS(3)
@@ -234,9 +236,11 @@ FDGB_DECLARE_FLOW_RADIUS(12)
 
 static cudaError_t launch_tma_flow_dispatch(int radius, int form, int storage, int tile_z, int tile_y, int rows,
                                             const FlowArgs &f, int ctas, bool check, cudaStream_t s) {
+    // receivers or extra sources: the variant that handles them per item
+    const bool ex = f.rec_start != nullptr || f.xs_start != nullptr;
     switch (radius) {
 #define FDGB_FLOW_R(R) \
-        case R: return tma_flow_radius_##R(form, storage, tile_z, tile_y, rows, f, ctas, check, s);
+        case R: return tma_flow_radius_##R(form, storage, tile_z, tile_y, rows, ex, f, ctas, check, s);
         FDGB_FLOW_R(1) FDGB_FLOW_R(2) FDGB_FLOW_R(3) FDGB_FLOW_R(4)
         FDGB_FLOW_R(5) FDGB_FLOW_R(6) FDGB_FLOW_R(7) FDGB_FLOW_R(8)
         FDGB_FLOW_R(9) FDGB_FLOW_R(10) FDGB_FLOW_R(11) FDGB_FLOW_R(12)
@@ -250,10 +254,10 @@ cudaError_t launch_tma_flow(int radius, int form, int storage, int tile_z, int t
     return counted(launch_tma_flow_dispatch(radius, form, storage, tile_z, tile_y, rows, f, ctas, check, s), s);
 }
 
-int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows) {
+int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile_y, int rows, bool ex) {
     switch (radius) {
 #define FDGB_FLOW_O(R) \
-        case R: return tma_flow_occ_radius_##R(form, storage, tile_z, tile_y, rows);
+        case R: return tma_flow_occ_radius_##R(form, storage, tile_z, tile_y, rows, ex);
         FDGB_FLOW_O(1) FDGB_FLOW_O(2) FDGB_FLOW_O(3) FDGB_FLOW_O(4)
         FDGB_FLOW_O(5) FDGB_FLOW_O(6) FDGB_FLOW_O(7) FDGB_FLOW_O(8)
         FDGB_FLOW_O(9) FDGB_FLOW_O(10) FDGB_FLOW_O(11) FDGB_FLOW_O(12)
@@ -337,14 +341,13 @@ __global__ void inject_extra_kernel(const StepArgs a, const int *sx, const int *
     for (int i = i0; i < i1; ++i) {
         const long long p = (long long)sx[i] * a.plane + (long long)sy[i] * a.pz + sz[i];
         const float q = a.wavelet[(long long)i * a.ld + a.step];
-        const float f1 = a.f1[p], f2 = a.f2[p];
-        const float w = expanded ? a.dt2 * __frcp_rn(fmaf(a.half_dt, f2, f1)) : f1;
-        if (un) {
+        const float w = extra_source_weight(a, p, expanded != 0);
+        if constexpr (std::is_same<T, float>::value) {
+            add_extra_source_f32(up, p, w, q);
+            if (hist) add_extra_source_f32(hist, p, w, q);  // the stored second time difference includes it
+        } else {
             up[p] = from_f<T>((to_f<T>(up[p]) * s_d + w * q) / s_d);
             un[p] = from_f<T>((to_f<T>(un[p]) * s_u + w * q) / s_u);
-        } else {
-            up[p] = from_f<T>(to_f<T>(up[p]) * s_u + w * q);
-            if (hist) hist[p] += w * q;  // the stored second time difference includes the source
         }
     }
 }

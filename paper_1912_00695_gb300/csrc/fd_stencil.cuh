@@ -127,6 +127,17 @@ __device__ __forceinline__ void reduce_amax(const StepArgs &a, unsigned bits, bo
     }
 }
 
+// A point source beyond the fused ones, added to the FP32 level u^{n+1} at
+// pitched offset p after the step (its weight: factored w; expanded
+// dt^2 / (m + dt/2 eta)); one fused multiply-add. Shared by the per-step
+// extra-source kernel and the flow schedule, so both give the same bits.
+__device__ __forceinline__ float extra_source_weight(const StepArgs &a, long long p, bool expanded) {
+    return expanded ? a.dt2 * __frcp_rn(fmaf(a.half_dt, a.f2[p], a.f1[p])) : a.f1[p];
+}
+__device__ __forceinline__ void add_extra_source_f32(float *level, long long p, float w, float q) {
+    level[p] = __fmaf_rn(w, q, level[p]);
+}
+
 __device__ __forceinline__ float source_value(const StepArgs &a, int s) {
     return (a.step >= 0 && a.step < a.ld) ? __ldg(a.wavelet + (long long)s * a.ld + a.step) : 0.0f;
 }

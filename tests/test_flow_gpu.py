@@ -4,7 +4,8 @@ bit for bit the per-step launches of the same kernel (every space order, both
 forms, several tiles and x-blocks down to x_block = k/2, ragged grids, chunked
 calls, sources at tile edges, the benchmark's full-size shot), the FP64 oracle
 within the FP32 bound, one kernel launch per call, and the unsupported cases
-rejected."""
+rejected. Receivers and sources beyond the four fused ones ride on the FP32
+flow: traces and fields bit for bit those of the per-step launches."""
 import numpy as np
 import pytest
 
@@ -111,13 +112,14 @@ def test_flow_rejections():
             with pytest.raises(fd.FdError) as e:
                 shot.forward_flow(3)
             assert e.value.code == fd.FD_ENOTSUP, kw
-    with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
+    # BF16 storage: receivers and sources beyond the fused four stay per-step
+    with fd.Shot(spec.interior, 8, H, dt, spec.nbl, storage="bf16") as shot:
         shot.set_model(spec.m)
         shot.set_receivers([(1.0, 1.0, 1.0)], 4)
         with pytest.raises(fd.FdError) as e:
             shot.forward_flow(2)
         assert e.value.code == fd.FD_ENOTSUP
-    with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
+    with fd.Shot(spec.interior, 8, H, dt, spec.nbl, storage="bf16") as shot:
         shot.set_model(spec.m)
         for i in range(5):
             shot.inject(3 + i, 4, 5, inputs.ricker(20.0, dt, 10))

@@ -125,9 +125,10 @@ def test_single_step_launch_count():
 
 
 def test_flow_launch_count():
-    """Automatic kernel choice at space order 8: one flow launch per call; with
-    more sources than the kernel fuses, back to one launch per step plus the
-    extra-source kernel."""
+    """Automatic kernel choice at space order 8: one flow launch per call, also
+    with more sources than the kernel fuses (the items add them) and with
+    receivers (the items sample them; one more launch samples the last level);
+    with FP16 storage, one launch per step plus the extra-source kernel."""
     spec = _spec(8, seed=8)
     dt = dt_for(spec)
     with fd.Shot(spec.interior, 8, H, dt, spec.nbl) as shot:
@@ -139,6 +140,21 @@ def test_flow_launch_count():
         assert fd.fd_kernel_launches() - n0 == 1
         for i in range(4):
             shot.inject(12 + i, 10, 10, inputs.ricker(20.0, dt, 40))
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 1
+        assert shot.schedule[1] == 1
+        shot.set_receivers([(3.5, 4.25, 5.0), (20.0, 1.0, 7.5)], 40)
+        shot.forward(6)
+        n0 = fd.fd_kernel_launches()
+        shot.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 2
+        assert shot.traces().shape == (2, 12)
+    with fd.Shot(spec.interior, 8, H, dt, spec.nbl, storage="f16") as shot:
+        shot.set_model(spec.m)
+        for i in range(5):
+            shot.inject(10 + i, 10, 10, inputs.ricker(20.0, dt, 40))
         shot.forward(6)
         n0 = fd.fd_kernel_launches()
         shot.forward(6)
