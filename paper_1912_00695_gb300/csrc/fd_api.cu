@@ -1557,8 +1557,8 @@ int fd_forward(fd_handle *hd, int nt) {
 // z fastest; a receiver belongs to the region of its lower corner node, a source
 // to that of its node; entries of a region in receiver / source order). One
 // device buffer: rec_start[P + 1], rec_row[n_rec], xs_start[P + 1],
-// xs_idx[n_x], then (64-byte aligned) rec_off[8 n_rec], xs_off[n_x] and
-// rec_w[8 n_rec]. Rebuilt when the x_block or the handle's state changes; a
+// xs_idx[n_x], then (64-byte aligned) rec_off[n_rec] (lower corner node),
+// xs_off[n_x] and rec_w[8 n_rec]. Rebuilt when the x_block or the handle's state changes; a
 // rebuild re-records the graphs.
 struct FlowTables {
     size_t rec_start, rec_row, xs_start, xs_idx, rec_off, xs_off, rec_w, bytes;
@@ -1577,7 +1577,7 @@ static FlowTables flow_table_layout(long long regions, int n_rec, int n_x) {
     t.xs_idx = b;
     b += size_t(n_x) * sizeof(int);
     t.rec_off = b = up(b, 64);
-    b += size_t(n_rec) * 8 * sizeof(long long);
+    b += size_t(n_rec) * sizeof(long long);
     t.xs_off = b;
     b += size_t(n_x) * sizeof(long long);
     t.rec_w = b = up(b, 64);
@@ -1620,10 +1620,8 @@ static int flow_tables(fd_handle *hd, int xb, int nbz, int nby, int nbx) {
         for (size_t e = 0; e < order.size(); ++e) {
             const size_t r = size_t(order[e]);
             row[e] = int(r);
-            for (int c = 0; c < 8; ++c) {
-                off[8 * e + size_t(c)] = hd->rec_off_h[8 * r + size_t(c)];
-                w[8 * e + size_t(c)] = hd->rec_w_h[8 * r + size_t(c)];
-            }
+            off[e] = hd->rec_off_h[8 * r];  // corner c = 4 dx + 2 dy + dz: + dx plane + dy pz + dz
+            for (int c = 0; c < 8; ++c) w[8 * e + size_t(c)] = hd->rec_w_h[8 * r + size_t(c)];
         }
     }
     if (n_x > 0) {

@@ -72,31 +72,54 @@ __device__ __forceinline__ ScaleState flow_scales(const FlowArgs &f, bool first)
 }
 
 // Receivers of the item of step s (FP32): entries [i0, i1) of the region's
-// list, one per thread. Each receiver's other corners lie in the neighbouring
-// regions, whose u^{step0+s} the dependency wait has seen completed and which no
-// item overwrites before this item's flag. The corners are summed in the
-// single-step kernel's order (same bits); the field loads bypass L1, since the
-// buffer held older levels earlier in the launch. Kept out of line: the
-// kernel's register allocation stays that of the plain flow.
+// list. Each receiver's other corners lie in the neighbouring regions, whose
+// u^{step0+s} the dependency wait has seen completed and which no item
+// overwrites before this item's flag. An entry holds the pitched offset of the
+// lower corner node; corner c = 4 dx + 2 dy + dz sits at that offset plus
+// dx plane + dy pz + dz, the node the receiver's own table names, and the
+// corners are summed in that order as the single-step kernel sums them (same
+// bits). A thread takes kRecBatch entries at a time so that their loads are in
+// flight together; the field loads bypass L1, since the buffer held older
+// levels earlier in the launch. Kept out of line: the kernel variant's
+// register allocation stays that of the plain flow.
+constexpr int kRecBatch = 1;
 static __device__ __noinline__ void flow_sample_receivers(const FlowArgs &f, const StepArgs &a, int s, int i0,
                                                           int i1) {
     const long long smp = f.step0 + s - f.rec_s0 - 1;
     if (smp < 0 || smp >= f.rec_stride) return;
     const float *__restrict__ u = static_cast<const float *>(a.u);
-    for (int i = i0 + int(threadIdx.x); i < i1; i += int(blockDim.x)) {
-        const longlong2 *o = reinterpret_cast<const longlong2 *>(f.rec_off) + 4 * (long long)i;
-        const float4 *wp = reinterpret_cast<const float4 *>(f.rec_w) + 2 * (long long)i;
-        const longlong2 o01 = __ldg(o), o23 = __ldg(o + 1), o45 = __ldg(o + 2), o67 = __ldg(o + 3);
-        const float4 w03 = __ldg(wp), w47 = __ldg(wp + 1);
-        const long long off[8] = {o01.x, o01.y, o23.x, o23.y, o45.x, o45.y, o67.x, o67.y};
-        const float w[8] = {w03.x, w03.y, w03.z, w03.w, w47.x, w47.y, w47.z, w47.w};
-        float c[8];
+    const long long dxy[4] = {0, a.pz, a.plane, a.plane + a.pz};
+    const int nthr = int(blockDim.x);
+    for (int i = i0 + int(threadIdx.x); i < i1; i += kRecBatch * nthr) {
+        long long base[kRecBatch];
+        float w[kRecBatch][8], c[kRecBatch][8];
+        int row[kRecBatch];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = __ldcg(u + off[k]);
-        float v = 0.0f;
+        for (int b = 0; b < kRecBatch; ++b) {
+            const int e = i + b * nthr;
+            if (e < i1) {
+                base[b] = __ldg(f.rec_off + e);
+                row[b] = __ldg(f.rec_row + e);
+                const float4 *wp = reinterpret_cast<const float4 *>(f.rec_w) + 2 * (long long)e;
+                const float4 w03 = __ldg(wp), w47 = __ldg(wp + 1);
+                w[b][0] = w03.x, w[b][1] = w03.y, w[b][2] = w03.z, w[b][3] = w03.w;
+                w[b][4] = w47.x, w[b][5] = w47.y, w[b][6] = w47.z, w[b][7] = w47.w;
+            }
+        }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v = fmaf(w[k], c[k], v);
-        f.traces[(long long)__ldg(f.rec_row + i) * f.rec_stride + smp] = v;
+        for (int b = 0; b < kRecBatch; ++b)
+            if (i + b * nthr < i1) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c[b][k] = __ldcg(u + base[b] + dxy[((k >> 2) << 1) | ((k >> 1) & 1)] + (k & 1));
+            }
+#pragma unroll
+        for (int b = 0; b < kRecBatch; ++b)
+            if (i + b * nthr < i1) {
+                float v = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v = fmaf(w[b][k], c[b][k], v);
+                f.traces[(long long)row[b] * f.rec_stride + smp] = v;
+            }
     }
 }
 

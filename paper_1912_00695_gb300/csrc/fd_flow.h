@@ -28,8 +28,8 @@ struct FlowArgs {
     // FP32 only, null / zero otherwise. Regions are numbered as the flags.
     // Receivers: the item of step s samples its input level u^{step0+s} at the
     // receivers of its region (entries rec_start[rem] .. rec_start[rem + 1] - 1:
-    // trace row rec_row, 8 pitched corner offsets rec_off and weights rec_w, in
-    // the corner order of the receivers' own tables) into
+    // trace row rec_row, the pitched offset rec_off of the lower corner node and
+    // 8 weights rec_w in the corner order of the receivers' own tables) into
     // traces[row * rec_stride + (step0 + s - rec_s0 - 1)] when that index lies in
     // [0, rec_stride). Sources beyond the fused ones: the item of step s adds the
     // sources of its region (entries xs_start[rem] ..: source index xs_idx and
