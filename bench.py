@@ -643,6 +643,7 @@ def leg_batched(args, world: int) -> dict:
     achieved = alg / (batch_ms * 1e-3) / 1e9
     active, items = batch.size()
     cfg = batch.config() if hasattr(batch, "config") else (args.batch_tile[0], args.batch_tile[1], args.batch_xb)
+    schedule = "one persistent launch per forward" if batch.schedule() else "one launch per step"
     rec = {
         "metric": "Gpts/s, 64 uneven shots advanced as one batch vs the same shots one by one",
         "value": round(value, 3), "unit": "Gpts/s", "steps": steps, "warmup": args.warmup,
@@ -650,7 +651,7 @@ def leg_batched(args, world: int) -> dict:
         "config": {"workload": f"batched: {len(specs)} shots, interiors U{{{args.shot_range[0]}.."
                                f"{args.shot_range[1]}}} per axis + 10, space order {k}, {nt} steps, "
                                "factored, FP32, smooth random velocity (sigma 8 cells)",
-                   "batch_tile_z_y_x_block": list(cfg), "points": sum(spec.points for spec in specs),
+                   "batch_tile_z_y_x_block": list(cfg), "schedule": schedule, "points": sum(spec.points for spec in specs),
                    "work_items_per_step": items, "l2": "inputs larger than L2 (5.6 GB of fields per copy)"},
         "plain_one_by_one": {"value": round(plain, 3), "unit": "Gpts/s",
                              "ms_per_step": round(plain_ms / steps, 3),

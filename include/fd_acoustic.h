@@ -374,8 +374,10 @@ int fd_destroy(fd_handle *hd);
 /* ---- batches of uneven shots ---------------------------------------------- */
 /* A batch advances many independent shots (each its own grid, model, dt and
  * sources; all with the same space order, h, storage and form) together: one
- * kernel launch per time step covers every shot's tiles, and the launches are
- * replayed from a CUDA graph. Shots keep their own step counters, so shots
+ * kernel launch per time step covers every shot's tiles, or (FP32, when the
+ * autotuner finds it cheaper, or on request) one persistent launch covers
+ * every step of a forward, and the launches are replayed from a CUDA graph.
+ * Shots keep their own step counters, so shots
  * added later run behind the others; a shot's result does not depend on which
  * other shots share the batch (same arithmetic per point as fd_forward). Each
  * shot is the time step of Sec. 2.1, Eq. 1 (see the top of this header). */
@@ -394,10 +396,14 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
  * loop blocking and auto-tuning Devito applies, Sec. 5) times the launch
  * shapes not forced — both tiles, x-chunks of 32/48/64/96/128 planes and whole
  * extents — on 3 real steps each of the first fd_batch_forward of at least
- * 39 steps (21 with a forced x_block) over at least 4 shots, and keeps the
- * fastest for the batch's lifetime (shots added later take it); before that,
- * 96-plane chunks. Results do not depend on the shape (same arithmetic per
- * point). */
+ * 39 steps (9 with a forced x_block; FP32 30 more) over at least 4 shots, and
+ * keeps the fastest for the batch's lifetime (shots added later take it);
+ * before that, 96-plane chunks. FP32 batches then time the persistent launch
+ * (fd_batch_forward_flow) on the chosen tile at the chosen x-chunks and at
+ * 48-plane chunks, and compare the cost of one more step of each schedule
+ * ((9-step time - 3-step time) / 6) to pick the schedule fd_batch_forward
+ * runs. Results do not depend on the shape or the schedule (same arithmetic
+ * per point). */
 int fd_batch_create(int space_order, double h, const fd_options *opt, fd_batch **out);
 
 /* Add a shot: interior nx*ny*nz, layer nbl, time step dt, HOST model m and
@@ -416,8 +422,22 @@ int fd_batch_inject(fd_batch *b, int slot, int ix, int iy, int iz, const float *
 int fd_batch_remove(fd_batch *b, int slot);
 
 /* Advance every shot in the batch by nt steps (asynchronous, on the batch's
- * stream). */
+ * stream), with the schedule the autotuner chose (one launch per step until
+ * it has run). Each step is Sec. 2.1, Eq. 1 for every shot. */
 int fd_batch_forward(fd_batch *b, int nt);
+
+/* As fd_batch_forward, in one persistent launch (FP32 storage; FD_ENOTSUP
+ * otherwise): resident CTAs claim (step, work item) pairs step-major and an
+ * item of step s starts once the 27 items of step s - 1 around it in its own
+ * shot are done (flags in device memory, waits bounded by the global timer:
+ * a wait that runs out sets FD_ETIMEOUT in that shot's status). The paper
+ * runs one kernel per step (Sec. 4); this schedule is the batch counterpart
+ * of the single-shot flow schedule. Same results bit for bit. */
+int fd_batch_forward_flow(fd_batch *b, int nt);
+
+/* *flow = 1 when fd_batch_forward runs the persistent launch (FP32, chosen by
+ * the autotuner), 0 for one launch per step. (The paper has no counterpart.) */
+int fd_batch_schedule(fd_batch *b, int *flow);
 
 /* Read a shot's wavefield level (as fd_read_wavefield / _device). */
 int fd_batch_read(fd_batch *b, int slot, float *out, int level);

@@ -12,7 +12,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_forward, fd_batch_get_config,  # noqa: F401
+from ._abi import (fd_batch_add, fd_batch_create, fd_batch_destroy, fd_batch_forward, fd_batch_forward_flow,  # noqa: F401
+                   fd_batch_get_config, fd_batch_schedule,
                    fd_batch_inject, fd_batch_read, fd_batch_read_device, fd_batch_remove, fd_batch_reset,
                    fd_batch_set_stream, fd_batch_shot_status, fd_batch_shot_step, fd_batch_size,
                    fd_batch_synchronize, fd_shot_device_bytes)
@@ -102,6 +103,14 @@ class Batch:
 
     def forward(self, nt):
         fd_batch_forward(self.handle, nt)
+
+    def forward_flow(self, nt):
+        """nt steps of every shot in one persistent launch (FP32): same bits as forward."""
+        fd_batch_forward_flow(self.handle, nt)
+
+    def schedule(self):
+        """1 when forward runs one persistent launch per call (autotuned), else 0."""
+        return fd_batch_schedule(self.handle)
 
     def wavefield(self, slot, level=0, out=None) -> np.ndarray:
         if out is None:

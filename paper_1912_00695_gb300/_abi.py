@@ -113,6 +113,8 @@ _SIGNATURES = {
     "fd_batch_inject": (_i, [_vp, _i, _i, _i, _i, _vp, _i]),
     "fd_batch_remove": (_i, [_vp, _i]),
     "fd_batch_forward": (_i, [_vp, _i]),
+    "fd_batch_forward_flow": (_i, [_vp, _i]),
+    "fd_batch_schedule": (_i, [_vp, _ip]),
     "fd_batch_read": (_i, [_vp, _i, _vp, _i]),
     "fd_batch_read_device": (_i, [_vp, _i, _vp, _i]),
     "fd_batch_shot_step": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
@@ -454,6 +456,17 @@ def fd_batch_remove(b, slot):
 
 def fd_batch_forward(b, nt):
     _check(lib().fd_batch_forward(b, nt), "fd_batch_forward")
+
+
+def fd_batch_forward_flow(b, nt):
+    _check(lib().fd_batch_forward_flow(b, nt), "fd_batch_forward_flow")
+
+
+def fd_batch_schedule(b):
+    """1 when fd_batch_forward runs one persistent launch per forward, else 0."""
+    v = ctypes.c_int(0)
+    _check(lib().fd_batch_schedule(b, ctypes.byref(v)), "fd_batch_schedule")
+    return v.value
 
 
 def fd_batch_read(b, slot, out: np.ndarray, level: int = 0):

@@ -2246,11 +2246,22 @@ struct fd_batch {
         cudaGraphExec_t exec = nullptr;
         int nt = 0;
         unsigned long long gen = 0;
+        bool flow = false;  // one persistent launch (else one launch per step)
     };
     std::vector<Graph> graphs;
     std::vector<int> seen_nt;              // chunk lengths launched once with this work list
     std::vector<cudaGraphExec_t> retired;  // replaced graphs, destroyed once the stream is idle
     std::vector<BatchShot> host_table;
+    // flow schedule (FP32): one persistent launch per forward over every shot, chosen by
+    // the autotuner when it times cheaper per step than the per-step launches. Per shot
+    // (z tiles, y tiles, x-chunks, first work item); the work counter, abort word and one
+    // flag per work item
+    bool flow = false;
+    int4 *d_geo = nullptr;
+    size_t cap_geo = 0;
+    void *flow_buf = nullptr;
+    size_t flow_cap = 0;
+    int flow_ctas = 0;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaEvent_t join_ev = nullptr;
     // pinned staging for the argument table and the work list: uploads are
@@ -2316,7 +2327,7 @@ void batch_destroy_retired(fd_batch *b) {
 
 int batch_rebuild(fd_batch *b) {
     b->order.clear();
-    std::vector<int4> items;
+    std::vector<int4> items, geo;
     for (size_t s = 0; s < b->slots.size(); ++s) {
         fd_handle *hd = b->slots[s];
         if (!hd) continue;
@@ -2331,6 +2342,7 @@ int batch_rebuild(fd_batch *b) {
         b->order.push_back(int(s));
         const int tz = (hd->Nz + b->tile_z - 1) / b->tile_z, ty = (hd->Ny + b->tile_y - 1) / b->tile_y;
         const int tx = (hd->Nx + hd->x_block - 1) / hd->x_block;
+        geo.push_back(make_int4(tz, ty, tx, int(items.size())));
         for (int x = 0; x < tx; ++x)
             for (int y = 0; y < ty; ++y)
                 for (int z = 0; z < tz; ++z) items.push_back(make_int4(idx, z, y, x));
@@ -2340,6 +2352,12 @@ int batch_rebuild(fd_batch *b) {
     if (rc == FD_OK)
         rc = batch_reserve(b, reinterpret_cast<void **>(&b->d_items), &b->cap_items, items.size(), sizeof(int4));
     if (rc == FD_OK) rc = batch_stage_upload(b, b->d_items, items.data(), items.size() * sizeof(int4));
+    if (rc == FD_OK && b->opt.storage == kF32) {
+        // the flow schedule's shot geometry and its counter, abort word and flags
+        rc = batch_reserve(b, reinterpret_cast<void **>(&b->d_geo), &b->cap_geo, geo.size(), sizeof(int4));
+        if (rc == FD_OK) rc = batch_stage_upload(b, b->d_geo, geo.data(), geo.size() * sizeof(int4));
+        if (rc == FD_OK) rc = batch_reserve(b, &b->flow_buf, &b->flow_cap, 16 + items.size() * sizeof(unsigned), 1);
+    }
     if (rc != FD_OK) return rc;
     b->n_items = int(items.size());
     // graphs of the old work list may still be queued: retire them, destroy them later
@@ -2379,6 +2397,7 @@ int batch_apply_shape(fd_batch *b, int tz, int ty, int xb) {
     b->tile_z = b->opt.tile_z = tz;
     b->tile_y = b->opt.tile_y = ty;
     b->xb_policy = xb;
+    if (tile_changed) b->flow_ctas = 0;  // another kernel: its resident count is read again
     for (fd_handle *hd : b->slots) {
         if (!hd) continue;
         hd->x_block = xb > 0 ? std::min(xb, hd->Nx) : hd->Nx;
@@ -2418,12 +2437,64 @@ int batch_timed_steps(fd_batch *b, int nt, float *ms) {
     return FD_OK;
 }
 
+// One persistent launch for nt steps of the current work list (FP32): the flags
+// zeroed, then the launch, on stream st.
+int batch_flow_enqueue(fd_batch *b, int nt, cudaStream_t st) {
+    if (b->flow_ctas == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = tma_batch_flow_ctas_per_sm(b->r, b->opt.form, b->tile_z, b->tile_y);
+        if (per_sm <= 0 || sms <= 0) return fail(FD_ENOTSUP, "no batch flow kernel for this launch shape");
+        b->flow_ctas = per_sm * sms;
+    }
+    if ((long long)b->n_items * nt > INT32_MAX / 2) return fail(FD_EINVAL, "nt too large for one batch flow launch");
+    BatchFlowArgs f;
+    unsigned char *fb = static_cast<unsigned char *>(b->flow_buf);
+    f.shots = b->d_shots;
+    f.items = b->d_items;
+    f.geo = b->d_geo;
+    f.n_items = b->n_items;
+    f.nt = nt;
+    f.counter = reinterpret_cast<int *>(fb);
+    f.abort = reinterpret_cast<unsigned *>(fb + 4);
+    f.flags = reinterpret_cast<unsigned *>(fb + 16);
+    const size_t bytes = 16 + size_t(b->n_items) * sizeof(unsigned);
+    const int ctas = int(std::min<long long>(b->flow_ctas, (long long)b->n_items * nt));
+    cudaError_t err = cudaMemsetAsync(b->flow_buf, 0, bytes, st);
+    if (err == cudaSuccess) err = launch_tma_batch_flow(b->r, b->opt.form, b->tile_z, b->tile_y, f, ctas, st);
+    if (err != cudaSuccess) return fail(FD_ECUDA, "batch flow launch failed: %s", cudaGetErrorString(err));
+    return FD_OK;
+}
+
+// One flow launch of nt steps outside a graph, timed on the batch stream (the shots
+// advance by nt steps).
+int batch_timed_flow(fd_batch *b, int nt, float *ms) {
+    int rc = batch_rebuild(b);
+    if (rc == FD_OK) rc = batch_upload_table(b);
+    if (rc != FD_OK) return rc;
+    FD_CUDA(cudaEventRecord(b->tev0, b->stream));
+    rc = batch_flow_enqueue(b, nt, b->stream);
+    if (rc != FD_OK) return rc;
+    FD_CUDA(cudaEventRecord(b->tev1, b->stream));
+    FD_CUDA(cudaEventSynchronize(b->tev1));
+    FD_CUDA(cudaEventElapsedTime(ms, b->tev0, b->tev1));
+    for (int s : b->order) {
+        fd_handle *hd = b->slots[s];
+        hd->step += nt;
+        hd->cur ^= (nt & 1);
+    }
+    return FD_OK;
+}
+
 // Launch shapes timed by the batch autotuner: both tiles (unless forced) and
 // x-chunk policies from short chunks (more CTAs, shorter queue warm-ups per
 // chunk: neither) to whole extents.
 constexpr int kBatchTuneSteps = 3;
 constexpr int kBatchTuneXb[] = {32, 48, 64, 96, 128, 0};
 constexpr int kBatchTuneMinShots = 4;
+constexpr int kBatchLongSteps = 9;   // the long probes of the schedule choice
+constexpr int kBatchFlowXb = 48;     // the flow's second x-chunk candidate
 
 // Times every candidate shape on kBatchTuneSteps real steps of this forward (*nt is
 // reduced by the steps they took) and keeps the fastest for the batch's lifetime.
@@ -2438,7 +2509,12 @@ int batch_autotune(fd_batch *b, int *nt) {
             ++n_tiles;
         }
     const int n_xb = b->opt.x_block > 0 ? 1 : int(sizeof(kBatchTuneXb) / sizeof(int));
-    const int needed = kBatchTuneSteps * (n_tiles * n_xb + 1);
+    // FP32: then the flow schedule on the chosen tile at two x-chunk policies, and the
+    // choice between the flow and per-step launches by differential timing
+    const bool try_flow = b->opt.storage == kF32 && (b->opt.x_block == 0 || b->opt.x_block >= b->r);
+    const int n_fx = b->opt.x_block > 0 ? 1 : 2;
+    const int needed = kBatchTuneSteps * (n_tiles * n_xb + 1) +
+                       (try_flow ? kBatchTuneSteps * n_fx + 2 * (kBatchTuneSteps + kBatchLongSteps) : 0);
     if (*nt < needed || int(b->order.size()) < kBatchTuneMinShots) return FD_OK;  // later, longer call
     float best = 1e30f, ms = 0.0f;
     int best_t = 0, best_x = b->xb_policy;
@@ -2459,6 +2535,37 @@ int batch_autotune(fd_batch *b, int *nt) {
                 best_x = xb;
             }
         }
+    b->flow = false;
+    if (try_flow) {
+        // the flow's x-chunks: the per-step choice, or chunks of kBatchFlowXb planes
+        // (shorter items balance a persistent launch better); then the cost of one more
+        // step, (t_long - t_short) / (kBatchLongSteps - kBatchTuneSteps), of both
+        // schedules (a flow launch's start-up and last tail cancel out)
+        float fbest = 1e30f;
+        int fbest_x = best_x;
+        for (int xi = 0; xi < n_fx; ++xi) {
+            const int xb = xi == 0 ? best_x : kBatchFlowXb;
+            int rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], xb);
+            if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &ms);
+            if (rc != FD_OK) return rc;
+            if (ms < fbest) {
+                fbest = ms;
+                fbest_x = xb;
+            }
+        }
+        float fs = 0.0f, fl = 0.0f, ss = 0.0f, sl = 0.0f;
+        int rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], fbest_x);
+        if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &fs);
+        if (rc == FD_OK) rc = batch_timed_flow(b, kBatchLongSteps, &fl);
+        if (rc == FD_OK) rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
+        if (rc == FD_OK) rc = batch_timed_steps(b, kBatchTuneSteps, &ss);
+        if (rc == FD_OK) rc = batch_timed_steps(b, kBatchLongSteps, &sl);
+        if (rc != FD_OK) return rc;
+        if (fl - fs <= sl - ss) {
+            b->flow = true;
+            best_x = fbest_x;
+        }
+    }
     *nt -= needed;
     b->tuned = true;
     return batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
@@ -2467,6 +2574,81 @@ int batch_autotune(fd_batch *b, int *nt) {
 fd_handle *batch_shot(fd_batch *b, int slot) {
     if (!b || slot < 0 || size_t(slot) >= b->slots.size()) return nullptr;
     return b->slots[slot];
+}
+
+// schedule: -1 the batch's own (autotuned), 1 one persistent launch
+int batch_forward(fd_batch *b, int nt, int schedule) {
+    if (!b) return fail(FD_EINVAL, "batch is NULL");
+    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
+    if (b->dirty) {
+        int rc = batch_rebuild(b);
+        if (rc != FD_OK) return rc;
+    }
+    if (nt == 0 || b->order.empty()) return FD_OK;
+    if (!b->tuned) {
+        int rc = batch_autotune(b, &nt);
+        if (rc != FD_OK) return rc;
+        if (b->dirty) {
+            rc = batch_rebuild(b);
+            if (rc != FD_OK) return rc;
+        }
+        if (nt == 0) return FD_OK;
+    }
+    int rc = batch_upload_table(b);
+    if (rc != FD_OK) return rc;
+    const bool flow = b->opt.storage == kF32 && (schedule == 1 || b->flow);
+    fd_batch::Graph *g = nullptr;
+    for (auto &e : b->graphs)
+        if (e.nt == nt && e.gen == b->gen && e.flow == flow) g = &e;
+    // a chunk length seen for the first time with this work list is launched
+    // directly (capturing a graph costs more than one replay saves); the second
+    // time it is captured and replayed from then on
+    const bool first = std::find(b->seen_nt.begin(), b->seen_nt.end(), nt) == b->seen_nt.end();
+    if (!g && first) {
+        b->seen_nt.push_back(nt);
+        if (flow) {
+            rc = batch_flow_enqueue(b, nt, b->stream);
+            if (rc != FD_OK) return rc;
+        }
+        for (int i = 0; i < nt && !flow; ++i) {
+            cudaError_t err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y,
+                                                    b->d_shots, b->d_items, b->n_items, i, b->stream);
+            if (err != cudaSuccess) return fail(FD_ECUDA, "batch launch failed: %s", cudaGetErrorString(err));
+        }
+    } else if (!g) {
+        cudaGraph_t graph = nullptr;
+        FD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        if (flow && batch_flow_enqueue(b, nt, b->stream) != FD_OK) err = cudaErrorLaunchFailure;
+        for (int i = 0; i < nt && err == cudaSuccess && !flow; ++i)
+            err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y, b->d_shots,
+                                        b->d_items, b->n_items, i, b->stream);
+        cudaError_t cap = cudaStreamEndCapture(b->stream, &graph);
+        if (err != cudaSuccess || cap != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(FD_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : cap));
+        }
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(FD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+        if (b->graphs.size() >= 8) {
+            b->retired.push_back(b->graphs.front().exec);  // may still be queued
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back({exec, nt, b->gen, flow});
+        g = &b->graphs.back();
+    }
+    if (g) {
+        FD_CUDA(cudaGraphLaunch(g->exec, b->stream));
+        count_replay(g->flow ? 1 : nt);  // one batch kernel per step, or one persistent launch
+    }
+    for (int s : b->order) {
+        fd_handle *hd = b->slots[s];
+        hd->step += nt;
+        hd->cur ^= (nt & 1);
+    }
+    return FD_OK;
 }
 
 }  // namespace
@@ -2590,71 +2772,19 @@ int fd_batch_remove(fd_batch *b, int slot) {
     return FD_OK;
 }
 
-int fd_batch_forward(fd_batch *b, int nt) {
-    if (!b) return fail(FD_EINVAL, "batch is NULL");
-    if (nt < 0) return fail(FD_EINVAL, "nt must be >= 0");
-    if (b->dirty) {
-        int rc = batch_rebuild(b);
-        if (rc != FD_OK) return rc;
-    }
-    if (nt == 0 || b->order.empty()) return FD_OK;
-    if (!b->tuned) {
-        int rc = batch_autotune(b, &nt);
-        if (rc != FD_OK) return rc;
-        if (b->dirty) {
-            rc = batch_rebuild(b);
-            if (rc != FD_OK) return rc;
-        }
-        if (nt == 0) return FD_OK;
-    }
-    int rc = batch_upload_table(b);
-    if (rc != FD_OK) return rc;
-    fd_batch::Graph *g = nullptr;
-    for (auto &e : b->graphs)
-        if (e.nt == nt && e.gen == b->gen) g = &e;
-    // a chunk length seen for the first time with this work list is launched
-    // directly (capturing a graph costs more than one replay saves); the second
-    // time it is captured and replayed from then on
-    const bool first = std::find(b->seen_nt.begin(), b->seen_nt.end(), nt) == b->seen_nt.end();
-    if (!g && first) {
-        b->seen_nt.push_back(nt);
-        for (int i = 0; i < nt; ++i) {
-            cudaError_t err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y,
-                                                    b->d_shots, b->d_items, b->n_items, i, b->stream);
-            if (err != cudaSuccess) return fail(FD_ECUDA, "batch launch failed: %s", cudaGetErrorString(err));
-        }
-    } else if (!g) {
-        cudaGraph_t graph = nullptr;
-        FD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t err = cudaSuccess;
-        for (int i = 0; i < nt && err == cudaSuccess; ++i)
-            err = launch_tma_batch_step(b->r, b->opt.form, b->opt.storage, b->tile_z, b->tile_y, b->d_shots,
-                                        b->d_items, b->n_items, i, b->stream);
-        cudaError_t cap = cudaStreamEndCapture(b->stream, &graph);
-        if (err != cudaSuccess || cap != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return fail(FD_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(err != cudaSuccess ? err : cap));
-        }
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ie != cudaSuccess) return fail(FD_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
-        if (b->graphs.size() >= 8) {
-            b->retired.push_back(b->graphs.front().exec);  // may still be queued
-            b->graphs.erase(b->graphs.begin());
-        }
-        b->graphs.push_back({exec, nt, b->gen});
-        g = &b->graphs.back();
-    }
-    if (g) {
-        FD_CUDA(cudaGraphLaunch(g->exec, b->stream));
-        count_replay(nt);  // one batch kernel per step
-    }
-    for (int s : b->order) {
-        fd_handle *hd = b->slots[s];
-        hd->step += nt;
-        hd->cur ^= (nt & 1);
-    }
+int fd_batch_forward(fd_batch *b, int nt) { return batch_forward(b, nt, -1); }
+
+int fd_batch_forward_flow(fd_batch *b, int nt) {
+    if (b && b->opt.storage != kF32) return fail(FD_ENOTSUP, "the batch flow schedule stores FP32");
+    // an item reads the queue planes and fronts of its x-neighbour chunks only
+    if (b && b->xb_policy > 0 && b->xb_policy < b->r)
+        return fail(FD_ENOTSUP, "the batch flow schedule needs x_block >= k/2");
+    return batch_forward(b, nt, 1);
+}
+
+int fd_batch_schedule(fd_batch *b, int *flow) {
+    if (!b || !flow) return fail(FD_EINVAL, "batch or flow is NULL");
+    *flow = b->flow ? 1 : 0;
     return FD_OK;
 }
 
@@ -2730,6 +2860,8 @@ int fd_batch_destroy(fd_batch *b) {
     batch_destroy_retired(b);
     dev_free(b->d_shots, b->stream);
     dev_free(b->d_items, b->stream);
+    dev_free(b->d_geo, b->stream);
+    dev_free(b->flow_buf, b->stream);
     cudaStreamSynchronize(b->stream);
     for (auto &sg : b->staging) {
         if (sg.done) cudaEventDestroy(sg.done);

@@ -362,6 +362,159 @@ int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows, bool
     return 0;
 }
 
+// Batch flow (FP32): one persistent launch advances every shot of a batch by nt
+// steps. Resident CTAs claim (step, work-list entry) items step-major; each item
+// runs the single-shot segment code on its shot's step arguments, which warp 1
+// copies into shared memory while warp 0 checks the dependencies (the 27 items
+// of step s - 1 around it in its own shot). Every dependency has a lower item
+// number, so the waits end (and are bounded all the same). Each item reduces
+// its non-finite check into its own shot's status word.
+template <int R, int FORM, int LZ, int W>
+__global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1))
+    fd_tma_batch_flow_kernel(const __grid_constant__ BatchFlowArgs f) {
+    static_assert(W >= 2, "warp 1 copies the arguments");
+    static_assert(sizeof(StepArgs) % 8 == 0, "arguments copied 8 bytes per lane");
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    __shared__ __align__(16) StepArgs sa;
+    __shared__ const TmaMaps *s_maps;
+    __shared__ long long s_step;
+    __shared__ int s_item[2];
+    __shared__ int s_fail;
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);
+    const ScaleState sc{1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
+    const int total = f.n_items * f.nt;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(f.counter, 1);
+    int g = 0;
+    bool ok_all = true;
+    for (int iter = 0;; ++iter) {
+        __syncthreads();  // s_item[iter & 1] is set; every thread is done with the previous item
+        const int item = s_item[iter & 1];
+        if (item >= total) break;
+        const int s = item / f.n_items, w = item - s * f.n_items;
+        const int4 it = __ldg(f.items + w);  // (shot, bz, by, bx)
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            if (l == 0) s_item[(iter + 1) & 1] = atomicAdd(f.counter, 1);
+            bool ok = true;
+            if (s > 0 && l < 27) {
+                const int4 ge = __ldg(f.geo + it.x);  // z tiles, y tiles, x-chunks, first entry
+                const int nx = it.w + l / 9 - 1, ny = it.z + (l / 3) % 3 - 1, nz = it.y + l % 3 - 1;
+                if (nx >= 0 && nx < ge.z && ny >= 0 && ny < ge.y && nz >= 0 && nz < ge.x)
+                    ok = flow_wait(&f.flags[ge.w + (nx * ge.y + ny) * ge.x + nz], unsigned(s), f.abort);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (l == 0) {
+                // the copy engine reads what the acquired flags published
+                if (s > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+                s_fail = ok ? 0 : 1;
+            }
+        } else if (threadIdx.x < 64) {
+            const int l = threadIdx.x - 32;
+            const BatchShot *sh = f.shots + it.x;
+            const int p = (__ldg(&sh->cur0) + s) & 1;
+            constexpr int n8 = int(sizeof(StepArgs) / 8);
+            const long long *src = reinterpret_cast<const long long *>(&sh->args[p]);
+            long long *dst = reinterpret_cast<long long *>(&sa);
+            for (int i = l; i < n8; i += 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+            if (l == 0) {
+                s_step = __ldg(&sh->step0) + s;
+                sa.step = s_step;
+                s_maps = &sh->maps[p];
+                // the maps were written to global memory by the host: acquire them for the copy engine
+                const CUtensorMap *m[5] = {&sh->maps[p].u_halo, &sh->maps[p].u_pt, &sh->maps[p].up_pt,
+                                           &sh->maps[p].f1_pt, &sh->maps[p].f2_pt};
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<uint64_t>(m[k]))
+                                 : "memory");
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            ok_all = false;
+            break;
+        }
+        const int xb = it.w * sa.x_block;
+        TmaAcc acc;
+        if (!tma_segment<R, FORM, LZ, W, float, kModeStep, true>(s_maps, sa, sc, it.y, it.z, xb,
+                                                                 min(xb + sa.x_block, sa.Nx), ring, g, acc, nullptr,
+                                                                 s_step)) {
+            ok_all = false;  // a ring wait gave up (status set); the ring's phases are no longer known
+            break;
+        }
+        reduce_amax(sa, acc.amax_bits, acc.over, acc.damax_bits);
+        __syncthreads();  // the item's stores precede the flag; every thread is done with sa
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_u32(&f.flags[w], unsigned(s + 1));
+        }
+    }
+    if (!ok_all && threadIdx.x == 0) {
+        if (sa.status) atomicOr(sa.status, kStatusTimeout);
+        atomicExch(f.abort, 1u);  // the other CTAs stop waiting and leave
+    }
+}
+
+template <int R, int FORM, int LZ, int W>
+cudaError_t tma_batch_flow_launch(const BatchFlowArgs &f, int ctas, cudaStream_t s) {
+    using G = TmaShape<R, LZ, W, float>;
+    auto kernel = fd_tma_batch_flow_kernel<R, FORM, LZ, W>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kernel<<<ctas, 32 * W, G::SMEM_BYTES, s>>>(f);
+    return cudaGetLastError();
+}
+
+template <int R, int FORM, int LZ, int W>
+int tma_batch_flow_occupancy() {
+    using G = TmaShape<R, LZ, W, float>;
+    auto kernel = fd_tma_batch_flow_kernel<R, FORM, LZ, W>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 32 * W, G::SMEM_BYTES) != cudaSuccess) return 0;
+    return n;
+}
+
+// The batch tiles: 32x16 (LZ 8, W 4) and 64x8 (LZ 16, W 4).
+template <int R>
+cudaError_t tma_batch_flow_r(int form, int tile_z, int tile_y, const BatchFlowArgs &f, int ctas, cudaStream_t s) {
+    if constexpr (R > kMaxBatchRadius) {
+        return cudaErrorInvalidValue;
+    } else {
+#define FDGB_BFLOW_CASE(LZ, W)                                                                   \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                       \
+        return form == kFactored ? tma_batch_flow_launch<R, kFactored, LZ, W>(f, ctas, s)         \
+                                 : tma_batch_flow_launch<R, kExpanded, LZ, W>(f, ctas, s);
+        FDGB_BFLOW_CASE(8, 4)
+        FDGB_BFLOW_CASE(16, 4)
+#undef FDGB_BFLOW_CASE
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+int tma_batch_flow_occ_r(int form, int tile_z, int tile_y) {
+    if constexpr (R > kMaxBatchRadius) {
+        return 0;
+    } else {
+#define FDGB_BFLOW_OCC(LZ, W)                                                                    \
+    if (tile_z == 4 * (LZ) && tile_y == (32 / (LZ)) * (W))                                       \
+        return form == kFactored ? tma_batch_flow_occupancy<R, kFactored, LZ, W>()                \
+                                 : tma_batch_flow_occupancy<R, kExpanded, LZ, W>();
+        FDGB_BFLOW_OCC(8, 4)
+        FDGB_BFLOW_OCC(16, 4)
+#undef FDGB_BFLOW_OCC
+        return 0;
+    }
+}
+
 }  // namespace fdgb
 
 #define FDGB_INSTANTIATE_FLOW_RADIUS(R)                                                           \
@@ -372,5 +525,12 @@ int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows, bool
     }                                                                                             \
     int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex) { \
         return tma_flow_occ_r<R>(form, storage, tile_z, tile_y, rows, ex);                        \
+    }                                                                                             \
+    cudaError_t tma_batch_flow_radius_##R(int form, int tile_z, int tile_y, const BatchFlowArgs &f, \
+                                          int ctas, cudaStream_t s) {                             \
+        return tma_batch_flow_r<R>(form, tile_z, tile_y, f, ctas, s);                             \
+    }                                                                                             \
+    int tma_batch_flow_occ_radius_##R(int form, int tile_z, int tile_y) {                         \
+        return tma_batch_flow_occ_r<R>(form, tile_z, tile_y);                                     \
     }                                                                                             \
     }

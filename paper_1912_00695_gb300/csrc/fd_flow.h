@@ -47,6 +47,31 @@ struct FlowArgs {
     int xs_distinct;
 };
 
+// Flow schedule of a batch (FP32): one persistent launch advances every shot of
+// the batch by nt steps. Work items (step s, work-list entry w) are numbered
+// step-major; an item waits for the 27 items of step s - 1 around it in its
+// own shot (x-chunks, y and z tiles +-1), as the single-shot flow does.
+struct BatchFlowArgs {
+    const BatchShot *shots;  // per shot: arguments and maps for both buffer parities, cur0, step0
+    const int4 *items;       // work list: (shot, bz, by, bx); each shot's entries contiguous,
+                             // x-chunk slowest and z tile fastest
+    const int4 *geo;         // per shot: (z tiles, y tiles, x-chunks, index of its first entry)
+    int n_items;             // work-list entries (items per step)
+    int nt;                  // steps of this launch
+    // zeroed before the launch: the work counter, the abort word, then one flag per
+    // work-list entry = the number of this launch's steps it has completed
+    int *counter;
+    unsigned *abort;
+    unsigned *flags;
+};
+
+// One persistent batch launch (radius <= 8, FP32, batch tiles); cudaErrorInvalidValue
+// for a configuration without one.
+cudaError_t launch_tma_batch_flow(int radius, int form, int tile_z, int tile_y, const BatchFlowArgs &f, int ctas,
+                                  cudaStream_t s);
+// Resident CTAs per SM of that kernel (0 if the configuration does not exist).
+int tma_batch_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y);
+
 // One persistent launch of the flow kernel for radius/form/tile; `ctas` is the
 // number of CTAs (at most the resident count). cudaErrorInvalidValue for a
 // configuration without a flow kernel.

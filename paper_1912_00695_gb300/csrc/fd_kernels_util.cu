@@ -219,7 +219,10 @@ cudaError_t launch_tma2_step(int radius, const TmaMaps &map, const StepArgs &a, 
 #define FDGB_DECLARE_FLOW_RADIUS(R)                                                              \
     cudaError_t tma_flow_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex,   \
                                     const FlowArgs &f, int ctas, bool check, cudaStream_t s);     \
-    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex);
+    int tma_flow_occ_radius_##R(int form, int storage, int tile_z, int tile_y, int rows, bool ex); \
+    cudaError_t tma_batch_flow_radius_##R(int form, int tile_z, int tile_y, const BatchFlowArgs &f, int ctas, \
+                                          cudaStream_t s);                                       \
+    int tma_batch_flow_occ_radius_##R(int form, int tile_z, int tile_y);
 FDGB_DECLARE_FLOW_RADIUS(1)
 FDGB_DECLARE_FLOW_RADIUS(2)
 FDGB_DECLARE_FLOW_RADIUS(3)
@@ -262,6 +265,34 @@ int tma_flow_ctas_per_sm(int radius, int form, int storage, int tile_z, int tile
         FDGB_FLOW_O(5) FDGB_FLOW_O(6) FDGB_FLOW_O(7) FDGB_FLOW_O(8)
         FDGB_FLOW_O(9) FDGB_FLOW_O(10) FDGB_FLOW_O(11) FDGB_FLOW_O(12)
 #undef FDGB_FLOW_O
+        default: return 0;
+    }
+}
+
+static cudaError_t launch_tma_batch_flow_dispatch(int radius, int form, int tile_z, int tile_y,
+                                                  const BatchFlowArgs &f, int ctas, cudaStream_t s) {
+    switch (radius) {
+#define FDGB_BFLOW_R(R) \
+        case R: return tma_batch_flow_radius_##R(form, tile_z, tile_y, f, ctas, s);
+        FDGB_BFLOW_R(1) FDGB_BFLOW_R(2) FDGB_BFLOW_R(3) FDGB_BFLOW_R(4)
+        FDGB_BFLOW_R(5) FDGB_BFLOW_R(6) FDGB_BFLOW_R(7) FDGB_BFLOW_R(8)
+#undef FDGB_BFLOW_R
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_tma_batch_flow(int radius, int form, int tile_z, int tile_y, const BatchFlowArgs &f, int ctas,
+                                  cudaStream_t s) {
+    return counted(launch_tma_batch_flow_dispatch(radius, form, tile_z, tile_y, f, ctas, s), s);
+}
+
+int tma_batch_flow_ctas_per_sm(int radius, int form, int tile_z, int tile_y) {
+    switch (radius) {
+#define FDGB_BFLOW_O(R) \
+        case R: return tma_batch_flow_occ_radius_##R(form, tile_z, tile_y);
+        FDGB_BFLOW_O(1) FDGB_BFLOW_O(2) FDGB_BFLOW_O(3) FDGB_BFLOW_O(4)
+        FDGB_BFLOW_O(5) FDGB_BFLOW_O(6) FDGB_BFLOW_O(7) FDGB_BFLOW_O(8)
+#undef FDGB_BFLOW_O
         default: return 0;
     }
 }

@@ -165,10 +165,11 @@ def test_batch_launch_per_step_16bit():
 
 @pytest.mark.parametrize("storage,k", [("f32", 4), ("f32", 16), ("bf16", 8)])
 def test_batch_autotune_keeps_results(k, storage):
-    """The first forward of at least 39 steps over at least 4 shots times the
-    launch shapes (both tiles, six x-chunk policies) on real steps and keeps
-    the fastest; every shot still equals the same shot alone, bit for bit,
-    and a shot added after the choice takes it."""
+    """The first forward of at least 39 steps (FP32: 69, the schedule choice
+    included) over at least 4 shots times the launch shapes (both tiles, six
+    x-chunk policies) on real steps and keeps the fastest; every shot still
+    equals the same shot alone, bit for bit, and a shot added after the choice
+    takes it."""
     specs = _shots(k, seed=50 + k, count=6)
     with fd.Batch(k, H, storage=storage) as b:
         assert b.config()[3] == 0
@@ -177,7 +178,7 @@ def test_batch_autotune_keeps_results(k, storage):
             s = b.add(spec.interior, spec.nbl, spec.dt, spec.m)
             b.inject(s, *spec.source, inputs.ricker(spec.f0, spec.dt, spec.nt))
             slots.append(s)
-        b.forward(45)
+        b.forward(75)
         tz, ty, xb, tuned = b.config()
         assert tuned == 1 and (tz, ty) in ((32, 16), (64, 8)) and xb in (32, 48, 64, 96, 128, 0)
         late = specs[5]
@@ -186,8 +187,8 @@ def test_batch_autotune_keeps_results(k, storage):
         b.forward(12)
         assert b.config() == (tz, ty, xb, 1)
         for spec, s in zip(specs[:5], slots):
-            want, want_prev = _alone(spec, 57, storage)
-            assert b.step(s) == 57
+            want, want_prev = _alone(spec, 87, storage)
+            assert b.step(s) == 87
             np.testing.assert_array_equal(b.wavefield(s, 0), want)
             np.testing.assert_array_equal(b.wavefield(s, 1), want_prev)
         want, _ = _alone(late, 12, storage)
