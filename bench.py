@@ -47,7 +47,7 @@ def _kernel_hash() -> str:
     """Hash of the step kernels' sources: a committed ncu traffic figure is used
     only while it was measured on these sources."""
     h = hashlib.sha256()
-    for name in ("fd_stencil.cuh", "fd_tma.cuh", "fd_tma2.cuh", "fd_internal.h"):
+    for name in ("fd_stencil.cuh", "fd_tma.cuh", "fd_tma2.cuh", "fd_flow.cuh", "fd_flow.h", "fd_internal.h"):
         with open(os.path.join(ROOT, "paper_1912_00695_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -607,7 +607,10 @@ def leg_batched(args, world: int) -> dict:
 
     def batch_step():
         batch.reset()
-        batch.forward(nt)
+        if args.batch_schedule == "flow":
+            batch.forward_flow(nt)
+        else:
+            batch.forward(nt)
 
     def timed(fn, steps):
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -643,7 +646,8 @@ def leg_batched(args, world: int) -> dict:
     achieved = alg / (batch_ms * 1e-3) / 1e9
     active, items = batch.size()
     cfg = batch.config() if hasattr(batch, "config") else (args.batch_tile[0], args.batch_tile[1], args.batch_xb)
-    schedule = "one persistent launch per forward" if batch.schedule() else "one launch per step"
+    schedule = ("one persistent launch per forward" if batch.schedule() or args.batch_schedule == "flow"
+                else "one launch per step")
     rec = {
         "metric": "Gpts/s, 64 uneven shots advanced as one batch vs the same shots one by one",
         "value": round(value, 3), "unit": "Gpts/s", "steps": steps, "warmup": args.warmup,
@@ -1077,6 +1081,8 @@ def main():
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of shots")
     ap.add_argument("--nt-batched", type=int, default=300, help="batched workload: steps per shot")
     ap.add_argument("--batch-xb", type=int, default=0, help="batched workload: x_block (0 = the library default)")
+    ap.add_argument("--batch-schedule", default="auto", choices=["auto", "flow"],
+                    help="batched workload: the autotuned schedule, or one persistent launch per forward")
     ap.add_argument("--batch-tile", type=lambda v: tuple(int(x) for x in v.split("x")), default=(0, 0),
                     help="batched workload: tile as ZxY (32x16 or 64x8; default 32x16)")
     ap.add_argument("--shot-range", type=lambda v: tuple(int(x) for x in v.split(",")), default=(96, 256),

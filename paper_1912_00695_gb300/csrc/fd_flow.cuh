@@ -380,7 +380,12 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
     __shared__ long long s_step;
     __shared__ int s_item[2];
     __shared__ int s_fail;
-    unsigned char *ring = tma_ring_init<R>(smem_dyn);
+    // (shot, parity) pairs whose maps thread 0 has acquired for the copy engine in this
+    // launch (the maps do not change during a launch): one bit each, the first shots
+    constexpr int kFenceWords = 16;
+    __shared__ unsigned s_fenced[kFenceWords];
+    if (threadIdx.x < kFenceWords) s_fenced[threadIdx.x] = 0u;
+    unsigned char *ring = tma_ring_init<R>(smem_dyn);  // (its barrier orders the zeroing)
     const ScaleState sc{1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
     const int total = f.n_items * f.nt;
     if (threadIdx.x == 0) s_item[0] = atomicAdd(f.counter, 1);
@@ -407,6 +412,22 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
                 // the copy engine reads what the acquired flags published
                 if (s > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
                 s_fail = ok ? 0 : 1;
+                // the maps were written to global memory by the host: thread 0, which issues
+                // the copies, acquires them for the copy engine once per launch
+                const BatchShot *sh = f.shots + it.x;
+                const int p = (__ldg(&sh->cur0) + s) & 1;
+                const int bit = 2 * it.x + p;
+                const bool known = bit < 32 * kFenceWords && ((s_fenced[bit >> 5] >> (bit & 31)) & 1u);
+                if (!known) {
+                    const CUtensorMap *m[5] = {&sh->maps[p].u_halo, &sh->maps[p].u_pt, &sh->maps[p].up_pt,
+                                               &sh->maps[p].f1_pt, &sh->maps[p].f2_pt};
+#pragma unroll
+                    for (int k = 0; k < 5; ++k)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                         reinterpret_cast<uint64_t>(m[k]))
+                                     : "memory");
+                    if (bit < 32 * kFenceWords) s_fenced[bit >> 5] |= 1u << (bit & 31);
+                }
             }
         } else if (threadIdx.x < 64) {
             const int l = threadIdx.x - 32;
@@ -421,14 +442,6 @@ __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_war
                 s_step = __ldg(&sh->step0) + s;
                 sa.step = s_step;
                 s_maps = &sh->maps[p];
-                // the maps were written to global memory by the host: acquire them for the copy engine
-                const CUtensorMap *m[5] = {&sh->maps[p].u_halo, &sh->maps[p].u_pt, &sh->maps[p].up_pt,
-                                           &sh->maps[p].f1_pt, &sh->maps[p].f2_pt};
-#pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                                     reinterpret_cast<uint64_t>(m[k]))
-                                 : "memory");
             }
         }
         __syncthreads();
