@@ -646,24 +646,26 @@ def leg_batched(args, world: int) -> dict:
     achieved = alg / (batch_ms * 1e-3) / 1e9
     active, items = batch.size()
     cfg = batch.config() if hasattr(batch, "config") else (args.batch_tile[0], args.batch_tile[1], args.batch_xb)
-    schedule = ("one persistent launch per forward" if batch.schedule() or args.batch_schedule == "flow"
-                else "one launch per step")
+    flow_sched = bool(batch.schedule()) or args.batch_schedule == "flow"
+    schedule = "one persistent launch per forward" if flow_sched else "one launch per step"
+    field_gb = 4 * 4 * sum(spec.points for spec in specs) / 1e9  # u, u^{n-1}, and two coefficient fields
     rec = {
-        "metric": "Gpts/s, 64 uneven shots advanced as one batch vs the same shots one by one",
+        "metric": f"Gpts/s, {len(specs)} uneven shots advanced as one batch vs the same shots one by one",
         "value": round(value, 3), "unit": "Gpts/s", "steps": steps, "warmup": args.warmup,
         "ms_per_step": round(batch_ms / steps, 3),
         "config": {"workload": f"batched: {len(specs)} shots, interiors U{{{args.shot_range[0]}.."
                                f"{args.shot_range[1]}}} per axis + 10, space order {k}, {nt} steps, "
                                "factored, FP32, smooth random velocity (sigma 8 cells)",
                    "batch_tile_z_y_x_block": list(cfg), "schedule": schedule, "points": sum(spec.points for spec in specs),
-                   "work_items_per_step": items, "l2": "inputs larger than L2 (5.6 GB of fields per copy)"},
+                   "work_items_per_step": items, "l2": f"inputs larger than L2 ({field_gb:.1f} GB of fields per copy)"},
         "plain_one_by_one": {"value": round(plain, 3), "unit": "Gpts/s",
                              "ms_per_step": round(plain_ms / steps, 3),
                              "what": "the same shots one after another through fd_forward (device-timed)"},
         "speedup_vs_plain": round(value / plain, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "fd_tma_batch_kernel", "peak_source": peak_kind,
+                     "kernel": "fd_tma_batch_flow_kernel" if flow_sched else "fd_tma_batch_kernel",
+                     "peak_source": peak_kind,
                      "algorithmic_bytes_per_step": int(alg / steps)},
         "gpu_launches": batch_launches,
         "clocks": clk,
