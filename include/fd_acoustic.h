@@ -396,14 +396,15 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
  * loop blocking and auto-tuning Devito applies, Sec. 5) times the launch
  * shapes not forced — both tiles, x-chunks of 32/48/64/96/128 planes and whole
  * extents — on 3 real steps each of the first fd_batch_forward of at least
- * 39 steps (9 with a forced x_block; FP32 30 more) over at least 4 shots, and
- * keeps the fastest for the batch's lifetime (shots added later take it);
- * before that, 96-plane chunks. FP32 batches then time the persistent launch
- * (fd_batch_forward_flow) on the chosen tile at the chosen x-chunks and at
- * 48-plane chunks, and compare the cost of one more step of each schedule
- * ((9-step time - 3-step time) / 6) to pick the schedule fd_batch_forward
- * runs. Results do not depend on the shape or the schedule (same arithmetic
- * per point). */
+ * 39 steps (9 with a forced x_block) over at least 4 shots, and keeps the
+ * fastest for the batch's lifetime (shots added later take it); before that,
+ * 96-plane chunks. FP32 batches then (on that forward if 30 steps remain,
+ * else on the next forward of at least 30 steps; 27 with a forced x_block)
+ * time the persistent launch (fd_batch_forward_flow) on the chosen tile at the
+ * chosen x-chunks and at 48-plane chunks, and compare the cost of one more
+ * step of each schedule ((9-step time - 3-step time) / 6) to pick the schedule
+ * fd_batch_forward runs. Results do not depend on the shape or the schedule
+ * (same arithmetic per point). */
 int fd_batch_create(int space_order, double h, const fd_options *opt, fd_batch **out);
 
 /* Add a shot: interior nx*ny*nz, layer nbl, time step dt, HOST model m and

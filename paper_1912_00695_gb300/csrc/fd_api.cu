@@ -2257,6 +2257,7 @@ struct fd_batch {
     // (z tiles, y tiles, x-chunks, first work item); the work counter, abort word and one
     // flag per work item
     bool flow = false;
+    bool flow_tuned = false;  // the schedule has been chosen (FP32), or there is no choice
     int4 *d_geo = nullptr;
     size_t cap_geo = 0;
     void *flow_buf = nullptr;
@@ -2499,6 +2500,49 @@ constexpr int kBatchFlowXb = 48;     // the flow's second x-chunk candidate
 // Times every candidate shape on kBatchTuneSteps real steps of this forward (*nt is
 // reduced by the steps they took) and keeps the fastest for the batch's lifetime.
 // Runs once, on the first forward long enough with at least kBatchTuneMinShots shots.
+// FP32 batches: whether one persistent launch per forward (the flow schedule) beats
+// one launch per step on the tuned shape. The flow is timed at the tuned x-chunks and
+// at kBatchFlowXb-plane chunks (shorter items balance a persistent launch better);
+// then the cost of one more step of each schedule, (t_long - t_short) /
+// (kBatchLongSteps - kBatchTuneSteps), decides (a flow launch's start-up and last
+// tail cancel out). Runs once, on a forward with enough steps left (*nt is reduced
+// by the steps it took; every probe is a real step of the batch).
+int batch_flow_choice(fd_batch *b, int *nt) {
+    const int n_fx = b->opt.x_block > 0 ? 1 : 2;
+    const int needed = kBatchTuneSteps * n_fx + 2 * (kBatchTuneSteps + kBatchLongSteps);
+    if (*nt < needed || int(b->order.size()) < kBatchTuneMinShots) return FD_OK;  // later, longer call
+    const int tz = b->tile_z, ty = b->tile_y, xb0 = b->xb_policy;
+    float ms = 0.0f, fbest = 1e30f;
+    int fx = xb0;
+    for (int xi = 0; xi < n_fx; ++xi) {
+        const int xb = xi == 0 ? xb0 : kBatchFlowXb;
+        int rc = batch_apply_shape(b, tz, ty, xb);
+        if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &ms);
+        if (rc != FD_OK) return rc;
+        if (ms < fbest) {
+            fbest = ms;
+            fx = xb;
+        }
+    }
+    float fs = 0.0f, fl = 0.0f, ss = 0.0f, sl = 0.0f;
+    int rc = batch_apply_shape(b, tz, ty, fx);
+    if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &fs);
+    if (rc == FD_OK) rc = batch_timed_flow(b, kBatchLongSteps, &fl);
+    if (rc == FD_OK) rc = batch_apply_shape(b, tz, ty, xb0);
+    if (rc == FD_OK) rc = batch_timed_steps(b, kBatchTuneSteps, &ss);
+    if (rc == FD_OK) rc = batch_timed_steps(b, kBatchLongSteps, &sl);
+    if (rc != FD_OK) return rc;
+    *nt -= needed;
+    b->flow_tuned = true;
+    b->flow = fl - fs <= sl - ss;
+    return b->flow ? batch_apply_shape(b, tz, ty, fx) : FD_OK;
+}
+
+// Times every candidate shape on kBatchTuneSteps real steps of this forward (*nt is
+// reduced by the steps they took) and keeps the fastest for the batch's lifetime.
+// Runs once, on the first forward long enough with at least kBatchTuneMinShots shots;
+// FP32 batches then choose their schedule (now if enough steps are left, else on a
+// later forward).
 int batch_autotune(fd_batch *b, int *nt) {
     int n_tiles = 0;
     int tiles[2][2];
@@ -2509,12 +2553,7 @@ int batch_autotune(fd_batch *b, int *nt) {
             ++n_tiles;
         }
     const int n_xb = b->opt.x_block > 0 ? 1 : int(sizeof(kBatchTuneXb) / sizeof(int));
-    // FP32: then the flow schedule on the chosen tile at two x-chunk policies, and the
-    // choice between the flow and per-step launches by differential timing
-    const bool try_flow = b->opt.storage == kF32 && (b->opt.x_block == 0 || b->opt.x_block >= b->r);
-    const int n_fx = b->opt.x_block > 0 ? 1 : 2;
-    const int needed = kBatchTuneSteps * (n_tiles * n_xb + 1) +
-                       (try_flow ? kBatchTuneSteps * n_fx + 2 * (kBatchTuneSteps + kBatchLongSteps) : 0);
+    const int needed = kBatchTuneSteps * (n_tiles * n_xb + 1);
     if (*nt < needed || int(b->order.size()) < kBatchTuneMinShots) return FD_OK;  // later, longer call
     float best = 1e30f, ms = 0.0f;
     int best_t = 0, best_x = b->xb_policy;
@@ -2535,40 +2574,11 @@ int batch_autotune(fd_batch *b, int *nt) {
                 best_x = xb;
             }
         }
-    b->flow = false;
-    if (try_flow) {
-        // the flow's x-chunks: the per-step choice, or chunks of kBatchFlowXb planes
-        // (shorter items balance a persistent launch better); then the cost of one more
-        // step, (t_long - t_short) / (kBatchLongSteps - kBatchTuneSteps), of both
-        // schedules (a flow launch's start-up and last tail cancel out)
-        float fbest = 1e30f;
-        int fbest_x = best_x;
-        for (int xi = 0; xi < n_fx; ++xi) {
-            const int xb = xi == 0 ? best_x : kBatchFlowXb;
-            int rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], xb);
-            if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &ms);
-            if (rc != FD_OK) return rc;
-            if (ms < fbest) {
-                fbest = ms;
-                fbest_x = xb;
-            }
-        }
-        float fs = 0.0f, fl = 0.0f, ss = 0.0f, sl = 0.0f;
-        int rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], fbest_x);
-        if (rc == FD_OK) rc = batch_timed_flow(b, kBatchTuneSteps, &fs);
-        if (rc == FD_OK) rc = batch_timed_flow(b, kBatchLongSteps, &fl);
-        if (rc == FD_OK) rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
-        if (rc == FD_OK) rc = batch_timed_steps(b, kBatchTuneSteps, &ss);
-        if (rc == FD_OK) rc = batch_timed_steps(b, kBatchLongSteps, &sl);
-        if (rc != FD_OK) return rc;
-        if (fl - fs <= sl - ss) {
-            b->flow = true;
-            best_x = fbest_x;
-        }
-    }
     *nt -= needed;
     b->tuned = true;
-    return batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
+    int rc = batch_apply_shape(b, tiles[best_t][0], tiles[best_t][1], best_x);
+    if (rc == FD_OK && !b->flow_tuned) rc = batch_flow_choice(b, nt);
+    return rc;
 }
 
 fd_handle *batch_shot(fd_batch *b, int slot) {
@@ -2585,8 +2595,8 @@ int batch_forward(fd_batch *b, int nt, int schedule) {
         if (rc != FD_OK) return rc;
     }
     if (nt == 0 || b->order.empty()) return FD_OK;
-    if (!b->tuned) {
-        int rc = batch_autotune(b, &nt);
+    if (!b->tuned || !b->flow_tuned) {
+        int rc = b->tuned ? batch_flow_choice(b, &nt) : batch_autotune(b, &nt);
         if (rc != FD_OK) return rc;
         if (b->dirty) {
             rc = batch_rebuild(b);
@@ -2692,7 +2702,9 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
     fd_batch *b = new fd_batch();
     b->tile_forced = opt.tile_z != 0 || opt.tile_y != 0;
     b->xb_policy = opt.x_block > 0 ? opt.x_block : kBatchXBlock;
-    b->tuned = opt.x_block > 0 && b->tile_forced;  // nothing left to time
+    b->tuned = opt.x_block > 0 && b->tile_forced;  // no shape left to time
+    // the schedule is timed for FP32 batches whose x-chunks the flow can take
+    b->flow_tuned = opt.storage != kF32 || (opt.x_block > 0 && opt.x_block < space_order / 2);
     b->k = space_order;
     b->r = space_order / 2;
     b->h = h;

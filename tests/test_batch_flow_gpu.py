@@ -81,6 +81,24 @@ def test_batch_flow_matches_oracle(oracle_mod):
             assert e <= 1e-5
 
 
+def test_batch_schedule_choice_on_a_later_forward():
+    """A forward too short for the schedule choice after the shape tuning (as a
+    server's 50-step chunks are) leaves it to the next one; the results do not
+    change."""
+    specs = _shots(8, seed=93, count=4)
+    with fd.Batch(8, H) as b:
+        slots = _fill(b, specs)
+        b.forward(50)  # shapes: 39 steps; 11 left, too few for the schedule probes
+        assert b.config()[3] == 1
+        b.forward(40)  # the schedule probes: 30 real steps
+        b.forward(7)
+        for spec, s in zip(specs, slots):
+            want, want_prev = _alone(spec, 97)
+            assert b.step(s) == 97
+            np.testing.assert_array_equal(b.wavefield(s, 0), want)
+            np.testing.assert_array_equal(b.wavefield(s, 1), want_prev)
+
+
 def test_batch_autotuned_schedule_equals_alone():
     """The autotuner times the per-step shapes, then the flow, and keeps one
     schedule; whichever it keeps, every shot equals its run alone."""

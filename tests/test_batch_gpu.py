@@ -165,11 +165,11 @@ def test_batch_launch_per_step_16bit():
 
 @pytest.mark.parametrize("storage,k", [("f32", 4), ("f32", 16), ("bf16", 8)])
 def test_batch_autotune_keeps_results(k, storage):
-    """The first forward of at least 39 steps (FP32: 69, the schedule choice
-    included) over at least 4 shots times the launch shapes (both tiles, six
-    x-chunk policies) on real steps and keeps the fastest; every shot still
-    equals the same shot alone, bit for bit, and a shot added after the choice
-    takes it."""
+    """The first forward of at least 39 steps over at least 4 shots times the
+    launch shapes (both tiles, six x-chunk policies) on real steps and keeps
+    the fastest (FP32 then chooses its schedule on the 30 steps after); every
+    shot still equals the same shot alone, bit for bit, and a shot added after
+    the choice takes it."""
     specs = _shots(k, seed=50 + k, count=6)
     with fd.Batch(k, H, storage=storage) as b:
         assert b.config()[3] == 0
