@@ -391,7 +391,9 @@ int fd_shot_device_bytes(int nx, int ny, int nz, int nbl, int storage, long long
  * opt: storage/form as for fd_acoustic_create_ex
  * (16-bit storage needs the factored form), tile_z/tile_y 0 (autotuned) or
  * one of 32x16, 64x8; x_block 0 (autotuned) or the planes per CTA of every
- * shot (the whole extent if shorter); rows 0 or 1; kernel is ignored.
+ * shot (the whole extent if shorter); rows 0 or 1; kernel FD_KERNEL_TMA pins
+ * one launch per step (no schedule probes), any other value lets FP32
+ * batches choose their schedule.
  * FD_ENOTSUP for other shapes. The autotuner (the batch counterpart of the
  * loop blocking and auto-tuning Devito applies, Sec. 5) times the launch
  * shapes not forced — both tiles, x-chunks of 32/48/64/96/128 planes and whole

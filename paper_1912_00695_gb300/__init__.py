@@ -77,12 +77,14 @@ class Batch:
     queued per batch without synchronising."""
 
     def __init__(self, space_order, h, storage="f32", form="factored", tile_z=0, tile_y=0,
-                 x_block=0, stream=None):
+                 x_block=0, stream=None, kernel="auto"):
+        # kernel="tma" pins one launch per step; "auto" lets an FP32 batch time the
+        # persistent launch against it
         self.space_order = int(space_order)
         self.h = float(h)
         self.handle = fd_batch_create(space_order, h, options(storage=storage, form=form,
                                                               tile_z=tile_z, tile_y=tile_y,
-                                                              x_block=x_block))
+                                                              x_block=x_block, kernel=kernel))
         self.shapes = {}
         self.stream = stream
         if stream is not None:

@@ -2704,7 +2704,8 @@ int fd_batch_create(int space_order, double h, const fd_options *opt_in, fd_batc
     b->xb_policy = opt.x_block > 0 ? opt.x_block : kBatchXBlock;
     b->tuned = opt.x_block > 0 && b->tile_forced;  // no shape left to time
     // the schedule is timed for FP32 batches whose x-chunks the flow can take
-    b->flow_tuned = opt.storage != kF32 || (opt.x_block > 0 && opt.x_block < space_order / 2);
+    b->flow_tuned = opt.storage != kF32 || (opt.x_block > 0 && opt.x_block < space_order / 2) ||
+                    opt.kernel == kTma;  // kernel TMA: one launch per step, pinned
     b->k = space_order;
     b->r = space_order / 2;
     b->h = h;

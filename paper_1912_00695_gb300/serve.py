@@ -69,7 +69,9 @@ class Request:
 
 def _default_batch(k, h, storage):
     import torch
-    return Batch(k, h, storage=storage, stream=torch.cuda.Stream())
+    # per-step launches pinned: a server's batches change as shots arrive and leave,
+    # and the schedule probes would block the loop once per batch
+    return Batch(k, h, storage=storage, stream=torch.cuda.Stream(), kernel="tma")
 
 
 class Server:

@@ -116,6 +116,22 @@ def test_batch_autotuned_schedule_equals_alone():
             np.testing.assert_array_equal(b.wavefield(s, 1), want_prev)
 
 
+def test_batch_pinned_per_step_launches():
+    """kernel="tma" pins one launch per step: the shape is still tuned, the
+    schedule is not probed."""
+    specs = _shots(8, seed=95, count=4)
+    with fd.Batch(8, H, kernel="tma") as b:
+        slots = _fill(b, specs)
+        b.forward(80)
+        assert b.config()[3] == 1 and b.schedule() == 0
+        n0 = fd.fd_kernel_launches()
+        b.forward(6)
+        assert fd.fd_kernel_launches() - n0 == 6
+        for spec, s in zip(specs, slots):
+            want, _ = _alone(spec, 86)
+            np.testing.assert_array_equal(b.wavefield(s, 0), want)
+
+
 def test_batch_flow_rejections():
     specs = _shots(8, seed=3, count=1)
     with fd.Batch(8, H, storage="bf16") as b:
