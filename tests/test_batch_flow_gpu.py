@@ -11,7 +11,7 @@ import pytest
 
 import paper_1912_00695_gb300 as fd
 from paper_1912_00695_gb300 import inputs
-from harness import rel_l2, run_oracle
+from harness import dt_for, eta_for, rel_l2, run_oracle
 from test_batch_gpu import _alone, _shots
 
 pytestmark = pytest.mark.gpu
@@ -74,8 +74,7 @@ def test_batch_flow_matches_oracle(oracle_mod):
         slots = _fill(b, specs)
         b.forward_flow(60)
         for spec, s in zip(specs, slots):
-            eta = fd.fd_default_damping(spec.m, spec.nbl, H)
-            want, _ = run_oracle(oracle_mod, spec, 60, spec.dt, eta)
+            want, _ = run_oracle(oracle_mod, spec, 60, spec.dt, eta_for(spec))
             e = rel_l2(b.wavefield(s, 0), want)
             print(f"PARITY batch_flow_so8_{spec.interior} {e:.3e}")
             assert e <= 1e-5
@@ -144,3 +143,34 @@ def test_batch_flow_rejections():
         with pytest.raises(fd.FdError) as e:
             b.forward_flow(3)
         assert e.value.code == fd.FD_ENOTSUP
+
+
+@pytest.mark.parametrize("schedule", ["auto", "flow"])
+def test_batch_full_size_equals_alone(schedule, oracle_mod):
+    """The batched workload's shots at their full sizes (the first four of its
+    seeded list: each axis 96-256 + 10, space order 8, smooth random velocity),
+    through the autotuned batch (shape and schedule timed on real steps) or the
+    persistent launch: every shot equals its run alone bit for bit, and the
+    first matches the FP64 oracle within the FP32 bound."""
+    specs = inputs.batched_shots(count=4, nt=120)
+    for spec in specs:
+        spec.dt = dt_for(spec)
+    with fd.Batch(8, H) as b:
+        slots = _fill(b, specs)
+        if schedule == "flow":
+            b.forward_flow(80)
+            b.forward_flow(20)
+        else:
+            b.forward(80)  # shapes (39 steps) and schedule (30 steps), then 11 more
+            assert b.config()[3] == 1 and b.schedule() in (0, 1)
+            b.forward(20)
+        for spec, s in zip(specs, slots):
+            want, want_prev = _alone(spec, 100)
+            assert b.step(s) == 100
+            np.testing.assert_array_equal(b.wavefield(s, 0), want)
+            np.testing.assert_array_equal(b.wavefield(s, 1), want_prev)
+        spec = specs[0]
+        ref, _ = run_oracle(oracle_mod, spec, 100, spec.dt, eta_for(spec))
+        e = rel_l2(b.wavefield(slots[0], 0), ref)
+        print(f"PARITY batch_full_{schedule}_{spec.interior} {e:.3e}")
+        assert e <= 1e-5

@@ -11,7 +11,7 @@ import pytest
 
 import paper_1912_00695_gb300 as fd
 from paper_1912_00695_gb300 import inputs
-from harness import rel_l2, run_oracle
+from harness import dt_for, eta_for, rel_l2, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def _shots(k, seed, count=5):
         vel = inputs.smooth_random_velocity(interior, nbl, rng, sigma=3.0)
         src = tuple(int(rng.integers(0, n)) for n in interior)
         spec = inputs.ShotSpec(interior, nbl, k, vel, src, float(rng.uniform(8, 30)), 200)
-        spec.dt = 0.9 * fd.fd_dt_max(k, H, spec.vmax)
+        spec.dt = dt_for(spec)
         out.append(spec)
     return out
 
@@ -71,8 +71,7 @@ def test_batch_matches_oracle(oracle_mod):
             slots.append(s)
         b.forward(60)
         for spec, s in zip(specs, slots):
-            eta = fd.fd_default_damping(spec.m, spec.nbl, H)
-            want, _ = run_oracle(oracle_mod, spec, 60, spec.dt, eta)
+            want, _ = run_oracle(oracle_mod, spec, 60, spec.dt, eta_for(spec))
             e = rel_l2(b.wavefield(s, 0), want)
             print(f"PARITY batch_so8_{spec.interior} {e:.3e}")
             assert e <= 1e-5
