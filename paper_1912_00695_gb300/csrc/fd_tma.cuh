@@ -218,6 +218,16 @@ __device__ __forceinline__ float2 ztap_pair(const float *win, int j) {
     return make_float2(win[W0 - j] + win[W0 + j], win[W0 + 1 - j] + win[W0 + 1 + j]);
 }
 
+// (win[W0 + o] - u.x, win[W0 + 1 + o] - u.y) for the pair (p, p+1) at window index W0
+// = RZ + p and tap offset o: one paired subtraction when the operands form an
+// aligned register pair (W0 + o even), else two scalar ones writing an aligned
+// result pair (the same roundings either way).
+template <int W0>
+__device__ __forceinline__ float2 zdiff_pair(const float *win, int o, float2 u) {
+    if (((W0 + o) & 1) == 0) return __fadd2_rn(make_float2(win[W0 + o], win[W0 + 1 + o]), make_float2(-u.x, -u.y));
+    return make_float2(win[W0 + o] - u.x, win[W0 + 1 + o] - u.y);
+}
+
 // Per-CTA accumulators of the max-|value| reduction, carried across segments.
 struct TmaAcc {
     unsigned amax_bits = 0, damax_bits = 0;
@@ -559,14 +569,14 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                             lapA[r] = fma2(cA, sub2(lo2(xp), ucA), lapA[r]);
                             lapA[r] = fma2(cA, sub2(lo2(ym[r]), ucA), lapA[r]);
                             lapA[r] = fma2(cA, sub2(lo2(yp[r]), ucA), lapA[r]);
-                            lapA[r] = fma2(cA, sub2(f2(w[RZ - j], w[RZ + 1 - j]), ucA), lapA[r]);
-                            lapA[r] = fma2(cA, sub2(f2(w[RZ + j], w[RZ + 1 + j]), ucA), lapA[r]);
+                            lapA[r] = fma2(cA, zdiff_pair<RZ>(w, -j, ucA), lapA[r]);
+                            lapA[r] = fma2(cA, zdiff_pair<RZ>(w, j, ucA), lapA[r]);
                             lapB[r] = fma2(cB, sub2(hi2(xm), ucB), lapB[r]);
                             lapB[r] = fma2(cB, sub2(hi2(xp), ucB), lapB[r]);
                             lapB[r] = fma2(cB, sub2(hi2(ym[r]), ucB), lapB[r]);
                             lapB[r] = fma2(cB, sub2(hi2(yp[r]), ucB), lapB[r]);
-                            lapB[r] = fma2(cB, sub2(f2(w[RZ + 2 - j], w[RZ + 3 - j]), ucB), lapB[r]);
-                            lapB[r] = fma2(cB, sub2(f2(w[RZ + 2 + j], w[RZ + 3 + j]), ucB), lapB[r]);
+                            lapB[r] = fma2(cB, zdiff_pair<RZ + 2>(w, -j, ucB), lapB[r]);
+                            lapB[r] = fma2(cB, zdiff_pair<RZ + 2>(w, j, ucB), lapB[r]);
                         }
                     }
 #pragma unroll
