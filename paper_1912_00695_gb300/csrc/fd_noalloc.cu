@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(32 * kNoAllocTY) noalloc_step_kernel(const Ste
             const float(*t)[SW] = tile[buf];
             const int cy = ty + R, cz = tz + R;
             const float uc = q[R];
-            const float inv = __frcp_rn(fmaf(a.half_dt, ce, cm));
+            const float inv = expanded_inv(fmaf(a.half_dt, ce, cm));
             float taps = 0.0f;
 #pragma unroll
             for (int j = 1; j <= R; ++j) {

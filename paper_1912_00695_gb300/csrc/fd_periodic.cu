@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) fd_periodic_kernel(const StepArgs a, int 
             }
             v = Update<kFactored>::apply(lap, uc, um, f1, f2, 0.0f, a, src_w);
         } else {
-            const float inv = __frcp_rn(fmaf(a.half_dt, f2, f1));
+            const float inv = expanded_inv(fmaf(a.half_dt, f2, f1));
             float taps = 0.0f;
 #pragma unroll
             for (int j = 1; j <= R; ++j) {

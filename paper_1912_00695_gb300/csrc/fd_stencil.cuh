@@ -127,12 +127,17 @@ __device__ __forceinline__ void reduce_amax(const StepArgs &a, unsigned bits, bo
     }
 }
 
+// The expanded form's 1/r0, r0 = m + dt/2 eta: the GPU's fast reciprocal
+// (within 2 ulp), taken once per point and step and multiplied into each tap's
+// coefficient. Every kernel of the expanded form uses it.
+__device__ __forceinline__ float expanded_inv(float r0) { return __fdividef(1.0f, r0); }
+
 // A point source beyond the fused ones, added to the FP32 level u^{n+1} at
 // pitched offset p after the step (its weight: factored w; expanded
 // dt^2 / (m + dt/2 eta)); one fused multiply-add. Shared by the per-step
 // extra-source kernel and the flow schedule, so both give the same bits.
 __device__ __forceinline__ float extra_source_weight(const StepArgs &a, long long p, bool expanded) {
-    return expanded ? a.dt2 * __frcp_rn(fmaf(a.half_dt, a.f2[p], a.f1[p])) : a.f1[p];
+    return expanded ? a.dt2 * expanded_inv(fmaf(a.half_dt, a.f2[p], a.f1[p])) : a.f1[p];
 }
 __device__ __forceinline__ void add_extra_source_f32(float *level, long long p, float w, float q) {
     level[p] = __fmaf_rn(w, q, level[p]);
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(256) fd_naive_kernel(const StepArgs a, int che
             }
             v = Update<kFactored>::apply(lap * sc.s_u, uc * sc.s_u, um, f1, f2, 0.0f, a, src_w);
         } else {
-            const float inv = __frcp_rn(fmaf(a.half_dt, f2, f1));
+            const float inv = expanded_inv(fmaf(a.half_dt, f2, f1));
             float taps = 0.0f;
 #pragma unroll
             for (int j = 1; j <= R; ++j) {
@@ -370,7 +375,7 @@ __global__ void __launch_bounds__(32 * TY) fd_stream_kernel(const StepArgs a, in
                 v = Update<kFactored>::apply(lap * sc.s_u, uc * sc.s_u, cum * sc.s_up, cf1, cf2, 0.0f,
                                              a, src_w);
             } else {
-                const float inv = __frcp_rn(fmaf(a.half_dt, cf2, cf1));
+                const float inv = expanded_inv(fmaf(a.half_dt, cf2, cf1));
                 float taps = 0.0f;
 #pragma unroll
                 for (int j = 1; j <= R; ++j) {

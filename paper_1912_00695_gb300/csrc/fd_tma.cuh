@@ -551,7 +551,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
                                              fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) inv[r][p] = __frcp_rn(r0[p]);
+                        for (int p = 0; p < 4; ++p) inv[r][p] = expanded_inv(r0[p]);
                         invA[r] = f2(inv[r][0], inv[r][1]);
                         invB[r] = f2(inv[r][2], inv[r][3]);
                     }
