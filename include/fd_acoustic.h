@@ -71,7 +71,9 @@ extern "C" {
 #define FD_FORM_FACTORED 0  /* common factors hoisted, equal-distance taps summed first,
                                dt^2/(m + dt/2 eta) precomputed per point */
 #define FD_FORM_EXPANDED 1  /* every tap multiplied by its own coefficient and divided
-                               by (m + dt/2 eta) per point, as Listing 2 is written */
+                               by (m + dt/2 eta) per point, as Listing 2 is written (the
+                               division as a multiply by the GPU's fast reciprocal,
+                               within 2 ulp, taken once per point and step) */
 
 /* Kernel schedule. */
 #define FD_KERNEL_AUTO 0    /* the TMA kernel, launch shape chosen by the autotuner */
