@@ -588,18 +588,21 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
                                              fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
                         // a = m / r0 by a correctly rounded division; where the damping vanishes
-                        // (the tile's plane inside the undamped box) r0 = m exactly and a = 1
-                        float am[4] = {1.0f, 1.0f, 1.0f, 1.0f};
-                        if (!gf) {
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) am[p] = __fdiv_rn(ms[p], r0[p]);
-                        }
+                        // (the tile's plane inside the undamped box) r0 = m exactly and a = 1,
+                        // so the level coefficients are the constants 2 and -1
                         float v[4];
+                        if (gf) {
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) {
-                            v[p] = fmaf(1.0f - 2.0f * am[p], ums[p], fmaf(2.0f * am[p], ucs[p], taps[p]));
-                            sw[r][p] = a.dt2 * inv[r][p];
+                            for (int p = 0; p < 4; ++p) v[p] = fmaf(-1.0f, ums[p], fmaf(2.0f, ucs[p], taps[p]));
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) {
+                                const float am = __fdiv_rn(ms[p], r0[p]);
+                                v[p] = fmaf(1.0f - 2.0f * am, ums[p], fmaf(2.0f * am, ucs[p], taps[p]));
+                            }
                         }
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) sw[r][p] = a.dt2 * inv[r][p];
                         out[r] = make_float4(v[0], v[1], v[2], v[3]);
                     }
                 }
@@ -642,8 +645,9 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         amax_bits = max(amax_bits, bits4(unew));
                         V::st(un[r] + x * P, unew);
                     } else {
-                        const float2 oA = f2(o.x, o.y), oB = f2(o.z, o.w);
-                        nonfinite = add2(nonfinite, add2(sub2(oA, oA), sub2(oB, oB)));
+                        // x * 0 is 0 for finite x and NaN otherwise
+                        nonfinite = fma2(f2(o.x, o.y), f2(0.f, 0.f), nonfinite);
+                        nonfinite = fma2(f2(o.z, o.w), f2(0.f, 0.f), nonfinite);
                     }
                     V::st(up[r] + x * P, o);
                     if constexpr (MODE == kModeForwardD) {
