@@ -244,6 +244,11 @@ struct fd_handle {
     int flow_tab_xb = 0;
 };
 
+// (defined with the forward path, with C linkage)
+extern "C" {
+static bool flow_eligible(const fd_handle *hd);
+}
+
 namespace {
 
 bool check_enabled(const fd_handle *hd) { return hd->opt.check_finite != 0 || hd->opt.storage != kF32; }
@@ -404,8 +409,13 @@ int autotune(fd_handle *hd) {
                force_xb = hd->opt.x_block > 0;
     std::vector<TileShape> tiles;
     if (kernel == kTma) {
+        // a shot that runs the flow schedule by default (FP32, BF16) takes one row per
+        // thread unless the options ask for two: two-row shapes time well in single
+        // launches but run slower under the flow (fewer resident warps for its items)
+        const bool one_row = hd->opt.rows == 0 && hd->opt.kernel == kAuto && flow_eligible(hd);
         for (auto &p : tma_tiles(hd->opt.storage, hd->opt.form, hd->r))
-            if (shape_matches(p, hd->opt.tile_z, hd->opt.tile_y, hd->opt.rows)) tiles.push_back(p);
+            if (shape_matches(p, hd->opt.tile_z, hd->opt.tile_y, hd->opt.rows) && !(one_row && p.rows > 1))
+                tiles.push_back(p);
     } else {
         for (int ty : {4, 8, 16})
             if (hd->opt.tile_y == 0 || hd->opt.tile_y == ty) tiles.push_back({32, ty, 1});

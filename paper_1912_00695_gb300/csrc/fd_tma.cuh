@@ -518,22 +518,28 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     for (int r = 0; r < YB; ++r) {
                         if constexpr (Io<T>::kScaled) {
                             // increment form: d+ = w L u + (1 - 2g) d, u+ = u + d+ (formed below,
-                            // after the source), directly in the output scales
+                            // after the source), directly in the output scales; where the damping
+                            // vanishes 1 - 2g is exactly 1
                             const float2 lA = mul2(lapA[r], su2), lB = mul2(lapB[r], su2);
-                            const float2 omA = fma2(f2(-2.f, -2.f), lo2(cf2[r]), f2(1.f, 1.f));
-                            const float2 omB = fma2(f2(-2.f, -2.f), hi2(cf2[r]), f2(1.f, 1.f));
-                            const float2 dA = fma2(lo2(cf1[r]), lA, mul2(omA, mul2(lo2(cum[r]), sd2)));
-                            const float2 dB = fma2(hi2(cf1[r]), lB, mul2(omB, mul2(hi2(cum[r]), sd2)));
+                            float2 pA = mul2(lo2(cum[r]), sd2), pB = mul2(hi2(cum[r]), sd2);
+                            if (!gf) {
+                                pA = mul2(fma2(f2(-2.f, -2.f), lo2(cf2[r]), f2(1.f, 1.f)), pA);
+                                pB = mul2(fma2(f2(-2.f, -2.f), hi2(cf2[r]), f2(1.f, 1.f)), pB);
+                            }
+                            const float2 dA = fma2(lo2(cf1[r]), lA, pA);
+                            const float2 dB = fma2(hi2(cf1[r]), lB, pB);
                             out[r] = make_float4(dA.x, dA.y, dB.x, dB.y);
                         } else {
-                            // u+ = w L + (2u - u-) - 2 g (u - u-)
+                            // u+ = w L + (2u - u-) - 2 g (u - u-); the last term only where the
+                            // damping does not vanish
                             const float2 ucA = lo2(uc[r]), ucB = hi2(uc[r]), umA = lo2(cum[r]), umB = hi2(cum[r]);
-                            const float2 m2gA = mul2(f2(-2.f, -2.f), lo2(cf2[r])), m2gB = mul2(f2(-2.f, -2.f), hi2(cf2[r]));
                             const float2 dA = fma2(f2(-1.f, -1.f), umA, ucA), dB = fma2(f2(-1.f, -1.f), umB, ucB);
                             float2 vA = fma2(lo2(cf1[r]), lapA[r], add2(ucA, dA));
                             float2 vB = fma2(hi2(cf1[r]), lapB[r], add2(ucB, dB));
-                            vA = fma2(m2gA, dA, vA);
-                            vB = fma2(m2gB, dB, vB);
+                            if (!gf) {
+                                vA = fma2(mul2(f2(-2.f, -2.f), lo2(cf2[r])), dA, vA);
+                                vB = fma2(mul2(f2(-2.f, -2.f), hi2(cf2[r])), dB, vB);
+                            }
                             out[r] = make_float4(vA.x, vA.y, vB.x, vB.y);
                         }
                         sw[r][0] = cf1[r].x * kd;  // kd = 1 for FP32 storage
