@@ -17,6 +17,10 @@
 // after them (proxy fence) and the CTA barrier orders the other threads'
 // loads; the queue prologue reads u^s with L1-bypassing loads, since the
 // same buffer held older levels earlier in the launch.
+//
+// The batch flow (fd_tma_batch_flow_kernel, below) applies the same schedule to
+// every shot of a batch, with each shot's arguments and tensor maps read from
+// device tables instead of the launch's parameters.
 #pragma once
 
 #include <type_traits>
@@ -366,9 +370,10 @@ int tma_flow_occ_r(int form, int storage, int tile_z, int tile_y, int rows, bool
 // steps. Resident CTAs claim (step, work-list entry) items step-major; each item
 // runs the single-shot segment code on its shot's step arguments, which warp 1
 // copies into shared memory while warp 0 checks the dependencies (the 27 items
-// of step s - 1 around it in its own shot). Every dependency has a lower item
-// number, so the waits end (and are bounded all the same). Each item reduces
-// its non-finite check into its own shot's status word.
+// of step s - 1 around it in its own shot) and thread 0, which issues the bulk
+// copies, acquires the shot's tensor maps (once per shot and launch). Every
+// dependency has a lower item number, so the waits end (and are bounded all the
+// same). Each item reduces its non-finite check into its own shot's status word.
 template <int R, int FORM, int LZ, int W>
 __global__ void __launch_bounds__(32 * W, (tma_warps_per_sm(R) / W > 0 ? tma_warps_per_sm(R) / W : 1))
     fd_tma_batch_flow_kernel(const __grid_constant__ BatchFlowArgs f) {
