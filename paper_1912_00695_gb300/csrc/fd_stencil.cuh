@@ -127,10 +127,15 @@ __device__ __forceinline__ void reduce_amax(const StepArgs &a, unsigned bits, bo
     }
 }
 
-// The expanded form's 1/r0, r0 = m + dt/2 eta: the GPU's fast reciprocal
-// (within 2 ulp), taken once per point and step and multiplied into each tap's
-// coefficient. Every kernel of the expanded form uses it.
-__device__ __forceinline__ float expanded_inv(float r0) { return __fdividef(1.0f, r0); }
+// The expanded form's 1/r0, r0 = m + dt/2 eta: the hardware's approximate
+// reciprocal (rcp.approx, within 1 ulp; r0 is a normal number), taken once per
+// point and step and multiplied into each tap's coefficient. Every kernel of the
+// expanded form uses it.
+__device__ __forceinline__ float expanded_inv(float r0) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r0));
+    return y;
+}
 
 // A point source beyond the fused ones, added to the FP32 level u^{n+1} at
 // pitched offset p after the step (its weight: factored w; expanded

@@ -551,13 +551,17 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     // expanded: every tap (u_tap - u_c) times (c_j dt^2/h^2)/r0
                     static_assert(!Io<T>::kScaled, "16-bit storage uses the factored form");
                     float inv[YB][4];
-                    float2 invA[YB], invB[YB];
+                    float2 invA[YB], invB[YB], r0A[YB], r0B[YB];
 #pragma unroll
                     for (int r = 0; r < YB; ++r) {
-                        const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
-                                             fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) inv[r][p] = expanded_inv(r0[p]);
+                        // r0 = m + dt/2 eta, two points per instruction
+                        const float2 hdt = f2(a.half_dt, a.half_dt);
+                        r0A[r] = fma2(hdt, lo2(cf2[r]), lo2(cf1[r]));
+                        r0B[r] = fma2(hdt, hi2(cf2[r]), hi2(cf1[r]));
+                        inv[r][0] = expanded_inv(r0A[r].x);
+                        inv[r][1] = expanded_inv(r0A[r].y);
+                        inv[r][2] = expanded_inv(r0B[r].x);
+                        inv[r][3] = expanded_inv(r0B[r].y);
                         invA[r] = f2(inv[r][0], inv[r][1]);
                         invB[r] = f2(inv[r][2], inv[r][3]);
                     }
@@ -587,29 +591,27 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                     }
 #pragma unroll
                     for (int r = 0; r < YB; ++r) {
-                        const float ms[4] = {cf1[r].x, cf1[r].y, cf1[r].z, cf1[r].w};
-                        const float ums[4] = {cum[r].x, cum[r].y, cum[r].z, cum[r].w};
-                        const float ucs[4] = {uc[r].x, uc[r].y, uc[r].z, uc[r].w};
-                        const float taps[4] = {lapA[r].x, lapA[r].y, lapB[r].x, lapB[r].y};
-                        const float r0[4] = {fmaf(a.half_dt, cf2[r].x, cf1[r].x), fmaf(a.half_dt, cf2[r].y, cf1[r].y),
-                                             fmaf(a.half_dt, cf2[r].z, cf1[r].z), fmaf(a.half_dt, cf2[r].w, cf1[r].w)};
-                        // a = m / r0 by a correctly rounded division; where the damping vanishes
-                        // (the tile's plane inside the undamped box) r0 = m exactly and a = 1,
-                        // so the level coefficients are the constants 2 and -1
-                        float v[4];
+                        // u+ = L + (2a) u + (1 - 2a) u-, a = m / r0 by a correctly rounded
+                        // division; where the damping vanishes (the tile's plane inside the
+                        // undamped box) r0 = m exactly and a = 1, so the level coefficients are
+                        // the constants 2 and -1
+                        float2 vA, vB;
                         if (gf) {
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) v[p] = fmaf(-1.0f, ums[p], fmaf(2.0f, ucs[p], taps[p]));
+                            vA = fma2(f2(-1.f, -1.f), lo2(cum[r]), fma2(f2(2.f, 2.f), lo2(uc[r]), lapA[r]));
+                            vB = fma2(f2(-1.f, -1.f), hi2(cum[r]), fma2(f2(2.f, 2.f), hi2(uc[r]), lapB[r]));
                         } else {
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) {
-                                const float am = __fdiv_rn(ms[p], r0[p]);
-                                v[p] = fmaf(1.0f - 2.0f * am, ums[p], fmaf(2.0f * am, ucs[p], taps[p]));
-                            }
+                            const float am[4] = {__fdiv_rn(cf1[r].x, r0A[r].x), __fdiv_rn(cf1[r].y, r0A[r].y),
+                                                 __fdiv_rn(cf1[r].z, r0B[r].x), __fdiv_rn(cf1[r].w, r0B[r].y)};
+                            vA = fma2(f2(1.0f - 2.0f * am[0], 1.0f - 2.0f * am[1]), lo2(cum[r]),
+                                      fma2(f2(2.0f * am[0], 2.0f * am[1]), lo2(uc[r]), lapA[r]));
+                            vB = fma2(f2(1.0f - 2.0f * am[2], 1.0f - 2.0f * am[3]), hi2(cum[r]),
+                                      fma2(f2(2.0f * am[2], 2.0f * am[3]), hi2(uc[r]), lapB[r]));
                         }
+                        if (src_mask[r]) {  // source weights dt^2 / r0, only where a source sits
 #pragma unroll
-                        for (int p = 0; p < 4; ++p) sw[r][p] = a.dt2 * inv[r][p];
-                        out[r] = make_float4(v[0], v[1], v[2], v[3]);
+                            for (int p = 0; p < 4; ++p) sw[r][p] = a.dt2 * inv[r][p];
+                        }
+                        out[r] = make_float4(vA.x, vA.y, vB.x, vB.y);
                     }
                 }
 #pragma unroll
