@@ -72,8 +72,8 @@ extern "C" {
                                dt^2/(m + dt/2 eta) precomputed per point */
 #define FD_FORM_EXPANDED 1  /* every tap multiplied by its own coefficient and divided
                                by (m + dt/2 eta) per point, as Listing 2 is written (the
-                               division as a multiply by the GPU's fast reciprocal,
-                               within 2 ulp, taken once per point and step) */
+                               division as a multiply by the hardware's approximate
+                               reciprocal, within 1 ulp, taken once per point and step) */
 
 /* Kernel schedule. */
 #define FD_KERNEL_AUTO 0    /* the TMA kernel, launch shape chosen by the autotuner */
