@@ -12,9 +12,9 @@ constant noise floor: the peak-relative figures are the stable ones.)
 
 The oracle needs minutes of host time at this size, so the test runs only
 with FDGB_RUN_SLOW=1; it writes the per-step series to
-gpurun_out/precision_error_424.json when that folder exists. Bounds: about
-twice the errors measured at this configuration (see CROP_BOUND and
-ENERGY_BOUND)."""
+precision_error_424.json in the folder FDGB_RECORD_DIR names, when it is set.
+Bounds: about twice the errors measured at this configuration (see CROP_BOUND
+and ENERGY_BOUND)."""
 import json
 import os
 import time
@@ -102,8 +102,8 @@ def test_precision_error_full_config(oracle_mod):
               "oracle_threads": oracle_mod.num_threads(), "wall_s": round(time.time() - t0, 1),
               "energy_every": ENERGY_EVERY, "summary": summary, "crop_norm": crop_norm,
               "energy_ref": energy_ref, "series": series}
-    out_dir = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out_dir):
+    out_dir = os.environ.get("FDGB_RECORD_DIR", "")
+    if out_dir and os.path.isdir(out_dir):
         with open(os.path.join(out_dir, "precision_error_424.json"), "w") as f:
             json.dump(record, f)
     # bounds: about twice the errors this configuration measured
