@@ -316,7 +316,14 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
     // the whole y-z tile lies where the damping field vanishes (in y and z): such planes
     // inside the box's x range need no g tile
     const bool tile_yz_box = y0 >= a.by0 && y0 + TY <= a.by1 && z0 >= a.bz0 && z0 + TZ <= a.bz1;
-    auto g_free = [&](int x) { return tile_yz_box && x >= a.bx0 && x < a.bx1; };
+    // the argument fields the plane loop reads, as scalars: arguments in shared memory
+    // (the batch kernels) would otherwise be read again after every memory clobber of
+    // the loop's barrier and copy code
+    const int a_Nx = a.Nx, a_bx0 = a.bx0, a_bx1 = a.bx1;
+    const float a_half_dt = a.half_dt, a_dt2 = a.dt2;
+    // the row's points past its end (kept zero: the pitch padding)
+    const unsigned tail_mask = (z4 + 1 >= a.Nz ? 2u : 0u) | (z4 + 2 >= a.Nz ? 4u : 0u) | (z4 + 3 >= a.Nz ? 8u : 0u);
+    auto g_free = [&](int x) { return tile_yz_box && x >= a_bx0 && x < a_bx1; };
     // every input of plane x arrives in its ring stage by bulk tensor copies
     auto issue = [&](int x, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
@@ -340,7 +347,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
             tma_prefetch_3d(&maps->up_pt, z0, y0, x);
             tma_prefetch_3d(&maps->f1_pt, z0, y0, x);
             if (!g_free(x)) tma_prefetch_3d(&maps->f2_pt, z0, y0, x);
-            if (x + R < a.Nx) tma_prefetch_3d(&maps->u_pt, z0, y0, x + R);
+            if (x + R < a_Nx) tma_prefetch_3d(&maps->u_pt, z0, y0, x + R);
         }
     };
     if (tid == 0) {
@@ -555,7 +562,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
 #pragma unroll
                     for (int r = 0; r < YB; ++r) {
                         // r0 = m + dt/2 eta, two points per instruction
-                        const float2 hdt = f2(a.half_dt, a.half_dt);
+                        const float2 hdt = f2(a_half_dt, a_half_dt);
                         r0A[r] = fma2(hdt, lo2(cf2[r]), lo2(cf1[r]));
                         r0B[r] = fma2(hdt, hi2(cf2[r]), hi2(cf1[r]));
                         inv[r][0] = expanded_inv(r0A[r].x);
@@ -609,7 +616,7 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                         }
                         if (src_mask[r]) {  // source weights dt^2 / r0, only where a source sits
 #pragma unroll
-                            for (int p = 0; p < 4; ++p) sw[r][p] = a.dt2 * inv[r][p];
+                            for (int p = 0; p < 4; ++p) sw[r][p] = a_dt2 * inv[r][p];
                         }
                         out[r] = make_float4(vA.x, vA.y, vB.x, vB.y);
                     }
@@ -633,10 +640,10 @@ __device__ __forceinline__ bool tma_segment(const TmaMaps *maps, const StepArgs 
                             }
                         }
                     }
-                    if (z4 + 3 >= a.Nz) {  // row tail: keep the pitch padding zero
-                        if (z4 + 1 >= a.Nz) o.y = 0.f;
-                        if (z4 + 2 >= a.Nz) o.z = 0.f;
-                        if (z4 + 3 >= a.Nz) o.w = 0.f;
+                    if (tail_mask) {  // row tail: keep the pitch padding zero
+                        if (tail_mask & 2u) o.y = 0.f;
+                        if (tail_mask & 4u) o.z = 0.f;
+                        if (tail_mask & 8u) o.w = 0.f;
                     }
                     auto bits4 = [](const float4 &v) {
                         return max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
