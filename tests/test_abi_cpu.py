@@ -136,3 +136,75 @@ def test_shot_device_bytes_counts_the_pitched_fields(built_lib):
         assert out.value == levels + 2 * n * 4 + (1 << 16)  # plus the two coefficient fields and slack
     assert built_lib.fd_shot_device_bytes(0, 1, 1, 0, 0, ctypes.byref(out)) == _abi.FD_EINVAL
     assert built_lib.fd_shot_device_bytes(1, 1, 1, 0, 3, ctypes.byref(out)) == _abi.FD_EINVAL
+
+
+def test_create_arguments_are_checked_on_the_host(built_lib):
+    """Every argument and option check of the create calls runs before any CUDA
+    call, so each rejection is reported here without a GPU and leaves the
+    output handle NULL."""
+    lib = built_lib
+
+    def opts(**kw):
+        o = _abi.fd_options_default()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def create(nx=16, ny=16, nz=16, k=8, h=10.0, dt=1e-3, nbl=2, opt=None):
+        out = ctypes.c_void_p(12345)
+        rc = lib.fd_acoustic_create_ex(nx, ny, nz, k, h, dt, nbl,
+                                       ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+        assert out.value is None, "a rejected create must leave the handle NULL"
+        return rc
+
+    EINVAL, ENOTSUP = _abi.FD_EINVAL, _abi.FD_ENOTSUP
+    for k in (-2, 0, 1, 3, 25, 26):
+        assert create(k=k) == EINVAL, k
+    for dims in ((0, 16, 16), (16, 0, 16), (16, 16, -1)):
+        assert create(*dims) == EINVAL, dims
+    assert create(nbl=-1) == EINVAL
+    for h, dt in ((0.0, 1e-3), (-10.0, 1e-3), (float("nan"), 1e-3), (float("inf"), 1e-3),
+                  (10.0, 0.0), (10.0, float("nan")), (10.0, -1e-3)):
+        assert create(h=h, dt=dt) == EINVAL, (h, dt)
+    # the largest extent is 65535 nodes per axis, layer included
+    assert create(nx=65536, nbl=0) == EINVAL
+    assert create(ny=65535 - 2 * 99, nbl=100) == EINVAL
+    assert create(nz=65534, nbl=1) == EINVAL
+    for kw in (dict(storage=3), dict(storage=-1), dict(form=2), dict(kernel=4), dict(boundary=2)):
+        assert create(opt=opts(**kw)) == ENOTSUP, kw
+    for kw in (dict(boundary=1, storage=1), dict(boundary=1, kernel=3),   # periodic: FP32, naive kernel
+               dict(storage=1, form=1), dict(storage=2, kernel=1), dict(storage=2, kernel=2),
+               dict(tile_z=48, tile_y=16), dict(kernel=1, tile_z=64, tile_y=8), dict(kernel=2, rows=2)):
+        assert create(opt=opts(**kw)) == ENOTSUP, kw
+    assert create(opt=opts(rows=3)) == EINVAL
+    assert create(opt=opts(rows=-1)) == EINVAL
+    assert create(opt=opts(x_block=-1)) == EINVAL
+    assert lib.fd_acoustic_create_ex(16, 16, 16, 8, 10.0, 1e-3, 2, None, None) == EINVAL
+
+    def slab(x0, x1, k=8, opt=None):
+        out = ctypes.c_void_p(12345)
+        rc = lib.fd_slab_create(16, 16, 16, k, 10.0, 1e-3, 2, x0, x1,
+                                ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+        assert out.value is None
+        return rc
+
+    assert slab(-1, 4) == EINVAL
+    assert slab(5, 5) == EINVAL
+    assert slab(0, 21) == EINVAL                 # past the 20 planes of the domain
+    assert slab(4, 7) == EINVAL                  # 3 planes, fewer than k/2 = 4
+    assert slab(0, 10, opt=opts(storage=1)) == ENOTSUP
+    assert slab(0, 10, opt=opts(kernel=2)) == ENOTSUP
+
+    def batch(k=8, h=10.0, opt=None):
+        out = ctypes.c_void_p(12345)
+        rc = lib.fd_batch_create(k, h, ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+        assert out.value is None
+        return rc
+
+    for k in (0, 3, 18, 24):
+        assert batch(k=k) == EINVAL, k
+    assert batch(h=0.0) == EINVAL
+    assert batch(h=float("nan")) == EINVAL
+    for kw in (dict(storage=3), dict(form=2), dict(storage=1, form=1), dict(boundary=1),
+               dict(tile_z=128, tile_y=8), dict(rows=2)):
+        assert batch(opt=opts(**kw)) == ENOTSUP, kw
