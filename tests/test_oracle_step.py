@@ -3,8 +3,9 @@
 Fixed against: the damped Eq. 1 discretised at space order 2 on a unit grid
 (sign of the damping and the r0 denominator as in Listing 2),
 a dense-matrix brute force with sources, the exact discrete plane-wave
-solution, discrete energy conservation (and decay with damping), reciprocity,
-linearity and the zero initial conditions of Eq. 1.
+solution, the closed form of the one-node domain (a damped scalar recurrence),
+discrete energy conservation (and decay with damping), reciprocity, linearity
+and the zero initial conditions of Eq. 1.
 """
 import os
 
@@ -214,3 +215,39 @@ def test_default_damping_invariants(oracle_mod):
     assert eta.max() == pytest.approx(eta[0, 0, 0])
     assert eta[0, 0, 0] == pytest.approx(m[0, 0, 0] * 3 * dmax, rel=1e-14)
     assert not oracle_mod.default_damping(m, 0, h).any()
+
+
+@pytest.mark.parametrize("k", [2, 4, 8, 16, 24])
+@pytest.mark.parametrize("damped", [False, True])
+def test_one_node_domain_is_a_scalar_recurrence(oracle_mod, k, damped):
+    """On a one-node domain every tap but the centre falls in the zero halo, so
+    the damped Eq. 1 at that node is the scalar recurrence
+    (m/dt^2 + eta/(2 dt)) u^{n+1} = (2 m/dt^2 + 3 c_0/h^2) u^n - (m/dt^2 - eta/(2 dt)) u^{n-1}.
+    Its characteristic roots are rho e^{+-i theta}, so u^n = rho^n (A cos n theta
+    + B sin n theta) with A, B fixed by u^0 and u^{-1}: a closed form of the
+    scheme's degenerate case (centre weight from exact rational arithmetic)."""
+    h, v = 10.0, 2000.0
+    m = 1.0 / v ** 2
+    dt = 0.8 * oracle_mod.dt_max(k, h, v)
+    eta = 0.01 * m / dt if damped else 0.0  # eta dt / (2 m) = 0.005: about 0.5 % decay per step
+    c0 = float(vandermonde_weights(k)[0])
+    a = m / dt ** 2 + eta / (2 * dt)
+    b = 2 * m / dt ** 2 + 3 * c0 / h ** 2
+    c = m / dt ** 2 - eta / (2 * dt)
+    rho = np.sqrt(c / a)
+    theta = np.arccos(b / (2 * a * rho))
+    u0, um1 = 0.7, -0.4
+    A = u0
+    B = (A * np.cos(theta) - rho * um1) / np.sin(theta)
+    nt = 400
+
+    def closed(n):
+        return rho ** n * (A * np.cos(n * theta) + B * np.sin(n * theta))
+
+    one = (1, 1, 1)
+    got, got_prev = oracle_mod.forward(np.full(one, m), np.full(one, eta), k, h, dt, nt,
+                                       u0=np.full(one, u0), u_prev0=np.full(one, um1))
+    assert abs(got[0, 0, 0] - closed(nt)) <= 1e-11
+    assert abs(got_prev[0, 0, 0] - closed(nt - 1)) <= 1e-11
+    if damped:  # the envelope decays as rho^n
+        assert rho < 1.0 and abs(closed(nt)) <= rho ** nt * np.hypot(A, B) * (1 + 1e-12)
