@@ -3,9 +3,11 @@ stencil's geometry: an item (step s, x-chunk, y tile, z tile) waits only for
 the 27 items of step s - 1 around it. That must cover every item that wrote a
 u^s value it uses (its taps reach R planes/rows/columns past its own points)
 and every item that still reads the u^{s-1} values it overwrites; both hold
-when the x-chunk, the tile height and the tile width are at least R. Checked
-for every tile shape the TMA kernel has, at each radius it is built for, with
-x-chunks down to R, on grids with ragged last chunks and tiles."""
+when every x-chunk and tile but the last along its axis spans at least R
+planes, rows or columns (the last may be shorter: nothing lies beyond it).
+Checked for every tile shape the TMA kernel has, at each radius it is built
+for, with x-chunks down to R, on grids with ragged last chunks and tiles, and on
+domains thinner than R (one chunk or tile along an axis)."""
 import itertools
 
 import numpy as np
@@ -72,3 +74,15 @@ def test_dependencies_have_lower_item_numbers():
                 if 0 <= nx < nbx and 0 <= ny < nby and 0 <= nz < nbz:
                     dep = (s - 1) * per_step + (nx * nby + ny) * nbz + nz
                     assert dep < item
+
+
+@pytest.mark.parametrize("R", [1, 2, 4, 8, 12])
+def test_short_last_items_and_thin_domains(R):
+    """A last chunk or tile shorter than R, after full ones, and a domain
+    thinner than R along an axis (a single chunk or tile) keep the rule."""
+    tz, ty = (32, 16)
+    cases = [((1, 1, 1), 40), ((3, 2, 5), 40), ((R - 1 or 1, 40, 70), 40),
+             ((3 * R + 1, 2 * ty + 1, 2 * tz + 1), R),      # last chunk, tile row and column: 1 wide
+             ((2 * R + R // 2 + 1, ty + 1, 70), R)]
+    for N, xb in cases:
+        assert _check(N, R, tz, ty, max(xb, R)) >= 1
