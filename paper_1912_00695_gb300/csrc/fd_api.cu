@@ -392,9 +392,20 @@ int build_maps(fd_handle *hd) {
     return FD_OK;
 }
 
+// SMs of the current device (a GB300's 152 if the query fails)
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return sms;
+}
+
 int heuristic_x_block(const fd_handle *hd, int tile_z, int tile_y) {
     const int tiles = ((hd->Nz + tile_z - 1) / tile_z) * ((hd->Ny + tile_y - 1) / tile_y);
-    int chunks = (2 * 152 + tiles - 1) / tiles;
+    int chunks = (2 * device_sms() + tiles - 1) / tiles;
     const int max_chunks = hd->Nx / 16 > 0 ? hd->Nx / 16 : 1;
     chunks = std::max(1, std::min(chunks, max_chunks));
     return (hd->Nx + chunks - 1) / chunks;
