@@ -125,7 +125,10 @@ void fd_options_default(fd_options *opt);
  * levels, the model fields) and zeroes the wavefields (Eq. 1: u = u_t = 0 at
  * t = 0). FD_EINVAL when k is odd or outside [2,24], n_a < 1, nbl < 0, a
  * computational extent N_a exceeds 65535, or h, dt are not positive finite;
- * FD_ENOMEM when the device buffers do not fit. *out is NULL on failure. */
+ * FD_ENOMEM when the device buffers do not fit. *out is NULL on failure.
+ * Any N_a >= 1 is a valid shot: taps beyond the domain read the zero halo,
+ * so a domain thinner than the stencil (down to one node) needs no special
+ * case. */
 int fd_acoustic_create(int nx, int ny, int nz, int space_order, double h, double dt, int nbl,
                        fd_handle **out);
 
