@@ -50,3 +50,33 @@ def test_clock_record_rules():
         assert not bench.clocks_ok(dict(ok, reasons=[r]))
     assert not bench.clocks_ok(dict(ok, sm_mhz=1200.0))  # locked low, no reason given
     assert bench.clocks_ok({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+
+
+def test_committed_traffic_is_keyed_to_the_kernel_code(tmp_path, monkeypatch):
+    """The ncu DRAM figure in profiles/traffic.json is used only while the step
+    kernels' code is the one it was measured on; comments and layout do not
+    count as a change. The committed figure lies between the algorithmic bytes
+    and 1.5 times them (re-reads, not a different workload)."""
+    h = bench._kernel_hash()
+    per_step = bench._ncu_traffic(h, "sweep_n256")
+    assert per_step is not None, "profiles/traffic.json is keyed to other kernel code"
+    alg = bench.algorithmic_bytes_per_step(inputs.sweep_shot(8, n=256, nt=10))
+    assert alg <= per_step <= 1.5 * alg
+    two = bench._ncu_traffic(h, "sweep_n256_two_step")
+    assert two is not None and bench.algorithmic_bytes_two_steps(inputs.sweep_shot(2, n=256, nt=10)) <= two
+    assert bench._ncu_traffic("0" * 16, "sweep_n256") is None
+    # a comment-only edit keeps the hash, a code edit changes it
+    src = os.path.join(ROOT, "paper_1912_00695_gb300", "csrc")
+    fake = tmp_path / "paper_1912_00695_gb300" / "csrc"
+    fake.mkdir(parents=True)
+    names = ("fd_stencil.cuh", "fd_tma.cuh", "fd_tma2.cuh", "fd_flow.cuh", "fd_flow.h", "fd_internal.h")
+    for name in names:
+        (fake / name).write_text(open(os.path.join(src, name), encoding="utf-8").read(), encoding="utf-8")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._kernel_hash() == h
+    with open(fake / "fd_flow.h", "a", encoding="utf-8") as f:
+        f.write("\n// a note\n/* and a block\n   comment */\n")
+    assert bench._kernel_hash() == h
+    with open(fake / "fd_flow.h", "a", encoding="utf-8") as f:
+        f.write("\nnamespace fdgb { constexpr int kUnused = 1; }\n")
+    assert bench._kernel_hash() != h
